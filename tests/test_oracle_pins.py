@@ -1,0 +1,363 @@
+"""Pins of the CPU oracle against facts other than itself.
+
+Each test checks one piece of the oracle against a closed form, an
+independent construction, an invariant of the mathematics, or a number the
+paper prints (golden fixtures under tests/golden/), chosen so that a dropped
+term, a wrong sign or index, or a transposed operand fails at least one.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import constants, fem, patch, quadrature, solver
+from tests.conftest import golden_rows
+
+
+# ---------------------------------------------------------------- quadrature
+def test_gll_closed_forms():
+    np.testing.assert_allclose(quadrature.gauss_lobatto_nodes(1), [0, 1], atol=1e-15)
+    np.testing.assert_allclose(quadrature.gauss_lobatto_nodes(2), [0, 0.5, 1], atol=1e-15)
+    s5 = 1 / math.sqrt(5)
+    np.testing.assert_allclose(quadrature.gauss_lobatto_nodes(3),
+                               [0, (1 - s5) / 2, (1 + s5) / 2, 1], atol=1e-15)
+    s37 = math.sqrt(3 / 7)
+    np.testing.assert_allclose(quadrature.gauss_lobatto_nodes(4),
+                               [0, (1 - s37) / 2, 0.5, (1 + s37) / 2, 1], atol=1e-15)
+
+
+def test_gauss_closed_form_and_library():
+    x, w = quadrature.gauss_legendre(2)
+    np.testing.assert_allclose(x, [0.5 - 0.5 / math.sqrt(3), 0.5 + 0.5 / math.sqrt(3)], atol=1e-15)
+    np.testing.assert_allclose(w, [0.5, 0.5], atol=1e-15)
+    for n in range(1, 12):
+        x, w = quadrature.gauss_legendre(n)
+        xl, wl = np.polynomial.legendre.leggauss(n)
+        np.testing.assert_allclose(x, (xl + 1) / 2, atol=1e-14)
+        np.testing.assert_allclose(w, wl / 2, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 9])
+def test_gauss_exactness(n):
+    x, w = quadrature.gauss_legendre(n)
+    assert abs(w.sum() - 1) < 1e-14
+    for m in range(2 * n):
+        assert abs(w @ x ** m - 1 / (m + 1)) < 1e-14, m
+    assert abs(w @ x ** (2 * n) - 1 / (2 * n + 1)) > 1e-12  # not exact beyond 2n-1
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_lagrange_basis(k):
+    nodes = quadrature.gauss_lobatto_nodes(k)
+    np.testing.assert_allclose(quadrature.lagrange_values(nodes, nodes), np.eye(k + 1), atol=1e-13)
+    x = np.linspace(0, 1, 13)
+    V = quadrature.lagrange_values(nodes, x)
+    D = quadrature.lagrange_derivatives(nodes, x)
+    np.testing.assert_allclose(V.sum(1), 1, atol=1e-13)
+    np.testing.assert_allclose(D.sum(1), 0, atol=1e-11)
+    for m in range(k + 1):   # interpolation reproduces x^m and its derivative
+        np.testing.assert_allclose(V @ nodes ** m, x ** m, atol=1e-12)
+        np.testing.assert_allclose(D @ nodes ** m, m * x ** max(m - 1, 0) * (m > 0), atol=1e-10)
+
+
+def test_q1_reference_matrices():
+    M, K = quadrature.reference_matrices_1d(1)
+    np.testing.assert_allclose(M, [[1 / 3, 1 / 6], [1 / 6, 1 / 3]], atol=1e-15)
+    np.testing.assert_allclose(K, [[1, -1], [-1, 1]], atol=1e-15)
+    for k in range(1, 9):
+        M, K = quadrature.reference_matrices_1d(k)
+        assert abs(M.sum() - 1) < 1e-13          # int 1 = 1
+        np.testing.assert_allclose(K.sum(1), 0, atol=1e-11)
+
+
+# ---------------------------------------------------------------- mesh / DoFs
+def test_paper_dof_counts():
+    for table, r, patches, p, dofs in golden_rows("dof_counts.txt"):
+        r, patches, p, dofs = int(r), int(patches), int(p), int(dofs)
+        m = fem.Mesh(3, 2 ** (r + 1), p)
+        assert m.n_dofs == dofs, (table, r, p)
+        assert (m.n - 1) ** 3 == patches
+    # enumerate the smallest case's patches explicitly
+    assert len(patch.interior_vertices(fem.Mesh(3, 8, 2))) == 343
+
+
+def test_p_hierarchy_golden():
+    for row in golden_rows("p_hierarchy.txt"):
+        k, levels = int(row[0]), [int(v) for v in row[1:]]
+        assert patch.p_hierarchy(k) == levels
+    assert patch.p_hierarchy(8) == [1, 3, 7, 8]
+    assert patch.p_hierarchy(2) == [1, 2]
+
+
+# ---------------------------------------------------------------- geometry
+def test_deformation_jacobian_vs_finite_differences():
+    for d in (2, 3):
+        m = fem.Mesh(d, 4, 2, "deformed", 0.05)
+        X = np.random.default_rng(0).random((7, d))
+        _, J = m.map_and_jacobian(X)
+        eps = 1e-6
+        for j in range(d):
+            e = np.zeros(d)
+            e[j] = eps
+            xp, _ = m.map_and_jacobian(X + e)
+            xm, _ = m.map_and_jacobian(X - e)
+            np.testing.assert_allclose(J[:, :, j], (xp - xm) / (2 * eps), atol=1e-8)
+
+
+def test_deformation_keeps_boundary_and_orientation():
+    m = fem.Mesh(3, 4, 2, "deformed", 0.05)
+    g = np.linspace(0, 1, 9)
+    for face in range(3):
+        for val in (0.0, 1.0):
+            P = np.random.default_rng(1).random((20, 3))
+            P[:, face] = val
+            x, _ = m.map_and_jacobian(P)
+            np.testing.assert_allclose(x, P, atol=1e-15)
+    X = np.random.default_rng(2).random((1000, 3))
+    _, J = m.map_and_jacobian(X)
+    assert np.linalg.det(J).min() > 0
+
+
+def test_deformed_volume_by_quadrature():
+    # sum_q w_q det J_q approximates |Omega| = 1 (F maps the cube onto itself)
+    for d in (2, 3):
+        m = fem.Mesh(d, 4, 3, "deformed", 0.05)
+        vol = 0.0
+        for c in m.cells():
+            G = m.cell_geometry(c, 4)
+            _, X, w = m.cell_quadrature(c, 4)
+            _, DF = m.map_and_jacobian(X)
+            vol += np.sum(w * np.linalg.det(DF * m.h))
+        assert abs(vol - 1) < 1e-6
+
+
+# ---------------------------------------------------------------- assembly
+@pytest.mark.parametrize("d,n,k", [(2, 3, 1), (2, 2, 4), (3, 2, 2), (3, 3, 1), (3, 2, 3)])
+def test_assembled_equals_kronecker_sum(d, n, k):
+    m = fem.Mesh(d, n, k)
+    A = fem.assemble(m)
+    B = fem.kron_stiffness_cartesian(m)
+    assert abs(A - B).max() < 1e-13 * abs(B).max()
+
+
+@pytest.mark.parametrize("geom", ["cartesian", "deformed"])
+@pytest.mark.parametrize("d,k", [(2, 3), (3, 2)])
+def test_symmetry_and_neumann_nullspace(geom, d, k):
+    m = fem.Mesh(d, 3, k, geom, 0.05)
+    Af = fem.assemble_full(m)
+    assert abs(Af - Af.T).max() < 1e-14 * abs(Af).max()
+    ones = np.ones(Af.shape[0])
+    assert np.abs(Af @ ones).max() < 1e-13 * abs(Af).max()
+    A = fem.assemble(m)
+    rng = np.random.default_rng(3)
+    u, v = rng.standard_normal((2, A.shape[0]))
+    assert abs(u @ (A @ v) - v @ (A @ u)) < 1e-12 * abs(u @ (A @ v))
+    assert u @ (A @ u) > 0
+
+
+def test_q1_patch_diagonal():
+    # Q1 stiffness diagonal at an interior vertex: 8/3 (2D), 8h/3 (3D)
+    for d, expect in ((2, 8 / 3), (3, 8 / 3 * 0.25)):
+        m = fem.Mesh(d, 4, 1)
+        A = fem.assemble(m)
+        np.testing.assert_allclose(A.diagonal(), expect, rtol=1e-14)
+
+
+@pytest.mark.parametrize("d,k", [(2, 1), (2, 3), (3, 2)])
+def test_energy_of_linear_function(d, k):
+    # u = x_1 lies in V_h on Cartesian meshes: a(u, u) = |Omega| = 1
+    m = fem.Mesh(d, 3, k)
+    Af = fem.assemble_full(m)
+    u = fem.dof_coordinates(m)[:, 0]
+    assert abs(u @ (Af @ u) - 1) < 1e-12
+
+
+# ---------------------------------------------------------------- transfers
+@pytest.mark.parametrize("d,k", [(2, 2), (2, 4), (3, 3)])
+def test_prolongation_reproduces_polynomials(d, k):
+    mc = fem.Mesh(d, 2, k)
+    mf = mc.with_level(n=4)
+    P = fem.prolongation(mc)
+    f = lambda x: np.prod(x ** (k - 1) * (1 - x), axis=1)   # degree k, zero on the boundary
+    uc = f(fem.dof_coordinates(mc))[mc.interior_index()]
+    uf = f(fem.dof_coordinates(mf))[mf.interior_index()]
+    np.testing.assert_allclose(P @ uc, uf, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,k", [(2, 1), (2, 3), (3, 2)])
+def test_galerkin_identity_cartesian(d, k):
+    # nested spaces + exact quadrature: P^T A_f P = A_c
+    mc = fem.Mesh(d, 2, k)
+    P = fem.prolongation(mc)
+    Af = fem.assemble(mc.with_level(n=4))
+    Ac = fem.assemble(mc)
+    assert abs(P.T @ Af @ P - Ac).max() < 1e-12 * abs(Ac).max()
+
+
+# ---------------------------------------------------------------- patches
+def test_p1_patch_is_single_dof():
+    for d in (2, 3):
+        m = fem.Mesh(d, 3, 1)
+        assert len(patch.patch_dofs(m, (1,) * d)) == 1
+        assert patch.patch_matrix(m, (1,) * d, 1).shape == (1, 1)
+
+
+@pytest.mark.parametrize("geom", ["cartesian", "deformed"])
+@pytest.mark.parametrize("d,k", [(2, 3), (3, 2)])
+def test_patch_matrix_is_submatrix(geom, d, k):
+    m = fem.Mesh(d, 3, k, geom, 0.05)
+    Af = fem.assemble_full(m).toarray()
+    for v in [(1,) * d, (2,) + (1,) * (d - 1)]:
+        idx = patch.patch_dofs(m, v)
+        Aj = patch.patch_matrix(m, v, k)
+        assert np.abs(Aj - Af[np.ix_(idx, idx)]).max() < 1e-15 * np.abs(Af).max() * 10
+
+
+@pytest.mark.parametrize("q,p", [(1, 2), (1, 3), (3, 4), (3, 7), (7, 8)])
+def test_p_transfer_reproduces_polynomials(q, p):
+    T = patch.transfer_1d(q, p)
+    nq, npn = quadrature.gauss_lobatto_nodes(q), quadrature.gauss_lobatto_nodes(p)
+    sq = np.concatenate([nq[1:], 1 + nq[1:-1]])
+    sp_ = np.concatenate([npn[1:], 1 + npn[1:-1]])
+    f = lambda s: s * (2 - s) * s ** (q - 2) if q >= 2 else np.minimum(s, 2 - s)
+    np.testing.assert_allclose(T @ f(sq), f(sp_), atol=1e-13)
+    # zero blocks: coarse nodes strictly inside cell 0 do not reach cell 1
+    assert np.all(T[p:, :q - 1] == 0) and np.all(T[:p - 1, q:] == 0)
+
+
+@pytest.mark.parametrize("d,q,p", [(2, 1, 3), (2, 3, 4), (3, 1, 2), (3, 1, 3)])
+def test_patch_galerkin_identity(d, q, p):
+    m = fem.Mesh(d, 2, p)
+    v = (1,) * d
+    T = patch.transfer(q, p, d)
+    Ap = patch.patch_matrix(m, v, p)
+    Aq = patch.patch_matrix(m, v, q)
+    assert np.abs(T.T @ Ap @ T - Aq).max() < 1e-12 * np.abs(Aq).max()
+
+
+# ---------------------------------------------------------------- local p-MG
+def _solver(d, k, geom="cartesian"):
+    m = fem.Mesh(d, 2, k, geom, 0.05)
+    return patch.PatchSolver(m, (1,) * d, constants.omega_jacobi(d, k))
+
+
+@pytest.mark.parametrize("d,k", [(2, 2), (2, 7), (3, 3), (3, 4)])
+def test_local_vcycle_symmetric_and_contracting(d, k):
+    ps = _solver(d, k)
+    A = ps.A[-1]
+    n = A.shape[0]
+    V = np.column_stack([ps.local_solve(e) for e in np.eye(n)])
+    assert np.abs(V - V.T).max() < 1e-12 * np.abs(V).max()
+    E = np.eye(n) - V @ A
+    rho = np.max(np.abs(np.linalg.eigvals(E)))
+    assert rho < 1
+    # V A has spectrum in (0, 1]
+    lam = np.linalg.eigvals(V @ A).real
+    assert lam.min() > 0 and lam.max() <= 1 + 1e-10
+
+
+def test_local_vcycle_k1_is_exact():
+    for d in (2, 3):
+        ps = _solver(d, 1)
+        r = np.array([0.7])
+        np.testing.assert_allclose(ps.local_solve(r), ps.exact_solve(r), rtol=1e-15)
+
+
+@pytest.mark.parametrize("d,k,geom", [(2, 4, "cartesian"), (3, 3, "cartesian"), (3, 2, "deformed")])
+def test_25_richardson_cycles_reach_cholesky(d, k, geom):
+    ps = _solver(d, k, geom)
+    r = np.random.default_rng(4).standard_normal(ps.A[-1].shape[0])
+    x = ps.exact_solve(r)
+    np.testing.assert_allclose(ps.A[-1] @ x, r, atol=1e-10)
+    y = ps.local_solve(r, n_iter=25)
+    assert np.linalg.norm(y - x) / np.linalg.norm(x) < 1e-6
+
+
+def test_vmult_counts():
+    # §2.2.1: with a zero initial guess the first full V-cycle costs two
+    # fine-level vmults and a half V-cycle one; later cycles three and two.
+    ps = _solver(2, 3)
+    r = np.ones(ps.A[-1].shape[0])
+    ps.local_solve(r, n_iter=1, full=True)
+    assert ps.vmults[-1] == 2
+    ps.vmults = [0] * len(ps.levels)
+    ps.local_solve(r, n_iter=2, full=True)
+    assert ps.vmults[-1] == 2 + 3
+    ps.vmults = [0] * len(ps.levels)
+    ps.local_solve(r, n_iter=1, full=False)
+    assert ps.vmults[-1] == 1
+    ps.vmults = [0] * len(ps.levels)
+    ps.local_solve(r, n_iter=2, full=False)
+    assert ps.vmults[-1] == 1 + 2
+
+
+# ---------------------------------------------------------------- smoother
+def test_k1_sweep_is_damped_jacobi():
+    # k = 1: every patch is one vertex, so the additive sweep is point Jacobi
+    for d in (2, 3):
+        m = fem.Mesh(d, 4, 1)
+        lev = solver.Level(m, constants.omega_jacobi(d, 1), 0.3)
+        rng = np.random.default_rng(5)
+        b, u = rng.standard_normal((2, lev.A.shape[0]))
+        expect = u + 0.3 * (b - lev.A @ u) / lev.A.diagonal()
+        np.testing.assert_allclose(lev.smooth(b, u), expect, rtol=1e-13)
+
+
+def test_single_patch_sweep_with_exact_local_solves():
+    # n = 2: one patch covers every free DoF; 25 local cycles ~ exact solve
+    m = fem.Mesh(2, 2, 3)
+    lev = solver.Level(m, constants.omega_jacobi(2, 3), 0.25, n_iter=25)
+    b = np.random.default_rng(6).standard_normal(lev.A.shape[0])
+    u = lev.smooth(b, np.zeros_like(b))
+    x = solver.direct_solve(lev.A, b)
+    np.testing.assert_allclose(u, 0.25 * x, rtol=1e-6, atol=1e-9 * np.abs(x).max())
+
+
+# ---------------------------------------------------------------- V-cycle / PCG
+def _hier(d, n, k, L, geom="cartesian"):
+    m = fem.Mesh(d, n, k, geom, 0.05)
+    return m, solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d))
+
+
+@pytest.mark.parametrize("d,n,k,L", [(2, 4, 2, 2), (2, 8, 1, 3), (3, 2, 2, 2)])
+def test_vcycle_symmetric_contraction(d, n, k, L):
+    m, h = _hier(d, n, k, L)
+    A = h.levels[-1].A.toarray()
+    N = A.shape[0]
+    B = np.column_stack([h.vcycle(e) for e in np.eye(N)])
+    assert np.abs(B - B.T).max() < 1e-12 * np.abs(B).max()
+    assert np.max(np.abs(np.linalg.eigvals(np.eye(N) - B @ A))) < 1
+
+
+@pytest.mark.parametrize("d,n,k,L,geom", [(2, 16, 2, 3, "cartesian"), (2, 8, 3, 3, "deformed"),
+                                           (3, 4, 2, 2, "cartesian")])
+def test_pcg_matches_direct_solve(d, n, k, L, geom):
+    m, h = _hier(d, n, k, L, geom)
+    b = fem.rhs_manufactured(m)[m.interior_index()]
+    x, it, hist = solver.solve(h, b, rtol=1e-8)
+    assert hist[-1] <= 1e-8 and it < 40
+    xs = solver.direct_solve(h.levels[-1].A, b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-6
+
+
+# ---------------------------------------------------------------- convergence
+def _l2_error(d, n, k, geom="cartesian"):
+    m = fem.Mesh(d, n, k, geom, 0.05)
+    A = fem.assemble(m)
+    b = fem.rhs_manufactured(m)
+    I = m.interior_index()
+    u = np.zeros(m.n_dofs)
+    u[I] = solver.direct_solve(A, b[I])
+    return fem.l2_error_manufactured(m, u)
+
+
+@pytest.mark.parametrize("d,k,ns,geom", [(2, 1, (8, 16, 32), "cartesian"), (2, 2, (4, 8, 16), "cartesian"),
+                                         (2, 3, (4, 8, 16), "cartesian"), (2, 4, (4, 8, 16), "cartesian"),
+                                         (2, 2, (4, 8, 16), "deformed"), (3, 1, (4, 8, 16), "cartesian"),
+                                         (3, 2, (2, 4, 8), "cartesian")])
+def test_l2_convergence_rate(d, k, ns, geom):
+    e = [_l2_error(d, n, k, geom) for n in ns]
+    rate = math.log(e[-2] / e[-1], 2)
+    assert abs(rate - (k + 1)) < 0.2, (e, rate)
