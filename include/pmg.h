@@ -1,0 +1,161 @@
+/*
+ * pmg.h -- C ABI of the GB300 matrix-free p-multigrid vertex-patch library.
+ *
+ * The library solves the discrete Poisson problem A_l u_l = b_l (Eq. (4) of
+ * arXiv 2512.02577) for the bilinear form a(u, v) = int grad u . grad v
+ * (Eq. (3)) with continuous Q_k elements (Gauss-Lobatto nodal basis, (k+1)
+ * Gauss points per direction) on a structured hierarchy of nested meshes of
+ * the unit square / cube (Eq. (1)), homogeneous Dirichlet conditions.
+ *
+ * Vectors.  Every vector argument is a contiguous array over the full
+ * (k n + 1)^d nodal grid of the level, lexicographic with x fastest.
+ * Boundary entries are ignored on input and written as 0 on output.  Unless
+ * a function says otherwise, vectors are DEVICE pointers owned by the caller
+ * (e.g. torch tensors), double for PMG_FP64 and float for PMG_FP32.
+ *
+ * Streams.  All device work of a context is enqueued on the stream given to
+ * pmg_create and is asynchronous unless the function says it synchronises.
+ * A NULL stream makes the context create its own blocking stream (ordered
+ * against the legacy default stream), because the V-cycle is captured into
+ * a CUDA graph and the legacy stream cannot be captured.  A context is not thread-safe; use one
+ * context per thread or request.
+ *
+ * Errors.  Functions return PMG_OK (0), PMG_NOT_CONVERGED (+1) or a negative
+ * PMG_ERR_* code; pmg_last_error() returns a message for the calling thread's
+ * last error.  On an error no device work is left half-enqueued by argument
+ * checks; CUDA errors are reported as PMG_ERR_CUDA.
+ */
+#ifndef PMG_H
+#define PMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum pmg_status {
+  PMG_OK = 0,
+  PMG_NOT_CONVERGED = 1,
+  PMG_ERR_ARG = -1,          /* invalid argument (NULL pointer, bad level, bad size) */
+  PMG_ERR_UNSUPPORTED = -2,  /* dim not 2/3, degree not 1..8, coarse problem too large */
+  PMG_ERR_OOM = -3,          /* device workspace could not be allocated / too small */
+  PMG_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed */
+  PMG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired */
+  PMG_ERR_STATE = -6         /* call not valid in the context's current state */
+};
+
+enum pmg_geometry {
+  PMG_GEOM_CARTESIAN = 0,   /* x = X on the uniform mesh */
+  PMG_GEOM_DEFORMED = 1     /* x = X + a prod_i sin(2 pi X_i) (1,..,1), analytic */
+};
+
+enum pmg_precision { PMG_FP64 = 0, PMG_FP32 = 1 };
+
+typedef struct pmg_ctx pmg_ctx;
+
+typedef struct pmg_config {
+  int dim;             /* 2 or 3 */
+  int n_cells;         /* cells per side on the finest level, n >= 1 */
+  int degree;          /* k in 1..8 */
+  int n_levels;        /* mesh levels; 0 = coarsen while n is even (n_0 = odd part of n) */
+  int geometry;        /* PMG_GEOM_CARTESIAN or PMG_GEOM_DEFORMED */
+  double deform_amp;   /* a of the deformation (0.05 in the deformed benchmark) */
+  int mg_precision;    /* PMG_FP64 or PMG_FP32: arithmetic of the V-cycle, smoother, transfers */
+  double omega_patch;  /* additive-Schwarz damping; <= 0 selects 1.5 / 2^d */
+  double omega_jacobi[4]; /* Jacobi damping per p-level (index 0 = p 1, unused);
+                             <= 0 selects 4 / (3 lambda_max(D^-1 A_{j,p})) of the Cartesian patch */
+  int local_cycles;    /* N_iter of the local Richardson iteration (Algorithm 2), >= 1 */
+  int smooth_steps;    /* pre- and post-smoothing sweeps per level, >= 1 */
+  int patches_per_block; /* 0 = autotuned; else patches per thread block in the smoother */
+} pmg_config;
+
+typedef struct pmg_solve_info {
+  int iterations;      /* CG iterations taken */
+  double rel_residual; /* ||b - A x||_2 / ||b||_2 of the recursively updated residual */
+  double time_ms;      /* wall time of the solve on the context's stream */
+  int status;          /* PMG_OK or PMG_NOT_CONVERGED */
+} pmg_solve_info;
+
+/* Fill *cfg with defaults: 3D, n 8, k 2, automatic levels, Cartesian, FP64,
+ * default damping, one local cycle, one smoothing step. */
+void pmg_config_default(pmg_config* cfg);
+
+/* Device bytes the context for *cfg needs (hierarchy vectors, geometry,
+ * inverse diagonals, coarse inverse, scratch).  Allocates nothing; used by
+ * serving admission.  Returns PMG_ERR_UNSUPPORTED / PMG_ERR_ARG for configs
+ * that pmg_create would reject. */
+int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes);
+
+/* Create a context: validate *cfg, lay out the level hierarchy n_l = n_0 2^l
+ * (Eq. (1)), compute geometry factors and inverse diagonals for every mesh
+ * level and p-level (§3.2), and factor the coarsest level.  `stream` is a
+ * cudaStream_t (NULL: the context creates a blocking stream of its own).  `workspace` is a device buffer of
+ * `workspace_bytes` >= pmg_bytes_required owned by the caller and used for
+ * all device storage of the context; NULL makes the library cudaMalloc its
+ * own (freed by pmg_destroy).  Synchronises the stream before returning. */
+int pmg_create(const pmg_config* cfg, void* stream, void* workspace, int64_t workspace_bytes,
+               pmg_ctx** out);
+
+/* Destroy a context; frees what pmg_create allocated. NULL is accepted. */
+int pmg_destroy(pmg_ctx* ctx);
+
+/* Number of levels and the nodal-grid length (k n_l + 1)^d of `level`
+ * (0 = coarsest, n_levels - 1 = finest). */
+int pmg_num_levels(const pmg_ctx* ctx, int* n_levels);
+int pmg_num_dofs(const pmg_ctx* ctx, int level, int64_t* n);
+
+/* y = A_level x (Eq. (4)), matrix-free by sum factorisation; `prec` selects
+ * the arithmetic and the element type of x and y. */
+int pmg_apply(pmg_ctx* ctx, int level, int prec, const void* x, void* y);
+
+/* r = b - A_level u (the "evaluate" step of Algorithm 1, here global). */
+int pmg_residual(pmg_ctx* ctx, int level, int prec, const void* b, const void* u, void* r);
+
+/* `sweeps` additive vertex-patch sweeps on `level` >= 1:
+ *   u <- u + omega_AS sum_j Pi_j^T LocalSolve_j(Pi_j (b - A u)),
+ * the patch update of Algorithm 1 summed over all patches, with LocalSolve
+ * = Algorithm 2 around the full p-multigrid V-cycle of Algorithm 3. */
+int pmg_smooth(pmg_ctx* ctx, int level, int prec, const void* b, void* u, int sweeps);
+
+/* One geometric V-cycle on the finest level from a zero guess: z = B r
+ * (double in and out; internally FP32 when mg_precision is PMG_FP32). */
+int pmg_vcycle(pmg_ctx* ctx, const double* r, double* z);
+
+/* Preconditioned CG (x_0 = 0, FP64 vectors and dots) with the V-cycle as
+ * preconditioner until ||r||_2 <= rtol ||b||_2 or maxit iterations.
+ * Synchronises the stream.  Returns PMG_OK or PMG_NOT_CONVERGED; *info may
+ * be NULL. */
+int pmg_solve(pmg_ctx* ctx, const double* b, double* x, double rtol, int maxit, pmg_solve_info* info);
+
+/* pmg_solve on HOST arrays: copies b to the device, solves, copies x back.
+ * b and x are host pointers of length pmg_num_dofs(finest); pinned memory
+ * makes the copies asynchronous. Synchronises the stream. */
+int pmg_solve_host(pmg_ctx* ctx, const double* b_host, double* x_host, double rtol, int maxit,
+                   pmg_solve_info* info);
+
+/* b_i = int f phi_i with f = d pi^2 prod_i sin(pi x_i), the load for the
+ * manufactured solution u = prod_i sin(pi x_i), (k+1)-point Gauss rule, on
+ * the finest level (device, double). */
+int pmg_rhs_manufactured(pmg_ctx* ctx, double* b);
+
+/* || x - u ||_{L2} for the manufactured u, (k+3)-point Gauss rule; x is a
+ * device double vector on the finest level. Synchronises the stream. */
+int pmg_l2_error_manufactured(pmg_ctx* ctx, const double* x, double* err);
+
+/* Wait for all work enqueued by the context. */
+int pmg_synchronize(pmg_ctx* ctx);
+
+/* Process-wide number of kernel launches the library has enqueued
+ * (instrumentation for benchmarks; a CUDA-graph replay counts its kernel
+ * nodes). */
+int64_t pmg_launch_count(void);
+
+const char* pmg_status_string(int status);
+const char* pmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMG_H */

@@ -1,0 +1,232 @@
+"""Python binding of the GB300 p-multigrid vertex-patch library (libpmg.so).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+the in-tree shared library, whose C ABI is declared in include/pmg.h.  PyTorch
+supplies device memory (the context workspace and the vectors) and the CUDA
+stream.  If libpmg.so is missing or fails to load, importing the library
+raises: there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmg.so")
+
+PMG_OK = 0
+PMG_NOT_CONVERGED = 1
+PMG_ERR_ARG = -1
+PMG_ERR_UNSUPPORTED = -2
+PMG_ERR_OOM = -3
+PMG_ERR_CUDA = -4
+PMG_ERR_DEVICE_TIMEOUT = -5
+PMG_ERR_STATE = -6
+CARTESIAN, DEFORMED = 0, 1
+FP64, FP32 = 0, 1
+
+# Every entry point declared in include/pmg.h.
+EXPORTED = [
+    "pmg_config_default", "pmg_bytes_required", "pmg_create", "pmg_destroy", "pmg_num_levels",
+    "pmg_num_dofs", "pmg_apply", "pmg_residual", "pmg_smooth", "pmg_vcycle", "pmg_solve",
+    "pmg_solve_host", "pmg_rhs_manufactured", "pmg_l2_error_manufactured", "pmg_synchronize",
+    "pmg_launch_count", "pmg_status_string", "pmg_last_error",
+]
+
+
+class PmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pmg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n_cells", ctypes.c_int), ("degree", ctypes.c_int),
+        ("n_levels", ctypes.c_int), ("geometry", ctypes.c_int), ("deform_amp", ctypes.c_double),
+        ("mg_precision", ctypes.c_int), ("omega_patch", ctypes.c_double),
+        ("omega_jacobi", ctypes.c_double * 4), ("local_cycles", ctypes.c_int),
+        ("smooth_steps", ctypes.c_int), ("patches_per_block", ctypes.c_int),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("time_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libpmg.so (raises OSError if it is missing: build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libpmg.so not found at %s; run __graft_entry__.build() or "
+                      "python paper_2512_02577_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    sigs = {
+        "pmg_config_default": (None, [ctypes.POINTER(Config)]),
+        "pmg_bytes_required": (cint, [ctypes.POINTER(Config), ctypes.POINTER(i64)]),
+        "pmg_create": (cint, [ctypes.POINTER(Config), vp, vp, i64, ctypes.POINTER(vp)]),
+        "pmg_destroy": (cint, [vp]),
+        "pmg_num_levels": (cint, [vp, ctypes.POINTER(cint)]),
+        "pmg_num_dofs": (cint, [vp, cint, ctypes.POINTER(i64)]),
+        "pmg_apply": (cint, [vp, cint, cint, vp, vp]),
+        "pmg_residual": (cint, [vp, cint, cint, vp, vp, vp]),
+        "pmg_smooth": (cint, [vp, cint, cint, vp, vp, cint]),
+        "pmg_vcycle": (cint, [vp, vp, vp]),
+        "pmg_solve": (cint, [vp, vp, vp, dbl, cint, ctypes.POINTER(SolveInfo)]),
+        "pmg_solve_host": (cint, [vp, vp, vp, dbl, cint, ctypes.POINTER(SolveInfo)]),
+        "pmg_rhs_manufactured": (cint, [vp, vp]),
+        "pmg_l2_error_manufactured": (cint, [vp, vp, ctypes.POINTER(dbl)]),
+        "pmg_synchronize": (cint, [vp]),
+        "pmg_launch_count": (i64, []),
+        "pmg_status_string": (ctypes.c_char_p, [cint]),
+        "pmg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code < 0:
+        raise PmgError(code, _lib.pmg_last_error().decode())
+    return code
+
+
+def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, deform_amp=0.05,
+                mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
+                smooth_steps=1, patches_per_block=0):
+    lib = load_library()
+    c = Config()
+    lib.pmg_config_default(ctypes.byref(c))
+    c.dim, c.n_cells, c.degree, c.n_levels = dim, n_cells, degree, n_levels
+    c.geometry, c.deform_amp, c.mg_precision = geometry, deform_amp, mg_precision
+    c.omega_patch = omega_patch
+    for i, w in enumerate(omega_jacobi or []):
+        c.omega_jacobi[i] = w
+    c.local_cycles, c.smooth_steps, c.patches_per_block = local_cycles, smooth_steps, patches_per_block
+    return c
+
+
+def bytes_required(cfg):
+    lib = load_library()
+    n = ctypes.c_int64()
+    _check(lib.pmg_bytes_required(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def launch_count():
+    return load_library().pmg_launch_count()
+
+
+def _ptr(t, dtype, n):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("expected a contiguous %s tensor of %d elements, got %s %s" % (dtype, n, t.dtype,
+                                                                                     tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One hierarchy on the current CUDA device; workspace owned by torch."""
+
+    def __init__(self, cfg, stream=None, device=None):
+        lib = load_library()
+        self.cfg = cfg
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = bytes_required(cfg)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            sh = self.stream.cuda_stream   # 0 (legacy default) -> the library makes its own stream
+            _check(lib.pmg_create(ctypes.byref(cfg), ctypes.c_void_p(sh or None),
+                                  ctypes.c_void_p(self.workspace.data_ptr()), nbytes, ctypes.byref(h)))
+        self.handle = h
+        self.n_levels = self._num_levels()
+        self.mg_dtype = torch.float32 if cfg.mg_precision == FP32 else torch.float64
+
+    def _num_levels(self):
+        n = ctypes.c_int()
+        _check(_lib.pmg_num_levels(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def num_dofs(self, level=-1):
+        level = self.n_levels - 1 if level < 0 else level
+        n = ctypes.c_int64()
+        _check(_lib.pmg_num_dofs(self.handle, level, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pmg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dt(self, prec):
+        return torch.float64 if prec == FP64 else torch.float32
+
+    def apply(self, x, y, level=-1, prec=FP64):
+        level = self.n_levels - 1 if level < 0 else level
+        n, dt = self.num_dofs(level), self._dt(prec)
+        _check(_lib.pmg_apply(self.handle, level, prec, _ptr(x, dt, n), _ptr(y, dt, n)))
+
+    def residual(self, b, u, r, level=-1, prec=FP64):
+        level = self.n_levels - 1 if level < 0 else level
+        n, dt = self.num_dofs(level), self._dt(prec)
+        _check(_lib.pmg_residual(self.handle, level, prec, _ptr(b, dt, n), _ptr(u, dt, n), _ptr(r, dt, n)))
+
+    def smooth(self, b, u, sweeps=1, level=-1):
+        level = self.n_levels - 1 if level < 0 else level
+        prec = self.cfg.mg_precision
+        n, dt = self.num_dofs(level), self._dt(prec)
+        _check(_lib.pmg_smooth(self.handle, level, prec, _ptr(b, dt, n), _ptr(u, dt, n), sweeps))
+
+    def vcycle(self, r, z):
+        n = self.num_dofs()
+        _check(_lib.pmg_vcycle(self.handle, _ptr(r, torch.float64, n), _ptr(z, torch.float64, n)))
+
+    def solve(self, b, x, rtol=1e-8, maxit=500):
+        n = self.num_dofs()
+        info = SolveInfo()
+        _check(_lib.pmg_solve(self.handle, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n), rtol, maxit,
+                              ctypes.byref(info)))
+        return info
+
+    def solve_host(self, b_host, x_host, rtol=1e-8, maxit=500):
+        """b_host, x_host: CPU float64 tensors (pinned for asynchronous copies)."""
+        n = self.num_dofs()
+        for t in (b_host, x_host):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("expected contiguous CPU float64 tensors of %d elements" % n)
+        info = SolveInfo()
+        _check(_lib.pmg_solve_host(self.handle, ctypes.c_void_p(b_host.data_ptr()),
+                                   ctypes.c_void_p(x_host.data_ptr()), rtol, maxit, ctypes.byref(info)))
+        return info
+
+    def rhs_manufactured(self, b):
+        _check(_lib.pmg_rhs_manufactured(self.handle, _ptr(b, torch.float64, self.num_dofs())))
+
+    def l2_error_manufactured(self, x):
+        e = ctypes.c_double()
+        _check(_lib.pmg_l2_error_manufactured(self.handle, _ptr(x, torch.float64, self.num_dofs()),
+                                              ctypes.byref(e)))
+        return e.value
+
+    def synchronize(self):
+        _check(_lib.pmg_synchronize(self.handle))

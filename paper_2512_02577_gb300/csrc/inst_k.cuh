@@ -1,0 +1,211 @@
+// Launch wrappers for one degree K (PMG_K) and the table that exposes them.
+// Each inst_k<K>.cu defines PMG_K and PMG_KNS, then includes this file.
+#pragma once
+#include "kernels.cuh"
+#include "kernels_def.cuh"
+
+namespace pmg {
+namespace PMG_KNS {
+
+static int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  const int64_t cap = 152 * 16;  // 152 SMs x resident blocks; grid-stride beyond
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+static cudaError_t upload(const double* coef) {
+  const int n = LAY.total;
+  float tmp[kMaxCoef];
+  for (int i = 0; i < n; ++i) tmp[i] = (float)coef[i];
+  cudaError_t e = cudaMemcpyToSymbol(c_coef64, coef, sizeof(double) * n);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_coef32, tmp, sizeof(float) * n);
+}
+
+template <int DIM, typename T>
+static cudaError_t cart_apply_t(const T* x, T* y, const T* b, T* t0, T* t1, T* t2, T* t3, int n, T s,
+                                cudaStream_t st) {
+  const int N1 = K * n + 1;
+  const int64_t work = (int64_t)(n + 1) * (DIM == 3 ? (int64_t)N1 * N1 : N1);
+  const int bs = 256;
+  const int g = grid_for(work, bs);
+  if (DIM == 3) {
+    cart_pass<3, 0, 0, false, T><<<g, bs, 0, st>>>(x, nullptr, t0, t1, nullptr, n, s);
+    cart_pass<3, 1, 1, false, T><<<g, bs, 0, st>>>(t0, t1, t2, t3, nullptr, n, s);
+    if (b) cart_pass<3, 2, 2, true, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, b, n, s);
+    else cart_pass<3, 2, 2, false, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, nullptr, n, s);
+    g_launches += 3;
+  } else {
+    cart_pass<2, 0, 0, false, T><<<g, bs, 0, st>>>(x, nullptr, t0, t1, nullptr, n, s);
+    if (b) cart_pass<2, 1, 2, true, T><<<g, bs, 0, st>>>(t0, t1, y, nullptr, b, n, s);
+    else cart_pass<2, 1, 2, false, T><<<g, bs, 0, st>>>(t0, t1, y, nullptr, nullptr, n, s);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t cart_apply(int dim, int prec, const void* x, void* y, const void* b, void* t0, void* t1,
+                              void* t2, void* t3, int n, double scale, cudaStream_t s) {
+  if (prec == 0) {
+    if (dim == 3)
+      return cart_apply_t<3, double>((const double*)x, (double*)y, (const double*)b, (double*)t0, (double*)t1,
+                                     (double*)t2, (double*)t3, n, scale, s);
+    return cart_apply_t<2, double>((const double*)x, (double*)y, (const double*)b, (double*)t0, (double*)t1,
+                                   (double*)t2, (double*)t3, n, scale, s);
+  }
+  if (dim == 3)
+    return cart_apply_t<3, float>((const float*)x, (float*)y, (const float*)b, (float*)t0, (float*)t1,
+                                  (float*)t2, (float*)t3, n, (float)scale, s);
+  return cart_apply_t<2, float>((const float*)x, (float*)y, (const float*)b, (float*)t0, (float*)t1,
+                                (float*)t2, (float*)t3, n, (float)scale, s);
+}
+
+static int patch_threads(int dim) { return dim == 3 ? PatchShape<3>::TPP : PatchShape<2>::TPP; }
+
+static int patch_smem(int dim, int prec, int n_iter) {
+  const int es = prec == 0 ? 8 : 4;
+  const int elems = dim == 3 ? PatchShape<3>::ELEMS + (n_iter > 1 ? 2 * PatchShape<3>::SZT : 0)
+                             : PatchShape<2>::ELEMS + (n_iter > 1 ? 2 * PatchShape<2>::SZT : 0);
+  return elems * es;
+}
+
+template <int DIM, typename T>
+static cudaError_t patch_cart_t(const T* r, T* u, int n, int colour, int ppc, int n_iter, const T* dinv,
+                                const PatchParamsHost& H, cudaStream_t st) {
+  using S = PatchShape<DIM>;
+  if (n < 2) return cudaSuccess;  // no interior vertex, no patch
+  if (K == 1) {
+    if (colour != 0) return cudaSuccess;  // one launch covers all single-vertex patches
+    const int64_t nv = DIM == 3 ? (int64_t)(n - 1) * (n - 1) * (n - 1) : (int64_t)(n - 1) * (n - 1);
+    patch_k1_kernel<DIM, T><<<grid_for(nv, 256), 256, 0, st>>>(r, u, n, (T)(H.omega_as * H.inv_a0));
+    g_launches += 1;
+    return cudaGetLastError();
+  }
+  const int cx = (colour & 1) ? n / 2 : (n - 1) / 2;
+  const int cy = ((colour >> 1) & 1) ? n / 2 : (n - 1) / 2;
+  const int cz = DIM == 3 ? (((colour >> 2) & 1) ? n / 2 : (n - 1) / 2) : 1;
+  const int64_t np = (int64_t)cx * cy * cz;
+  if (np == 0) return cudaSuccess;
+  const int64_t blocks = (np + ppc - 1) / ppc;
+  const int threads = ppc * S::TPP;
+  const int smem = ppc * patch_smem(DIM, sizeof(T) == 8 ? 0 : 1, n_iter);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  patch_cart_kernel<DIM, T><<<(unsigned)blocks, threads, smem, st>>>(r, u, n, colour, ppc, n_iter, dinv,
+                                                                    to_params<T>(H));
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+static cudaError_t patch_cart(int dim, int prec, const void* r, void* u, int n, int colour, int ppc, int n_iter,
+                              const void* dinv, const PatchParamsHost& P, cudaStream_t s) {
+  if (prec == 0) {
+    if (dim == 3) return patch_cart_t<3, double>((const double*)r, (double*)u, n, colour, ppc, n_iter,
+                                                 (const double*)dinv, P, s);
+    return patch_cart_t<2, double>((const double*)r, (double*)u, n, colour, ppc, n_iter, (const double*)dinv, P, s);
+  }
+  if (dim == 3)
+    return patch_cart_t<3, float>((const float*)r, (float*)u, n, colour, ppc, n_iter, (const float*)dinv, P, s);
+  return patch_cart_t<2, float>((const float*)r, (float*)u, n, colour, ppc, n_iter, (const float*)dinv, P, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t h_prolong_t(const T* uc, T* uf, T* t0, T* t1, int nc, cudaStream_t st) {
+  const int c1 = K * nc + 1, f1 = 2 * K * nc + 1;
+  const int bs = 256;
+  if (DIM == 3) {
+    hprolong_pass<0, false, T><<<grid_for((int64_t)f1 * c1 * c1, bs), bs, 0, st>>>(uc, t0, nc, f1, c1, c1);
+    hprolong_pass<1, false, T><<<grid_for((int64_t)f1 * f1 * c1, bs), bs, 0, st>>>(t0, t1, nc, f1, f1, c1);
+    hprolong_pass<2, true, T><<<grid_for((int64_t)f1 * f1 * f1, bs), bs, 0, st>>>(t1, uf, nc, f1, f1, f1);
+    g_launches += 3;
+  } else {
+    hprolong_pass<0, false, T><<<grid_for((int64_t)f1 * c1, bs), bs, 0, st>>>(uc, t0, nc, f1, c1, 1);
+    hprolong_pass<1, true, T><<<grid_for((int64_t)f1 * f1, bs), bs, 0, st>>>(t0, uf, nc, f1, f1, 1);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+template <int DIM, typename T>
+static cudaError_t h_restrict_t(const T* rf, T* rc, T* t0, T* t1, int nc, cudaStream_t st) {
+  const int c1 = K * nc + 1, f1 = 2 * K * nc + 1;
+  const int bs = 256;
+  if (DIM == 3) {
+    hrestrict_pass<2, T><<<grid_for((int64_t)f1 * f1 * c1, bs), bs, 0, st>>>(rf, t0, nc, f1, f1, c1);
+    hrestrict_pass<1, T><<<grid_for((int64_t)f1 * c1 * c1, bs), bs, 0, st>>>(t0, t1, nc, f1, c1, c1);
+    hrestrict_pass<0, T><<<grid_for((int64_t)c1 * c1 * c1, bs), bs, 0, st>>>(t1, rc, nc, c1, c1, c1);
+    g_launches += 3;
+  } else {
+    hrestrict_pass<1, T><<<grid_for((int64_t)f1 * c1, bs), bs, 0, st>>>(rf, t0, nc, f1, c1, 1);
+    hrestrict_pass<0, T><<<grid_for((int64_t)c1 * c1, bs), bs, 0, st>>>(t0, rc, nc, c1, c1, 1);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t h_prolong_add(int dim, int prec, const void* uc, void* uf, void* t0, void* t1, int nc,
+                                 cudaStream_t s) {
+  if (prec == 0) {
+    if (dim == 3) return h_prolong_t<3, double>((const double*)uc, (double*)uf, (double*)t0, (double*)t1, nc, s);
+    return h_prolong_t<2, double>((const double*)uc, (double*)uf, (double*)t0, (double*)t1, nc, s);
+  }
+  if (dim == 3) return h_prolong_t<3, float>((const float*)uc, (float*)uf, (float*)t0, (float*)t1, nc, s);
+  return h_prolong_t<2, float>((const float*)uc, (float*)uf, (float*)t0, (float*)t1, nc, s);
+}
+
+static cudaError_t h_restrict(int dim, int prec, const void* rf, void* rc, void* t0, void* t1, int nc,
+                              cudaStream_t s) {
+  if (prec == 0) {
+    if (dim == 3) return h_restrict_t<3, double>((const double*)rf, (double*)rc, (double*)t0, (double*)t1, nc, s);
+    return h_restrict_t<2, double>((const double*)rf, (double*)rc, (double*)t0, (double*)t1, nc, s);
+  }
+  if (dim == 3) return h_restrict_t<3, float>((const float*)rf, (float*)rc, (float*)t0, (float*)t1, nc, s);
+  return h_restrict_t<2, float>((const float*)rf, (float*)rc, (float*)t0, (float*)t1, nc, s);
+}
+
+// Opt every kernel of this degree into the full shared-memory carve-out
+// (called once per device at context creation, outside any stream capture).
+static cudaError_t prepare() {
+  const int mx = 227 * 1024;
+  cudaFuncSetAttribute(patch_cart_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_cart_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_cart_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_cart_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_def_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_def_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_def_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(patch_def_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<2, 1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<3, 1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<2, -1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<3, -1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<2, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<3, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<2, -1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(def_cell_kernel<3, -1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return cudaGetLastError();
+}
+
+}  // namespace PMG_KNS
+
+const KernelTable* PMG_TABLE_FN() {
+  static KernelTable t = {
+      PMG_K,
+      PMG_KNS::prepare,
+      PMG_KNS::upload,
+      PMG_KNS::cart_apply,
+      PMG_KNS::patch_cart,
+      PMG_KNS::patch_threads,
+      PMG_KNS::patch_smem,
+      PMG_KNS::h_prolong_add,
+      PMG_KNS::h_restrict,
+      PMG_KNS::def_apply,
+      PMG_KNS::patch_def,
+      PMG_KNS::patch_def_threads,
+      PMG_KNS::patch_def_smem,
+  };
+  return &t;
+}
+
+}  // namespace pmg

@@ -1,0 +1,629 @@
+// Degree-templated CUDA kernels of the p-multigrid vertex-patch library.
+// Included once per degree K by inst_k<K>.cu, which instantiates the launch
+// wrappers into a per-degree function table.
+//
+// Layout on the device: every level vector is the full (K n + 1)^DIM nodal
+// grid, x fastest; boundary entries are zero.  The per-degree 1D matrices
+// (reference mass/stiffness, patch matrices, p-transfers, h-prolongation
+// tables, Gauss tables) live in __constant__ memory of this translation unit,
+// in float64 and float32 copies (coef_layout in pmg_common.cuh).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pmg_common.cuh"
+#include "pmg_kernels_api.h"
+#include "vec.h"
+
+namespace pmg {
+namespace PMG_KNS {
+
+constexpr int K = PMG_K;
+constexpr CoefLayout LAY = coef_layout(K);
+
+static __constant__ double c_coef64[kMaxCoef];
+static __constant__ float c_coef32[kMaxCoef];
+
+template <typename T>
+__device__ __forceinline__ const T* coef();
+template <>
+__device__ __forceinline__ const double* coef<double>() { return c_coef64; }
+template <>
+__device__ __forceinline__ const float* coef<float>() { return c_coef32; }
+
+// ===========================================================================
+// Cartesian operator A = s * sum_dir (K on dir, M elsewhere), applied by one
+// pass per direction over the global grid (the 1D matrices are the
+// reference element matrices assembled along each grid line, i.e. banded
+// with bandwidth K).  Sum factorisation with the 1D Gauss-quadrature
+// matrices folded into M and K, exact for Cartesian cells (Eq. (3)).
+//
+// MODE 0 (first axis):  out0 = M in0, out1 = K in0   (in0 read with y_B = 0)
+// MODE 1 (middle axis): out0 = M in0, out1 = K in0 + M in1
+// MODE 2 (last axis):   out0 = s (K in0 + M in1)   or  b - s (...) (RESID)
+// One thread owns the K outputs of one cell segment of one grid line.
+// ===========================================================================
+template <int DIM, int AX, int MODE, bool RESID, typename T>
+__global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, const T* __restrict__ in1,
+                                                 T* __restrict__ out0, T* __restrict__ out1,
+                                                 const T* __restrict__ bvec, int n, T s) {
+  const int N1 = K * n + 1;
+  const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
+  const int64_t total = (int64_t)(n + 1) * lines;
+  const T* C = coef<T>();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c, p, q;
+    if (AX == 0) {
+      c = (int)(t % (n + 1));
+      const int64_t r = t / (n + 1);
+      p = (int)(r % N1);
+      q = (int)(r / N1);
+    } else {
+      p = (int)(t % N1);
+      const int64_t r = t / N1;
+      c = (int)(r % (n + 1));
+      q = (int)(r / (n + 1));
+    }
+    int64_t base, stride;
+    if (DIM == 3) {
+      if (AX == 0) { base = ((int64_t)q * N1 + p) * N1; stride = 1; }
+      else if (AX == 1) { base = (int64_t)q * N1 * N1 + p; stride = N1; }
+      else { base = (int64_t)q * N1 + p; stride = (int64_t)N1 * N1; }
+    } else {
+      if (AX == 0) { base = (int64_t)p * N1; stride = 1; }
+      else { base = p; stride = N1; }
+    }
+    if (c == n) {  // the last grid node of the line is on the boundary
+      const int64_t o = base + (int64_t)K * n * stride;
+      out0[o] = T(0);
+      if (MODE != 2) out1[o] = T(0);
+      continue;
+    }
+    bool line_zero = false;
+    if (MODE == 0) line_zero = (p == 0 || p == N1 - 1 || (DIM == 3 && (q == 0 || q == N1 - 1)));
+    T xr0[K + 1], xl0[K + 1], xr1[K + 1], xl1[K + 1];
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      const int g = K * c + b;
+      T v = in0[base + (int64_t)g * stride];
+      if (MODE == 0 && (line_zero || g == 0 || g == K * n)) v = T(0);
+      xr0[b] = v;
+      xr1[b] = MODE == 0 ? T(0) : in1[base + (int64_t)g * stride];
+      if (c > 0) {
+        const int gl = K * (c - 1) + b;
+        T w = in0[base + (int64_t)gl * stride];
+        if (MODE == 0 && (line_zero || gl == 0)) w = T(0);
+        xl0[b] = w;
+        xl1[b] = MODE == 0 ? T(0) : in1[base + (int64_t)gl * stride];
+      } else {
+        xl0[b] = T(0);
+        xl1[b] = T(0);
+      }
+    }
+    const T* Me = C + LAY.Me;
+    const T* Ke = C + LAY.Ke;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const int g = K * c + a;
+      T m0 = 0, k0 = 0, m1 = 0;
+#pragma unroll
+      for (int b = 0; b <= K; ++b) {
+        m0 += Me[a * (K + 1) + b] * xr0[b];
+        k0 += Ke[a * (K + 1) + b] * xr0[b];
+        if (MODE != 0) m1 += Me[a * (K + 1) + b] * xr1[b];
+      }
+      if (a == 0) {  // vertex node: add the row of the left cell
+#pragma unroll
+        for (int b = 0; b <= K; ++b) {
+          m0 += Me[K * (K + 1) + b] * xl0[b];
+          k0 += Ke[K * (K + 1) + b] * xl0[b];
+          if (MODE != 0) m1 += Me[K * (K + 1) + b] * xl1[b];
+        }
+      }
+      // node 0 of the line is a boundary node; for the last axis, so is any
+      // node whose other coordinates lie on the boundary (y_B = 0, r_B = 0)
+      const bool bnd = (g == 0) || (MODE == 2 && (p == 0 || p == N1 - 1 || (DIM == 3 && (q == 0 || q == N1 - 1))));
+      const int64_t o = base + (int64_t)g * stride;
+      if (MODE == 0) {
+        out0[o] = bnd ? T(0) : m0;
+        out1[o] = bnd ? T(0) : k0;
+      } else if (MODE == 1) {
+        out0[o] = bnd ? T(0) : m0;
+        out1[o] = bnd ? T(0) : k0 + m1;
+      } else {
+        T v = s * (k0 + m1);
+        if (RESID) v = bvec[o] - v;
+        out0[o] = bnd ? T(0) : v;
+      }
+    }
+  }
+}
+
+// ===========================================================================
+// Vertex-patch smoother with the local p-multigrid solver (§2.1, §2.2, §3).
+// One group of TPP threads per patch; TPP = number of grid lines of the
+// finest patch level, so every 1D contraction step gives each thread at most
+// one line.  All patch vectors live in shared memory:
+//   [t0 | t1 | r_top | d_top | r_{top-1} | d_{top-1} | ... | r_0 d_0 | (rj | ds)]
+// ===========================================================================
+template <int DIM>
+struct PatchShape {
+  static constexpr int L = nlev(K);
+  static constexpr int M(int l) { return mp(plev(K, l)); }
+  static constexpr int MT = mp(K);
+  static constexpr int SZ(int l) { return ipow(M(l), DIM); }
+  static constexpr int SZT = ipow(MT, DIM);
+  static constexpr int TPP = ipow(MT, DIM - 1);
+  static constexpr int off_r(int l) {
+    int o = 2 * SZT;
+    for (int j = L - 1; j > l; --j) o += 2 * SZ(j);
+    return o;
+  }
+  static constexpr int off_d(int l) { return off_r(l) + (l == 0 ? 1 : SZ(l)); }
+  static constexpr int ELEMS = ((off_r(0) + 2) + 1) / 2 * 2;
+};
+
+template <int AX, int EX, int EY, int EZ>
+__device__ __forceinline__ int line_base(int L) {
+  if constexpr (AX == 0) return L * EX;
+  else if constexpr (AX == 1) return (L % EX) + EX * EY * (L / EX);
+  else return L;
+}
+template <int AX, int EX, int EY>
+__host__ __device__ constexpr int line_stride() {
+  return AX == 0 ? 1 : (AX == 1 ? EX : EX * EY);
+}
+
+// y = C x for a patch matrix of degree p (m x m, row-major), skipping the
+// structural zeros between the two cells of the patch.
+template <int p, typename T>
+__device__ __forceinline__ void pmv(const T* C, const T* x, T* y) {
+  constexpr int m = mp(p);
+#pragma unroll
+  for (int i = 0; i < m; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < m; ++j)
+      if (pnz(p, p, i, j)) acc += C[i * m + j] * x[j];
+    y[i] = acc;
+  }
+}
+
+// Cartesian patch geometry: A_{j,p} = s sum_dir (KP on dir, MP elsewhere);
+// inverse diagonal from a shared table (scale-free, divided by s).
+template <int DIM, typename T>
+struct CartGeo {
+  const T* dinv;  // concatenated per-level tables, level l at dinv_off(l)
+  T scale;
+  T inv_scale;
+
+  static constexpr int dinv_off(int l) {
+    int o = 0;
+    for (int j = 1; j < l; ++j) o += ipow(mp(plev(K, j)), DIM);
+    return o;
+  }
+  __device__ __forceinline__ T dinv_at(int l, int i) const { return dinv[dinv_off(l) + i] * inv_scale; }
+
+  // out = r - A_l d  (out may alias t0; d, r distinct from t0, t1)
+  template <int l>
+  __device__ __forceinline__ void resid(const T* d, const T* r, T* out, T* t0, T* t1, int lane, int tpp) const {
+    constexpr int p = plev(K, l);
+    constexpr int m = mp(p);
+    const T* MP = coef<T>() + LAY.MP[l];
+    const T* KP = coef<T>() + LAY.KP[l];
+    if constexpr (DIM == 3) {
+      for (int L = lane; L < m * m; L += tpp) {
+        const int b = line_base<0, m, m, m>(L);
+        T x[m], y0[m], y1[m];
+#pragma unroll
+        for (int j = 0; j < m; ++j) x[j] = d[b + j];
+        pmv<p>(MP, x, y0);
+        pmv<p>(KP, x, y1);
+#pragma unroll
+        for (int i = 0; i < m; ++i) { t0[b + i] = y0[i]; t1[b + i] = y1[i]; }
+      }
+      __syncthreads();
+      for (int L = lane; L < m * m; L += tpp) {
+        const int b = line_base<1, m, m, m>(L);
+        T a[m], c[m], y0[m], y1[m], y2[m];
+#pragma unroll
+        for (int j = 0; j < m; ++j) { a[j] = t0[b + j * m]; c[j] = t1[b + j * m]; }
+        pmv<p>(MP, a, y0);
+        pmv<p>(KP, a, y1);
+        pmv<p>(MP, c, y2);
+#pragma unroll
+        for (int i = 0; i < m; ++i) { t0[b + i * m] = y0[i]; t1[b + i * m] = y1[i] + y2[i]; }
+      }
+      __syncthreads();
+      for (int L = lane; L < m * m; L += tpp) {
+        const int b = line_base<2, m, m, m>(L);
+        T a[m], c[m], y1[m], y2[m];
+#pragma unroll
+        for (int j = 0; j < m; ++j) { a[j] = t0[b + j * m * m]; c[j] = t1[b + j * m * m]; }
+        pmv<p>(KP, a, y1);
+        pmv<p>(MP, c, y2);
+#pragma unroll
+        for (int i = 0; i < m; ++i) out[b + i * m * m] = r[b + i * m * m] - scale * (y1[i] + y2[i]);
+      }
+      __syncthreads();
+    } else {
+      for (int L = lane; L < m; L += tpp) {
+        const int b = line_base<0, m, m, 1>(L);
+        T x[m], y0[m], y1[m];
+#pragma unroll
+        for (int j = 0; j < m; ++j) x[j] = d[b + j];
+        pmv<p>(MP, x, y0);
+        pmv<p>(KP, x, y1);
+#pragma unroll
+        for (int i = 0; i < m; ++i) { t0[b + i] = y0[i]; t1[b + i] = y1[i]; }
+      }
+      __syncthreads();
+      for (int L = lane; L < m; L += tpp) {
+        const int b = line_base<1, m, m, 1>(L);
+        T a[m], c[m], y1[m], y2[m];
+#pragma unroll
+        for (int j = 0; j < m; ++j) { a[j] = t0[b + j * m]; c[j] = t1[b + j * m]; }
+        pmv<p>(KP, a, y1);
+        pmv<p>(MP, c, y2);
+#pragma unroll
+        for (int i = 0; i < m; ++i) out[b + i * m] = r[b + i * m] - scale * (y1[i] + y2[i]);
+      }
+      __syncthreads();
+    }
+  }
+};
+
+// Restriction rc = T_l^T t (t: fine level l in t0; rc: level l-1), using t1.
+template <int DIM, int l, typename T>
+__device__ __forceinline__ void restrict_p(T* t0, T* t1, T* rc, int lane, int tpp) {
+  constexpr int pf = plev(K, l), pc = plev(K, l - 1);
+  constexpr int m = mp(pf), mc = mp(pc);
+  const T* Tr = coef<T>() + LAY.Tr[l];  // m x mc, row-major
+  constexpr int EZ = DIM == 3 ? m : 1;
+  constexpr int EZC = DIM == 3 ? mc : 1;
+  // x: (m, m, EZ) -> (mc, m, EZ) in t1
+  for (int L = lane; L < m * EZ; L += tpp) {
+    const int bi = line_base<0, m, m, EZ>(L), bo = line_base<0, mc, m, EZ>(L);
+    T x[m];
+#pragma unroll
+    for (int j = 0; j < m; ++j) x[j] = t0[bi + j];
+#pragma unroll
+    for (int i = 0; i < mc; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < m; ++j)
+        if (pnz(pf, pc, j, i)) acc += Tr[j * mc + i] * x[j];
+      t1[bo + i] = acc;
+    }
+  }
+  __syncthreads();
+  // y: (mc, m, EZ) -> (mc, mc, EZ) into t0 (2D: directly into rc)
+  T* ydst = DIM == 3 ? t0 : rc;
+  for (int L = lane; L < mc * EZ; L += tpp) {
+    const int bi = line_base<1, mc, m, EZ>(L), bo = line_base<1, mc, mc, EZ>(L);
+    T x[m];
+#pragma unroll
+    for (int j = 0; j < m; ++j) x[j] = t1[bi + j * mc];
+#pragma unroll
+    for (int i = 0; i < mc; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < m; ++j)
+        if (pnz(pf, pc, j, i)) acc += Tr[j * mc + i] * x[j];
+      ydst[bo + i * mc] = acc;
+    }
+  }
+  __syncthreads();
+  if constexpr (DIM == 3) {
+    for (int L = lane; L < mc * mc; L += tpp) {
+      const int bi = line_base<2, mc, mc, m>(L), bo = line_base<2, mc, mc, mc>(L);
+      T x[m];
+#pragma unroll
+      for (int j = 0; j < m; ++j) x[j] = t0[bi + j * mc * mc];
+#pragma unroll
+      for (int i = 0; i < mc; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < m; ++j)
+          if (pnz(pf, pc, j, i)) acc += Tr[j * mc + i] * x[j];
+        rc[bo + i * mc * mc] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Prolongation d += T_l dc (dc: level l-1), using t0, t1.
+template <int DIM, int l, typename T>
+__device__ __forceinline__ void prolong_p(const T* dc, T* t0, T* t1, T* d, int lane, int tpp) {
+  constexpr int pf = plev(K, l), pc = plev(K, l - 1);
+  constexpr int m = mp(pf), mc = mp(pc);
+  const T* Tr = coef<T>() + LAY.Tr[l];
+  constexpr int EZC = DIM == 3 ? mc : 1;
+  // x: (mc, mc, EZC) -> (m, mc, EZC) in t0
+  for (int L = lane; L < mc * EZC; L += tpp) {
+    const int bi = line_base<0, mc, mc, EZC>(L), bo = line_base<0, m, mc, EZC>(L);
+    T x[mc];
+#pragma unroll
+    for (int j = 0; j < mc; ++j) x[j] = dc[bi + j];
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < mc; ++j)
+        if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
+      t0[bo + i] = acc;
+    }
+  }
+  __syncthreads();
+  if constexpr (DIM == 3) {
+    // y: (m, mc, mc) -> (m, m, mc) in t1
+    for (int L = lane; L < m * mc; L += tpp) {
+      const int bi = line_base<1, m, mc, mc>(L), bo = line_base<1, m, m, mc>(L);
+      T x[mc];
+#pragma unroll
+      for (int j = 0; j < mc; ++j) x[j] = t0[bi + j * m];
+#pragma unroll
+      for (int i = 0; i < m; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < mc; ++j)
+          if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
+        t1[bo + i * m] = acc;
+      }
+    }
+    __syncthreads();
+    // z: (m, m, mc) -> (m, m, m) added into d
+    for (int L = lane; L < m * m; L += tpp) {
+      const int bi = line_base<2, m, m, mc>(L), bo = line_base<2, m, m, m>(L);
+      T x[mc];
+#pragma unroll
+      for (int j = 0; j < mc; ++j) x[j] = t1[bi + j * m * m];
+#pragma unroll
+      for (int i = 0; i < m; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < mc; ++j)
+          if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
+        d[bo + i * m * m] += acc;
+      }
+    }
+    __syncthreads();
+  } else {
+    // y: (m, mc) -> (m, m) added into d
+    for (int L = lane; L < m; L += tpp) {
+      const int bi = line_base<1, m, mc, 1>(L), bo = line_base<1, m, m, 1>(L);
+      T x[mc];
+#pragma unroll
+      for (int j = 0; j < mc; ++j) x[j] = t0[bi + j * m];
+#pragma unroll
+      for (int i = 0; i < m; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < mc; ++j)
+          if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
+        d[bo + i * m] += acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Algorithm 3 (full V-cycle) on p-level l for the residual in r_l, result
+// in d_l; level 0 (p = 1) is the exact 1x1 solve (§3.2).
+template <int DIM, int l, typename T, class Geo>
+__device__ void pvcycle(T* sm, const Geo& geo, const PatchParams<T>& P, T inv_a0, int lane, int tpp) {
+  using S = PatchShape<DIM>;
+  if constexpr (l == 0) {
+    if (lane == 0) sm[S::off_d(0)] = sm[S::off_r(0)] * inv_a0;
+    __syncthreads();
+  } else {
+    constexpr int SZ = S::SZ(l);
+    T* r = sm + S::off_r(l);
+    T* d = sm + S::off_d(l);
+    T* t0 = sm;
+    T* t1 = sm + S::SZT;
+    const T om = P.omega[l];
+    for (int i = lane; i < SZ; i += tpp) d[i] = om * geo.dinv_at(l, i) * r[i];  // pre-smoothing
+    __syncthreads();
+    geo.template resid<l>(d, r, t0, t0, t1, lane, tpp);                        // residual
+    restrict_p<DIM, l>(t0, t1, sm + S::off_r(l - 1), lane, tpp);               // restrict
+    pvcycle<DIM, l - 1, T, Geo>(sm, geo, P, inv_a0, lane, tpp);                // recurse
+    prolong_p<DIM, l>(sm + S::off_d(l - 1), t0, t1, d, lane, tpp);             // prolongate, add
+    geo.template resid<l>(d, r, t0, t0, t1, lane, tpp);                        // residual
+    for (int i = lane; i < SZ; i += tpp) d[i] += om * geo.dinv_at(l, i) * t0[i];  // post-smoothing
+    __syncthreads();
+  }
+}
+
+// Patches of one parity colour: vertex v_d = 2 i_d + (bit_d ? 1 : 2).
+__device__ __forceinline__ int colour_count(int n, int bit) { return bit ? n / 2 : (n - 1) / 2; }
+
+template <int DIM, typename T>
+__global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ u, int n, int colour, int ppc,
+                                  int n_iter, const T* __restrict__ dinv, PatchParams<T> P) {
+  using S = PatchShape<DIM>;
+  constexpr int TPP = S::TPP;
+  constexpr int MT = S::MT;
+  constexpr int L = S::L;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int grp = threadIdx.x / TPP, lane = threadIdx.x % TPP;
+  const int gstride = S::ELEMS + (n_iter > 1 ? 2 * S::SZT : 0);
+  T* sm = reinterpret_cast<T*>(smraw) + (int64_t)grp * gstride;
+  const int cx = colour_count(n, colour & 1), cy = colour_count(n, (colour >> 1) & 1);
+  const int cz = DIM == 3 ? colour_count(n, (colour >> 2) & 1) : 1;
+  const int64_t npatch = (int64_t)cx * cy * cz;
+  const int64_t pid = (int64_t)blockIdx.x * ppc + grp;
+  const bool active = pid < npatch;
+  int v[3] = {0, 0, 0};
+  if (active) {
+    int64_t t = pid;
+    const int ix = (int)(t % cx); t /= cx;
+    const int iy = (int)(t % cy); t /= cy;
+    const int iz = (int)t;
+    v[0] = 2 * ix + ((colour & 1) ? 1 : 2);
+    v[1] = 2 * iy + (((colour >> 1) & 1) ? 1 : 2);
+    v[2] = DIM == 3 ? 2 * iz + (((colour >> 2) & 1) ? 1 : 2) : 0;
+  }
+  const int N1 = K * n + 1;
+  const int g0x = K * (v[0] - 1) + 1, g0y = K * (v[1] - 1) + 1, g0z = DIM == 3 ? K * (v[2] - 1) + 1 : 0;
+  T* rt = sm + S::off_r(L - 1);
+  T* dt = sm + S::off_d(L - 1);
+  // gather r_j = Pi_j r
+  for (int i = lane; i < S::SZT; i += TPP) {
+    T val = T(0);
+    if (active) {
+      const int ix = i % MT, iy = (i / MT) % MT, iz = DIM == 3 ? i / (MT * MT) : 0;
+      const int64_t g = (int64_t)(g0x + ix) + (int64_t)N1 * ((g0y + iy) + (int64_t)N1 * (DIM == 3 ? g0z + iz : 0));
+      val = r[g];
+    }
+    rt[i] = val;
+  }
+  __syncthreads();
+  CartGeo<DIM, T> geo{dinv, P.scale, T(1) / P.scale};
+  if (n_iter > 1) {
+    // Algorithm 2: keep r_j and the running correction ds
+    T* rj = sm + S::ELEMS;
+    T* ds = rj + S::SZT;
+    for (int i = lane; i < S::SZT; i += TPP) { rj[i] = rt[i]; }
+    __syncthreads();
+    pvcycle<DIM, L - 1, T>(sm, geo, P, P.inv_a0, lane, TPP);
+    for (int i = lane; i < S::SZT; i += TPP) ds[i] = dt[i];
+    __syncthreads();
+    for (int it = 1; it < n_iter; ++it) {
+      geo.template resid<L - 1>(ds, rj, rt, sm, sm + S::SZT, lane, TPP);
+      pvcycle<DIM, L - 1, T>(sm, geo, P, P.inv_a0, lane, TPP);
+      for (int i = lane; i < S::SZT; i += TPP) ds[i] += dt[i];
+      __syncthreads();
+    }
+    for (int i = lane; i < S::SZT; i += TPP) dt[i] = ds[i];
+    __syncthreads();
+  } else {
+    pvcycle<DIM, L - 1, T>(sm, geo, P, P.inv_a0, lane, TPP);
+  }
+  // scatter u += omega_AS Pi_j^T d_j (patches of one colour are disjoint)
+  if (active) {
+    for (int i = lane; i < S::SZT; i += TPP) {
+      const int ix = i % MT, iy = (i / MT) % MT, iz = DIM == 3 ? i / (MT * MT) : 0;
+      const int64_t g = (int64_t)(g0x + ix) + (int64_t)N1 * ((g0y + iy) + (int64_t)N1 * (DIM == 3 ? g0z + iz : 0));
+      u[g] += P.omega_as * dt[i];
+    }
+  }
+}
+
+// K = 1: every patch interior is the single vertex; the local solve is the
+// exact 1x1 inverse, so a colour sweep is u_v += omega_AS r_v / A_vv.
+template <int DIM, typename T>
+__global__ void patch_k1_kernel(const T* __restrict__ r, T* __restrict__ u, int n, T factor) {
+  const int64_t nv = DIM == 3 ? (int64_t)(n - 1) * (n - 1) * (n - 1) : (int64_t)(n - 1) * (n - 1);
+  const int N1 = n + 1;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % (n - 1)) + 1;
+    const int64_t rr = t / (n - 1);
+    const int y = (int)(rr % (n - 1)) + 1;
+    const int z = DIM == 3 ? (int)(rr / (n - 1)) + 1 : 0;
+    const int64_t g = x + (int64_t)N1 * (y + (int64_t)N1 * z);
+    u[g] += factor * r[g];
+  }
+}
+
+// ===========================================================================
+// h-transfers (Eq. (2)): prolongation = embedding, one pass per axis,
+// restriction = its transpose, one pass per axis in reverse order.
+// ===========================================================================
+// Prolongation along AX: in has extent nc1 = K nc + 1 along AX, out nf1 =
+// K (2 nc) + 1; e0, e1 are the extents of the two other axes (x-fastest order
+// of the remaining axes).  ADD: out += result.
+template <int AX, bool ADD, typename T>
+__global__ void hprolong_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
+  // ex, ey, ez: extents of the OUTPUT array
+  const int nf = 2 * nc;
+  const int nc1 = K * nc + 1;
+  const int64_t total = (int64_t)ex * ey * ez;
+  const T* Pt = coef<T>() + LAY.Pt;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % ex);
+    const int64_t rr = t / ex;
+    const int y = (int)(rr % ey);
+    const int z = (int)(rr / ey);
+    const int gf = AX == 0 ? x : (AX == 1 ? y : z);
+    const int cf = min(gf / K, nf - 1);
+    const int a = gf - K * cf;
+    const int cc = cf / 2, ch = cf % 2;
+    // input extents: same as output except nc1 along AX
+    const int ix = AX == 0 ? nc1 : ex, iy = AX == 1 ? nc1 : ey;
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      const int gc = K * cc + b;
+      const int64_t ii = AX == 0 ? (gc + (int64_t)ix * (y + (int64_t)iy * z))
+                                 : (AX == 1 ? (x + (int64_t)ix * (gc + (int64_t)iy * z))
+                                            : (x + (int64_t)ix * (y + (int64_t)iy * gc)));
+      acc += Pt[(ch * (K + 1) + a) * (K + 1) + b] * in[ii];
+    }
+    if (ADD) out[t] += acc; else out[t] = acc;
+  }
+}
+
+// Restriction along AX: in has extent nf1 along AX, out nc1; outputs on the
+// boundary nodes of AX are zero (restriction acts on free DoFs).
+template <int AX, typename T>
+__global__ void hrestrict_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
+  const int nc1 = K * nc + 1;
+  const int nf1 = 2 * K * nc + 1;
+  const int64_t total = (int64_t)ex * ey * ez;
+  const T* Pt = coef<T>() + LAY.Pt;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % ex);
+    const int64_t rr = t / ex;
+    const int y = (int)(rr % ey);
+    const int z = (int)(rr / ey);
+    const int gc = AX == 0 ? x : (AX == 1 ? y : z);
+    if (gc == 0 || gc == nc1 - 1) { out[t] = T(0); continue; }
+    const int ix = AX == 0 ? nf1 : ex, iy = AX == 1 ? nf1 : ey;
+    auto at = [&](int gf) -> T {
+      const int64_t ii = AX == 0 ? (gf + (int64_t)ix * (y + (int64_t)iy * z))
+                                 : (AX == 1 ? (x + (int64_t)ix * (gf + (int64_t)iy * z))
+                                            : (x + (int64_t)ix * (y + (int64_t)iy * gf)));
+      return in[ii];
+    };
+    const int cc = gc / K, bb = gc - K * cc;
+    T acc = T(0);
+    if (bb == 0) {
+      // vertex node: fine nodes of coarse cells cc-1 (local index K) and cc (local 0)
+      const int Cl = cc - 1;
+#pragma unroll
+      for (int tt = 0; tt <= 2 * K; ++tt) {
+        const int ch = tt < K ? 0 : 1, a = tt - K * ch;
+        acc += Pt[(ch * (K + 1) + a) * (K + 1) + K] * at(2 * K * Cl + tt);
+      }
+#pragma unroll
+      for (int tt = 1; tt <= 2 * K; ++tt) {
+        const int ch = tt < K ? 0 : 1, a = tt - K * ch;
+        acc += Pt[(ch * (K + 1) + a) * (K + 1) + 0] * at(2 * K * cc + tt);
+      }
+    } else {
+#pragma unroll
+      for (int tt = 0; tt <= 2 * K; ++tt) {
+        const int ch = tt < K ? 0 : 1, a = tt - K * ch;
+        acc += Pt[(ch * (K + 1) + a) * (K + 1) + bb] * at(2 * K * cc + tt);
+      }
+    }
+    out[t] = acc;
+  }
+}
+
+template <typename T>
+static PatchParams<T> to_params(const PatchParamsHost& H) {
+  PatchParams<T> P;
+  P.scale = (T)H.scale;
+  P.omega_as = (T)H.omega_as;
+  for (int i = 0; i < 4; ++i) P.omega[i] = (T)H.omega[i];
+  P.inv_a0 = (T)H.inv_a0;
+  return P;
+}
+
+}  // namespace PMG_KNS
+}  // namespace pmg

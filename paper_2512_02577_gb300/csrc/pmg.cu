@@ -1,0 +1,813 @@
+// Host runtime of the library: context and device memory plan, hierarchy
+// set-up, the geometric V-cycle (captured once as a CUDA graph), the FP64
+// preconditioned CG driver, and the C ABI declared in include/pmg.h.
+//
+// Method: §2 of arXiv 2512.02577 -- nested meshes (Eq. (1)), embedding
+// prolongation and its l2-adjoint restriction (Eq. (2)), level matrices of
+// the bilinear form (Eq. (3), Eq. (4)), vertex-patch smoothing (§2.1, here
+// additive), local p-multigrid (§2.2, Algorithms 2 and 3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pmg.h"
+#include "pmg_common.cuh"
+#include "pmg_kernels_api.h"
+#include "setup.h"
+#include "vec.h"
+
+namespace pmg {
+const KernelTable* kernel_table_k1();
+const KernelTable* kernel_table_k2();
+const KernelTable* kernel_table_k3();
+const KernelTable* kernel_table_k4();
+const KernelTable* kernel_table_k5();
+const KernelTable* kernel_table_k6();
+const KernelTable* kernel_table_k7();
+const KernelTable* kernel_table_k8();
+
+const KernelTable* kernel_table(int K) {
+  switch (K) {
+    case 1: return kernel_table_k1();
+    case 2: return kernel_table_k2();
+    case 3: return kernel_table_k3();
+    case 4: return kernel_table_k4();
+    case 5: return kernel_table_k5();
+    case 6: return kernel_table_k6();
+    case 7: return kernel_table_k7();
+    case 8: return kernel_table_k8();
+    default: return nullptr;
+  }
+}
+}  // namespace pmg
+
+using namespace pmg;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+int fail(int code, const std::string& msg) {
+  t_last_error = msg;
+  return code;
+}
+
+#define PMG_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(PMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kMaxCoarse = 4096;
+constexpr int64_t kAlign = 256;
+
+enum Scal { S_RZ = 0, S_PAP = 1, S_RR = 2, S_RZN = 3, S_BB = 4, S_TMP = 5, S_COUNT = 16 };
+
+int64_t ipow64(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+struct LevelData {
+  int n = 0, N1 = 0;
+  int64_t N = 0;
+  void *b = nullptr, *u = nullptr, *r = nullptr;  // MG precision
+  double scale = 1.0;                             // h^{d-2}
+  double inv_a0 = 0.0;                            // Cartesian 1 / A_{j,1}
+  float* G[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* dinv[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* dinv1 = nullptr;
+};
+
+// Byte layout of every device array of a context.
+struct Plan {
+  int dim = 3, K = 2, nlev = 1, nplev = 1, n0 = 1, mg_es = 8;
+  bool deformed = false, mg32 = false;
+  std::vector<int> ns;
+  int nc = 0;  // free DoFs on the coarsest level
+  int64_t total = 0;
+  // offsets
+  struct LOff {
+    int64_t b, u, r, G[4], dinv[4], dinv1;
+  };
+  std::vector<LOff> lo;
+  int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv;
+  int64_t dtab_len = 0;
+};
+
+int64_t bump(int64_t& cur, int64_t bytes) {
+  const int64_t o = cur;
+  cur += (bytes + kAlign - 1) / kAlign * kAlign;
+  return o;
+}
+
+int make_plan(const pmg_config* cfg, Plan& P) {
+  if (!cfg) return fail(PMG_ERR_ARG, "config is NULL");
+  if (cfg->dim != 2 && cfg->dim != 3) return fail(PMG_ERR_UNSUPPORTED, "dim must be 2 or 3");
+  if (cfg->degree < 1 || cfg->degree > 8) return fail(PMG_ERR_UNSUPPORTED, "degree must be in 1..8");
+  if (cfg->n_cells < 1) return fail(PMG_ERR_ARG, "n_cells must be >= 1");
+  if (cfg->geometry != PMG_GEOM_CARTESIAN && cfg->geometry != PMG_GEOM_DEFORMED)
+    return fail(PMG_ERR_ARG, "unknown geometry");
+  if (cfg->mg_precision != PMG_FP64 && cfg->mg_precision != PMG_FP32) return fail(PMG_ERR_ARG, "unknown precision");
+  if (cfg->local_cycles < 1 || cfg->smooth_steps < 1) return fail(PMG_ERR_ARG, "local_cycles, smooth_steps >= 1");
+  P.dim = cfg->dim;
+  P.K = cfg->degree;
+  P.deformed = cfg->geometry == PMG_GEOM_DEFORMED;
+  P.mg32 = cfg->mg_precision == PMG_FP32;
+  P.mg_es = P.mg32 ? 4 : 8;
+  P.nplev = nlev(P.K);
+  // mesh levels: n_l = n_0 2^l
+  int n = cfg->n_cells, L = cfg->n_levels;
+  if (L <= 0) {
+    L = 1;
+    while (n % 2 == 0 && n / 2 >= 1) { n /= 2; ++L; }
+  } else {
+    for (int i = 1; i < L; ++i) {
+      if (n % 2) return fail(PMG_ERR_UNSUPPORTED, "n_cells must be divisible by 2^(n_levels-1)");
+      n /= 2;
+    }
+  }
+  P.n0 = n;
+  P.nlev = L;
+  P.ns.resize(L);
+  for (int l = 0; l < L; ++l) P.ns[l] = P.n0 << l;
+  const int64_t nc1 = (int64_t)P.K * P.n0 - 1;
+  const int64_t nc = ipow64(std::max<int64_t>(nc1, 0), P.dim);
+  if (nc > kMaxCoarse) return fail(PMG_ERR_UNSUPPORTED, "coarsest level has more than 4096 free DoFs");
+  P.nc = (int)nc;
+  const int ncomp = P.dim == 3 ? 6 : 3;
+  int64_t cur = 0;
+  P.lo.resize(L);
+  for (int l = 0; l < L; ++l) {
+    const int nl = P.ns[l];
+    const int64_t N = ipow64((int64_t)P.K * nl + 1, P.dim);
+    auto& o = P.lo[l];
+    o.b = bump(cur, N * P.mg_es);
+    o.u = bump(cur, N * P.mg_es);
+    o.r = bump(cur, N * P.mg_es);
+    for (int i = 0; i < 4; ++i) o.G[i] = o.dinv[i] = -1;
+    o.dinv1 = -1;
+    if (P.deformed) {
+      for (int pl = 0; pl < P.nplev; ++pl) {
+        const int p = plev(P.K, pl);
+        const bool top = pl == P.nplev - 1;
+        if (!top && l == 0) continue;  // coarsest level: only the operator itself
+        o.G[pl] = bump(cur, ipow64(nl, P.dim) * ipow64(p + 1, P.dim) * ncomp * 4);
+        if (l > 0 && pl > 0) o.dinv[pl] = bump(cur, ipow64((int64_t)p * nl + 1, P.dim) * P.mg_es);
+      }
+      if (l > 0) o.dinv1 = bump(cur, ipow64(nl + 1, P.dim) * P.mg_es);
+    }
+  }
+  const int64_t NF = ipow64((int64_t)P.K * cfg->n_cells + 1, P.dim);
+  for (int i = 0; i < 4; ++i) P.t64[i] = bump(cur, NF * 8);
+  for (int i = 0; i < 4; ++i) P.t_mg[i] = P.mg32 ? bump(cur, NF * 4) : P.t64[i];
+  for (int i = 0; i < 6; ++i) P.cg[i] = bump(cur, NF * 8);
+  P.scal = bump(cur, S_COUNT * 8);
+  P.partial = bump(cur, kDotBlocks * 8 * 2);
+  P.dtab_len = 0;
+  for (int pl = 1; pl < P.nplev; ++pl) P.dtab_len += ipow64(mp(plev(P.K, pl)), P.dim);
+  P.dtab64 = bump(cur, std::max<int64_t>(P.dtab_len, 1) * 8);
+  P.dtab32 = bump(cur, std::max<int64_t>(P.dtab_len, 1) * 4);
+  P.cidx = bump(cur, std::max(P.nc, 1) * 4);
+  P.ainv = bump(cur, std::max<int64_t>((int64_t)P.nc * P.nc, 1) * P.mg_es);
+  P.total = cur;
+  return PMG_OK;
+}
+
+}  // namespace
+
+struct pmg_ctx {
+  pmg_config cfg{};
+  Plan plan;
+  int dim = 3, K = 2, L = 1, nplev = 1;
+  bool deformed = false, mg32 = false;
+  int mgprec = PMG_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  const KernelTable* kt = nullptr;
+  std::vector<LevelData> lv;
+  char* ws = nullptr;
+  bool own_ws = false;
+  void* t_mg[4] = {};
+  double* t64[4] = {};
+  double *cg_x = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *cg_z = nullptr, *cg_b = nullptr;
+  double* scal = nullptr;
+  double* partial = nullptr;
+  double* host_scal = nullptr;  // pinned
+  void* dtab_mg = nullptr;
+  double* dtab64 = nullptr;
+  float* dtab32 = nullptr;
+  int* cidx = nullptr;
+  void* ainv = nullptr;
+  int ppc = 1;
+  double omega_as = 0;
+  double omega_j[4] = {1, 1, 1, 1};
+  cudaGraphExec_t vgraph = nullptr;
+  int64_t vgraph_launches = 0;
+  cudaEvent_t ev_rr = nullptr, ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+void* at(pmg_ctx* c, int64_t off) { return off < 0 ? nullptr : (void*)(c->ws + off); }
+
+PatchParamsHost patch_params(const pmg_ctx* c, int level) {
+  PatchParamsHost P;
+  P.scale = c->lv[level].scale;
+  P.omega_as = c->omega_as;
+  for (int i = 0; i < 4; ++i) P.omega[i] = c->omega_j[i];
+  P.inv_a0 = c->lv[level].inv_a0;
+  return P;
+}
+
+QuadTab make_tab(int p, int nq) {
+  QuadTab t{};
+  std::vector<double> w;
+  auto x = host::gauss_points(nq, &w);
+  auto nodes = host::gll_points(p);
+  t.nq = nq;
+  for (int q = 0; q < nq; ++q) {
+    t.x[q] = x[q];
+    t.w[q] = w[q];
+    for (int a = 0; a <= p; ++a) {
+      t.V[q * 12 + a] = host::lagrange(nodes, a, x[q]);
+      t.D[q * 12 + a] = host::lagrange_deriv(nodes, a, x[q]);
+    }
+  }
+  return t;
+}
+
+// r = b - A u (b != nullptr) or r = A u on mesh level `level`, precision prec.
+int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const void* b) {
+  LevelData& L = c->lv[level];
+  cudaError_t e;
+  if (c->deformed) {
+    e = c->kt->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], L.n, c->stream);
+  } else {
+    void** t = prec == PMG_FP64 ? (void**)c->t64 : c->t_mg;
+    e = c->kt->cart_apply(c->dim, prec, u, r, b, t[0], t[1], t[2], t[3], L.n, L.scale, c->stream);
+  }
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("apply: ") + cudaGetErrorString(e));
+  return PMG_OK;
+}
+
+// One additive sweep's patch corrections: u += S r (all 2^d colours).
+int patch_sweep(pmg_ctx* c, int level, const void* r, void* u) {
+  LevelData& L = c->lv[level];
+  const PatchParamsHost P = patch_params(c, level);
+  for (int colour = 0; colour < (1 << c->dim); ++colour) {
+    cudaError_t e;
+    if (c->deformed) {
+      DefLevel D{};
+      for (int i = 0; i < 4; ++i) {
+        D.G[i] = L.G[i];
+        D.dinv[i] = L.dinv[i];
+      }
+      D.dinv1 = L.dinv1;
+      if (c->K == 1) {
+        // single-vertex patches: u_v += omega_AS r_v / A_vv via the p = 1 diagonal
+        e = c->kt->patch_def(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+      } else {
+        e = c->kt->patch_def(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+      }
+    } else {
+      e = c->kt->patch_cart(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
+                            c->stream);
+    }
+    if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
+  }
+  return PMG_OK;
+}
+
+int smooth_level(pmg_ctx* c, int level, const void* b, void* u, int sweeps) {
+  LevelData& L = c->lv[level];
+  for (int s = 0; s < sweeps; ++s) {
+    int rc = level_apply(c, level, c->mgprec, u, L.r, b);
+    if (rc) return rc;
+    rc = patch_sweep(c, level, L.r, u);
+    if (rc) return rc;
+  }
+  return PMG_OK;
+}
+
+// z_l = B_l b_l from a zero guess (Eq. (1)-(4) V-cycle with additive patch
+// smoothing), MG precision, vectors in the level buffers.
+int vcycle_level(pmg_ctx* c, int level) {
+  LevelData& L = c->lv[level];
+  const size_t es = c->mg32 ? 4 : 8;
+  if (level == 0) {
+    cudaError_t e = coarse_solve(c->mgprec, c->ainv, c->cidx, c->plan.nc, L.b, L.u, L.N, c->stream);
+    if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("coarse: ") + cudaGetErrorString(e));
+    return PMG_OK;
+  }
+  PMG_CUDA(cudaMemsetAsync(L.u, 0, es * L.N, c->stream));
+  const int nu = c->cfg.smooth_steps;
+  int rc;
+  for (int s = 0; s < nu; ++s) {
+    if (s == 0) {
+      rc = patch_sweep(c, level, L.b, L.u);  // zero guess: the residual is b
+    } else {
+      rc = smooth_level(c, level, L.b, L.u, 1);
+    }
+    if (rc) return rc;
+  }
+  if ((rc = level_apply(c, level, c->mgprec, L.u, L.r, L.b))) return rc;
+  LevelData& C = c->lv[level - 1];
+  cudaError_t e = c->kt->h_restrict(c->dim, c->mgprec, L.r, C.b, c->t_mg[0], c->t_mg[1], C.n, c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("restrict: ") + cudaGetErrorString(e));
+  if ((rc = vcycle_level(c, level - 1))) return rc;
+  e = c->kt->h_prolong_add(c->dim, c->mgprec, C.u, L.u, c->t_mg[0], c->t_mg[1], C.n, c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("prolongate: ") + cudaGetErrorString(e));
+  return smooth_level(c, level, L.b, L.u, nu);
+}
+
+// Capture the finest-level V-cycle once as a CUDA graph.
+int ensure_vgraph(pmg_ctx* c) {
+  if (c->vgraph) return PMG_OK;
+  cudaGraph_t g = nullptr;
+  const int64_t before = g_launches.load();
+  PMG_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = vcycle_level(c, c->L - 1);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  const int64_t n = g_launches.load() - before;
+  g_launches -= n;  // captured, not launched
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->vgraph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->vgraph_launches = n;
+  return PMG_OK;
+}
+
+// z = B r for FP64 device vectors r, z on the finest level.
+int precondition(pmg_ctx* c, const double* r, double* z) {
+  LevelData& F = c->lv[c->L - 1];
+  int rc = ensure_vgraph(c);
+  if (rc) return rc;
+  if (c->mg32) {
+    PMG_CUDA(cast_d2f(r, (float*)F.b, F.N, c->stream));
+  } else {
+    PMG_CUDA(cudaMemcpyAsync(F.b, r, 8 * F.N, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  PMG_CUDA(cudaGraphLaunch(c->vgraph, c->stream));
+  g_launches += c->vgraph_launches;
+  if (c->mg32) {
+    PMG_CUDA(cast_f2d((const float*)F.u, z, F.N, c->stream));
+  } else {
+    PMG_CUDA(cudaMemcpyAsync(z, F.u, 8 * F.N, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return PMG_OK;
+}
+
+int check_ctx(const pmg_ctx* c) { return c ? PMG_OK : fail(PMG_ERR_ARG, "context is NULL"); }
+
+int setup_context(pmg_ctx* c) {
+  const Plan& P = c->plan;
+  c->lv.resize(c->L);
+  for (int l = 0; l < c->L; ++l) {
+    LevelData& D = c->lv[l];
+    D.n = P.ns[l];
+    D.N1 = c->K * D.n + 1;
+    D.N = ipow64(D.N1, c->dim);
+    D.b = at(c, P.lo[l].b);
+    D.u = at(c, P.lo[l].u);
+    D.r = at(c, P.lo[l].r);
+    const double h = 1.0 / D.n;
+    D.scale = std::pow(h, c->dim - 2);
+    // Cartesian A_{j,1} = h^{d-2} d (2) (2/3)^{d-1}
+    D.inv_a0 = 1.0 / (D.scale * c->dim * 2.0 * std::pow(2.0 / 3.0, c->dim - 1));
+    for (int i = 0; i < 4; ++i) {
+      D.G[i] = (float*)at(c, P.lo[l].G[i]);
+      D.dinv[i] = at(c, P.lo[l].dinv[i]);
+    }
+    D.dinv1 = at(c, P.lo[l].dinv1);
+  }
+  for (int i = 0; i < 4; ++i) {
+    c->t64[i] = (double*)at(c, P.t64[i]);
+    c->t_mg[i] = at(c, P.t_mg[i]);
+  }
+  double** cg[6] = {&c->cg_x, &c->cg_r, &c->cg_p, &c->cg_Ap, &c->cg_z, &c->cg_b};
+  for (int i = 0; i < 6; ++i) *cg[i] = (double*)at(c, P.cg[i]);
+  c->scal = (double*)at(c, P.scal);
+  c->partial = (double*)at(c, P.partial);
+  c->dtab64 = (double*)at(c, P.dtab64);
+  c->dtab32 = (float*)at(c, P.dtab32);
+  c->dtab_mg = c->mg32 ? (void*)c->dtab32 : (void*)c->dtab64;
+  c->cidx = (int*)at(c, P.cidx);
+  c->ainv = at(c, P.ainv);
+
+  // coefficients and kernel attributes
+  std::vector<double> coef(kMaxCoef, 0.0);
+  host::fill_coefficients(c->K, coef.data());
+  PMG_CUDA(c->kt->prepare());
+  PMG_CUDA(c->kt->upload(coef.data()));
+
+  // damping
+  const pmg_config& cf = c->cfg;
+  c->omega_as = cf.omega_patch > 0 ? cf.omega_patch : 1.5 / (1 << c->dim);
+  for (int l = 0; l < 4; ++l) {
+    if (l < c->nplev && l > 0)
+      c->omega_j[l] = cf.omega_jacobi[l] > 0 ? cf.omega_jacobi[l]
+                                             : host::default_omega_jacobi(c->dim, plev(c->K, l));
+    else
+      c->omega_j[l] = 1.0;
+  }
+
+  // Cartesian scale-free inverse diagonal tables of the patch operators
+  {
+    const CoefLayout LA = coef_layout(c->K);
+    std::vector<double> t64;
+    for (int pl = 1; pl < c->nplev; ++pl) {
+      const int m = mp(plev(c->K, pl));
+      const int64_t S = ipow64(m, c->dim);
+      for (int64_t i = 0; i < S; ++i) {
+        const int ii[3] = {(int)(i % m), (int)((i / m) % m), c->dim == 3 ? (int)(i / (m * m)) : 0};
+        double s = 0.0;
+        for (int dir = 0; dir < c->dim; ++dir) {
+          double t = 1.0;
+          for (int dd = 0; dd < c->dim; ++dd)
+            t *= dd == dir ? coef[LA.dK[pl] + ii[dd]] : coef[LA.dM[pl] + ii[dd]];
+          s += t;
+        }
+        t64.push_back(1.0 / s);
+      }
+    }
+    if (!t64.empty()) {
+      std::vector<float> t32(t64.begin(), t64.end());
+      PMG_CUDA(cudaMemcpyAsync(c->dtab64, t64.data(), 8 * t64.size(), cudaMemcpyHostToDevice, c->stream));
+      PMG_CUDA(cudaMemcpyAsync(c->dtab32, t32.data(), 4 * t32.size(), cudaMemcpyHostToDevice, c->stream));
+      PMG_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  }
+
+  // deformed geometry: G_q per level and p-level, inverse diagonals
+  if (c->deformed) {
+    for (int l = 0; l < c->L; ++l) {
+      LevelData& D = c->lv[l];
+      for (int pl = 0; pl < c->nplev; ++pl) {
+        if (!D.G[pl]) continue;
+        const int p = plev(c->K, pl);
+        PMG_CUDA(compute_geometry(c->dim, D.n, p, cf.deform_amp, make_tab(p, p + 1), D.G[pl], c->stream));
+        if (D.dinv[pl])
+          PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, p, make_tab(p, p + 1), D.G[pl], c->t64[0], D.dinv[pl],
+                                            c->mgprec, c->stream));
+      }
+      if (D.dinv1)
+        PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, 1, make_tab(1, 2), D.G[0], c->t64[0], D.dinv1, c->mgprec,
+                                          c->stream));
+    }
+    PMG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+
+  // patches per block: fill ~256 threads within the shared-memory budget
+  {
+    const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
+    const int smem = c->deformed ? c->kt->patch_def_smem(c->dim, c->mgprec, cf.local_cycles)
+                                 : c->kt->patch_smem(c->dim, c->mgprec, cf.local_cycles);
+    if (smem > 227 * 1024) return fail(PMG_ERR_UNSUPPORTED, "patch does not fit in shared memory for this degree");
+    int ppc = cf.patches_per_block > 0 ? cf.patches_per_block : std::max(1, 256 / tpp);
+    while (ppc > 1 && (ppc * smem > 100 * 1024 || ppc * tpp > 1024)) --ppc;
+    if (ppc * smem > 227 * 1024 || ppc * tpp > 1024) return fail(PMG_ERR_ARG, "patches_per_block too large");
+    c->ppc = ppc;
+  }
+
+  // coarsest level: assemble A_0 column by column with the FP64 operator,
+  // invert on the host (Cholesky), store in MG precision
+  {
+    LevelData& C = c->lv[0];
+    const int N1 = C.N1;
+    std::vector<int> idx;
+    for (int64_t g = 0; g < C.N; ++g) {
+      const int x = (int)(g % N1), y = (int)((g / N1) % N1), z = c->dim == 3 ? (int)(g / ((int64_t)N1 * N1)) : 1;
+      if (x > 0 && x < N1 - 1 && y > 0 && y < N1 - 1 && (c->dim == 2 || (z > 0 && z < N1 - 1)))
+        idx.push_back((int)g);
+    }
+    const int nc = (int)idx.size();
+    if (nc != c->plan.nc) return fail(PMG_ERR_STATE, "coarse size mismatch");
+    if (nc > 0) {
+      std::vector<double> A((size_t)nc * nc), col(C.N);
+      double* xd = c->t64[0];
+      double* yd = c->t64[1];
+      // the FP64 apply of level 0 uses t64[0..3] as scratch: use cg vectors for x, y
+      xd = c->cg_x;
+      yd = c->cg_r;
+      const double one = 1.0;
+      for (int j = 0; j < nc; ++j) {
+        PMG_CUDA(cudaMemsetAsync(xd, 0, 8 * C.N, c->stream));
+        PMG_CUDA(cudaMemcpyAsync(xd + idx[j], &one, 8, cudaMemcpyHostToDevice, c->stream));
+        int rc = level_apply(c, 0, PMG_FP64, xd, yd, nullptr);
+        if (rc) return rc;
+        PMG_CUDA(cudaMemcpyAsync(col.data(), yd, 8 * C.N, cudaMemcpyDeviceToHost, c->stream));
+        PMG_CUDA(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < nc; ++i) A[(size_t)i * nc + j] = col[idx[i]];
+      }
+      for (int i = 0; i < nc; ++i)  // symmetrise the rounding
+        for (int j = 0; j < i; ++j) {
+          const double s = 0.5 * (A[(size_t)i * nc + j] + A[(size_t)j * nc + i]);
+          A[(size_t)i * nc + j] = A[(size_t)j * nc + i] = s;
+        }
+      if (!host::spd_inverse(A, nc)) return fail(PMG_ERR_STATE, "coarse matrix is not positive definite");
+      PMG_CUDA(cudaMemcpyAsync(c->cidx, idx.data(), 4 * nc, cudaMemcpyHostToDevice, c->stream));
+      if (c->mg32) {
+        std::vector<float> Af(A.begin(), A.end());
+        PMG_CUDA(cudaMemcpyAsync(c->ainv, Af.data(), 4 * Af.size(), cudaMemcpyHostToDevice, c->stream));
+        PMG_CUDA(cudaStreamSynchronize(c->stream));
+      } else {
+        PMG_CUDA(cudaMemcpyAsync(c->ainv, A.data(), 8 * A.size(), cudaMemcpyHostToDevice, c->stream));
+        PMG_CUDA(cudaStreamSynchronize(c->stream));
+      }
+    }
+  }
+  PMG_CUDA(cudaMallocHost((void**)&c->host_scal, 8 * S_COUNT));
+  PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
+  PMG_CUDA(cudaEventCreate(&c->ev0));
+  PMG_CUDA(cudaEventCreate(&c->ev1));
+  PMG_CUDA(cudaStreamSynchronize(c->stream));
+  return PMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pmg_config_default(pmg_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->dim = 3;
+  cfg->n_cells = 8;
+  cfg->degree = 2;
+  cfg->n_levels = 0;
+  cfg->geometry = PMG_GEOM_CARTESIAN;
+  cfg->deform_amp = 0.05;
+  cfg->mg_precision = PMG_FP64;
+  cfg->omega_patch = 0;
+  cfg->local_cycles = 1;
+  cfg->smooth_steps = 1;
+  cfg->patches_per_block = 0;
+}
+
+int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {
+  if (!bytes) return fail(PMG_ERR_ARG, "bytes is NULL");
+  Plan P;
+  int rc = make_plan(cfg, P);
+  if (rc) return rc;
+  *bytes = P.total;
+  return PMG_OK;
+}
+
+int pmg_create(const pmg_config* cfg, void* stream, void* workspace, int64_t workspace_bytes, pmg_ctx** out) {
+  if (!out) return fail(PMG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  pmg_ctx* c = new pmg_ctx();
+  int rc = make_plan(cfg, c->plan);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  c->cfg = *cfg;
+  c->dim = cfg->dim;
+  c->K = cfg->degree;
+  c->L = c->plan.nlev;
+  c->nplev = c->plan.nplev;
+  c->deformed = c->plan.deformed;
+  c->mg32 = c->plan.mg32;
+  c->mgprec = cfg->mg_precision;
+  c->stream = (cudaStream_t)stream;
+  if (!c->stream) {
+    // the legacy default stream cannot be captured into a CUDA graph: use a
+    // blocking stream of our own, which still orders against it
+    cudaError_t e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(PMG_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  c->kt = kernel_table(c->K);
+  if (workspace) {
+    if (workspace_bytes < c->plan.total) {
+      delete c;
+      return fail(PMG_ERR_OOM, "workspace smaller than pmg_bytes_required");
+    }
+    if ((uintptr_t)workspace % kAlign) {
+      delete c;
+      return fail(PMG_ERR_ARG, "workspace must be 256-byte aligned");
+    }
+    c->ws = (char*)workspace;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&c->ws, c->plan.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return fail(PMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->own_ws = true;
+  }
+  rc = setup_context(c);
+  if (rc) {
+    pmg_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return PMG_OK;
+}
+
+int pmg_destroy(pmg_ctx* c) {
+  if (!c) return PMG_OK;
+  if (c->vgraph) cudaGraphExecDestroy(c->vgraph);
+  if (c->ev_rr) cudaEventDestroy(c->ev_rr);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->host_scal) cudaFreeHost(c->host_scal);
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->own_stream && c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+  }
+  delete c;
+  return PMG_OK;
+}
+
+int pmg_num_levels(const pmg_ctx* c, int* n) {
+  if (check_ctx(c) || !n) return fail(PMG_ERR_ARG, "NULL argument");
+  *n = c->L;
+  return PMG_OK;
+}
+
+int pmg_num_dofs(const pmg_ctx* c, int level, int64_t* n) {
+  if (check_ctx(c) || !n) return fail(PMG_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= c->L) return fail(PMG_ERR_ARG, "level out of range");
+  *n = c->lv[level].N;
+  return PMG_OK;
+}
+
+static int check_prec(const pmg_ctx* c, int prec) {
+  if (prec != PMG_FP64 && prec != PMG_FP32) return fail(PMG_ERR_ARG, "unknown precision");
+  if (prec == PMG_FP32 && !c->mg32) return fail(PMG_ERR_ARG, "FP32 calls need a context with mg_precision FP32");
+  return PMG_OK;
+}
+
+int pmg_apply(pmg_ctx* c, int level, int prec, const void* x, void* y) {
+  if (check_ctx(c) || !x || !y) return fail(PMG_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= c->L) return fail(PMG_ERR_ARG, "level out of range");
+  if (int rc = check_prec(c, prec)) return rc;
+  return level_apply(c, level, prec, x, y, nullptr);
+}
+
+int pmg_residual(pmg_ctx* c, int level, int prec, const void* b, const void* u, void* r) {
+  if (check_ctx(c) || !b || !u || !r) return fail(PMG_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= c->L) return fail(PMG_ERR_ARG, "level out of range");
+  if (int rc = check_prec(c, prec)) return rc;
+  return level_apply(c, level, prec, u, r, b);
+}
+
+int pmg_smooth(pmg_ctx* c, int level, int prec, const void* b, void* u, int sweeps) {
+  if (check_ctx(c) || !b || !u) return fail(PMG_ERR_ARG, "NULL argument");
+  if (level < 1 || level >= c->L) return fail(PMG_ERR_ARG, "smoothing level must be in 1..n_levels-1");
+  if (prec != c->mgprec) return fail(PMG_ERR_ARG, "smoother precision must equal mg_precision");
+  if (sweeps < 0) return fail(PMG_ERR_ARG, "sweeps < 0");
+  return smooth_level(c, level, b, u, sweeps);
+}
+
+int pmg_vcycle(pmg_ctx* c, const double* r, double* z) {
+  if (check_ctx(c) || !r || !z) return fail(PMG_ERR_ARG, "NULL argument");
+  return precondition(c, r, z);
+}
+
+static int solve_device(pmg_ctx* c, const double* b, double rtol, int maxit, pmg_solve_info* info) {
+  LevelData& F = c->lv[c->L - 1];
+  const int64_t N = F.N;
+  cudaStream_t s = c->stream;
+  PMG_CUDA(cudaEventRecord(c->ev0, s));
+  PMG_CUDA(cudaMemsetAsync(c->cg_x, 0, 8 * N, s));
+  PMG_CUDA(cudaMemcpyAsync(c->cg_r, b, 8 * N, cudaMemcpyDeviceToDevice, s));
+  PMG_CUDA(dot(c->cg_r, c->cg_r, N, c->partial, c->scal + S_BB, s));
+  PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_BB, c->scal + S_BB, 8, cudaMemcpyDeviceToHost, s));
+  int rc = precondition(c, c->cg_r, c->cg_z);
+  if (rc) return rc;
+  PMG_CUDA(dot(c->cg_r, c->cg_z, N, c->partial, c->scal + S_RZ, s));
+  PMG_CUDA(cudaMemcpyAsync(c->cg_p, c->cg_z, 8 * N, cudaMemcpyDeviceToDevice, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  const double nb = std::sqrt(c->host_scal[S_BB]);
+  int it = 0;
+  double rel = nb > 0 ? 1.0 : 0.0;
+  int status = PMG_OK;
+  if (nb > 0) {
+    status = PMG_NOT_CONVERGED;
+    while (it < maxit) {
+      if ((rc = level_apply(c, c->L - 1, PMG_FP64, c->cg_p, c->cg_Ap, nullptr))) return rc;
+      PMG_CUDA(dot(c->cg_p, c->cg_Ap, N, c->partial, c->scal + S_PAP, s));
+      PMG_CUDA(cg_update_xr(c->cg_x, c->cg_r, c->cg_p, c->cg_Ap, N, c->scal, S_RZ, S_PAP, c->partial,
+                            c->scal + S_RR, s));
+      PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_RR, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s));
+      PMG_CUDA(cudaEventRecord(c->ev_rr, s));
+      ++it;
+      // enqueue the next preconditioner step before checking convergence
+      if ((rc = precondition(c, c->cg_r, c->cg_z))) return rc;
+      PMG_CUDA(dot(c->cg_r, c->cg_z, N, c->partial, c->scal + S_RZN, s));
+      PMG_CUDA(cg_update_p(c->cg_p, c->cg_z, N, c->scal, S_RZN, S_RZ, 0, s));
+      PMG_CUDA(cudaEventSynchronize(c->ev_rr));
+      rel = std::sqrt(std::max(c->host_scal[S_RR], 0.0)) / nb;
+      if (!(rel == rel)) return fail(PMG_ERR_STATE, "CG breakdown (NaN residual)");
+      if (rel <= rtol) {
+        status = PMG_OK;
+        break;
+      }
+    }
+  }
+  PMG_CUDA(cudaEventRecord(c->ev1, s));
+  PMG_CUDA(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = rel;
+    info->time_ms = ms;
+    info->status = status;
+  }
+  return status;
+}
+
+int pmg_solve(pmg_ctx* c, const double* b, double* x, double rtol, int maxit, pmg_solve_info* info) {
+  if (check_ctx(c) || !b || !x) return fail(PMG_ERR_ARG, "NULL argument");
+  if (maxit < 0 || !(rtol >= 0)) return fail(PMG_ERR_ARG, "bad rtol / maxit");
+  int rc = solve_device(c, b, rtol, maxit, info);
+  if (rc < 0) return rc;
+  cudaError_t e = cudaMemcpyAsync(x, c->cg_x, 8 * c->lv[c->L - 1].N, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
+  return rc;
+}
+
+int pmg_solve_host(pmg_ctx* c, const double* b_host, double* x_host, double rtol, int maxit, pmg_solve_info* info) {
+  if (check_ctx(c) || !b_host || !x_host) return fail(PMG_ERR_ARG, "NULL argument");
+  if (maxit < 0 || !(rtol >= 0)) return fail(PMG_ERR_ARG, "bad rtol / maxit");
+  const int64_t N = c->lv[c->L - 1].N;
+  cudaError_t e = cudaMemcpyAsync(c->cg_b, b_host, 8 * N, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
+  int rc = solve_device(c, c->cg_b, rtol, maxit, info);
+  if (rc < 0) return rc;
+  e = cudaMemcpyAsync(x_host, c->cg_x, 8 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
+  return rc;
+}
+
+int pmg_rhs_manufactured(pmg_ctx* c, double* b) {
+  if (check_ctx(c) || !b) return fail(PMG_ERR_ARG, "NULL argument");
+  LevelData& F = c->lv[c->L - 1];
+  PMG_CUDA(rhs_manufactured(c->dim, F.n, c->K, c->cfg.deform_amp, c->deformed ? 1 : 0, make_tab(c->K, c->K + 1), b,
+                            c->stream));
+  return PMG_OK;
+}
+
+int pmg_l2_error_manufactured(pmg_ctx* c, const double* x, double* err) {
+  if (check_ctx(c) || !x || !err) return fail(PMG_ERR_ARG, "NULL argument");
+  LevelData& F = c->lv[c->L - 1];
+  PMG_CUDA(l2_error_partials(c->dim, F.n, c->K, c->cfg.deform_amp, c->deformed ? 1 : 0, make_tab(c->K, c->K + 3), x,
+                             c->partial, c->scal + S_TMP, c->stream));
+  PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_TMP, c->scal + S_TMP, 8, cudaMemcpyDeviceToHost, c->stream));
+  PMG_CUDA(cudaStreamSynchronize(c->stream));
+  *err = std::sqrt(std::max(c->host_scal[S_TMP], 0.0));
+  return PMG_OK;
+}
+
+int pmg_synchronize(pmg_ctx* c) {
+  if (check_ctx(c)) return PMG_ERR_ARG;
+  PMG_CUDA(cudaStreamSynchronize(c->stream));
+  return PMG_OK;
+}
+
+int64_t pmg_launch_count(void) { return g_launches.load(); }
+
+const char* pmg_status_string(int s) {
+  switch (s) {
+    case PMG_OK: return "ok";
+    case PMG_NOT_CONVERGED: return "not converged";
+    case PMG_ERR_ARG: return "invalid argument";
+    case PMG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PMG_ERR_OOM: return "out of device memory";
+    case PMG_ERR_CUDA: return "CUDA error";
+    case PMG_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case PMG_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+  }
+}
+
+const char* pmg_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

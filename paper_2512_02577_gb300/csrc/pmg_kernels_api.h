@@ -1,0 +1,55 @@
+// Per-degree table of kernel launchers, filled by inst_k<K>.cu.  Host code
+// (pmg.cu) dispatches on the degree k through kernel_table(k); every entry
+// enqueues on the given stream and returns the launch's cudaError_t.
+// Precision flag: 0 = double, 1 = float (element type of every vector).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pmg {
+
+struct PatchParamsHost {
+  double scale;      // h^{d-2}
+  double omega_as;
+  double omega[4];
+  double inv_a0;     // 1 / A_{j,1} (Cartesian)
+};
+
+// Deformed-geometry arrays of one mesh level (device pointers).
+struct DefLevel {
+  const float* G[4];      // per p-level l >= 1: per cell, (p+1)^d points x ncomp (x fastest), float32
+  const void* dinv[4];    // per p-level l >= 1: inverse diagonal on the degree-p global grid (MG precision)
+  const void* dinv1;      // p = 1: inverse Q1 diagonal on the vertex grid (n+1)^d (MG precision)
+};
+
+struct KernelTable {
+  int K;
+  cudaError_t (*prepare)();
+  cudaError_t (*upload)(const double* coef);
+  // y = A x (b == nullptr) or y = b - A x; Cartesian; t0..t3: scratch of N
+  cudaError_t (*cart_apply)(int dim, int prec, const void* x, void* y, const void* b, void* t0, void* t1,
+                            void* t2, void* t3, int n, double scale, cudaStream_t s);
+  // one parity colour of the Cartesian patch smoother
+  cudaError_t (*patch_cart)(int dim, int prec, const void* r, void* u, int n, int colour, int ppc, int n_iter,
+                            const void* dinv, const PatchParamsHost& P, cudaStream_t s);
+  int (*patch_threads)(int dim);                  // threads per patch
+  int (*patch_smem)(int dim, int prec, int n_iter);  // shared bytes per patch
+  // u_f += P u_c  /  r_c = P^T r_f  (nc = coarse cells per side); t0, t1 scratch of N_f
+  cudaError_t (*h_prolong_add)(int dim, int prec, const void* uc, void* uf, void* t0, void* t1, int nc,
+                               cudaStream_t s);
+  cudaError_t (*h_restrict)(int dim, int prec, const void* rf, void* rc, void* t0, void* t1, int nc,
+                            cudaStream_t s);
+  // deformed geometry: y = A x or y = b - A x with stored G (float32)
+  cudaError_t (*def_apply)(int dim, int prec, const void* x, void* y, const void* b, const float* G, int n,
+                           cudaStream_t s);
+  // one colour of the deformed patch smoother
+  cudaError_t (*patch_def)(int dim, int prec, const void* r, void* u, int n, int colour, int ppc, int n_iter,
+                           const DefLevel& lev, const PatchParamsHost& P, cudaStream_t s);
+  int (*patch_def_threads)(int dim);
+  int (*patch_def_smem)(int dim, int prec, int n_iter);
+};
+
+const KernelTable* kernel_table(int K);
+
+}  // namespace pmg

@@ -1,0 +1,471 @@
+// Degree-independent kernels: FP64 CG vector algebra with device-resident
+// scalars (deterministic two-pass reductions: fixed grid, fixed summation
+// order), precision casts, the dense coarse-level solve, and the set-up
+// kernels for the deformed geometry (quadrature-point tensors G_q, operator
+// diagonals), the manufactured right-hand side and the L2 error.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vec.h"
+
+namespace pmg {
+
+std::atomic<int64_t> g_launches{0};
+
+static inline int grid_for(int64_t work, int block, int cap = 152 * 8) {
+  int64_t g = (work + block - 1) / block;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of v into out (thread 0 writes). blockDim.x == 256.
+__device__ __forceinline__ void block_store_sum(double v, double* out) {
+  __shared__ double ws[8];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < 8 ? ws[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) *out = t;
+  }
+}
+
+// partial[b] = sum over this block's grid-stride slice of x*y
+__global__ void __launch_bounds__(256) dot_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                          int64_t n, double* __restrict__ partial) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  block_store_sum(s, partial + blockIdx.x);
+}
+
+// out = sum of nb partials, in a fixed order (one block)
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restrict__ partial, int nb,
+                                                           double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+  block_store_sum(s, out);
+}
+
+cudaError_t dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st) {
+  dot_partial_kernel<<<kDotBlocks, 256, 0, st>>>(x, y, n, partial);
+  sum_partials_kernel<<<1, 256, 0, st>>>(partial, kDotBlocks, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// x += alpha p, r -= alpha Ap with alpha = s[num] / s[den]; partial sums of
+// r.r for the updated r.
+__global__ void __launch_bounds__(256) cg_xr_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                    const double* __restrict__ p, const double* __restrict__ Ap,
+                                                    int64_t n, const double* __restrict__ s, int num, int den,
+                                                    double* __restrict__ partial) {
+  const double alpha = s[num] / s[den];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * Ap[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  block_store_sum(acc, partial + blockIdx.x);
+}
+
+cudaError_t cg_update_xr(double* x, double* r, const double* p, const double* Ap, int64_t n, const double* s,
+                         int num, int den, double* partial, double* rr_out, cudaStream_t st) {
+  cg_xr_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, Ap, n, s, num, den, partial);
+  sum_partials_kernel<<<1, 256, 0, st>>>(partial, kDotBlocks, rr_out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// p = z + beta p with beta = s[num] / s[den] (beta = 0 if first); then s[den] = s[num]
+__global__ void __launch_bounds__(256) cg_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                                                   const double* __restrict__ s, int num, int den, int first) {
+  const double beta = first ? 0.0 : s[num] / s[den];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void copy_scalar_kernel(double* s, int dst, int src) { s[dst] = s[src]; }
+
+cudaError_t cg_update_p(double* p, const double* z, int64_t n, double* s, int num, int den, int first,
+                        cudaStream_t st) {
+  cg_p_kernel<<<grid_for(n, 256), 256, 0, st>>>(p, z, n, s, num, den, first);
+  copy_scalar_kernel<<<1, 1, 0, st>>>(s, den, num);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// Flexible (Polak-Ribiere) variant: s[num] = r.z_new - r_old.z_new computed
+// by the caller; identical structure.
+
+// ------------------------------------------------------------ casts
+__global__ void d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f2d_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+cudaError_t cast_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
+  d2f_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, b, n);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+cudaError_t cast_f2d(const float* a, double* b, int64_t n, cudaStream_t st) {
+  f2d_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, b, n);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ coarse solve
+// u[idx[i]] = sum_j Ainv[i][j] b[idx[j]]; one warp per row; boundary of u
+// must be zero (caller clears u).
+template <typename T>
+__global__ void coarse_kernel(const T* __restrict__ Ainv, const int* __restrict__ idx, int nc, const T* __restrict__ b,
+                              T* __restrict__ u) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;
+  T s = T(0);
+  for (int j = lane; j < nc; j += 32) s += Ainv[(int64_t)warp * nc + j] * b[idx[j]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) u[idx[warp]] = s;
+}
+
+cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, const void* b, void* u, int64_t N,
+                         cudaStream_t st) {
+  const size_t es = prec == 0 ? 8 : 4;
+  cudaError_t e = cudaMemsetAsync(u, 0, es * (size_t)N, st);
+  if (e != cudaSuccess) return e;
+  if (nc == 0) return cudaSuccess;
+  const int blocks = (nc * 32 + 255) / 256;
+  if (prec == 0) coarse_kernel<double><<<blocks, 256, 0, st>>>((const double*)Ainv, idx, nc, (const double*)b, (double*)u);
+  else coarse_kernel<float><<<blocks, 256, 0, st>>>((const float*)Ainv, idx, nc, (const float*)b, (float*)u);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ geometry
+// Deformation F(X) = X + a prod_m sin(2 pi X_m) (1, ..., 1) and
+// dF_i/dX_j = delta_ij + a 2 pi cos(2 pi X_j) prod_{m != j} sin(2 pi X_m).
+__device__ void map_point(int dim, double a, const double* X, double* x, double J[3][3]) {
+  const double tp = 6.283185307179586476925286766559;
+  double s[3], c[3];
+  for (int m = 0; m < dim; ++m) {
+    sincos(tp * X[m], &s[m], &c[m]);
+  }
+  double prod = 1.0;
+  for (int m = 0; m < dim; ++m) prod *= s[m];
+  for (int i = 0; i < dim; ++i) x[i] = X[i] + a * prod;
+  for (int j = 0; j < dim; ++j) {
+    double o = 1.0;
+    for (int m = 0; m < dim; ++m)
+      if (m != j) o *= s[m];
+    const double dj = a * tp * c[j] * o;
+    for (int i = 0; i < dim; ++i) J[i][j] = (i == j ? 1.0 : 0.0) + dj;
+  }
+}
+
+// G[cell][comp][q] = w_q det J J^{-1} J^{-T} with J = dF/dX h, rounded to float.
+__global__ void geometry_kernel(int dim, int n, int p, double amp, QuadTab tab, float* __restrict__ G) {
+  const int nq = p + 1;
+  const int NP = dim == 3 ? nq * nq * nq : nq * nq;
+  const int nc = dim == 3 ? 6 : 3;
+  const int64_t ncell = dim == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const double h = 1.0 / n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncell * NP;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % NP);
+    const int64_t cell = t / NP;
+    const int cidx[3] = {(int)(cell % n), (int)((cell / n) % n), dim == 3 ? (int)(cell / ((int64_t)n * n)) : 0};
+    const int qi[3] = {q % nq, (q / nq) % nq, dim == 3 ? q / (nq * nq) : 0};
+    double X[3], x[3], J[3][3];
+    double w = 1.0;
+    for (int m = 0; m < dim; ++m) {
+      X[m] = h * (cidx[m] + tab.x[qi[m]]);
+      w *= tab.w[qi[m]];
+    }
+    map_point(dim, amp, X, x, J);
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j) J[i][j] *= h;
+    double Gq[3][3];
+    if (dim == 3) {
+      const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      double inv[3][3];
+      inv[0][0] = c00 / det;
+      inv[1][0] = c01 / det;
+      inv[2][0] = c02 / det;
+      inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+      inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+      inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+      inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+      inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+      inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+          double s = 0.0;
+          for (int j = 0; j < 3; ++j) s += inv[i][j] * inv[k][j];
+          Gq[i][k] = w * det * s;
+        }
+    } else {
+      const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      double inv[2][2];
+      inv[0][0] = J[1][1] / det;
+      inv[0][1] = -J[0][1] / det;
+      inv[1][0] = -J[1][0] / det;
+      inv[1][1] = J[0][0] / det;
+      for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 2; ++k) Gq[i][k] = w * det * (inv[i][0] * inv[k][0] + inv[i][1] * inv[k][1]);
+    }
+    float* Gc = G + cell * nc * NP;
+    if (dim == 3) {
+      Gc[0 * NP + q] = (float)Gq[0][0];
+      Gc[1 * NP + q] = (float)Gq[0][1];
+      Gc[2 * NP + q] = (float)Gq[0][2];
+      Gc[3 * NP + q] = (float)Gq[1][1];
+      Gc[4 * NP + q] = (float)Gq[1][2];
+      Gc[5 * NP + q] = (float)Gq[2][2];
+    } else {
+      Gc[0 * NP + q] = (float)Gq[0][0];
+      Gc[1 * NP + q] = (float)Gq[0][1];
+      Gc[2 * NP + q] = (float)Gq[1][1];
+    }
+  }
+}
+
+cudaError_t compute_geometry(int dim, int n, int p, double amp, const QuadTab& tab, float* G, cudaStream_t st) {
+  const int nq = p + 1;
+  const int64_t work = (dim == 3 ? (int64_t)n * n * n * nq * nq * nq : (int64_t)n * n * nq * nq);
+  geometry_kernel<<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, amp, tab, G);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// Diagonal of the degree-p operator, one parity colour of cells:
+// diag[node] += sum_q grad phi_a^T G_q grad phi_a.
+__global__ void diag_kernel(int dim, int n, int p, QuadTab tab, const float* __restrict__ G, double* __restrict__ diag,
+                            int colour) {
+  const int n1 = p + 1;
+  const int NP = dim == 3 ? n1 * n1 * n1 : n1 * n1;
+  const int nc = dim == 3 ? 6 : 3;
+  const int cx = (colour & 1) ? n / 2 : (n + 1) / 2, cy = ((colour >> 1) & 1) ? n / 2 : (n + 1) / 2;
+  const int cz = dim == 3 ? (((colour >> 2) & 1) ? n / 2 : (n + 1) / 2) : 1;
+  const int64_t ncell = (int64_t)cx * cy * cz;
+  const int N1 = p * n + 1;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncell * NP;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t % NP);
+    int64_t ci = t / NP;
+    const int c0 = 2 * (int)(ci % cx) + (colour & 1);
+    ci /= cx;
+    const int c1 = 2 * (int)(ci % cy) + ((colour >> 1) & 1);
+    ci /= cy;
+    const int c2 = dim == 3 ? 2 * (int)ci + ((colour >> 2) & 1) : 0;
+    const int64_t cell = c0 + (int64_t)n * (c1 + (int64_t)n * c2);
+    const int ai[3] = {a % n1, (a / n1) % n1, dim == 3 ? a / (n1 * n1) : 0};
+    const float* Gc = G + cell * nc * NP;
+    double s = 0.0;
+    for (int q = 0; q < NP; ++q) {
+      const int qi[3] = {q % n1, (q / n1) % n1, dim == 3 ? q / (n1 * n1) : 0};
+      double gr[3];
+      for (int d = 0; d < dim; ++d) {
+        double v = 1.0;
+        for (int e = 0; e < dim; ++e) v *= (d == e ? tab.D[qi[e] * 12 + ai[e]] : tab.V[qi[e] * 12 + ai[e]]);
+        gr[d] = v;
+      }
+      if (dim == 3) {
+        s += gr[0] * ((double)Gc[0 * NP + q] * gr[0] + (double)Gc[1 * NP + q] * gr[1] + (double)Gc[2 * NP + q] * gr[2]);
+        s += gr[1] * ((double)Gc[1 * NP + q] * gr[0] + (double)Gc[3 * NP + q] * gr[1] + (double)Gc[4 * NP + q] * gr[2]);
+        s += gr[2] * ((double)Gc[2 * NP + q] * gr[0] + (double)Gc[4 * NP + q] * gr[1] + (double)Gc[5 * NP + q] * gr[2]);
+      } else {
+        s += gr[0] * ((double)Gc[0 * NP + q] * gr[0] + (double)Gc[1 * NP + q] * gr[1]);
+        s += gr[1] * ((double)Gc[1 * NP + q] * gr[0] + (double)Gc[2 * NP + q] * gr[1]);
+      }
+    }
+    const int gx = p * c0 + ai[0], gy = p * c1 + ai[1], gz = p * c2 + ai[2];
+    diag[gx + (int64_t)N1 * (gy + (int64_t)N1 * gz)] += s;
+  }
+}
+
+// inv = 1/diag on free nodes, 0 on the boundary (precision of inv: prec)
+__global__ void invert_kernel(const double* __restrict__ diag, void* inv, int prec, int dim, int N1) {
+  const int64_t N = dim == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % N1), y = (int)((t / N1) % N1), z = dim == 3 ? (int)(t / ((int64_t)N1 * N1)) : 1;
+    const bool bnd = x == 0 || x == N1 - 1 || y == 0 || y == N1 - 1 || (dim == 3 && (z == 0 || z == N1 - 1));
+    const double v = bnd ? 0.0 : 1.0 / diag[t];
+    if (prec == 0) ((double*)inv)[t] = v;
+    else ((float*)inv)[t] = (float)v;
+  }
+}
+
+cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
+                                     void* inv, int prec, cudaStream_t st) {
+  const int N1 = p * n + 1;
+  const int64_t N = dim == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
+  cudaError_t e = cudaMemsetAsync(diag_tmp, 0, sizeof(double) * N, st);
+  if (e != cudaSuccess) return e;
+  const int NP = dim == 3 ? (p + 1) * (p + 1) * (p + 1) : (p + 1) * (p + 1);
+  for (int colour = 0; colour < (1 << dim); ++colour) {
+    const int64_t work = (dim == 3 ? (int64_t)n * n * n : (int64_t)n * n) / (1 << dim) * NP + NP * 8;
+    diag_kernel<<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, p, tab, G, diag_tmp, colour);
+    g_launches += 1;
+  }
+  invert_kernel<<<grid_for(N, 256), 256, 0, st>>>(diag_tmp, inv, prec, dim, N1);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ RHS, L2 error
+// b_a += sum_q f(F(X_q)) phi_a(xi_q) w_q det J_q  for one colour of cells
+__global__ void rhs_kernel(int dim, int n, int K, double amp, int deformed, QuadTab tab, double* __restrict__ b,
+                           int colour) {
+  const int n1 = K + 1;
+  const int NP = dim == 3 ? n1 * n1 * n1 : n1 * n1;
+  const int nq = tab.nq;
+  const int NQ = dim == 3 ? nq * nq * nq : nq * nq;
+  const int cx = (colour & 1) ? n / 2 : (n + 1) / 2, cy = ((colour >> 1) & 1) ? n / 2 : (n + 1) / 2;
+  const int cz = dim == 3 ? (((colour >> 2) & 1) ? n / 2 : (n + 1) / 2) : 1;
+  const int64_t ncell = (int64_t)cx * cy * cz;
+  const int N1 = K * n + 1;
+  const double h = 1.0 / n;
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncell * NP;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t % NP);
+    int64_t ci = t / NP;
+    const int c[3] = {0, 0, 0};
+    int cc[3];
+    cc[0] = 2 * (int)(ci % cx) + (colour & 1);
+    ci /= cx;
+    cc[1] = 2 * (int)(ci % cy) + ((colour >> 1) & 1);
+    ci /= cy;
+    cc[2] = dim == 3 ? 2 * (int)ci + ((colour >> 2) & 1) : 0;
+    (void)c;
+    const int ai[3] = {a % n1, (a / n1) % n1, dim == 3 ? a / (n1 * n1) : 0};
+    double s = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      const int qi[3] = {q % nq, (q / nq) % nq, dim == 3 ? q / (nq * nq) : 0};
+      double X[3], x[3], J[3][3], w = 1.0, phi = 1.0;
+      for (int m = 0; m < dim; ++m) {
+        X[m] = h * (cc[m] + tab.x[qi[m]]);
+        w *= tab.w[qi[m]];
+        phi *= tab.V[qi[m] * 12 + ai[m]];
+      }
+      double det;
+      if (deformed) {
+        map_point(dim, amp, X, x, J);
+        if (dim == 3)
+          det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        else
+          det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      } else {
+        for (int m = 0; m < dim; ++m) x[m] = X[m];
+        det = 1.0;
+      }
+      for (int m = 0; m < dim; ++m) det *= h;
+      double f = dim * pi * pi;
+      for (int m = 0; m < dim; ++m) f *= sin(pi * x[m]);
+      s += f * phi * w * det;
+    }
+    const int gx = K * cc[0] + ai[0], gy = K * cc[1] + ai[1], gz = K * cc[2] + ai[2];
+    const bool bnd = gx == 0 || gx == N1 - 1 || gy == 0 || gy == N1 - 1 || (dim == 3 && (gz == 0 || gz == N1 - 1));
+    if (!bnd) b[gx + (int64_t)N1 * (gy + (int64_t)N1 * gz)] += s;
+  }
+}
+
+cudaError_t rhs_manufactured(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, double* b,
+                             cudaStream_t st) {
+  const int N1 = K * n + 1;
+  const int64_t N = dim == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
+  cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * N, st);
+  if (e != cudaSuccess) return e;
+  const int NP = dim == 3 ? (K + 1) * (K + 1) * (K + 1) : (K + 1) * (K + 1);
+  for (int colour = 0; colour < (1 << dim); ++colour) {
+    const int64_t work = (dim == 3 ? (int64_t)n * n * n : (int64_t)n * n) / (1 << dim) * NP + NP * 8;
+    rhs_kernel<<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, K, amp, deformed, tab, b, colour);
+    g_launches += 1;
+  }
+  return cudaGetLastError();
+}
+
+// per-block partial of sum over cells of sum_q (u_h - u)^2 w det J
+__global__ void __launch_bounds__(256) l2err_kernel(int dim, int n, int K, double amp, int deformed, QuadTab tab,
+                                                    const double* __restrict__ xv, double* __restrict__ partial) {
+  const int n1 = K + 1;
+  const int nq = tab.nq;
+  const int NQ = dim == 3 ? nq * nq * nq : nq * nq;
+  const int64_t ncell = dim == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const int N1 = K * n + 1;
+  const double h = 1.0 / n;
+  const double pi = 3.141592653589793238462643383279502884;
+  double acc = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncell * NQ;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % NQ);
+    const int64_t cell = t / NQ;
+    const int cc[3] = {(int)(cell % n), (int)((cell / n) % n), dim == 3 ? (int)(cell / ((int64_t)n * n)) : 0};
+    const int qi[3] = {q % nq, (q / nq) % nq, dim == 3 ? q / (nq * nq) : 0};
+    double X[3], x[3], J[3][3], w = 1.0;
+    for (int m = 0; m < dim; ++m) {
+      X[m] = h * (cc[m] + tab.x[qi[m]]);
+      w *= tab.w[qi[m]];
+    }
+    double det;
+    if (deformed) {
+      map_point(dim, amp, X, x, J);
+      if (dim == 3)
+        det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      else
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    } else {
+      for (int m = 0; m < dim; ++m) x[m] = X[m];
+      det = 1.0;
+    }
+    for (int m = 0; m < dim; ++m) det *= h;
+    double uh = 0.0;
+    const int NPn = dim == 3 ? n1 * n1 * n1 : n1 * n1;
+    for (int a = 0; a < NPn; ++a) {
+      const int ai[3] = {a % n1, (a / n1) % n1, dim == 3 ? a / (n1 * n1) : 0};
+      double phi = 1.0;
+      for (int m = 0; m < dim; ++m) phi *= tab.V[qi[m] * 12 + ai[m]];
+      const int gx = K * cc[0] + ai[0], gy = K * cc[1] + ai[1], gz = K * cc[2] + ai[2];
+      const bool bnd = gx == 0 || gx == N1 - 1 || gy == 0 || gy == N1 - 1 || (dim == 3 && (gz == 0 || gz == N1 - 1));
+      if (!bnd) uh += phi * xv[gx + (int64_t)N1 * (gy + (int64_t)N1 * gz)];
+    }
+    double u = 1.0;
+    for (int m = 0; m < dim; ++m) u *= sin(pi * x[m]);
+    acc += (uh - u) * (uh - u) * w * det;
+  }
+  block_store_sum(acc, partial + blockIdx.x);
+}
+
+cudaError_t l2_error_partials(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, const double* x,
+                              double* partial, double* out, cudaStream_t st) {
+  l2err_kernel<<<kDotBlocks, 256, 0, st>>>(dim, n, K, amp, deformed, tab, x, partial);
+  sum_partials_kernel<<<1, 256, 0, st>>>(partial, kDotBlocks, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace pmg

@@ -1,0 +1,42 @@
+// Degree-independent device routines (vec.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+namespace pmg {
+
+// Process-wide count of kernel launches enqueued by the library.
+extern std::atomic<int64_t> g_launches;
+
+constexpr int kDotBlocks = 304;  // fixed reduction grid: 2 x 152 SMs
+
+// 1D tables passed by value to set-up kernels: nq points x[q], weights w[q],
+// GLL basis values V[q*12 + a] and derivatives D[q*12 + a] at the points.
+struct QuadTab {
+  double x[12];
+  double w[12];
+  double V[12 * 12];
+  double D[12 * 12];
+  int nq;
+};
+
+cudaError_t dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st);
+cudaError_t cg_update_xr(double* x, double* r, const double* p, const double* Ap, int64_t n, const double* s,
+                         int num, int den, double* partial, double* rr_out, cudaStream_t st);
+cudaError_t cg_update_p(double* p, const double* z, int64_t n, double* s, int num, int den, int first,
+                        cudaStream_t st);
+cudaError_t cast_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
+cudaError_t cast_f2d(const float* a, double* b, int64_t n, cudaStream_t st);
+cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, const void* b, void* u, int64_t N,
+                         cudaStream_t st);
+cudaError_t compute_geometry(int dim, int n, int p, double amp, const QuadTab& tab, float* G, cudaStream_t st);
+cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
+                                     void* inv, int prec, cudaStream_t st);
+cudaError_t rhs_manufactured(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, double* b,
+                             cudaStream_t st);
+cudaError_t l2_error_partials(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, const double* x,
+                              double* partial, double* out, cudaStream_t st);
+
+}  // namespace pmg

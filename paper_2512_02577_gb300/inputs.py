@@ -1,0 +1,45 @@
+"""Seeded synthetic inputs shared by the tests and the benchmark.
+
+Holds none of the method's arithmetic: only random vectors on the nodal
+grid (standard normal on the free nodes, zero on the boundary, the i.i.d.
+N(0,1) right-hand sides of the degree-sweep and serving workloads) and the
+serving workload recipe (Poisson arrivals, log-uniform mesh sizes, uniform
+degrees).  The same vector is handed to the oracle and to the library.
+"""
+import numpy as np
+
+
+def interior_mask(dim, n, k):
+    n1 = k * n + 1
+    g = np.arange(n1)
+    m1 = (g > 0) & (g < n1 - 1)
+    m = m1
+    for _ in range(dim - 1):
+        m = np.multiply.outer(m1, m)
+    return m.reshape(-1)
+
+
+def random_vector(dim, n, k, seed):
+    """N(0,1) on the free nodes of the (k n + 1)^dim grid, 0 on the boundary
+    (numpy default_rng(seed), PCG64)."""
+    rng = np.random.default_rng(seed)
+    m = interior_mask(dim, n, k)
+    v = np.zeros(m.size)
+    v[m] = rng.standard_normal(int(m.sum()))
+    return v
+
+
+def serving_requests(n_requests=256, rate=50.0, arrival_seed=7, size_seed=11, rhs_seed0=1000,
+                     n_lo=8, n_hi=64, k_lo=2, k_hi=7):
+    """Serving workload: Poisson arrivals at ``rate`` per second; cells per
+    side log-uniform in [n_lo, n_hi] snapped in log space to a power of two
+    (so every mesh coarsens to one cell); degree uniform in k_lo..k_hi."""
+    ra = np.random.default_rng(arrival_seed)
+    rs = np.random.default_rng(size_seed)
+    gaps = ra.exponential(1.0 / rate, n_requests)
+    t = np.cumsum(gaps) - gaps[0]
+    logn = rs.uniform(np.log2(n_lo), np.log2(n_hi), n_requests)
+    ns = (2 ** np.round(logn)).astype(int)
+    ks = rs.integers(k_lo, k_hi + 1, n_requests)
+    return [dict(id=i, t_arrival=float(t[i]), n=int(ns[i]), k=int(ks[i]), rhs_seed=rhs_seed0 + i)
+            for i in range(n_requests)]

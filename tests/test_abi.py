@@ -1,0 +1,62 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/pmg.h, and validates configurations on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2512_02577_gb300 as p
+from tests.conftest import ROOT
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pmg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = p.load_library()
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(p.EXPORTED) == names
+
+
+def test_status_strings():
+    lib = p.load_library()
+    assert lib.pmg_status_string(0) == b"ok"
+    assert lib.pmg_status_string(p.PMG_ERR_UNSUPPORTED) == b"unsupported configuration"
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(degree=9), p.PMG_ERR_UNSUPPORTED),
+    (dict(degree=0), p.PMG_ERR_UNSUPPORTED),
+    (dict(dim=4), p.PMG_ERR_UNSUPPORTED),
+    (dict(n_cells=0), p.PMG_ERR_ARG),
+    (dict(n_cells=12, n_levels=4), p.PMG_ERR_UNSUPPORTED),   # 12 not divisible by 8
+    (dict(n_cells=5, degree=8), p.PMG_ERR_UNSUPPORTED),      # coarse (39)^3 > 4096
+    (dict(local_cycles=0), p.PMG_ERR_ARG),
+])
+def test_bytes_required_rejects(kw, code):
+    with pytest.raises(p.PmgError) as e:
+        p.bytes_required(p.make_config(**kw))
+    assert e.value.code == code
+
+
+def test_bytes_required_grows_with_size():
+    small = p.bytes_required(p.make_config(dim=3, n_cells=8, degree=2))
+    big = p.bytes_required(p.make_config(dim=3, n_cells=16, degree=2))
+    assert 6 * small < big < 10 * small
+    fp32 = p.bytes_required(p.make_config(dim=3, n_cells=16, degree=2, mg_precision=p.FP32))
+    assert fp32 > big  # FP32 MG keeps FP64 outer vectors and adds FP32 scratch
+    # 3D n=32 Q4 (2.1M DoFs): a few hundred MB
+    assert 1e8 < p.bytes_required(p.make_config(dim=3, n_cells=32, degree=4)) < 1e9
+
+
+def test_create_null_out_is_rejected():
+    lib = p.load_library()
+    cfg = p.make_config()
+    assert lib.pmg_create(ctypes.byref(cfg), None, None, 0, None) == p.PMG_ERR_ARG
