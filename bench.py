@@ -1,0 +1,390 @@
+"""Benchmark: 3D Poisson, unit cube, 32^3 hexes, Q4 (2,146,689 DoFs), FP64.
+
+One step = one pass of the whole hot path on the resident problem:
+  operator apply (FP64) + one additive vertex-patch sweep with the local
+  p-multigrid solver (FP64) + a full PCG solve with the geometric V-cycle
+  preconditioner to ||r|| <= 1e-8 ||b|| (FP64 throughout, manufactured RHS).
+value = DoFs / step time (whole job, summed over ranks).  L2 is flushed
+between timed steps (a 512 MB write outside the timed events).
+
+Also reported: apply and sweep throughput, FP64 and mixed (FP32 V-cycle)
+solve times p50/p99, the roofline of the dominant kernel (the patch
+smoother, FP64-ALU bound), the CPU oracle on a bounded sample, the
+end-to-end number through the host-buffer C-ABI calls, and SM clocks.
+
+--impl reference times the CPU oracle (the reference arm of this build).
+Multi-GPU: replicas only (one independent problem per rank, no collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "3D unit cube, 32^3 hexes, Q4 (2,146,689 DoFs), FP64: apply + patch sweep + PCG/GMG solve to 1e-8"
+METRIC = "DoFs/s of operator apply + patch smoother; solve time to 1e-8 residual, FP32-MG vs FP64; p50/p99"
+D, NCELL, K = 3, 32, 4
+ORACLE_N = 4          # bounded CPU sample: same degree and dimension, 4^3 cells (4,913 DoFs)
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (measured 1.255 with a project FMA probe)
+FP32_PEAK_TFLOPS = 78.5  # measured FP32 FMA (128 lanes x 152 SMs x 2 x ~2.0 GHz)
+
+
+# ----------------------------------------------------------------- flop model
+def pnz(p, q, i, j):
+    side = lambda pp, ii: 0 if ii < pp - 1 else (1 if ii == pp - 1 else 2)
+    a, b = side(p, i), side(q, j)
+    return not ((a == 0 and b == 2) or (a == 2 and b == 0))
+
+
+def p_hierarchy(k):
+    lv, p = [], 1
+    while p < k:
+        lv.append(p)
+        p = 2 * p + 1
+    return lv + [k]
+
+
+def patch_flops(d, k, n_iter=1):
+    """Floating-point operations of one Cartesian patch solve as executed by
+    the patch kernel: gather, full p-multigrid V-cycle (two patch vmults per
+    level), scatter.  Counts an FMA as 2."""
+    levels = p_hierarchy(k)
+
+    def vmult(p):
+        m = 2 * p - 1
+        nnz = sum(pnz(p, p, i, j) for i in range(m) for j in range(m))
+        if d == 3:
+            return m * m * (2 * nnz * 2 + (3 * 2 * nnz + m) + (2 * 2 * nnz + 3 * m))
+        return m * (2 * 2 * nnz + (2 * 2 * nnz + 3 * m))
+
+    def vcycle(l):
+        if l == 0:
+            return 1
+        p = levels[l]
+        m = 2 * p - 1
+        S = m ** d
+        f = 3 * S + vmult(p) + vcycle(l - 1) + 4 * S + vmult(p)
+        pc = levels[l - 1]
+        mc = 2 * pc - 1
+        nnz_t = sum(pnz(p, pc, i, j) for i in range(m) for j in range(mc))
+        lines_r = (m * m + mc * m + mc * mc) if d == 3 else (m + mc)
+        f += 2 * 2 * nnz_t * lines_r + S  # restriction + prolongation (+ add)
+        return f
+
+    top = len(levels) - 1
+    m = 2 * k - 1
+    f = vcycle(top) * n_iter + (n_iter - 1) * (vmult(k) + m ** d)
+    return f + 2 * m ** d  # scatter u += omega d
+
+
+def apply_flops_per_dof(d, k):
+    """Cartesian apply: each 1D matrix costs (K+1) FMAs per output plus
+    (K+1) more at the cell vertex; 7 matrix applications in 3D (4 in 2D)."""
+    per_seg = 2 * (k + 1) * k + 2 * (k + 1)
+    mats = 7 if d == 3 else 4
+    return mats * per_seg / k
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0],
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self._proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_child(seconds):
+    """Runs in a fresh single-threaded process: time the oracle's step
+    (apply + sweep + PCG solve) on the bounded sample, set-up excluded."""
+    import numpy as np
+    from oracle import constants, fem, solver
+    m = fem.Mesh(D, ORACLE_N, K)
+    L, nn = 1, ORACLE_N
+    while nn % 2 == 0:
+        nn //= 2
+        L += 1
+    h = solver.Hierarchy(m, L, constants.omega_jacobi(D, K), constants.omega_patch(D))
+    b = fem.rhs_manufactured(m)[m.interior_index()]
+    fine = h.levels[-1]
+    times = []
+    t_end = time.time() + seconds
+    while time.time() < t_end or len(times) < 3:
+        t0 = time.perf_counter()
+        fine.A @ b
+        fine.smooth(b, np.zeros_like(b))
+        x, it, hist = solver.solve(h, b)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"dofs": m.n_dofs, "times": times, "iterations": it}))
+
+
+def run_oracle(seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(seconds)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle child failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(res):
+    t = statistics.median(res["times"])
+    return {"value": res["dofs"] / t, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
+            "sample": "same step (apply + sweep + PCG/GMG solve to 1e-8, FP64, Q4, 3D, manufactured RHS) on "
+                      "4^3 cells (%d DoFs), set-up excluded, median of %d steps, single thread"
+                      % (res["dofs"], len(res["times"]))}
+
+
+# ----------------------------------------------------------------- main
+def pct(xs, q):
+    xs = sorted(xs)
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--oracle-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-child", type=float, default=None)
+    args = ap.parse_args()
+    if args.oracle_child is not None:
+        oracle_child(args.oracle_child)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        res = run_oracle(max(args.oracle_seconds, 1.0) * (args.steps + args.warmup) / max(args.steps, 1))
+        times = res["times"][args.warmup:] or res["times"]
+        t = statistics.median(times)
+        value = res["dofs"] / t
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": args.gpus,
+                "steps": len(times), "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "sample": "4^3 cells of the same workload (%d DoFs)" % res["dofs"]},
+                "cpu_baseline": dict(cpu_baseline_entry(res), value=value),
+                "e2e": {"value": value, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_2512_02577_gb300 as p
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    # CPU baseline before any GPU work of this process's children
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(run_oracle(args.oracle_seconds))
+
+    stream = torch.cuda.Stream(device=dev)
+    cfg = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP64)
+    cfg32 = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32)
+    with torch.cuda.stream(stream):
+        ctx = p.Context(cfg, stream=stream, device=dev)
+        ctx32 = p.Context(cfg32, stream=stream, device=dev)
+        N = ctx.num_dofs()
+        b = torch.empty(N, dtype=torch.float64, device=dev)
+        ctx.rhs_manufactured(b)
+        xa = torch.empty_like(b)
+        ctx.rhs_manufactured(xa)
+        ya = torch.empty_like(b)
+        u = torch.empty_like(b)
+        xs = torch.empty_like(b)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+        def step(info_out=None):
+            ctx.apply(xa, ya)
+            u.zero_()
+            ctx.smooth(b, u)
+            info = ctx.solve(b, xs, rtol=1e-8)
+            if info_out is not None:
+                info_out.append(info)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        infos = []
+        clocks = ClockSampler()
+        clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = p.launch_count()
+        torch.cuda.nvtx.range_push("timed_step")
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(infos)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        launches = p.launch_count() - l0
+        if world > 1:
+            torch.distributed.barrier()
+        clocks.stop()
+        step_ms = [a.elapsed_time(z) for a, z in ev]
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms_per_step = total_ms / args.steps
+        value = world * N * args.steps / (total_ms * 1e-3)
+
+        # ---- component timings (not part of value): apply, sweep, residual, solves
+        def timed(fn, reps):
+            for _ in range(2):
+                fn()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return ts
+
+        t_apply = timed(lambda: ctx.apply(xa, ya), 20)
+        t_res = timed(lambda: ctx.residual(b, xa, ya), 20)
+        t_sweep = timed(lambda: ctx.smooth(b, u), 10)
+        solve64 = [i.time_ms for i in infos]
+        it64 = infos[-1].iterations
+        res64 = infos[-1].rel_residual
+        info32 = []
+        for _ in range(2):
+            ctx32.solve(b, xs)
+        for _ in range(max(args.steps, 5)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            info32.append(ctx32.solve(b, xs, rtol=1e-8))
+        l2err = ctx32.l2_error_manufactured(xs)
+        ctx.solve(b, xs)
+        l2err64 = ctx.l2_error_manufactured(xs)
+        solve32 = [i.time_ms for i in info32]
+
+        # roofline of the dominant kernel: one colour launch of the FP64 patch smoother
+        colours = 1 << D
+        sweep_ms = statistics.median(t_sweep)
+        res_ms = statistics.median(t_res)
+        patch_launch_ms = max(sweep_ms - res_ms, 1e-6) / colours
+        n_patches = (NCELL - 1) ** D
+        flops_launch = patch_flops(D, K) * n_patches / colours
+        achieved = flops_launch / (patch_launch_ms * 1e-3) / 1e12
+
+        # ---- end-to-end through the host-buffer C-ABI path
+        pin_b = b.cpu().pin_memory()
+        pin_x = torch.empty(N, dtype=torch.float64).pin_memory()
+        pin_xa = xa.cpu().pin_memory()
+        pin_ya = torch.empty(N, dtype=torch.float64).pin_memory()
+        pin_u = torch.empty(N, dtype=torch.float64).pin_memory()
+        db = torch.empty_like(b)
+
+        def e2e_step():
+            xa.copy_(pin_xa, non_blocking=True)
+            db.copy_(pin_b, non_blocking=True)
+            ctx.apply(xa, ya)
+            u.zero_()
+            ctx.smooth(db, u)
+            ctx.solve_host(pin_b, pin_x, rtol=1e-8)
+            pin_ya.copy_(ya, non_blocking=True)
+            pin_u.copy_(u, non_blocking=True)
+            torch.cuda.synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dofs": N, "l2_flush": "512 MB write between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "smoother": "additive vertex patch",
+                   "local_solver": "full p-multigrid V-cycle", "levels": ctx.n_levels},
+        "gpu_launches": launches,
+        "apply_dofs_per_s": N / (statistics.median(t_apply) * 1e-3),
+        "sweep_dofs_per_s": N / (sweep_ms * 1e-3),
+        "solve_fp64_ms": {"p50": pct(solve64, 50), "p99": pct(solve64, 99), "iterations": it64,
+                          "rel_residual": res64, "l2_error": l2err64},
+        "solve_mixed_ms": {"p50": pct(solve32, 50), "p99": pct(solve32, 99), "iterations": info32[-1].iterations,
+                           "rel_residual": info32[-1].rel_residual, "l2_error": l2err},
+        "mixed_speedup_vs_fp64": pct(solve64, 50) / pct(solve32, 50),
+        "roofline": {"kernel": "patch_cart_kernel<3,double> (one parity colour, 1/8 of the patches)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "flops_per_launch": flops_launch, "launch_ms": patch_launch_ms},
+        "e2e": {"value": N / e2e_s, "unit": "DoFs/s", "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 3 * 8 * N},
+        "clocks": clocks.summary(),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()
