@@ -99,7 +99,7 @@ struct Plan {
     int64_t b, u, r, G[4], dinv[4], dinv1;
   };
   std::vector<LOff> lo;
-  int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv;
+  int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad;
   int64_t dtab_len = 0;
 };
 
@@ -178,6 +178,10 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   P.dtab32 = bump(cur, std::max<int64_t>(P.dtab_len, 1) * 4);
   P.cidx = bump(cur, std::max(P.nc, 1) * 4);
   P.ainv = bump(cur, std::max<int64_t>((int64_t)P.nc * P.nc, 1) * P.mg_es);
+  P.a64 = P.mg32 ? bump(cur, std::max<int64_t>((int64_t)P.nc * P.nc, 1) * 8) : P.ainv;
+  P.gjrow = bump(cur, std::max(P.nc, 1) * 8);
+  P.gjcol = bump(cur, std::max(P.nc, 1) * 8);
+  P.gjbad = bump(cur, 8);
   P.total = cur;
   return PMG_OK;
 }
@@ -207,6 +211,7 @@ struct pmg_ctx {
   float* dtab32 = nullptr;
   int* cidx = nullptr;
   void* ainv = nullptr;
+  bool coarse_ready = false;
   int ppc = 1;
   double omega_as = 0;
   double omega_j[4] = {1, 1, 1, 1};
@@ -329,9 +334,49 @@ int vcycle_level(pmg_ctx* c, int level) {
   return smooth_level(c, level, L.b, L.u, nu);
 }
 
+// Coarsest level, set up before the first V-cycle: assemble A_0 on the free
+// DoFs by applying the FP64 operator to unit vectors (one row per free DoF,
+// A_0 being symmetric), invert it on the device (Gauss-Jordan, SPD so no
+// pivoting), store the inverse in the MG precision.
+int ensure_coarse(pmg_ctx* c) {
+  if (c->coarse_ready) return PMG_OK;
+  LevelData& C = c->lv[0];
+  const int N1 = C.N1;
+  std::vector<int> idx;
+  for (int64_t g = 0; g < C.N; ++g) {
+    const int x = (int)(g % N1), y = (int)((g / N1) % N1), z = c->dim == 3 ? (int)(g / ((int64_t)N1 * N1)) : 1;
+    if (x > 0 && x < N1 - 1 && y > 0 && y < N1 - 1 && (c->dim == 2 || (z > 0 && z < N1 - 1))) idx.push_back((int)g);
+  }
+  const int nc = (int)idx.size();
+  if (nc != c->plan.nc) return fail(PMG_ERR_STATE, "coarse size mismatch");
+  if (nc > 0) {
+    double* A = (double*)at(c, c->plan.a64);
+    double* xd = c->cg_x;  // the level-0 FP64 apply uses t64[0..3]
+    double* yd = c->cg_r;
+    int* bad = (int*)at(c, c->plan.gjbad);
+    PMG_CUDA(cudaMemcpyAsync(c->cidx, idx.data(), 4 * nc, cudaMemcpyHostToDevice, c->stream));
+    PMG_CUDA(cudaMemsetAsync(bad, 0, 4, c->stream));
+    for (int j = 0; j < nc; ++j) {
+      PMG_CUDA(coarse_unit(xd, C.N, idx[j], c->stream));
+      int rc = level_apply(c, 0, PMG_FP64, xd, yd, nullptr);
+      if (rc) return rc;
+      PMG_CUDA(coarse_gather_row(yd, c->cidx, nc, A, j, c->stream));
+    }
+    PMG_CUDA(coarse_invert(A, nc, (double*)at(c, c->plan.gjrow), (double*)at(c, c->plan.gjcol), bad, c->ainv,
+                           c->mgprec, c->stream));
+    int hbad = 0;
+    PMG_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, c->stream));
+    PMG_CUDA(cudaStreamSynchronize(c->stream));
+    if (hbad) return fail(PMG_ERR_STATE, "coarse matrix is not positive definite");
+  }
+  c->coarse_ready = true;
+  return PMG_OK;
+}
+
 // Capture the finest-level V-cycle once as a CUDA graph.
 int ensure_vgraph(pmg_ctx* c) {
   if (c->vgraph) return PMG_OK;
+  if (int rc = ensure_coarse(c)) return rc;
   cudaGraph_t g = nullptr;
   const int64_t before = g_launches.load();
   PMG_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -483,53 +528,6 @@ int setup_context(pmg_ctx* c) {
     c->ppc = ppc;
   }
 
-  // coarsest level: assemble A_0 column by column with the FP64 operator,
-  // invert on the host (Cholesky), store in MG precision
-  {
-    LevelData& C = c->lv[0];
-    const int N1 = C.N1;
-    std::vector<int> idx;
-    for (int64_t g = 0; g < C.N; ++g) {
-      const int x = (int)(g % N1), y = (int)((g / N1) % N1), z = c->dim == 3 ? (int)(g / ((int64_t)N1 * N1)) : 1;
-      if (x > 0 && x < N1 - 1 && y > 0 && y < N1 - 1 && (c->dim == 2 || (z > 0 && z < N1 - 1)))
-        idx.push_back((int)g);
-    }
-    const int nc = (int)idx.size();
-    if (nc != c->plan.nc) return fail(PMG_ERR_STATE, "coarse size mismatch");
-    if (nc > 0) {
-      std::vector<double> A((size_t)nc * nc), col(C.N);
-      double* xd = c->t64[0];
-      double* yd = c->t64[1];
-      // the FP64 apply of level 0 uses t64[0..3] as scratch: use cg vectors for x, y
-      xd = c->cg_x;
-      yd = c->cg_r;
-      const double one = 1.0;
-      for (int j = 0; j < nc; ++j) {
-        PMG_CUDA(cudaMemsetAsync(xd, 0, 8 * C.N, c->stream));
-        PMG_CUDA(cudaMemcpyAsync(xd + idx[j], &one, 8, cudaMemcpyHostToDevice, c->stream));
-        int rc = level_apply(c, 0, PMG_FP64, xd, yd, nullptr);
-        if (rc) return rc;
-        PMG_CUDA(cudaMemcpyAsync(col.data(), yd, 8 * C.N, cudaMemcpyDeviceToHost, c->stream));
-        PMG_CUDA(cudaStreamSynchronize(c->stream));
-        for (int i = 0; i < nc; ++i) A[(size_t)i * nc + j] = col[idx[i]];
-      }
-      for (int i = 0; i < nc; ++i)  // symmetrise the rounding
-        for (int j = 0; j < i; ++j) {
-          const double s = 0.5 * (A[(size_t)i * nc + j] + A[(size_t)j * nc + i]);
-          A[(size_t)i * nc + j] = A[(size_t)j * nc + i] = s;
-        }
-      if (!host::spd_inverse(A, nc)) return fail(PMG_ERR_STATE, "coarse matrix is not positive definite");
-      PMG_CUDA(cudaMemcpyAsync(c->cidx, idx.data(), 4 * nc, cudaMemcpyHostToDevice, c->stream));
-      if (c->mg32) {
-        std::vector<float> Af(A.begin(), A.end());
-        PMG_CUDA(cudaMemcpyAsync(c->ainv, Af.data(), 4 * Af.size(), cudaMemcpyHostToDevice, c->stream));
-        PMG_CUDA(cudaStreamSynchronize(c->stream));
-      } else {
-        PMG_CUDA(cudaMemcpyAsync(c->ainv, A.data(), 8 * A.size(), cudaMemcpyHostToDevice, c->stream));
-        PMG_CUDA(cudaStreamSynchronize(c->stream));
-      }
-    }
-  }
   PMG_CUDA(cudaMallocHost((void**)&c->host_scal, 8 * S_COUNT));
   PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
   PMG_CUDA(cudaEventCreate(&c->ev0));

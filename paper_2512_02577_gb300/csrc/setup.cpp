@@ -1,8 +1,7 @@
 // Host-side numerical set-up of the library (float64 / long double):
 // 1D Gauss-Lobatto nodes and Gauss rules, Lagrange bases, the reference and
 // patch 1D matrices, p-transfers and h-prolongation tables that fill the
-// per-degree coefficient block, the default Jacobi damping per p-level, and a
-// small dense Cholesky inverse for the coarsest mesh level.
+// per-degree coefficient block, and the default Jacobi damping per p-level.
 //
 // The nodal Q_k basis on Gauss-Lobatto points and (k+1)-point Gauss
 // quadrature are the discretisation of the bilinear form of Eq. (3); the
@@ -199,9 +198,9 @@ static double lambda_max_patch(int d, int p) {
     for (int i = 0; i < N; ++i) {
       const int ii = idx(i, axis);
       const int base = i - ii * stride;
-      LD s = 0;
-      for (int j = 0; j < m; ++j) s += LD(C[ii * m + j]) * in[base + j * stride];
-      out[i] = double(s);
+      double s = 0;
+      for (int j = 0; j < m; ++j) s += C[ii * m + j] * in[base + j * stride];
+      out[i] = s;
     }
   };
   auto matvec = [&](const std::vector<double>& x, std::vector<double>& y) {
@@ -344,42 +343,6 @@ void cell_tables(int p, std::vector<double>& S, std::vector<double>& Dq, std::ve
       S[a * (p + 1) + b] = lagrange(np, b, xq[a]);
       Dq[a * (p + 1) + b] = lagrange_deriv(xq, b, xq[a]);
     }
-}
-
-// In-place inverse of a dense SPD matrix (row-major, n x n) by Cholesky.
-// Returns false if the matrix is not positive definite.
-bool spd_inverse(std::vector<double>& A, int n) {
-  std::vector<double> Lm(A.size(), 0.0);
-  for (int j = 0; j < n; ++j) {
-    LD s = A[j * n + j];
-    for (int k = 0; k < j; ++k) s -= LD(Lm[j * n + k]) * Lm[j * n + k];
-    if (s <= 0) return false;
-    const double ljj = double(std::sqrt(s));
-    Lm[j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
-      LD t = A[i * n + j];
-      for (int k = 0; k < j; ++k) t -= LD(Lm[i * n + k]) * Lm[j * n + k];
-      Lm[i * n + j] = double(t / ljj);
-    }
-  }
-  // inverse of L (lower triangular)
-  std::vector<double> Li(A.size(), 0.0);
-  for (int j = 0; j < n; ++j) {
-    Li[j * n + j] = 1.0 / Lm[j * n + j];
-    for (int i = j + 1; i < n; ++i) {
-      LD s = 0;
-      for (int k = j; k < i; ++k) s += LD(Lm[i * n + k]) * Li[k * n + j];
-      Li[i * n + j] = double(-s / Lm[i * n + i]);
-    }
-  }
-  // A^{-1} = L^{-T} L^{-1}
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j) {
-      LD s = 0;
-      for (int k = i; k < n; ++k) s += LD(Li[k * n + i]) * Li[k * n + j];
-      A[i * n + j] = A[j * n + i] = double(s);
-    }
-  return true;
 }
 
 }  // namespace host

@@ -15,7 +15,6 @@ std::vector<double> p_transfer(int q, int p);
 double default_omega_jacobi(int d, int p);
 void fill_coefficients(int K, double* out);
 void cell_tables(int p, std::vector<double>& S, std::vector<double>& Dq, std::vector<double>& W);
-bool spd_inverse(std::vector<double>& A, int n);
 
 }  // namespace host
 }  // namespace pmg

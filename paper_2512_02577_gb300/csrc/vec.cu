@@ -160,6 +160,86 @@ cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, con
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ coarse set-up
+// Dense coarse matrix A_0 on the free DoFs: row j = (A_0 e_j) restricted to
+// the free nodes (A_0 is symmetric), then an in-place Gauss-Jordan inverse.
+__global__ void unit_vector_kernel(double* __restrict__ x, int64_t N, int64_t pos) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = i == pos ? 1.0 : 0.0;
+}
+__global__ void gather_row_kernel(const double* __restrict__ y, const int* __restrict__ idx, int nc,
+                                  double* __restrict__ A, int row) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+    A[(int64_t)row * nc + i] = y[idx[i]];
+}
+__global__ void symmetrize_kernel(double* A, int nc) {
+  const int64_t n2 = (int64_t)nc * nc;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / nc), j = (int)(t % nc);
+    if (j < i) {
+      const double s = 0.5 * (A[(int64_t)i * nc + j] + A[(int64_t)j * nc + i]);
+      A[(int64_t)i * nc + j] = s;
+      A[(int64_t)j * nc + i] = s;
+    }
+  }
+}
+__global__ void gj_pivot_kernel(const double* __restrict__ A, int nc, int p, double* __restrict__ row,
+                                double* __restrict__ col) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    row[i] = A[(int64_t)p * nc + i];
+    col[i] = A[(int64_t)i * nc + p];
+  }
+}
+// sweep of pivot p: a_ij -= c_i r_j / a_pp; a_pj = r_j / a_pp; a_ip = -c_i / a_pp; a_pp = 1 / a_pp
+__global__ void gj_update_kernel(double* __restrict__ A, int nc, int p, const double* __restrict__ row,
+                                 const double* __restrict__ col, int* __restrict__ bad) {
+  const double piv = row[p];
+  if (!(piv > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bad = 1;
+    return;
+  }
+  const double ip = 1.0 / piv;
+  const int64_t n2 = (int64_t)nc * nc;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / nc), j = (int)(t % nc);
+    double v;
+    if (i == p && j == p) v = ip;
+    else if (i == p) v = row[j] * ip;
+    else if (j == p) v = -col[i] * ip;
+    else v = A[t] - col[i] * row[j] * ip;
+    A[t] = v;
+  }
+}
+__global__ void store_inverse_kernel(const double* __restrict__ A, int64_t n2, void* out, int prec) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
+    if (prec == 0) ((double*)out)[t] = A[t];
+    else ((float*)out)[t] = (float)A[t];
+  }
+}
+
+cudaError_t coarse_unit(double* x, int64_t N, int64_t pos, cudaStream_t st) {
+  unit_vector_kernel<<<grid_for(N, 256), 256, 0, st>>>(x, N, pos);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+cudaError_t coarse_gather_row(const double* y, const int* idx, int nc, double* A, int row, cudaStream_t st) {
+  gather_row_kernel<<<grid_for(nc, 256), 256, 0, st>>>(y, idx, nc, A, row);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+cudaError_t coarse_invert(double* A, int nc, double* row, double* col, int* bad, void* out, int prec,
+                          cudaStream_t st) {
+  const int64_t n2 = (int64_t)nc * nc;
+  symmetrize_kernel<<<grid_for(n2, 256), 256, 0, st>>>(A, nc);
+  for (int p = 0; p < nc; ++p) {
+    gj_pivot_kernel<<<grid_for(nc, 256), 256, 0, st>>>(A, nc, p, row, col);
+    gj_update_kernel<<<grid_for(n2, 256), 256, 0, st>>>(A, nc, p, row, col, bad);
+  }
+  store_inverse_kernel<<<grid_for(n2, 256), 256, 0, st>>>(A, n2, out, prec);
+  g_launches += 2 + 2 * (int64_t)nc;
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ geometry
 // Deformation F(X) = X + a prod_m sin(2 pi X_m) (1, ..., 1) and
 // dF_i/dX_j = delta_ij + a 2 pi cos(2 pi X_j) prod_{m != j} sin(2 pi X_m).

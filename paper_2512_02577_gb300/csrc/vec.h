@@ -31,6 +31,13 @@ cudaError_t cast_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
 cudaError_t cast_f2d(const float* a, double* b, int64_t n, cudaStream_t st);
 cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, const void* b, void* u, int64_t N,
                          cudaStream_t st);
+cudaError_t coarse_unit(double* x, int64_t N, int64_t pos, cudaStream_t st);
+cudaError_t coarse_gather_row(const double* y, const int* idx, int nc, double* A, int row, cudaStream_t st);
+// In-place inverse of the dense SPD matrix A (nc x nc, FP64) by Gauss-Jordan
+// sweeps, stored into `out` in precision prec; *bad = 1 if a pivot is not
+// positive.  row, col: nc scratch each.
+cudaError_t coarse_invert(double* A, int nc, double* row, double* col, int* bad, void* out, int prec,
+                          cudaStream_t st);
 cudaError_t compute_geometry(int dim, int n, int p, double amp, const QuadTab& tab, float* G, cudaStream_t st);
 cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
                                      void* inv, int prec, cudaStream_t st);
