@@ -99,7 +99,7 @@ struct Plan {
     int64_t b, u, r, G[4], dinv[4], dinv1;
   };
   std::vector<LOff> lo;
-  int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad;
+  int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad, cx0, cy0;
   int64_t dtab_len = 0;
 };
 
@@ -182,6 +182,9 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   P.gjrow = bump(cur, std::max(P.nc, 1) * 8);
   P.gjcol = bump(cur, std::max(P.nc, 1) * 8);
   P.gjbad = bump(cur, 8);
+  const int64_t N0 = ipow64((int64_t)P.K * P.n0 + 1, P.dim);
+  P.cx0 = bump(cur, N0 * 8);  // unit vectors and operator columns of the coarse set-up
+  P.cy0 = bump(cur, N0 * 8);
   P.total = cur;
   return PMG_OK;
 }
@@ -351,8 +354,8 @@ int ensure_coarse(pmg_ctx* c) {
   if (nc != c->plan.nc) return fail(PMG_ERR_STATE, "coarse size mismatch");
   if (nc > 0) {
     double* A = (double*)at(c, c->plan.a64);
-    double* xd = c->cg_x;  // the level-0 FP64 apply uses t64[0..3]
-    double* yd = c->cg_r;
+    double* xd = (double*)at(c, c->plan.cx0);  // dedicated: the CG vectors may be live here
+    double* yd = (double*)at(c, c->plan.cy0);
     int* bad = (int*)at(c, c->plan.gjbad);
     PMG_CUDA(cudaMemcpyAsync(c->cidx, idx.data(), 4 * nc, cudaMemcpyHostToDevice, c->stream));
     PMG_CUDA(cudaMemsetAsync(bad, 0, 4, c->stream));
