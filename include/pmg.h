@@ -154,6 +154,26 @@ int64_t pmg_launch_count(void);
 const char* pmg_status_string(int status);
 const char* pmg_last_error(void);
 
+/* Largest nodal grid (k n + 1)^d that pmg_apply_cartesian_noalloc accepts. */
+#define PMG_NOALLOC_MAX_DOFS 2097152
+
+/* y = A x for the Cartesian Q_k operator on the unit square/cube with
+ * n_cells per side (FP64, device vectors of (k n + 1)^d entries, the layout
+ * and boundary convention above), enqueued on `stream` (NULL = legacy
+ * default stream), without a context and without allocating device memory.
+ * The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory -- code running inside another framework's memory
+ * pool or under a hard memory cap, and real-time loops where cudaMalloc,
+ * which may synchronise the device, is not allowed.  Its scratch (four grid
+ * vectors) is a file-scope device array of 4 x PMG_NOALLOC_MAX_DOFS doubles
+ * (64 MiB) that every GPU loading the library holds until exit.  The first
+ * call on a device (and the first for each degree) resolves that array's
+ * address and loads the degree's 1D matrices into constant memory, which
+ * synchronises: make it before any stream capture.  All calls share the
+ * array; calls that overlap on the GPU race on it.  Grids above
+ * PMG_NOALLOC_MAX_DOFS are rejected with PMG_ERR_UNSUPPORTED. */
+int pmg_apply_cartesian_noalloc(int dim, int n_cells, int degree, const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

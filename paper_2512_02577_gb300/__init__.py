@@ -30,8 +30,9 @@ EXPORTED = [
     "pmg_config_default", "pmg_bytes_required", "pmg_create", "pmg_destroy", "pmg_num_levels",
     "pmg_num_dofs", "pmg_apply", "pmg_residual", "pmg_smooth", "pmg_vcycle", "pmg_solve",
     "pmg_solve_host", "pmg_rhs_manufactured", "pmg_l2_error_manufactured", "pmg_synchronize",
-    "pmg_launch_count", "pmg_status_string", "pmg_last_error",
+    "pmg_launch_count", "pmg_status_string", "pmg_last_error", "pmg_apply_cartesian_noalloc",
 ]
+NOALLOC_MAX_DOFS = 2097152
 
 
 class PmgError(RuntimeError):
@@ -87,6 +88,7 @@ def load_library(path=LIB_PATH):
         "pmg_launch_count": (i64, []),
         "pmg_status_string": (ctypes.c_char_p, [cint]),
         "pmg_last_error": (ctypes.c_char_p, []),
+        "pmg_apply_cartesian_noalloc": (cint, [cint, cint, cint, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -126,6 +128,16 @@ def bytes_required(cfg):
 
 def launch_count():
     return load_library().pmg_launch_count()
+
+
+def apply_cartesian_noalloc(dim, n_cells, degree, x, y, stream=None):
+    """y = A x (FP64, Cartesian) through the allocation-free entry point, for
+    callers that cannot allocate device memory; see include/pmg.h."""
+    lib = load_library()
+    n = (degree * n_cells + 1) ** dim
+    sh = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(lib.pmg_apply_cartesian_noalloc(dim, n_cells, degree, _ptr(x, torch.float64, n),
+                                           _ptr(y, torch.float64, n), ctypes.c_void_p(sh or None)))
 
 
 def _ptr(t, dtype, n):

@@ -51,8 +51,14 @@ const KernelTable* kernel_table(int K) {
 using namespace pmg;
 
 namespace {
-
 thread_local std::string t_last_error;
+}  // namespace
+
+namespace pmg {
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+}  // namespace pmg
+
+namespace {
 
 int fail(int code, const std::string& msg) {
   t_last_error = msg;
