@@ -151,6 +151,13 @@ int pmg_synchronize(pmg_ctx* ctx);
  * nodes). */
 int64_t pmg_launch_count(void);
 
+/* Patches per thread block the smoother kernels of this context use: the
+ * config's value, or the autotuned one (timed per dimension, degree,
+ * precision, geometry and local cycles on the finest level; cached for the
+ * process and, if the environment variable PMG_TUNE_FILE names a file, in
+ * that file). */
+int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
+
 const char* pmg_status_string(int status);
 const char* pmg_last_error(void);
 

@@ -31,6 +31,7 @@ EXPORTED = [
     "pmg_num_dofs", "pmg_apply", "pmg_residual", "pmg_smooth", "pmg_vcycle", "pmg_solve",
     "pmg_solve_host", "pmg_rhs_manufactured", "pmg_l2_error_manufactured", "pmg_synchronize",
     "pmg_launch_count", "pmg_status_string", "pmg_last_error", "pmg_apply_cartesian_noalloc",
+    "pmg_patches_per_block",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -89,6 +90,7 @@ def load_library(path=LIB_PATH):
         "pmg_status_string": (ctypes.c_char_p, [cint]),
         "pmg_last_error": (ctypes.c_char_p, []),
         "pmg_apply_cartesian_noalloc": (cint, [cint, cint, cint, vp, vp, vp]),
+        "pmg_patches_per_block": (cint, [vp, ctypes.POINTER(cint)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -239,6 +241,11 @@ class Context:
         _check(_lib.pmg_l2_error_manufactured(self.handle, _ptr(x, torch.float64, self.num_dofs()),
                                               ctypes.byref(e)))
         return e.value
+
+    def patches_per_block(self):
+        n = ctypes.c_int()
+        _check(_lib.pmg_patches_per_block(self.handle, ctypes.byref(n)))
+        return n.value
 
     def synchronize(self):
         _check(_lib.pmg_synchronize(self.handle))

@@ -88,10 +88,11 @@ static cudaError_t patch_cart_t(const T* r, T* u, int n, int colour, int ppc, in
   const int cz = DIM == 3 ? (((colour >> 2) & 1) ? n / 2 : (n - 1) / 2) : 1;
   const int64_t np = (int64_t)cx * cy * cz;
   if (np == 0) return cudaSuccess;
+  if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
   const int64_t blocks = (np + ppc - 1) / ppc;
-  const int threads = ppc * S::TPP;
+  const int threads = std::min(1024, (ppc * S::TPP + 31) / 32 * 32);
   const int smem = ppc * patch_smem(DIM, sizeof(T) == 8 ? 0 : 1, n_iter);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
   patch_cart_kernel<DIM, T><<<(unsigned)blocks, threads, smem, st>>>(r, u, n, colour, ppc, n_iter, dinv,
                                                                     to_params<T>(H));
   g_launches += 1;
@@ -164,27 +165,63 @@ static cudaError_t h_restrict(int dim, int prec, const void* rf, void* rc, void*
   return h_restrict_t<2, float>((const float*)rf, (float*)rc, (float*)t0, (float*)t1, nc, s);
 }
 
-// Opt every kernel of this degree into the full shared-memory carve-out
-// (called once per device at context creation, outside any stream capture).
+// Opt every kernel of this degree into the largest dynamic shared memory the
+// device allows next to the kernel's static shared memory (called once per
+// device at context creation, outside any stream capture).
+template <class Kern>
+static cudaError_t allow_smem(Kern k, int optin) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, k);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+}
+
+static int max_threads_of(const void* k) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return a.maxThreadsPerBlock;
+}
+
+static int patch_max_threads(int dim, int prec, int deformed) {
+  if (deformed) {
+    if (prec == 0) return dim == 3 ? max_threads_of((const void*)patch_def_kernel<3, double>)
+                                   : max_threads_of((const void*)patch_def_kernel<2, double>);
+    return dim == 3 ? max_threads_of((const void*)patch_def_kernel<3, float>)
+                    : max_threads_of((const void*)patch_def_kernel<2, float>);
+  }
+  if (prec == 0) return dim == 3 ? max_threads_of((const void*)patch_cart_kernel<3, double>)
+                                 : max_threads_of((const void*)patch_cart_kernel<2, double>);
+  return dim == 3 ? max_threads_of((const void*)patch_cart_kernel<3, float>)
+                  : max_threads_of((const void*)patch_cart_kernel<2, float>);
+}
+
 static cudaError_t prepare() {
-  const int mx = 227 * 1024;
-  cudaFuncSetAttribute(patch_cart_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_cart_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_cart_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_cart_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_def_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_def_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_def_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(patch_def_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<2, 1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<3, 1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<2, -1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<3, -1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<2, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<3, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<2, -1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(def_cell_kernel<3, -1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  return cudaGetLastError();
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaError_t r = cudaSuccess;
+  auto acc = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
+  acc(allow_smem(patch_cart_kernel<2, double>, optin));
+  acc(allow_smem(patch_cart_kernel<3, double>, optin));
+  acc(allow_smem(patch_cart_kernel<2, float>, optin));
+  acc(allow_smem(patch_cart_kernel<3, float>, optin));
+  acc(allow_smem(patch_def_kernel<2, double>, optin));
+  acc(allow_smem(patch_def_kernel<3, double>, optin));
+  acc(allow_smem(patch_def_kernel<2, float>, optin));
+  acc(allow_smem(patch_def_kernel<3, float>, optin));
+  acc(allow_smem(def_cell_kernel<2, 1, double>, optin));
+  acc(allow_smem(def_cell_kernel<3, 1, double>, optin));
+  acc(allow_smem(def_cell_kernel<2, -1, double>, optin));
+  acc(allow_smem(def_cell_kernel<3, -1, double>, optin));
+  acc(allow_smem(def_cell_kernel<2, 1, float>, optin));
+  acc(allow_smem(def_cell_kernel<3, 1, float>, optin));
+  acc(allow_smem(def_cell_kernel<2, -1, float>, optin));
+  acc(allow_smem(def_cell_kernel<3, -1, float>, optin));
+  return r;
 }
 
 }  // namespace PMG_KNS
@@ -204,6 +241,7 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::patch_def,
       PMG_KNS::patch_def_threads,
       PMG_KNS::patch_def_smem,
+      PMG_KNS::patch_max_threads,
   };
   return &t;
 }

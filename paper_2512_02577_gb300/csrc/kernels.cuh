@@ -143,9 +143,12 @@ __global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, cons
 
 // ===========================================================================
 // Vertex-patch smoother with the local p-multigrid solver (§2.1, §2.2, §3).
-// One group of TPP threads per patch; TPP = number of grid lines of the
-// finest patch level, so every 1D contraction step gives each thread at most
-// one line.  All patch vectors live in shared memory:
+// A thread block owns `np` patches, processed in lockstep.  Every step of
+// the local V-cycle is a set of independent 1D line contractions (or
+// element-wise updates); the (patch, line) pairs of all patches of the block
+// are spread over all threads, so warps stay full at every p-level (an idle
+// lane of an active warp still occupies the FP64 pipe; an idle warp does
+// not).  Per-patch shared memory, in elements of T:
 //   [t0 | t1 | r_top | d_top | r_{top-1} | d_{top-1} | ... | r_0 d_0 | (rj | ds)]
 // ===========================================================================
 template <int DIM>
@@ -155,7 +158,7 @@ struct PatchShape {
   static constexpr int MT = mp(K);
   static constexpr int SZ(int l) { return ipow(M(l), DIM); }
   static constexpr int SZT = ipow(MT, DIM);
-  static constexpr int TPP = ipow(MT, DIM - 1);
+  static constexpr int TPP = ipow(MT, DIM - 1);  // lines of a top-level step
   static constexpr int off_r(int l) {
     int o = 2 * SZT;
     for (int j = L - 1; j > l; --j) o += 2 * SZ(j);
@@ -165,15 +168,32 @@ struct PatchShape {
   static constexpr int ELEMS = ((off_r(0) + 2) + 1) / 2 * 2;
 };
 
+constexpr int kMaxPatchesPerBlock = 64;
+
 template <int AX, int EX, int EY, int EZ>
 __device__ __forceinline__ int line_base(int L) {
   if constexpr (AX == 0) return L * EX;
   else if constexpr (AX == 1) return (L % EX) + EX * EY * (L / EX);
   else return L;
 }
-template <int AX, int EX, int EY>
-__host__ __device__ constexpr int line_stride() {
-  return AX == 0 ? 1 : (AX == 1 ? EX : EX * EY);
+
+// Shared memory of the patches of one block.
+template <typename T>
+struct PBlock {
+  T* base;
+  int stride;  // elements per patch
+  int np;      // patches in the block
+  __device__ __forceinline__ T* at(int g) const { return base + g * stride; }
+};
+
+// for every (g, i), g < np, i < COUNT, spread over the block's threads
+template <int COUNT, class F>
+__device__ __forceinline__ void pfor(int np, F&& f) {
+  const int total = np * COUNT;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int g = t / COUNT;
+    f(g, t - g * COUNT);
+  }
 }
 
 // y = C x for a patch matrix of degree p (m x m, row-major), skipping the
@@ -192,325 +212,371 @@ __device__ __forceinline__ void pmv(const T* C, const T* x, T* y) {
 }
 
 // Cartesian patch geometry: A_{j,p} = s sum_dir (KP on dir, MP elsewhere);
-// inverse diagonal from a shared table (scale-free, divided by s).
+// inverse diagonal from a table shared by all patches (scale-free).
 template <int DIM, typename T>
 struct CartGeo {
   const T* dinv;  // concatenated per-level tables, level l at dinv_off(l)
   T scale;
   T inv_scale;
+  T inv_a0;
 
   static constexpr int dinv_off(int l) {
     int o = 0;
     for (int j = 1; j < l; ++j) o += ipow(mp(plev(K, j)), DIM);
     return o;
   }
-  __device__ __forceinline__ T dinv_at(int l, int i) const { return dinv[dinv_off(l) + i] * inv_scale; }
+  __device__ __forceinline__ T dinv_at(int, int l, int i) const { return dinv[dinv_off(l) + i] * inv_scale; }
+  __device__ __forceinline__ T a0inv(int) const { return inv_a0; }
 
-  // out = r - A_l d  (out may alias t0; d, r distinct from t0, t1)
+  // out = r - A_l d for every patch of the block (offsets within a patch;
+  // out may be t0 = offset 0; d and r distinct from t0, t1)
   template <int l>
-  __device__ __forceinline__ void resid(const T* d, const T* r, T* out, T* t0, T* t1, int lane, int tpp) const {
+  __device__ __forceinline__ void resid(const PBlock<T>& pb, int od, int orr, int oo) const {
     constexpr int p = plev(K, l);
     constexpr int m = mp(p);
+    constexpr int SZT = PatchShape<DIM>::SZT;
     const T* MP = coef<T>() + LAY.MP[l];
     const T* KP = coef<T>() + LAY.KP[l];
+    const T s = scale;
     if constexpr (DIM == 3) {
-      for (int L = lane; L < m * m; L += tpp) {
+      pfor<m * m>(pb.np, [&](int g, int L) {
+        T* sm = pb.at(g);
         const int b = line_base<0, m, m, m>(L);
         T x[m], y0[m], y1[m];
 #pragma unroll
-        for (int j = 0; j < m; ++j) x[j] = d[b + j];
+        for (int j = 0; j < m; ++j) x[j] = sm[od + b + j];
         pmv<p>(MP, x, y0);
         pmv<p>(KP, x, y1);
 #pragma unroll
-        for (int i = 0; i < m; ++i) { t0[b + i] = y0[i]; t1[b + i] = y1[i]; }
-      }
+        for (int i = 0; i < m; ++i) { sm[b + i] = y0[i]; sm[SZT + b + i] = y1[i]; }
+      });
       __syncthreads();
-      for (int L = lane; L < m * m; L += tpp) {
+      pfor<m * m>(pb.np, [&](int g, int L) {
+        T* sm = pb.at(g);
         const int b = line_base<1, m, m, m>(L);
         T a[m], c[m], y0[m], y1[m], y2[m];
 #pragma unroll
-        for (int j = 0; j < m; ++j) { a[j] = t0[b + j * m]; c[j] = t1[b + j * m]; }
+        for (int j = 0; j < m; ++j) { a[j] = sm[b + j * m]; c[j] = sm[SZT + b + j * m]; }
         pmv<p>(MP, a, y0);
         pmv<p>(KP, a, y1);
         pmv<p>(MP, c, y2);
 #pragma unroll
-        for (int i = 0; i < m; ++i) { t0[b + i * m] = y0[i]; t1[b + i * m] = y1[i] + y2[i]; }
-      }
+        for (int i = 0; i < m; ++i) { sm[b + i * m] = y0[i]; sm[SZT + b + i * m] = y1[i] + y2[i]; }
+      });
       __syncthreads();
-      for (int L = lane; L < m * m; L += tpp) {
+      pfor<m * m>(pb.np, [&](int g, int L) {
+        T* sm = pb.at(g);
         const int b = line_base<2, m, m, m>(L);
         T a[m], c[m], y1[m], y2[m];
 #pragma unroll
-        for (int j = 0; j < m; ++j) { a[j] = t0[b + j * m * m]; c[j] = t1[b + j * m * m]; }
+        for (int j = 0; j < m; ++j) { a[j] = sm[b + j * m * m]; c[j] = sm[SZT + b + j * m * m]; }
         pmv<p>(KP, a, y1);
         pmv<p>(MP, c, y2);
 #pragma unroll
-        for (int i = 0; i < m; ++i) out[b + i * m * m] = r[b + i * m * m] - scale * (y1[i] + y2[i]);
-      }
+        for (int i = 0; i < m; ++i) sm[oo + b + i * m * m] = sm[orr + b + i * m * m] - s * (y1[i] + y2[i]);
+      });
       __syncthreads();
     } else {
-      for (int L = lane; L < m; L += tpp) {
+      pfor<m>(pb.np, [&](int g, int L) {
+        T* sm = pb.at(g);
         const int b = line_base<0, m, m, 1>(L);
         T x[m], y0[m], y1[m];
 #pragma unroll
-        for (int j = 0; j < m; ++j) x[j] = d[b + j];
+        for (int j = 0; j < m; ++j) x[j] = sm[od + b + j];
         pmv<p>(MP, x, y0);
         pmv<p>(KP, x, y1);
 #pragma unroll
-        for (int i = 0; i < m; ++i) { t0[b + i] = y0[i]; t1[b + i] = y1[i]; }
-      }
+        for (int i = 0; i < m; ++i) { sm[b + i] = y0[i]; sm[SZT + b + i] = y1[i]; }
+      });
       __syncthreads();
-      for (int L = lane; L < m; L += tpp) {
+      pfor<m>(pb.np, [&](int g, int L) {
+        T* sm = pb.at(g);
         const int b = line_base<1, m, m, 1>(L);
         T a[m], c[m], y1[m], y2[m];
 #pragma unroll
-        for (int j = 0; j < m; ++j) { a[j] = t0[b + j * m]; c[j] = t1[b + j * m]; }
+        for (int j = 0; j < m; ++j) { a[j] = sm[b + j * m]; c[j] = sm[SZT + b + j * m]; }
         pmv<p>(KP, a, y1);
         pmv<p>(MP, c, y2);
 #pragma unroll
-        for (int i = 0; i < m; ++i) out[b + i * m] = r[b + i * m] - scale * (y1[i] + y2[i]);
-      }
+        for (int i = 0; i < m; ++i) sm[oo + b + i * m] = sm[orr + b + i * m] - s * (y1[i] + y2[i]);
+      });
       __syncthreads();
     }
   }
 };
 
-// Restriction rc = T_l^T t (t: fine level l in t0; rc: level l-1), using t1.
+// Restriction: level l-1 residual at `dst` = T_l^T (level-l vector in t0),
+// using t1 (and t0 again in 3D) as intermediates.
 template <int DIM, int l, typename T>
-__device__ __forceinline__ void restrict_p(T* t0, T* t1, T* rc, int lane, int tpp) {
+__device__ __forceinline__ void restrict_p(const PBlock<T>& pb, int dst) {
   constexpr int pf = plev(K, l), pc = plev(K, l - 1);
   constexpr int m = mp(pf), mc = mp(pc);
-  const T* Tr = coef<T>() + LAY.Tr[l];  // m x mc, row-major
+  constexpr int SZT = PatchShape<DIM>::SZT;
   constexpr int EZ = DIM == 3 ? m : 1;
-  constexpr int EZC = DIM == 3 ? mc : 1;
-  // x: (m, m, EZ) -> (mc, m, EZ) in t1
-  for (int L = lane; L < m * EZ; L += tpp) {
+  const T* Tr = coef<T>() + LAY.Tr[l];  // m x mc, row-major
+  // x: (m, m, EZ) in t0 -> (mc, m, EZ) in t1
+  pfor<m * EZ>(pb.np, [&](int g, int L) {
+    T* sm = pb.at(g);
     const int bi = line_base<0, m, m, EZ>(L), bo = line_base<0, mc, m, EZ>(L);
     T x[m];
 #pragma unroll
-    for (int j = 0; j < m; ++j) x[j] = t0[bi + j];
+    for (int j = 0; j < m; ++j) x[j] = sm[bi + j];
 #pragma unroll
     for (int i = 0; i < mc; ++i) {
       T acc = T(0);
 #pragma unroll
       for (int j = 0; j < m; ++j)
         if (pnz(pf, pc, j, i)) acc += Tr[j * mc + i] * x[j];
-      t1[bo + i] = acc;
+      sm[SZT + bo + i] = acc;
     }
-  }
+  });
   __syncthreads();
-  // y: (mc, m, EZ) -> (mc, mc, EZ) into t0 (2D: directly into rc)
-  T* ydst = DIM == 3 ? t0 : rc;
-  for (int L = lane; L < mc * EZ; L += tpp) {
+  // y: (mc, m, EZ) in t1 -> (mc, mc, EZ) in t0 (2D: directly into dst)
+  const int ydst = DIM == 3 ? 0 : dst;
+  pfor<mc * EZ>(pb.np, [&](int g, int L) {
+    T* sm = pb.at(g);
     const int bi = line_base<1, mc, m, EZ>(L), bo = line_base<1, mc, mc, EZ>(L);
     T x[m];
 #pragma unroll
-    for (int j = 0; j < m; ++j) x[j] = t1[bi + j * mc];
+    for (int j = 0; j < m; ++j) x[j] = sm[SZT + bi + j * mc];
 #pragma unroll
     for (int i = 0; i < mc; ++i) {
       T acc = T(0);
 #pragma unroll
       for (int j = 0; j < m; ++j)
         if (pnz(pf, pc, j, i)) acc += Tr[j * mc + i] * x[j];
-      ydst[bo + i * mc] = acc;
+      sm[ydst + bo + i * mc] = acc;
     }
-  }
+  });
   __syncthreads();
   if constexpr (DIM == 3) {
-    for (int L = lane; L < mc * mc; L += tpp) {
+    pfor<mc * mc>(pb.np, [&](int g, int L) {
+      T* sm = pb.at(g);
       const int bi = line_base<2, mc, mc, m>(L), bo = line_base<2, mc, mc, mc>(L);
       T x[m];
 #pragma unroll
-      for (int j = 0; j < m; ++j) x[j] = t0[bi + j * mc * mc];
+      for (int j = 0; j < m; ++j) x[j] = sm[bi + j * mc * mc];
 #pragma unroll
       for (int i = 0; i < mc; ++i) {
         T acc = T(0);
 #pragma unroll
         for (int j = 0; j < m; ++j)
           if (pnz(pf, pc, j, i)) acc += Tr[j * mc + i] * x[j];
-        rc[bo + i * mc * mc] = acc;
+        sm[dst + bo + i * mc * mc] = acc;
       }
-    }
+    });
     __syncthreads();
   }
 }
 
-// Prolongation d += T_l dc (dc: level l-1), using t0, t1.
+// Prolongation: level-l vector at `dst` += T_l (level l-1 vector at `src`),
+// using t0, t1.
 template <int DIM, int l, typename T>
-__device__ __forceinline__ void prolong_p(const T* dc, T* t0, T* t1, T* d, int lane, int tpp) {
+__device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst) {
   constexpr int pf = plev(K, l), pc = plev(K, l - 1);
   constexpr int m = mp(pf), mc = mp(pc);
-  const T* Tr = coef<T>() + LAY.Tr[l];
+  constexpr int SZT = PatchShape<DIM>::SZT;
   constexpr int EZC = DIM == 3 ? mc : 1;
+  const T* Tr = coef<T>() + LAY.Tr[l];
   // x: (mc, mc, EZC) -> (m, mc, EZC) in t0
-  for (int L = lane; L < mc * EZC; L += tpp) {
+  pfor<mc * EZC>(pb.np, [&](int g, int L) {
+    T* sm = pb.at(g);
     const int bi = line_base<0, mc, mc, EZC>(L), bo = line_base<0, m, mc, EZC>(L);
     T x[mc];
 #pragma unroll
-    for (int j = 0; j < mc; ++j) x[j] = dc[bi + j];
+    for (int j = 0; j < mc; ++j) x[j] = sm[src + bi + j];
 #pragma unroll
     for (int i = 0; i < m; ++i) {
       T acc = T(0);
 #pragma unroll
       for (int j = 0; j < mc; ++j)
         if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
-      t0[bo + i] = acc;
+      sm[bo + i] = acc;
     }
-  }
+  });
   __syncthreads();
   if constexpr (DIM == 3) {
-    // y: (m, mc, mc) -> (m, m, mc) in t1
-    for (int L = lane; L < m * mc; L += tpp) {
+    // y: (m, mc, mc) in t0 -> (m, m, mc) in t1
+    pfor<m * mc>(pb.np, [&](int g, int L) {
+      T* sm = pb.at(g);
       const int bi = line_base<1, m, mc, mc>(L), bo = line_base<1, m, m, mc>(L);
       T x[mc];
 #pragma unroll
-      for (int j = 0; j < mc; ++j) x[j] = t0[bi + j * m];
+      for (int j = 0; j < mc; ++j) x[j] = sm[bi + j * m];
 #pragma unroll
       for (int i = 0; i < m; ++i) {
         T acc = T(0);
 #pragma unroll
         for (int j = 0; j < mc; ++j)
           if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
-        t1[bo + i * m] = acc;
+        sm[SZT + bo + i * m] = acc;
       }
-    }
+    });
     __syncthreads();
-    // z: (m, m, mc) -> (m, m, m) added into d
-    for (int L = lane; L < m * m; L += tpp) {
+    // z: (m, m, mc) in t1 -> (m, m, m) added into dst
+    pfor<m * m>(pb.np, [&](int g, int L) {
+      T* sm = pb.at(g);
       const int bi = line_base<2, m, m, mc>(L), bo = line_base<2, m, m, m>(L);
       T x[mc];
 #pragma unroll
-      for (int j = 0; j < mc; ++j) x[j] = t1[bi + j * m * m];
+      for (int j = 0; j < mc; ++j) x[j] = sm[SZT + bi + j * m * m];
 #pragma unroll
       for (int i = 0; i < m; ++i) {
         T acc = T(0);
 #pragma unroll
         for (int j = 0; j < mc; ++j)
           if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
-        d[bo + i * m * m] += acc;
+        sm[dst + bo + i * m * m] += acc;
       }
-    }
+    });
     __syncthreads();
   } else {
-    // y: (m, mc) -> (m, m) added into d
-    for (int L = lane; L < m; L += tpp) {
+    // y: (m, mc) in t0 -> (m, m) added into dst
+    pfor<m>(pb.np, [&](int g, int L) {
+      T* sm = pb.at(g);
       const int bi = line_base<1, m, mc, 1>(L), bo = line_base<1, m, m, 1>(L);
       T x[mc];
 #pragma unroll
-      for (int j = 0; j < mc; ++j) x[j] = t0[bi + j * m];
+      for (int j = 0; j < mc; ++j) x[j] = sm[bi + j * m];
 #pragma unroll
       for (int i = 0; i < m; ++i) {
         T acc = T(0);
 #pragma unroll
         for (int j = 0; j < mc; ++j)
           if (pnz(pf, pc, i, j)) acc += Tr[i * mc + j] * x[j];
-        d[bo + i * m] += acc;
+        sm[dst + bo + i * m] += acc;
       }
-    }
+    });
     __syncthreads();
   }
 }
 
-// Algorithm 3 (full V-cycle) on p-level l for the residual in r_l, result
-// in d_l; level 0 (p = 1) is the exact 1x1 solve (§3.2).
+// Algorithm 3 (full V-cycle) on p-level l for the residuals r_l of all
+// patches of the block, results in d_l; level 0 (p = 1) is the exact 1x1
+// solve (§3.2).
 template <int DIM, int l, typename T, class Geo>
-__device__ void pvcycle(T* sm, const Geo& geo, const PatchParams<T>& P, T inv_a0, int lane, int tpp) {
+__device__ void pvcycle(const PBlock<T>& pb, const Geo& geo, const PatchParams<T>& P) {
   using S = PatchShape<DIM>;
   if constexpr (l == 0) {
-    if (lane == 0) sm[S::off_d(0)] = sm[S::off_r(0)] * inv_a0;
+    pfor<1>(pb.np, [&](int g, int) {
+      T* sm = pb.at(g);
+      sm[S::off_d(0)] = sm[S::off_r(0)] * geo.a0inv(g);
+    });
     __syncthreads();
   } else {
     constexpr int SZ = S::SZ(l);
-    T* r = sm + S::off_r(l);
-    T* d = sm + S::off_d(l);
-    T* t0 = sm;
-    T* t1 = sm + S::SZT;
+    constexpr int R = S::off_r(l), D = S::off_d(l);
     const T om = P.omega[l];
-    for (int i = lane; i < SZ; i += tpp) d[i] = om * geo.dinv_at(l, i) * r[i];  // pre-smoothing
+    pfor<SZ>(pb.np, [&](int g, int i) {  // pre-smoothing (zero initial guess)
+      T* sm = pb.at(g);
+      sm[D + i] = om * geo.dinv_at(g, l, i) * sm[R + i];
+    });
     __syncthreads();
-    geo.template resid<l>(d, r, t0, t0, t1, lane, tpp);                        // residual
-    restrict_p<DIM, l>(t0, t1, sm + S::off_r(l - 1), lane, tpp);               // restrict
-    pvcycle<DIM, l - 1, T, Geo>(sm, geo, P, inv_a0, lane, tpp);                // recurse
-    prolong_p<DIM, l>(sm + S::off_d(l - 1), t0, t1, d, lane, tpp);             // prolongate, add
-    geo.template resid<l>(d, r, t0, t0, t1, lane, tpp);                        // residual
-    for (int i = lane; i < SZ; i += tpp) d[i] += om * geo.dinv_at(l, i) * t0[i];  // post-smoothing
+    geo.template resid<l>(pb, D, R, 0);                   // residual into t0
+    restrict_p<DIM, l>(pb, S::off_r(l - 1));               // restrict
+    pvcycle<DIM, l - 1, T>(pb, geo, P);                    // recurse
+    prolong_p<DIM, l>(pb, S::off_d(l - 1), D);             // prolongate, add
+    geo.template resid<l>(pb, D, R, 0);                   // residual
+    pfor<SZ>(pb.np, [&](int g, int i) {  // post-smoothing
+      T* sm = pb.at(g);
+      sm[D + i] += om * geo.dinv_at(g, l, i) * sm[i];
+    });
     __syncthreads();
   }
+}
+
+// Algorithm 2 around Algorithm 3 for every patch of the block: the top-level
+// residual in r_top on entry, the correction in d_top on exit.
+template <int DIM, typename T, class Geo>
+__device__ __forceinline__ void local_solve(const PBlock<T>& pb, const Geo& geo, const PatchParams<T>& P,
+                                            int n_iter, int extra) {
+  using S = PatchShape<DIM>;
+  constexpr int L = S::L, SZT = S::SZT;
+  constexpr int RT = S::off_r(L - 1), DT = S::off_d(L - 1);
+  if (n_iter <= 1) {
+    pvcycle<DIM, L - 1, T>(pb, geo, P);
+    return;
+  }
+  const int RJ = extra, DS = extra + SZT;  // keep r_j and the running correction
+  pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[RJ + i] = sm[RT + i]; });
+  __syncthreads();
+  pvcycle<DIM, L - 1, T>(pb, geo, P);
+  pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[DS + i] = sm[DT + i]; });
+  __syncthreads();
+  for (int it = 1; it < n_iter; ++it) {
+    geo.template resid<L - 1>(pb, DS, RJ, RT);
+    pvcycle<DIM, L - 1, T>(pb, geo, P);
+    pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[DS + i] += sm[DT + i]; });
+    __syncthreads();
+  }
+  pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[DT + i] = sm[DS + i]; });
+  __syncthreads();
 }
 
 // Patches of one parity colour: vertex v_d = 2 i_d + (bit_d ? 1 : 2).
 __device__ __forceinline__ int colour_count(int n, int bit) { return bit ? n / 2 : (n - 1) / 2; }
 
-template <int DIM, typename T>
-__global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ u, int n, int colour, int ppc,
-                                  int n_iter, const T* __restrict__ dinv, PatchParams<T> P) {
-  using S = PatchShape<DIM>;
-  constexpr int TPP = S::TPP;
-  constexpr int MT = S::MT;
-  constexpr int L = S::L;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int grp = threadIdx.x / TPP, lane = threadIdx.x % TPP;
-  const int gstride = S::ELEMS + (n_iter > 1 ? 2 * S::SZT : 0);
-  T* sm = reinterpret_cast<T*>(smraw) + (int64_t)grp * gstride;
+// Per-patch set-up shared by the Cartesian and deformed kernels: vertex of
+// patch g of this block (or inactive), first global node of its interior.
+struct PatchMeta {
+  int v[3];
+  int g0[3];
+  int active;
+};
+
+template <int DIM>
+__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n, int colour) {
   const int cx = colour_count(n, colour & 1), cy = colour_count(n, (colour >> 1) & 1);
   const int cz = DIM == 3 ? colour_count(n, (colour >> 2) & 1) : 1;
   const int64_t npatch = (int64_t)cx * cy * cz;
-  const int64_t pid = (int64_t)blockIdx.x * ppc + grp;
-  const bool active = pid < npatch;
-  int v[3] = {0, 0, 0};
-  if (active) {
-    int64_t t = pid;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    const int64_t pid = (int64_t)blockIdx.x * np + g;
+    PatchMeta m;
+    m.active = pid < npatch;
+    int64_t t = m.active ? pid : 0;
     const int ix = (int)(t % cx); t /= cx;
     const int iy = (int)(t % cy); t /= cy;
     const int iz = (int)t;
-    v[0] = 2 * ix + ((colour & 1) ? 1 : 2);
-    v[1] = 2 * iy + (((colour >> 1) & 1) ? 1 : 2);
-    v[2] = DIM == 3 ? 2 * iz + (((colour >> 2) & 1) ? 1 : 2) : 0;
+    m.v[0] = 2 * ix + ((colour & 1) ? 1 : 2);
+    m.v[1] = 2 * iy + (((colour >> 1) & 1) ? 1 : 2);
+    m.v[2] = DIM == 3 ? 2 * iz + (((colour >> 2) & 1) ? 1 : 2) : 0;
+    for (int d = 0; d < 3; ++d) m.g0[d] = (d < DIM) ? K * (m.v[d] - 1) + 1 : 0;
+    meta[g] = m;
   }
-  const int N1 = K * n + 1;
-  const int g0x = K * (v[0] - 1) + 1, g0y = K * (v[1] - 1) + 1, g0z = DIM == 3 ? K * (v[2] - 1) + 1 : 0;
-  T* rt = sm + S::off_r(L - 1);
-  T* dt = sm + S::off_d(L - 1);
-  // gather r_j = Pi_j r
-  for (int i = lane; i < S::SZT; i += TPP) {
-    T val = T(0);
-    if (active) {
-      const int ix = i % MT, iy = (i / MT) % MT, iz = DIM == 3 ? i / (MT * MT) : 0;
-      const int64_t g = (int64_t)(g0x + ix) + (int64_t)N1 * ((g0y + iy) + (int64_t)N1 * (DIM == 3 ? g0z + iz : 0));
-      val = r[g];
-    }
-    rt[i] = val;
-  }
+}
+
+template <int DIM>
+__device__ __forceinline__ int64_t patch_node(const PatchMeta& m, int i, int N1) {
+  constexpr int MT = mp(K);
+  const int ix = i % MT, iy = (i / MT) % MT, iz = DIM == 3 ? i / (MT * MT) : 0;
+  return (int64_t)(m.g0[0] + ix) + (int64_t)N1 * ((m.g0[1] + iy) + (int64_t)N1 * (m.g0[2] + iz));
+}
+
+template <int DIM, typename T>
+__global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ u, int n, int colour, int np,
+                                  int n_iter, const T* __restrict__ dinv, PatchParams<T> P) {
+  using S = PatchShape<DIM>;
+  constexpr int SZT = S::SZT;
+  constexpr int RT = S::off_r(S::L - 1), DT = S::off_d(S::L - 1);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ PatchMeta meta[kMaxPatchesPerBlock];
+  const int stride = S::ELEMS + (n_iter > 1 ? 2 * SZT : 0);
+  const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
+  patch_meta_init<DIM>(meta, np, n, colour);
   __syncthreads();
-  CartGeo<DIM, T> geo{dinv, P.scale, T(1) / P.scale};
-  if (n_iter > 1) {
-    // Algorithm 2: keep r_j and the running correction ds
-    T* rj = sm + S::ELEMS;
-    T* ds = rj + S::SZT;
-    for (int i = lane; i < S::SZT; i += TPP) { rj[i] = rt[i]; }
-    __syncthreads();
-    pvcycle<DIM, L - 1, T>(sm, geo, P, P.inv_a0, lane, TPP);
-    for (int i = lane; i < S::SZT; i += TPP) ds[i] = dt[i];
-    __syncthreads();
-    for (int it = 1; it < n_iter; ++it) {
-      geo.template resid<L - 1>(ds, rj, rt, sm, sm + S::SZT, lane, TPP);
-      pvcycle<DIM, L - 1, T>(sm, geo, P, P.inv_a0, lane, TPP);
-      for (int i = lane; i < S::SZT; i += TPP) ds[i] += dt[i];
-      __syncthreads();
-    }
-    for (int i = lane; i < S::SZT; i += TPP) dt[i] = ds[i];
-    __syncthreads();
-  } else {
-    pvcycle<DIM, L - 1, T>(sm, geo, P, P.inv_a0, lane, TPP);
-  }
+  const int N1 = K * n + 1;
+  pfor<SZT>(np, [&](int g, int i) {  // gather r_j = Pi_j r
+    const PatchMeta& m = meta[g];
+    pb.at(g)[RT + i] = m.active ? r[patch_node<DIM>(m, i, N1)] : T(0);
+  });
+  __syncthreads();
+  const CartGeo<DIM, T> geo{dinv, P.scale, T(1) / P.scale, P.inv_a0};
+  local_solve<DIM, T>(pb, geo, P, n_iter, S::ELEMS);
   // scatter u += omega_AS Pi_j^T d_j (patches of one colour are disjoint)
-  if (active) {
-    for (int i = lane; i < S::SZT; i += TPP) {
-      const int ix = i % MT, iy = (i / MT) % MT, iz = DIM == 3 ? i / (MT * MT) : 0;
-      const int64_t g = (int64_t)(g0x + ix) + (int64_t)N1 * ((g0y + iy) + (int64_t)N1 * (DIM == 3 ? g0z + iz : 0));
-      u[g] += P.omega_as * dt[i];
-    }
-  }
+  pfor<SZT>(np, [&](int g, int i) {
+    const PatchMeta& m = meta[g];
+    if (m.active) u[patch_node<DIM>(m, i, N1)] += P.omega_as * pb.at(g)[DT + i];
+  });
 }
 
 // K = 1: every patch interior is the single vertex; the local solve is the

@@ -13,7 +13,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -273,31 +276,31 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   return PMG_OK;
 }
 
-// One additive sweep's patch corrections: u += S r (all 2^d colours).
-int patch_sweep(pmg_ctx* c, int level, const void* r, void* u) {
+// Patch corrections of one parity colour: u += omega_AS sum_{j in colour} Pi_j^T V_j Pi_j r.
+int patch_sweep_colour(pmg_ctx* c, int level, const void* r, void* u, int colour) {
   LevelData& L = c->lv[level];
   const PatchParamsHost P = patch_params(c, level);
-  for (int colour = 0; colour < (1 << c->dim); ++colour) {
-    cudaError_t e;
-    if (c->deformed) {
-      DefLevel D{};
-      for (int i = 0; i < 4; ++i) {
-        D.G[i] = L.G[i];
-        D.dinv[i] = L.dinv[i];
-      }
-      D.dinv1 = L.dinv1;
-      if (c->K == 1) {
-        // single-vertex patches: u_v += omega_AS r_v / A_vv via the p = 1 diagonal
-        e = c->kt->patch_def(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, D, P, c->stream);
-      } else {
-        e = c->kt->patch_def(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, D, P, c->stream);
-      }
-    } else {
-      e = c->kt->patch_cart(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
-                            c->stream);
+  cudaError_t e;
+  if (c->deformed) {
+    DefLevel D{};
+    for (int i = 0; i < 4; ++i) {
+      D.G[i] = L.G[i];
+      D.dinv[i] = L.dinv[i];
     }
-    if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
+    D.dinv1 = L.dinv1;
+    e = c->kt->patch_def(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+  } else {
+    e = c->kt->patch_cart(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
+                          c->stream);
   }
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
+  return PMG_OK;
+}
+
+// One additive sweep's patch corrections: u += S r (all 2^d colours).
+int patch_sweep(pmg_ctx* c, int level, const void* r, void* u) {
+  for (int colour = 0; colour < (1 << c->dim); ++colour)
+    if (int rc = patch_sweep_colour(c, level, r, u, colour)) return rc;
   return PMG_OK;
 }
 
@@ -425,6 +428,124 @@ int precondition(pmg_ctx* c, const double* r, double* z) {
   return PMG_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Patches per thread block of the smoother kernels, per (dim, degree, MG
+// precision, geometry, local cycles): every admissible value is timed on one
+// parity colour of the finest level (CUDA events, best of 3 after a warm-up)
+// and the fastest is kept for the process; with PMG_TUNE_FILE set, results
+// are also read from and appended to that file ("dim k prec geom cycles ppc"
+// per line).  Small meshes, whose launches are too short to time, use the
+// rule "about 256 threads per block" without caching it.
+struct TuneKey {
+  int dim, K, prec, geom, cycles;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dim, K, prec, geom, cycles) < std::tie(o.dim, o.K, o.prec, o.geom, o.cycles);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+bool g_tune_file_read = false;
+
+void tune_file_read_locked() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = std::getenv("PMG_TUNE_FILE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int d, k, pr, ge, cy, ppc;
+  while (std::fscanf(f, "%d %d %d %d %d %d", &d, &k, &pr, &ge, &cy, &ppc) == 6) g_tune[{d, k, pr, ge, cy}] = ppc;
+  std::fclose(f);
+}
+
+void tune_file_append_locked(const TuneKey& key, int ppc) {
+  const char* path = std::getenv("PMG_TUNE_FILE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d\n", key.dim, key.K, key.prec, key.geom, key.cycles, ppc);
+  std::fclose(f);
+}
+
+int admissible_ppc(const pmg_ctx* c, int ppc) {
+  const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
+  const int smem = c->deformed ? c->kt->patch_def_smem(c->dim, c->mgprec, c->cfg.local_cycles)
+                               : c->kt->patch_smem(c->dim, c->mgprec, c->cfg.local_cycles);
+  const int maxt = c->kt->patch_max_threads(c->dim, c->mgprec, c->deformed ? 1 : 0);
+  return ppc >= 1 && ppc <= 64 && (ppc * tpp + 31) / 32 * 32 <= std::min(1024, maxt) && ppc * smem <= kMaxDynSmem;
+}
+
+int rule_ppc(const pmg_ctx* c) {
+  const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
+  int ppc = std::max(1, 256 / tpp);
+  while (ppc > 1 && !admissible_ppc(c, ppc)) --ppc;
+  return ppc;
+}
+
+int choose_patches_per_block(pmg_ctx* c) {
+  const pmg_config& cf = c->cfg;
+  if (!admissible_ppc(c, 1)) return fail(PMG_ERR_UNSUPPORTED, "patch does not fit in shared memory for this degree");
+  if (cf.patches_per_block > 0) {
+    if (!admissible_ppc(c, cf.patches_per_block)) return fail(PMG_ERR_ARG, "patches_per_block not admissible");
+    c->ppc = cf.patches_per_block;
+    return PMG_OK;
+  }
+  c->ppc = rule_ppc(c);
+  LevelData& F = c->lv[c->L - 1];
+  const int64_t patches = ipow64(std::max(F.n - 1, 0), c->dim);
+  if (c->K == 1 || patches < 4096) return PMG_OK;
+  const TuneKey key{c->dim, c->K, c->mgprec, c->deformed ? 1 : 0, cf.local_cycles};
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_file_read_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && admissible_ppc(c, it->second)) {
+      c->ppc = it->second;
+      return PMG_OK;
+    }
+  }
+  const size_t es = c->mg32 ? 4 : 8;
+  PMG_CUDA(cudaMemsetAsync(F.r, 0, es * F.N, c->stream));
+  PMG_CUDA(cudaMemsetAsync(F.u, 0, es * F.N, c->stream));
+  cudaEvent_t e0, e1;
+  PMG_CUDA(cudaEventCreate(&e0));
+  PMG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_ppc = c->ppc;
+  const int64_t before = g_launches.load();
+  for (int ppc = 1; ppc <= 64; ++ppc) {
+    if (!admissible_ppc(c, ppc)) continue;
+    c->ppc = ppc;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      int rc = patch_sweep_colour(c, c->L - 1, F.r, F.u, 0);
+      cudaEventRecord(e1, c->stream);
+      if (rc) {  // a launch the device rejects (resources): not a candidate
+        cudaGetLastError();
+        tmin = 1e30f;
+        break;
+      }
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    if (tmin < best * 0.995f) {
+      best = tmin;
+      best_ppc = ppc;
+    }
+  }
+  g_launches -= g_launches.load() - before;  // tuning launches are not the caller's work
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->ppc = best_ppc;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[key] = best_ppc;
+  tune_file_append_locked(key, best_ppc);
+  return PMG_OK;
+}
+
 int check_ctx(const pmg_ctx* c) { return c ? PMG_OK : fail(PMG_ERR_ARG, "context is NULL"); }
 
 int setup_context(pmg_ctx* c) {
@@ -525,17 +646,8 @@ int setup_context(pmg_ctx* c) {
     PMG_CUDA(cudaStreamSynchronize(c->stream));
   }
 
-  // patches per block: fill ~256 threads within the shared-memory budget
-  {
-    const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
-    const int smem = c->deformed ? c->kt->patch_def_smem(c->dim, c->mgprec, cf.local_cycles)
-                                 : c->kt->patch_smem(c->dim, c->mgprec, cf.local_cycles);
-    if (smem > 227 * 1024) return fail(PMG_ERR_UNSUPPORTED, "patch does not fit in shared memory for this degree");
-    int ppc = cf.patches_per_block > 0 ? cf.patches_per_block : std::max(1, 256 / tpp);
-    while (ppc > 1 && (ppc * smem > 100 * 1024 || ppc * tpp > 1024)) --ppc;
-    if (ppc * smem > 227 * 1024 || ppc * tpp > 1024) return fail(PMG_ERR_ARG, "patches_per_block too large");
-    c->ppc = ppc;
-  }
+  // patches per block: the autotuned value (or the caller's)
+  if (int rc = choose_patches_per_block(c)) return rc;
 
   PMG_CUDA(cudaMallocHost((void**)&c->host_scal, 8 * S_COUNT));
   PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
@@ -800,6 +912,12 @@ int pmg_synchronize(pmg_ctx* c) {
 }
 
 int64_t pmg_launch_count(void) { return g_launches.load(); }
+
+int pmg_patches_per_block(const pmg_ctx* c, int* ppc) {
+  if (check_ctx(c) || !ppc) return fail(PMG_ERR_ARG, "NULL argument");
+  *ppc = c->ppc;
+  return PMG_OK;
+}
 
 const char* pmg_status_string(int s) {
   switch (s) {

@@ -83,6 +83,9 @@ __host__ __device__ constexpr CoefLayout coef_layout(int K) {
 }
 
 constexpr int kMaxCoef = 2048;   // >= coef_layout(8).total
+// Dynamic shared memory any kernel of the library may request: the 227 KB
+// per-block opt-in of sm_103a minus room for the kernels' static arrays.
+constexpr int kMaxDynSmem = 220 * 1024;
 
 // Per-call scalars of the patch smoother (host fills, passed by value).
 template <typename T>

@@ -48,6 +48,8 @@ struct KernelTable {
                            const DefLevel& lev, const PatchParamsHost& P, cudaStream_t s);
   int (*patch_def_threads)(int dim);
   int (*patch_def_smem)(int dim, int prec, int n_iter);
+  // largest block the patch kernel can launch with (registers included)
+  int (*patch_max_threads)(int dim, int prec, int deformed);
 };
 
 const KernelTable* kernel_table(int K);

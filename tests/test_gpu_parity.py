@@ -403,3 +403,35 @@ def test_full_size_3d_q4_smoother_and_vcycle_symmetry_and_solve():
     assert true_res <= 2e-8
     err = ctx.l2_error_manufactured(x)
     assert err < 1e-6        # O(h^5) with h = 1/32
+
+
+# ------------------------------------------------------------------ autotuner
+@pytest.mark.parametrize("geom,prec", [("cartesian", p.FP64), ("cartesian", p.FP32), ("deformed", p.FP32)])
+def test_patches_per_block_does_not_change_results(geom, prec):
+    # each patch is computed by the same code whatever the block packing, so
+    # every admissible value gives bitwise the same sweep
+    d, n, k = 3, 8, 3
+    dt = torch.float64 if prec == p.FP64 else torch.float32
+    b = to_dev(random_vector(d, n, k, seed=81), dt)
+    outs = []
+    for ppc in (1, 3, 7):
+        ctx = make_ctx(d, n, k, L=2, geom=geom, prec=prec, patches_per_block=ppc)
+        assert ctx.patches_per_block() == ppc
+        u = torch.zeros_like(b)
+        ctx.smooth(b, u)
+        outs.append(u)
+        ctx.close()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_autotuned_patches_per_block_is_admissible():
+    ctx = make_ctx(3, 32, 2)            # 29,791 patches: the tuner times candidates
+    ppc = ctx.patches_per_block()
+    assert 1 <= ppc <= 64
+    b = to_dev(random_vector(3, 32, 2, seed=82))
+    u = torch.zeros_like(b)
+    ctx.smooth(b, u)
+    ref = make_ctx(3, 32, 2, patches_per_block=1)
+    u1 = torch.zeros_like(b)
+    ref.smooth(b, u1)
+    assert torch.equal(u, u1)
