@@ -134,6 +134,18 @@ int pmg_solve(pmg_ctx* ctx, const double* b, double* x, double rtol, int maxit, 
 int pmg_solve_host(pmg_ctx* ctx, const double* b_host, double* x_host, double rtol, int maxit,
                    pmg_solve_info* info);
 
+/* Incremental form of pmg_solve, for drivers that interleave many contexts
+ * (the serving loop): pmg_solve_start enqueues the set-up and the first
+ * preconditioner step and returns; pmg_solve_progress never blocks -- it
+ * advances the CG iteration as far as completed device work allows (each
+ * iteration enqueues the next V-cycle before its residual norm is read) and
+ * sets *done = 1 once x has been written (x on the host if x_on_host, then
+ * pinned memory is required for the copy to overlap), filling *info and
+ * returning the solve's status.  Same iterations and result as pmg_solve.
+ * One solve per context at a time (PMG_ERR_STATE otherwise). */
+int pmg_solve_start(pmg_ctx* ctx, const double* b, int b_on_host, double* x, int x_on_host, double rtol, int maxit);
+int pmg_solve_progress(pmg_ctx* ctx, int* done, pmg_solve_info* info);
+
 /* b_i = int f phi_i with f = d pi^2 prod_i sin(pi x_i), the load for the
  * manufactured solution u = prod_i sin(pi x_i), (k+1)-point Gauss rule, on
  * the finest level (device, double). */
@@ -160,6 +172,34 @@ int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
 
 const char* pmg_status_string(int status);
 const char* pmg_last_error(void);
+
+/* ------------------------------------------------------------------ serving
+ * Many solves resident on one GPU (not in the paper: the serving layer of
+ * this library).  pmg_server_submit queues a request (config, host b and x
+ * of pmg_num_dofs(finest) doubles each -- pinned memory for overlapping
+ * copies -- tolerance, iteration cap); pmg_server_poll never blocks: it
+ * admits queued requests in arrival order while fewer than max_active run
+ * and the request's pmg_bytes_required fits in the budget (idle resident
+ * contexts with the same dim/n/degree/precision/geometry/levels/cycles are
+ * reused; least-recently-used idle contexts are evicted to make room),
+ * advances every running solve (pmg_solve_progress) and retires finished
+ * ones.  Each resident context has its own stream, so the kernels of
+ * concurrent requests overlap on the device.  One host thread drives a
+ * server.  Budget <= 0 selects 90% of the free device memory. */
+typedef struct pmg_server pmg_server;
+int pmg_server_create(int64_t memory_budget_bytes, int max_active, pmg_server** out);
+int pmg_server_destroy(pmg_server* server);
+/* PMG_ERR_OOM if the request can never fit in the budget. */
+int pmg_server_submit(pmg_server* server, const pmg_config* cfg, const double* b_host, double* x_host, double rtol,
+                      int maxit, int64_t* request_id);
+int pmg_server_poll(pmg_server* server, int* n_running, int* n_queued);
+/* *state: 0 queued, 1 running, 2 done (x_host written, *info filled), 3
+ * failed (the return value is its error).  Times in seconds on the host's
+ * steady clock: submission, admission, completion. */
+int pmg_server_result(pmg_server* server, int64_t request_id, int* state, pmg_solve_info* info, double* t_submit,
+                      double* t_start, double* t_done);
+int pmg_server_stats(const pmg_server* server, int64_t* used_bytes, int* resident_contexts,
+                     int64_t* created_contexts);
 
 /* Largest nodal grid (k n + 1)^d that pmg_apply_cartesian_noalloc accepts. */
 #define PMG_NOALLOC_MAX_DOFS 2097152

@@ -31,7 +31,8 @@ EXPORTED = [
     "pmg_num_dofs", "pmg_apply", "pmg_residual", "pmg_smooth", "pmg_vcycle", "pmg_solve",
     "pmg_solve_host", "pmg_rhs_manufactured", "pmg_l2_error_manufactured", "pmg_synchronize",
     "pmg_launch_count", "pmg_status_string", "pmg_last_error", "pmg_apply_cartesian_noalloc",
-    "pmg_patches_per_block",
+    "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
+    "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -91,6 +92,15 @@ def load_library(path=LIB_PATH):
         "pmg_last_error": (ctypes.c_char_p, []),
         "pmg_apply_cartesian_noalloc": (cint, [cint, cint, cint, vp, vp, vp]),
         "pmg_patches_per_block": (cint, [vp, ctypes.POINTER(cint)]),
+        "pmg_solve_start": (cint, [vp, vp, cint, vp, cint, dbl, cint]),
+        "pmg_solve_progress": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(SolveInfo)]),
+        "pmg_server_create": (cint, [i64, cint, ctypes.POINTER(vp)]),
+        "pmg_server_destroy": (cint, [vp]),
+        "pmg_server_submit": (cint, [vp, ctypes.POINTER(Config), vp, vp, dbl, cint, ctypes.POINTER(i64)]),
+        "pmg_server_poll": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)]),
+        "pmg_server_result": (cint, [vp, i64, ctypes.POINTER(cint), ctypes.POINTER(SolveInfo),
+                                     ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "pmg_server_stats": (cint, [vp, ctypes.POINTER(i64), ctypes.POINTER(cint), ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -249,3 +259,59 @@ class Context:
 
     def synchronize(self):
         _check(_lib.pmg_synchronize(self.handle))
+
+
+class Server:
+    """Serving loop over resident contexts (native, see include/pmg.h).
+
+    submit() takes CPU float64 tensors (pinned for overlapped copies) for b
+    and x; poll() never blocks; result() reports state, solve info and the
+    submit/admit/done host times."""
+
+    def __init__(self, memory_budget_bytes=0, max_active=8):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.pmg_server_create(int(memory_budget_bytes), int(max_active), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, cfg, b_host, x_host, rtol=1e-8, maxit=500):
+        for t in (b_host, x_host):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("expected contiguous CPU float64 tensors")
+        rid = ctypes.c_int64()
+        _check(_lib.pmg_server_submit(self.handle, ctypes.byref(cfg), ctypes.c_void_p(b_host.data_ptr()),
+                                      ctypes.c_void_p(x_host.data_ptr()), rtol, maxit, ctypes.byref(rid)))
+        self._keep[rid.value] = (cfg, b_host, x_host)
+        return rid.value
+
+    def poll(self):
+        nr, nq = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.pmg_server_poll(self.handle, ctypes.byref(nr), ctypes.byref(nq)))
+        return nr.value, nq.value
+
+    def result(self, rid):
+        st = ctypes.c_int()
+        info = SolveInfo()
+        ts, ta, td = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        code = _lib.pmg_server_result(self.handle, rid, ctypes.byref(st), ctypes.byref(info), ctypes.byref(ts),
+                                      ctypes.byref(ta), ctypes.byref(td))
+        return dict(state=st.value, code=code, iterations=info.iterations, rel_residual=info.rel_residual,
+                    device_ms=info.time_ms, status=info.status, t_submit=ts.value, t_start=ta.value,
+                    t_done=td.value)
+
+    def stats(self):
+        used, res, created = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        _check(_lib.pmg_server_stats(self.handle, ctypes.byref(used), ctypes.byref(res), ctypes.byref(created)))
+        return dict(used_bytes=used.value, resident_contexts=res.value, created_contexts=created.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pmg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -200,6 +200,15 @@ int make_plan(const pmg_config* cfg, Plan& P) {
 
 }  // namespace
 
+// Progress of an incremental solve (see solve_progress).
+struct SolveState {
+  int phase = 0;
+  int it = 0, maxit = 0, status = 0;
+  double rtol = 0, nb = 0, rel = 0, time_ms = 0;
+  double* x_out = nullptr;
+  bool x_host = false;
+};
+
 struct pmg_ctx {
   pmg_config cfg{};
   Plan plan;
@@ -229,7 +238,8 @@ struct pmg_ctx {
   double omega_j[4] = {1, 1, 1, 1};
   cudaGraphExec_t vgraph = nullptr;
   int64_t vgraph_launches = 0;
-  cudaEvent_t ev_rr = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev_rr = nullptr, ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+  SolveState sv;
 };
 
 namespace {
@@ -653,6 +663,7 @@ int setup_context(pmg_ctx* c) {
   PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
   PMG_CUDA(cudaEventCreate(&c->ev0));
   PMG_CUDA(cudaEventCreate(&c->ev1));
+  PMG_CUDA(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
   PMG_CUDA(cudaStreamSynchronize(c->stream));
   return PMG_OK;
 }
@@ -749,6 +760,7 @@ int pmg_destroy(pmg_ctx* c) {
   if (c->ev_rr) cudaEventDestroy(c->ev_rr);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->own_stream && c->stream) {
@@ -805,85 +817,164 @@ int pmg_vcycle(pmg_ctx* c, const double* r, double* z) {
   return precondition(c, r, z);
 }
 
-static int solve_device(pmg_ctx* c, const double* b, double rtol, int maxit, pmg_solve_info* info) {
-  LevelData& F = c->lv[c->L - 1];
-  const int64_t N = F.N;
+// ---------------------------------------------------------------- PCG
+// The solve is a state machine so that a server can interleave many
+// contexts: every step enqueues device work and records an event; the host
+// only reads ||r||^2 once the event has completed, while the preconditioner
+// of the next iteration is already enqueued behind it.
+enum SolvePhase { SP_IDLE = 0, SP_WAIT_BB = 1, SP_WAIT_RR = 2, SP_COPY_OUT = 3, SP_DONE = 4 };
+
+static int enqueue_iteration(pmg_ctx* c) {
+  const int64_t N = c->lv[c->L - 1].N;
   cudaStream_t s = c->stream;
+  if (int rc = level_apply(c, c->L - 1, PMG_FP64, c->cg_p, c->cg_Ap, nullptr)) return rc;
+  PMG_CUDA(dot(c->cg_p, c->cg_Ap, N, c->partial, c->scal + S_PAP, s));
+  PMG_CUDA(cg_update_xr(c->cg_x, c->cg_r, c->cg_p, c->cg_Ap, N, c->scal, S_RZ, S_PAP, c->partial, c->scal + S_RR, s));
+  PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_RR, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaEventRecord(c->ev_rr, s));
+  ++c->sv.it;
+  // the next preconditioner step goes in before the host looks at ||r||
+  if (int rc = precondition(c, c->cg_r, c->cg_z)) return rc;
+  PMG_CUDA(dot(c->cg_r, c->cg_z, N, c->partial, c->scal + S_RZN, s));
+  PMG_CUDA(cg_update_p(c->cg_p, c->cg_z, N, c->scal, S_RZN, S_RZ, 0, s));
+  return PMG_OK;
+}
+
+static int solve_start(pmg_ctx* c, const double* b, bool b_host, double rtol, int maxit) {
+  const int64_t N = c->lv[c->L - 1].N;
+  cudaStream_t s = c->stream;
+  c->sv = SolveState();
+  c->sv.rtol = rtol;
+  c->sv.maxit = maxit;
   PMG_CUDA(cudaEventRecord(c->ev0, s));
+  if (b_host) PMG_CUDA(cudaMemcpyAsync(c->cg_r, b, 8 * N, cudaMemcpyHostToDevice, s));
+  else PMG_CUDA(cudaMemcpyAsync(c->cg_r, b, 8 * N, cudaMemcpyDeviceToDevice, s));
   PMG_CUDA(cudaMemsetAsync(c->cg_x, 0, 8 * N, s));
-  PMG_CUDA(cudaMemcpyAsync(c->cg_r, b, 8 * N, cudaMemcpyDeviceToDevice, s));
   PMG_CUDA(dot(c->cg_r, c->cg_r, N, c->partial, c->scal + S_BB, s));
   PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_BB, c->scal + S_BB, 8, cudaMemcpyDeviceToHost, s));
-  int rc = precondition(c, c->cg_r, c->cg_z);
-  if (rc) return rc;
+  PMG_CUDA(cudaEventRecord(c->ev_rr, s));
+  if (int rc = precondition(c, c->cg_r, c->cg_z)) return rc;
   PMG_CUDA(dot(c->cg_r, c->cg_z, N, c->partial, c->scal + S_RZ, s));
   PMG_CUDA(cudaMemcpyAsync(c->cg_p, c->cg_z, 8 * N, cudaMemcpyDeviceToDevice, s));
-  PMG_CUDA(cudaStreamSynchronize(s));
-  const double nb = std::sqrt(c->host_scal[S_BB]);
-  int it = 0;
-  double rel = nb > 0 ? 1.0 : 0.0;
-  int status = PMG_OK;
-  if (nb > 0) {
-    status = PMG_NOT_CONVERGED;
-    while (it < maxit) {
-      if ((rc = level_apply(c, c->L - 1, PMG_FP64, c->cg_p, c->cg_Ap, nullptr))) return rc;
-      PMG_CUDA(dot(c->cg_p, c->cg_Ap, N, c->partial, c->scal + S_PAP, s));
-      PMG_CUDA(cg_update_xr(c->cg_x, c->cg_r, c->cg_p, c->cg_Ap, N, c->scal, S_RZ, S_PAP, c->partial,
-                            c->scal + S_RR, s));
-      PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_RR, c->scal + S_RR, 8, cudaMemcpyDeviceToHost, s));
-      PMG_CUDA(cudaEventRecord(c->ev_rr, s));
-      ++it;
-      // enqueue the next preconditioner step before checking convergence
-      if ((rc = precondition(c, c->cg_r, c->cg_z))) return rc;
-      PMG_CUDA(dot(c->cg_r, c->cg_z, N, c->partial, c->scal + S_RZN, s));
-      PMG_CUDA(cg_update_p(c->cg_p, c->cg_z, N, c->scal, S_RZN, S_RZ, 0, s));
-      PMG_CUDA(cudaEventSynchronize(c->ev_rr));
-      rel = std::sqrt(std::max(c->host_scal[S_RR], 0.0)) / nb;
-      if (!(rel == rel)) return fail(PMG_ERR_STATE, "CG breakdown (NaN residual)");
-      if (rel <= rtol) {
-        status = PMG_OK;
-        break;
+  c->sv.phase = SP_WAIT_BB;
+  return PMG_OK;
+}
+
+static int solve_finish(pmg_ctx* c, int status) {
+  const int64_t N = c->lv[c->L - 1].N;
+  c->sv.status = status;
+  PMG_CUDA(cudaEventRecord(c->ev1, c->stream));
+  if (c->sv.x_out) {
+    PMG_CUDA(cudaMemcpyAsync(c->sv.x_out, c->cg_x, 8 * N,
+                             c->sv.x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  }
+  PMG_CUDA(cudaEventRecord(c->ev_done, c->stream));
+  c->sv.phase = SP_COPY_OUT;
+  return PMG_OK;
+}
+
+// Advance the solve as far as completed device work allows; with `block`,
+// wait for each pending event.  *state: 0 running, 1 done.
+static int solve_progress(pmg_ctx* c, bool block, int* state) {
+  *state = 0;
+  for (;;) {
+    if (c->sv.phase == SP_IDLE) return fail(PMG_ERR_STATE, "no solve in progress");
+    if (c->sv.phase == SP_DONE) {
+      *state = 1;
+      return PMG_OK;
+    }
+    cudaEvent_t ev = c->sv.phase == SP_COPY_OUT ? c->ev_done : c->ev_rr;
+    if (block) {
+      PMG_CUDA(cudaEventSynchronize(ev));
+    } else {
+      const cudaError_t q = cudaEventQuery(ev);
+      if (q == cudaErrorNotReady) return PMG_OK;
+      if (q != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(q));
+    }
+    if (c->sv.phase == SP_COPY_OUT) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+      c->sv.time_ms = ms;
+      c->sv.phase = SP_DONE;
+      continue;
+    }
+    if (c->sv.phase == SP_WAIT_BB) {
+      c->sv.nb = std::sqrt(c->host_scal[S_BB]);
+      if (!(c->sv.nb > 0)) {
+        c->sv.rel = 0.0;
+        if (int rc = solve_finish(c, PMG_OK)) return rc;
+        continue;
+      }
+      c->sv.rel = 1.0;
+    } else {
+      c->sv.rel = std::sqrt(std::max(c->host_scal[S_RR], 0.0)) / c->sv.nb;
+      if (!(c->sv.rel == c->sv.rel)) return fail(PMG_ERR_STATE, "CG breakdown (NaN residual)");
+      if (c->sv.rel <= c->sv.rtol) {
+        if (int rc = solve_finish(c, PMG_OK)) return rc;
+        continue;
       }
     }
+    if (c->sv.it >= c->sv.maxit) {
+      if (int rc = solve_finish(c, PMG_NOT_CONVERGED)) return rc;
+      continue;
+    }
+    if (int rc = enqueue_iteration(c)) return rc;
+    c->sv.phase = SP_WAIT_RR;
   }
-  PMG_CUDA(cudaEventRecord(c->ev1, s));
-  PMG_CUDA(cudaEventSynchronize(c->ev1));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-  if (info) {
-    info->iterations = it;
-    info->rel_residual = rel;
-    info->time_ms = ms;
-    info->status = status;
-  }
+}
+
+static void solve_info(const pmg_ctx* c, pmg_solve_info* info) {
+  if (!info) return;
+  info->iterations = c->sv.it;
+  info->rel_residual = c->sv.rel;
+  info->time_ms = c->sv.time_ms;
+  info->status = c->sv.status;
+}
+
+static int solve_blocking(pmg_ctx* c, const double* b, bool b_host, double* x, bool x_host, double rtol, int maxit,
+                          pmg_solve_info* info) {
+  if (check_ctx(c) || !b || !x) return fail(PMG_ERR_ARG, "NULL argument");
+  if (maxit < 0 || !(rtol >= 0)) return fail(PMG_ERR_ARG, "bad rtol / maxit");
+  if (int rc = solve_start(c, b, b_host, rtol, maxit)) return rc;
+  c->sv.x_out = x;
+  c->sv.x_host = x_host;
+  int state = 0;
+  if (int rc = solve_progress(c, true, &state)) return rc;
+  solve_info(c, info);
+  const int status = c->sv.status;
+  c->sv.phase = SP_IDLE;
   return status;
 }
 
 int pmg_solve(pmg_ctx* c, const double* b, double* x, double rtol, int maxit, pmg_solve_info* info) {
-  if (check_ctx(c) || !b || !x) return fail(PMG_ERR_ARG, "NULL argument");
-  if (maxit < 0 || !(rtol >= 0)) return fail(PMG_ERR_ARG, "bad rtol / maxit");
-  int rc = solve_device(c, b, rtol, maxit, info);
-  if (rc < 0) return rc;
-  cudaError_t e = cudaMemcpyAsync(x, c->cg_x, 8 * c->lv[c->L - 1].N, cudaMemcpyDeviceToDevice, c->stream);
-  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
-  return rc;
+  return solve_blocking(c, b, false, x, false, rtol, maxit, info);
 }
 
 int pmg_solve_host(pmg_ctx* c, const double* b_host, double* x_host, double rtol, int maxit, pmg_solve_info* info) {
-  if (check_ctx(c) || !b_host || !x_host) return fail(PMG_ERR_ARG, "NULL argument");
+  return solve_blocking(c, b_host, true, x_host, true, rtol, maxit, info);
+}
+
+int pmg_solve_start(pmg_ctx* c, const double* b, int b_on_host, double* x, int x_on_host, double rtol, int maxit) {
+  if (check_ctx(c) || !b || !x) return fail(PMG_ERR_ARG, "NULL argument");
   if (maxit < 0 || !(rtol >= 0)) return fail(PMG_ERR_ARG, "bad rtol / maxit");
-  const int64_t N = c->lv[c->L - 1].N;
-  cudaError_t e = cudaMemcpyAsync(c->cg_b, b_host, 8 * N, cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
-  int rc = solve_device(c, c->cg_b, rtol, maxit, info);
-  if (rc < 0) return rc;
-  e = cudaMemcpyAsync(x_host, c->cg_x, 8 * N, cudaMemcpyDeviceToHost, c->stream);
-  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(e));
-  return rc;
+  if (c->sv.phase != SP_IDLE && c->sv.phase != SP_DONE) return fail(PMG_ERR_STATE, "a solve is already in progress");
+  if (int rc = solve_start(c, b, b_on_host != 0, rtol, maxit)) return rc;
+  c->sv.x_out = x;
+  c->sv.x_host = x_on_host != 0;
+  return PMG_OK;
+}
+
+int pmg_solve_progress(pmg_ctx* c, int* done, pmg_solve_info* info) {
+  if (check_ctx(c) || !done) return fail(PMG_ERR_ARG, "NULL argument");
+  int state = 0;
+  if (int rc = solve_progress(c, false, &state)) return rc;
+  *done = state;
+  if (state) {
+    solve_info(c, info);
+    c->sv.phase = SP_IDLE;
+    return c->sv.status;
+  }
+  return PMG_OK;
 }
 
 int pmg_rhs_manufactured(pmg_ctx* c, double* b) {

@@ -1,0 +1,80 @@
+"""Serving loop: admission, concurrency, and the same result alone and in the
+mix (through the native server and the C ABI)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2512_02577_gb300 as p
+from paper_2512_02577_gb300 import serve
+from paper_2512_02577_gb300.inputs import serving_requests
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(n_req, seed_shift=0, n_hi=16):
+    return serving_requests(n_requests=n_req, rate=400.0, arrival_seed=7 + seed_shift, size_seed=11 + seed_shift,
+                            n_lo=8, n_hi=n_hi, k_lo=2, k_hi=5)
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    reqs = _stream(10)
+    mix, summary = serve.run(reqs, precision=p.FP32, max_active=6)
+    assert summary["failed"] == 0
+    assert all(rec["rel_residual"] <= 1e-8 for rec in mix)
+    for rec in mix[:4]:
+        alone, _ = serve.run([dict(rec, t_arrival=0.0)], precision=p.FP32, max_active=1)
+        a, m = alone[0]["x"], rec["x"]
+        rel = float(torch.linalg.norm(a - m) / torch.linalg.norm(a))
+        assert rel <= 1e-12, (rec["n"], rec["k"], rel)
+        assert alone[0]["iterations"] == rec["iterations"]
+
+
+def test_results_match_direct_solve():
+    reqs = _stream(4, seed_shift=3)
+    recs, _ = serve.run(reqs, precision=p.FP64, max_active=4)
+    for rec in recs:
+        ctx = p.Context(p.make_config(dim=3, n_cells=rec["n"], degree=rec["k"]), device="cuda:0")
+        b = serve._rhs(3, rec["n"], rec["k"], rec["rhs_seed"]).cuda()
+        x = torch.zeros_like(b)
+        info = ctx.solve(b, x)
+        assert info.iterations == rec["iterations"]
+        assert torch.equal(x.cpu(), rec["x"])
+        ctx.close()
+
+
+def test_admission_by_memory_budget():
+    # a budget that holds one context of the largest request at a time: the
+    # others wait in the queue, all finish, and contexts are evicted/reused
+    reqs = _stream(6, seed_shift=5)
+    sizes = [p.bytes_required(p.make_config(dim=3, n_cells=r["n"], degree=r["k"], mg_precision=p.FP32))
+             for r in reqs]
+    recs, summary = serve.run(reqs, precision=p.FP32, max_active=6, budget=int(max(sizes) * 1.01))
+    assert summary["failed"] == 0
+    assert summary["used_bytes"] <= max(sizes) * 1.01
+    assert all(rec["rel_residual"] <= 1e-8 for rec in recs)
+
+
+def test_request_larger_than_budget_is_rejected():
+    srv = p.Server(memory_budget_bytes=1 << 20, max_active=2)
+    cfg = p.make_config(dim=3, n_cells=16, degree=4)
+    n = (4 * 16 + 1) ** 3
+    b = torch.zeros(n, dtype=torch.float64)
+    with pytest.raises(p.PmgError) as e:
+        srv.submit(cfg, b, torch.zeros_like(b))
+    assert e.value.code == p.PMG_ERR_OOM
+    srv.close()
+
+
+def test_concurrent_requests_overlap():
+    # six requests arriving together with six slots are all in flight at once
+    reqs = [dict(id=i, t_arrival=0.0, n=16, k=4, rhs_seed=500 + i) for i in range(6)]
+    recs, summary = serve.run(reqs, precision=p.FP32, max_active=6)
+    assert summary["failed"] == 0
+    assert max(r["t_start"] for r in recs) < min(r["t_done"] for r in recs)
+    # one slot: strictly one after the other
+    recs1, _ = serve.run(reqs, precision=p.FP32, max_active=1)
+    order = sorted(recs1, key=lambda r: r["t_start"])
+    assert all(a["t_done"] <= b["t_start"] + 1e-6 for a, b in zip(order, order[1:]))
