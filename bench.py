@@ -179,6 +179,47 @@ def cpu_baseline_entry(res):
                       % (res["dofs"], len(res["times"]))}
 
 
+# ----------------------------------------------------------------- profiling
+def profile_region(region, n_def):
+    """One NVTX range named 'profile' after warm-up, for
+    ncu --nvtx --nvtx-include "profile/": either one mixed-precision solve of
+    the 32^3 Q4 problem, or one FP32 apply and one FP32 sweep of the deformed
+    Q3 problem on n_def^3 cells."""
+    import torch
+    import paper_2512_02577_gb300 as p
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        if region == "mixed_solve":
+            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32), stream=stream,
+                            device=dev)
+            b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
+            ctx.rhs_manufactured(b)
+            x = torch.zeros_like(b)
+            for _ in range(3):
+                ctx.solve(b, x)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("profile")
+            ctx.solve(b, x)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        else:
+            ctx = p.Context(p.make_config(dim=3, n_cells=n_def, degree=3, geometry=p.DEFORMED,
+                                          mg_precision=p.FP32), stream=stream, device=dev)
+            N = ctx.num_dofs()
+            x = torch.randn(N, dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                ctx.apply(x, y, prec=p.FP32)
+                ctx.smooth(x, y)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("profile")
+            ctx.apply(x, y, prec=p.FP32)
+            ctx.smooth(x, y)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+
+
 # ----------------------------------------------------------------- main
 def pct(xs, q):
     xs = sorted(xs)
@@ -195,9 +236,15 @@ def main():
     ap.add_argument("--oracle-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-child", type=float, default=None)
+    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "deformed"],
+                    help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
+    ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
     args = ap.parse_args()
     if args.oracle_child is not None:
         oracle_child(args.oracle_child)
+        return
+    if args.profile_region:
+        profile_region(args.profile_region, args.profile_n)
         return
     args.warmup = max(args.warmup, 3)
 
@@ -323,14 +370,15 @@ def main():
         l2err64 = ctx.l2_error_manufactured(xs)
         solve32 = [i.time_ms for i in info32]
 
-        # roofline of the dominant kernel: one colour launch of the FP64 patch smoother
-        colours = 1 << D
+        # roofline of the dominant kernel: the FP64 patch launch (every local
+        # solve of the finest level), timed live on the library's stream
         sweep_ms = statistics.median(t_sweep)
-        res_ms = statistics.median(t_res)
-        patch_launch_ms = max(sweep_ms - res_ms, 1e-6) / colours
+        phases = ctx.smoother_phase_times(reps=10)
+        patch_launch_ms = phases[1]
         n_patches = (NCELL - 1) ** D
-        flops_launch = patch_flops(D, K) * n_patches / colours
+        flops_launch = patch_flops(D, K) * n_patches
         achieved = flops_launch / (patch_launch_ms * 1e-3) / 1e12
+        phases32 = ctx32.smoother_phase_times(reps=10)
 
         # ---- end-to-end through the host-buffer C-ABI path
         pin_b = b.cpu().pin_memory()
@@ -374,10 +422,16 @@ def main():
         "solve_mixed_ms": {"p50": pct(solve32, 50), "p99": pct(solve32, 99), "iterations": info32[-1].iterations,
                            "rel_residual": info32[-1].rel_residual, "l2_error": l2err},
         "mixed_speedup_vs_fp64": pct(solve64, 50) / pct(solve32, 50),
-        "roofline": {"kernel": "patch_cart_kernel<3,double> (one parity colour, 1/8 of the patches)",
+        "roofline": {"kernel": "patch_cart_kernel<3,double> (all 29,791 patches of the finest level)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "flops_per_launch": flops_launch, "launch_ms": patch_launch_ms},
+                     "flops_per_launch": flops_launch, "launch_ms": patch_launch_ms,
+                     "peak_note": "nominal FP64 (measured FMA probe 1.255 TFLOP/s)"},
+        "smoother_phases_ms": {"fp64": {"residual": phases[0], "patch": phases[1], "gather": phases[2]},
+                               "fp32": {"residual": phases32[0], "patch": phases32[1], "gather": phases32[2],
+                                        "patch_tflops": flops_launch / (phases32[1] * 1e-3) / 1e12,
+                                        "patch_frac_of_fp32_peak":
+                                            flops_launch / (phases32[1] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}},
         "e2e": {"value": N / e2e_s, "unit": "DoFs/s", "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 3 * 8 * N},
         "clocks": clocks.summary(),
     }

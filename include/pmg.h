@@ -170,6 +170,13 @@ int64_t pmg_launch_count(void);
  * that file). */
 int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
 
+/* Instrumentation: mean device times (ms, CUDA events on the context's
+ * stream) of the three phases of one smoothing step on `level`, over `reps`
+ * repetitions after one warm-up, on the level's own vectors: ms[0] residual
+ * r = b - A u, ms[1] the patch launch (every local solve), ms[2] the gather
+ * u += sum_j Pi_j^T d_j.  Overwrites the level's work vectors. */
+int pmg_smoother_phase_times(pmg_ctx* ctx, int level, int reps, double* ms);
+
 const char* pmg_status_string(int status);
 const char* pmg_last_error(void);
 

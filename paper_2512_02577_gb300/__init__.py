@@ -33,6 +33,7 @@ EXPORTED = [
     "pmg_launch_count", "pmg_status_string", "pmg_last_error", "pmg_apply_cartesian_noalloc",
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
+    "pmg_smoother_phase_times",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -101,6 +102,7 @@ def load_library(path=LIB_PATH):
         "pmg_server_result": (cint, [vp, i64, ctypes.POINTER(cint), ctypes.POINTER(SolveInfo),
                                      ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_server_stats": (cint, [vp, ctypes.POINTER(i64), ctypes.POINTER(cint), ctypes.POINTER(i64)]),
+        "pmg_smoother_phase_times": (cint, [vp, cint, cint, ctypes.POINTER(dbl)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -251,6 +253,13 @@ class Context:
         _check(_lib.pmg_l2_error_manufactured(self.handle, _ptr(x, torch.float64, self.num_dofs()),
                                               ctypes.byref(e)))
         return e.value
+
+    def smoother_phase_times(self, level=-1, reps=10):
+        """Mean ms of (residual, patch launch, gather) of one smoothing step."""
+        level = self.n_levels - 1 if level < 0 else level
+        out = (ctypes.c_double * 3)()
+        _check(_lib.pmg_smoother_phase_times(self.handle, level, reps, out))
+        return tuple(out)
 
     def patches_per_block(self):
         n = ctypes.c_int()

@@ -7,14 +7,6 @@
 namespace pmg {
 namespace PMG_KNS {
 
-static int grid_for(int64_t work, int block) {
-  int64_t g = (work + block - 1) / block;
-  const int64_t cap = 152 * 16;  // 152 SMs x resident blocks; grid-stride beyond
-  if (g > cap) g = cap;
-  if (g < 1) g = 1;
-  return (int)g;
-}
-
 static cudaError_t upload(const double* coef) {
   const int n = LAY.total;
   float tmp[kMaxCoef];
@@ -71,44 +63,61 @@ static int patch_smem(int dim, int prec, int n_iter) {
   return elems * es;
 }
 
+static int dinv_len(int dim) {
+  int len = 0;
+  for (int l = 1; l < nlev(K); ++l) len += ipow(mp(plev(K, l)), dim);
+  return len;
+}
+
+// shared memory of the block besides its patches: the inverse-diagonal tables
+static int patch_cart_extra_smem(int dim, int prec) { return dinv_len(dim) * (prec == 0 ? 8 : 4); }
+
 template <int DIM, typename T>
-static cudaError_t patch_cart_t(const T* r, T* u, int n, int colour, int ppc, int n_iter, const T* dinv,
+static cudaError_t patch_cart_t(const T* r, T* dst, int n, int ppc, int n_iter, const T* dinv,
                                 const PatchParamsHost& H, cudaStream_t st) {
   using S = PatchShape<DIM>;
   if (n < 2) return cudaSuccess;  // no interior vertex, no patch
-  if (K == 1) {
-    if (colour != 0) return cudaSuccess;  // one launch covers all single-vertex patches
-    const int64_t nv = DIM == 3 ? (int64_t)(n - 1) * (n - 1) * (n - 1) : (int64_t)(n - 1) * (n - 1);
-    patch_k1_kernel<DIM, T><<<grid_for(nv, 256), 256, 0, st>>>(r, u, n, (T)(H.omega_as * H.inv_a0));
-    g_launches += 1;
-    return cudaGetLastError();
-  }
-  const int cx = (colour & 1) ? n / 2 : (n - 1) / 2;
-  const int cy = ((colour >> 1) & 1) ? n / 2 : (n - 1) / 2;
-  const int cz = DIM == 3 ? (((colour >> 2) & 1) ? n / 2 : (n - 1) / 2) : 1;
-  const int64_t np = (int64_t)cx * cy * cz;
-  if (np == 0) return cudaSuccess;
   if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
+  const int64_t np = ipow(n - 1, DIM);
   const int64_t blocks = (np + ppc - 1) / ppc;
   const int threads = std::min(1024, (ppc * S::TPP + 31) / 32 * 32);
-  const int smem = ppc * patch_smem(DIM, sizeof(T) == 8 ? 0 : 1, n_iter);
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int smem = ppc * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
-  patch_cart_kernel<DIM, T><<<(unsigned)blocks, threads, smem, st>>>(r, u, n, colour, ppc, n_iter, dinv,
+  patch_cart_kernel<DIM, T><<<(unsigned)blocks, threads, smem, st>>>(r, dst, n, ppc, n_iter, dinv, dinv_len(DIM),
                                                                     to_params<T>(H));
   g_launches += 1;
   return cudaGetLastError();
 }
 
-static cudaError_t patch_cart(int dim, int prec, const void* r, void* u, int n, int colour, int ppc, int n_iter,
+static cudaError_t patch_cart(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                               const void* dinv, const PatchParamsHost& P, cudaStream_t s) {
   if (prec == 0) {
-    if (dim == 3) return patch_cart_t<3, double>((const double*)r, (double*)u, n, colour, ppc, n_iter,
-                                                 (const double*)dinv, P, s);
-    return patch_cart_t<2, double>((const double*)r, (double*)u, n, colour, ppc, n_iter, (const double*)dinv, P, s);
+    if (dim == 3)
+      return patch_cart_t<3, double>((const double*)r, (double*)dst, n, ppc, n_iter, (const double*)dinv, P, s);
+    return patch_cart_t<2, double>((const double*)r, (double*)dst, n, ppc, n_iter, (const double*)dinv, P, s);
   }
-  if (dim == 3)
-    return patch_cart_t<3, float>((const float*)r, (float*)u, n, colour, ppc, n_iter, (const float*)dinv, P, s);
-  return patch_cart_t<2, float>((const float*)r, (float*)u, n, colour, ppc, n_iter, (const float*)dinv, P, s);
+  if (dim == 3) return patch_cart_t<3, float>((const float*)r, (float*)dst, n, ppc, n_iter, (const float*)dinv, P, s);
+  return patch_cart_t<2, float>((const float*)r, (float*)dst, n, ppc, n_iter, (const float*)dinv, P, s);
+}
+
+// u (+)= the summed patch corrections held in dst (add = 0: u = sum)
+template <int DIM, typename T>
+static cudaError_t patch_gather_t(const T* dst, T* u, int n, int add, cudaStream_t st) {
+  const int64_t N = ipow(K * n + 1, DIM);
+  if (add) patch_gather_kernel<DIM, true, T><<<grid_for(N, 256), 256, 0, st>>>(dst, u, n);
+  else patch_gather_kernel<DIM, false, T><<<grid_for(N, 256), 256, 0, st>>>(dst, u, n);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+static cudaError_t patch_gather(int dim, int prec, const void* dst, void* u, int n, int add, cudaStream_t s) {
+  if (prec == 0) {
+    if (dim == 3) return patch_gather_t<3, double>((const double*)dst, (double*)u, n, add, s);
+    return patch_gather_t<2, double>((const double*)dst, (double*)u, n, add, s);
+  }
+  if (dim == 3) return patch_gather_t<3, float>((const float*)dst, (float*)u, n, add, s);
+  return patch_gather_t<2, float>((const float*)dst, (float*)u, n, add, s);
 }
 
 template <int DIM, typename T>
@@ -213,14 +222,10 @@ static cudaError_t prepare() {
   acc(allow_smem(patch_def_kernel<3, double>, optin));
   acc(allow_smem(patch_def_kernel<2, float>, optin));
   acc(allow_smem(patch_def_kernel<3, float>, optin));
-  acc(allow_smem(def_cell_kernel<2, 1, double>, optin));
-  acc(allow_smem(def_cell_kernel<3, 1, double>, optin));
-  acc(allow_smem(def_cell_kernel<2, -1, double>, optin));
-  acc(allow_smem(def_cell_kernel<3, -1, double>, optin));
-  acc(allow_smem(def_cell_kernel<2, 1, float>, optin));
-  acc(allow_smem(def_cell_kernel<3, 1, float>, optin));
-  acc(allow_smem(def_cell_kernel<2, -1, float>, optin));
-  acc(allow_smem(def_cell_kernel<3, -1, float>, optin));
+  acc(allow_smem(def_cell_kernel<2, double>, optin));
+  acc(allow_smem(def_cell_kernel<3, double>, optin));
+  acc(allow_smem(def_cell_kernel<2, float>, optin));
+  acc(allow_smem(def_cell_kernel<3, float>, optin));
   return r;
 }
 
@@ -233,6 +238,8 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::upload,
       PMG_KNS::cart_apply,
       PMG_KNS::patch_cart,
+      PMG_KNS::patch_gather,
+      PMG_KNS::patch_cart_extra_smem,
       PMG_KNS::patch_threads,
       PMG_KNS::patch_smem,
       PMG_KNS::h_prolong_add,

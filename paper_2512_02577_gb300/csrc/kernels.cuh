@@ -25,6 +25,14 @@ constexpr CoefLayout LAY = coef_layout(K);
 static __constant__ double c_coef64[kMaxCoef];
 static __constant__ float c_coef32[kMaxCoef];
 
+static inline int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  const int64_t cap = 152 * 16;  // 152 SMs x resident blocks; grid-stride beyond
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
 template <typename T>
 __device__ __forceinline__ const T* coef();
 template <>
@@ -513,11 +521,12 @@ __device__ __forceinline__ void local_solve(const PBlock<T>& pb, const Geo& geo,
   __syncthreads();
 }
 
-// Patches of one parity colour: vertex v_d = 2 i_d + (bit_d ? 1 : 2).
-__device__ __forceinline__ int colour_count(int n, int bit) { return bit ? n / 2 : (n - 1) / 2; }
-
-// Per-patch set-up shared by the Cartesian and deformed kernels: vertex of
-// patch g of this block (or inactive), first global node of its interior.
+// All patches of a level in one launch: patch index pid, lexicographic over
+// the interior vertices (x fastest).  Every patch reads the same residual
+// (additive smoother), so no colouring is needed to compute the corrections;
+// each patch writes omega_AS d_j to its own slot of a per-patch buffer and
+// patch_gather_kernel sums, per node, the contributions of the (at most 2^d)
+// patches whose interior holds it, in a fixed order.
 struct PatchMeta {
   int v[3];
   int g0[3];
@@ -525,21 +534,19 @@ struct PatchMeta {
 };
 
 template <int DIM>
-__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n, int colour) {
-  const int cx = colour_count(n, colour & 1), cy = colour_count(n, (colour >> 1) & 1);
-  const int cz = DIM == 3 ? colour_count(n, (colour >> 2) & 1) : 1;
-  const int64_t npatch = (int64_t)cx * cy * cz;
+__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n) {
+  const int nv = n - 1;
+  const int64_t npatch = DIM == 3 ? (int64_t)nv * nv * nv : (int64_t)nv * nv;
   for (int g = threadIdx.x; g < np; g += blockDim.x) {
     const int64_t pid = (int64_t)blockIdx.x * np + g;
     PatchMeta m;
     m.active = pid < npatch;
     int64_t t = m.active ? pid : 0;
-    const int ix = (int)(t % cx); t /= cx;
-    const int iy = (int)(t % cy); t /= cy;
-    const int iz = (int)t;
-    m.v[0] = 2 * ix + ((colour & 1) ? 1 : 2);
-    m.v[1] = 2 * iy + (((colour >> 1) & 1) ? 1 : 2);
-    m.v[2] = DIM == 3 ? 2 * iz + (((colour >> 2) & 1) ? 1 : 2) : 0;
+    m.v[0] = (int)(t % nv) + 1;
+    t /= nv;
+    m.v[1] = (int)(t % nv) + 1;
+    t /= nv;
+    m.v[2] = DIM == 3 ? (int)t + 1 : 0;
     for (int d = 0; d < 3; ++d) m.g0[d] = (d < DIM) ? K * (m.v[d] - 1) + 1 : 0;
     meta[g] = m;
   }
@@ -552,9 +559,10 @@ __device__ __forceinline__ int64_t patch_node(const PatchMeta& m, int i, int N1)
   return (int64_t)(m.g0[0] + ix) + (int64_t)N1 * ((m.g0[1] + iy) + (int64_t)N1 * (m.g0[2] + iz));
 }
 
+// Cartesian patches: gather r_j, Algorithm 2/3, write omega_AS d_j.
 template <int DIM, typename T>
-__global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ u, int n, int colour, int np,
-                                  int n_iter, const T* __restrict__ dinv, PatchParams<T> P) {
+__global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
+                                  const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
   using S = PatchShape<DIM>;
   constexpr int SZT = S::SZT;
   constexpr int RT = S::off_r(S::L - 1), DT = S::off_d(S::L - 1);
@@ -562,7 +570,9 @@ __global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ u, in
   __shared__ PatchMeta meta[kMaxPatchesPerBlock];
   const int stride = S::ELEMS + (n_iter > 1 ? 2 * SZT : 0);
   const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
-  patch_meta_init<DIM>(meta, np, n, colour);
+  T* sdinv = reinterpret_cast<T*>(smraw) + np * stride;  // inverse-diagonal tables of all p-levels
+  for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
+  patch_meta_init<DIM>(meta, np, n);
   __syncthreads();
   const int N1 = K * n + 1;
   pfor<SZT>(np, [&](int g, int i) {  // gather r_j = Pi_j r
@@ -570,28 +580,50 @@ __global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ u, in
     pb.at(g)[RT + i] = m.active ? r[patch_node<DIM>(m, i, N1)] : T(0);
   });
   __syncthreads();
-  const CartGeo<DIM, T> geo{dinv, P.scale, T(1) / P.scale, P.inv_a0};
+  const CartGeo<DIM, T> geo{sdinv, P.scale, T(1) / P.scale, P.inv_a0};
   local_solve<DIM, T>(pb, geo, P, n_iter, S::ELEMS);
-  // scatter u += omega_AS Pi_j^T d_j (patches of one colour are disjoint)
   pfor<SZT>(np, [&](int g, int i) {
-    const PatchMeta& m = meta[g];
-    if (m.active) u[patch_node<DIM>(m, i, N1)] += P.omega_as * pb.at(g)[DT + i];
+    if (meta[g].active) dst[((int64_t)blockIdx.x * np + g) * SZT + i] = P.omega_as * pb.at(g)[DT + i];
   });
 }
 
-// K = 1: every patch interior is the single vertex; the local solve is the
-// exact 1x1 inverse, so a colour sweep is u_v += omega_AS r_v / A_vv.
-template <int DIM, typename T>
-__global__ void patch_k1_kernel(const T* __restrict__ r, T* __restrict__ u, int n, T factor) {
-  const int64_t nv = DIM == 3 ? (int64_t)(n - 1) * (n - 1) * (n - 1) : (int64_t)(n - 1) * (n - 1);
-  const int N1 = n + 1;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % (n - 1)) + 1;
-    const int64_t rr = t / (n - 1);
-    const int y = (int)(rr % (n - 1)) + 1;
-    const int z = DIM == 3 ? (int)(rr / (n - 1)) + 1 : 0;
-    const int64_t g = x + (int64_t)N1 * (y + (int64_t)N1 * z);
-    u[g] += factor * r[g];
+// u (+)= sum over the patches whose interior holds the node of their
+// correction (patch buffer written by a patch kernel); boundary nodes get
+// no contribution.  Fixed summation order: patches by increasing vertex.
+template <int DIM, bool ADD, typename T>
+__global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ dst, T* __restrict__ u, int n) {
+  constexpr int MT = mp(K);
+  constexpr int SZT = ipow(MT, DIM);
+  const int N1 = K * n + 1, nv = n - 1;
+  const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    int gd[3] = {(int)(t % N1), (int)((t / N1) % N1), DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0};
+    int vlo[3], vcnt[3];
+    bool any = true;
+    for (int d = 0; d < DIM; ++d) {
+      const int g = gd[d], c = g / K, a = g - K * c;
+      int lo = a == 0 ? c : c, hi = a == 0 ? c : c + 1;  // vertices v with the node inside (v-1, v+1) cells
+      lo = lo < 1 ? 1 : lo;
+      hi = hi > nv ? nv : hi;
+      vlo[d] = lo;
+      vcnt[d] = hi - lo + 1;
+      if (vcnt[d] <= 0) any = false;
+    }
+    T s = T(0);
+    if (any) {
+      const int cz = DIM == 3 ? vcnt[2] : 1;
+      for (int jz = 0; jz < cz; ++jz)
+        for (int jy = 0; jy < vcnt[1]; ++jy)
+          for (int jx = 0; jx < vcnt[0]; ++jx) {
+            const int vx = vlo[0] + jx, vy = vlo[1] + jy, vz = DIM == 3 ? vlo[2] + jz : 1;
+            const int ix = gd[0] - (K * (vx - 1) + 1), iy = gd[1] - (K * (vy - 1) + 1);
+            const int iz = DIM == 3 ? gd[2] - (K * (vz - 1) + 1) : 0;
+            const int64_t pid = (vx - 1) + (int64_t)nv * ((vy - 1) + (int64_t)nv * (DIM == 3 ? vz - 1 : 0));
+            s += dst[pid * SZT + ix + MT * (iy + MT * iz)];
+          }
+    }
+    if (ADD) u[t] += s;
+    else u[t] = s;
   }
 }
 

@@ -135,43 +135,37 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
   }
 }
 
-// Global deformed apply, one parity colour of cells: y += SIGN * A_cell x.
-// Boundary nodes of y are written as 0.  `cpb` cells per block.
-template <int DIM, int SIGN, typename T>
-__global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ y, const float* __restrict__ G, int n,
-                                int colour, int cpb) {
+// Global deformed apply, all cells in one launch: the cell results go to a
+// per-cell buffer (cell-major, (K+1)^DIM values each) and cell_gather_kernel
+// sums, per node, the contributions of the (at most 2^d) cells holding it in
+// a fixed order.  `cpb` cells per block.
+template <int DIM, typename T>
+__global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ cellout, const float* __restrict__ G, int n,
+                                int cpb) {
   constexpr int l = nlev(K) - 1;
   constexpr int n1 = K + 1;
   constexpr int NP = ipow(n1, DIM);
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int cell_of[kMaxPatchesPerBlock][4];
   T* base = reinterpret_cast<T*>(smraw);
-  const int cx = (colour & 1) ? n / 2 : (n + 1) / 2, cy = ((colour >> 1) & 1) ? n / 2 : (n + 1) / 2;
-  const int cz = DIM == 3 ? (((colour >> 2) & 1) ? n / 2 : (n + 1) / 2) : 1;
-  const int64_t ncell = (int64_t)cx * cy * cz;
+  const int64_t ncell = DIM == 3 ? (int64_t)n * n * n : (int64_t)n * n;
   for (int g = threadIdx.x; g < cpb; g += blockDim.x) {
     const int64_t cid = (int64_t)blockIdx.x * cpb + g;
     int64_t t = cid < ncell ? cid : 0;
-    cell_of[g][0] = 2 * (int)(t % cx) + (colour & 1);
-    t /= cx;
-    cell_of[g][1] = 2 * (int)(t % cy) + ((colour >> 1) & 1);
-    t /= cy;
-    cell_of[g][2] = DIM == 3 ? 2 * (int)t + ((colour >> 2) & 1) : 0;
+    cell_of[g][0] = (int)(t % n);
+    t /= n;
+    cell_of[g][1] = (int)(t % n);
+    cell_of[g][2] = DIM == 3 ? (int)(t / n) : 0;
     cell_of[g][3] = cid < ncell;
   }
   __syncthreads();
   const int N1 = K * n + 1;
   auto tile = [&](int g, int) { return base + g * 5 * NP; };
-  auto node = [&](int g, int i, bool& bnd) {
+  pfor<NP>(cpb, [&](int g, int i) {
     const int ax = i % n1, ay = (i / n1) % n1, az = DIM == 3 ? i / (n1 * n1) : 0;
     const int gx = K * cell_of[g][0] + ax, gy = K * cell_of[g][1] + ay, gz = K * cell_of[g][2] + az;
-    bnd = gx == 0 || gx == N1 - 1 || gy == 0 || gy == N1 - 1 || (DIM == 3 && (gz == 0 || gz == N1 - 1));
-    return gx + (int64_t)N1 * (gy + (int64_t)N1 * gz);
-  };
-  pfor<NP>(cpb, [&](int g, int i) {
-    bool bnd;
-    const int64_t gi = node(g, i, bnd);
-    tile(g, 0)[i] = (cell_of[g][3] && !bnd) ? x[gi] : T(0);
+    const bool bnd = gx == 0 || gx == N1 - 1 || gy == 0 || gy == N1 - 1 || (DIM == 3 && (gz == 0 || gz == N1 - 1));
+    tile(g, 0)[i] = (cell_of[g][3] && !bnd) ? x[gx + (int64_t)N1 * (gy + (int64_t)N1 * gz)] : T(0);
   });
   __syncthreads();
   auto gptr = [&](int g, int) {
@@ -180,16 +174,51 @@ __global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ y, cons
   };
   cell_op<DIM, l, 1, T>(cpb, tile, gptr);
   pfor<NP>(cpb, [&](int g, int i) {
-    if (!cell_of[g][3]) return;
-    bool bnd;
-    const int64_t gi = node(g, i, bnd);
-    if (bnd) y[gi] = T(0);
-    else y[gi] += (SIGN > 0 ? tile(g, 0)[i] : -tile(g, 0)[i]);
+    if (cell_of[g][3]) cellout[((int64_t)blockIdx.x * cpb + g) * NP + i] = tile(g, 0)[i];
   });
 }
 
+// y = sum of the cell contributions at each node (b == nullptr), or
+// y = b - that sum; boundary nodes of y are 0.
 template <int DIM, typename T>
-static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, int n, cudaStream_t st) {
+__global__ void __launch_bounds__(256) cell_gather_kernel(const T* __restrict__ cellout, T* __restrict__ y,
+                                                          const T* __restrict__ b, int n) {
+  constexpr int n1 = K + 1;
+  const int N1 = K * n + 1;
+  const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    const int gd[3] = {(int)(t % N1), (int)((t / N1) % N1), DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0};
+    bool bnd = false;
+    int clo[3], ccnt[3];
+    for (int d = 0; d < DIM; ++d) {
+      const int g = gd[d];
+      bnd |= g == 0 || g == N1 - 1;
+      const int c = g / K, a = g - K * c;
+      int lo = (a == 0 && c > 0) ? c - 1 : c, hi = c;
+      hi = hi > n - 1 ? n - 1 : hi;
+      clo[d] = lo;
+      ccnt[d] = hi - lo + 1;
+    }
+    if (bnd) {
+      y[t] = T(0);
+      continue;
+    }
+    T s = T(0);
+    const int cz = DIM == 3 ? ccnt[2] : 1;
+    for (int jz = 0; jz < cz; ++jz)
+      for (int jy = 0; jy < ccnt[1]; ++jy)
+        for (int jx = 0; jx < ccnt[0]; ++jx) {
+          const int cx = clo[0] + jx, cy = clo[1] + jy, czz = DIM == 3 ? clo[2] + jz : 0;
+          const int ax = gd[0] - K * cx, ay = gd[1] - K * cy, az = DIM == 3 ? gd[2] - K * czz : 0;
+          const int64_t cell = cx + (int64_t)n * (cy + (int64_t)n * czz);
+          s += cellout[cell * ipow(n1, DIM) + ax + n1 * (ay + n1 * az)];
+        }
+    y[t] = b ? b[t] - s : s;
+  }
+}
+
+template <int DIM, typename T>
+static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, T* cellbuf, int n, cudaStream_t st) {
   constexpr int n1 = K + 1;
   constexpr int NP = ipow(n1, DIM);
   constexpr int LINES = ipow(n1, DIM - 1);
@@ -200,31 +229,23 @@ static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, int
   const int threads = std::min(256, (cpb * LINES + 31) / 32 * 32);
   const int smem = cpb * 5 * NP * (int)sizeof(T);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
-  cudaError_t e;
-  if (b) e = cudaMemcpyAsync(y, b, sizeof(T) * (size_t)ipow(K * n + 1, DIM), cudaMemcpyDeviceToDevice, st);
-  else e = cudaMemsetAsync(y, 0, sizeof(T) * (size_t)ipow(K * n + 1, DIM), st);
-  if (e != cudaSuccess) return e;
-  for (int colour = 0; colour < (1 << DIM); ++colour) {
-    const int cx = (colour & 1) ? n / 2 : (n + 1) / 2, cy = ((colour >> 1) & 1) ? n / 2 : (n + 1) / 2;
-    const int cz = DIM == 3 ? (((colour >> 2) & 1) ? n / 2 : (n + 1) / 2) : 1;
-    const int64_t nc = (int64_t)cx * cy * cz;
-    if (nc == 0) continue;
-    const unsigned blocks = (unsigned)((nc + cpb - 1) / cpb);
-    if (b) def_cell_kernel<DIM, -1, T><<<blocks, threads, smem, st>>>(x, y, G, n, colour, cpb);
-    else def_cell_kernel<DIM, 1, T><<<blocks, threads, smem, st>>>(x, y, G, n, colour, cpb);
-    g_launches += 1;
-  }
+  const int64_t ncell = DIM == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  def_cell_kernel<DIM, T><<<(unsigned)((ncell + cpb - 1) / cpb), threads, smem, st>>>(x, cellbuf, G, n, cpb);
+  const int64_t N = ipow(K * n + 1, DIM);
+  cell_gather_kernel<DIM, T><<<grid_for(N, 256), 256, 0, st>>>(cellbuf, y, b, n);
+  g_launches += 2;
   return cudaGetLastError();
 }
 
-static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const void* b, const float* G, int n,
-                             cudaStream_t s) {
+static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const void* b, const float* G, void* cellbuf,
+                             int n, cudaStream_t s) {
   if (prec == 0) {
-    if (dim == 3) return def_apply_t<3, double>((const double*)x, (double*)y, (const double*)b, G, n, s);
-    return def_apply_t<2, double>((const double*)x, (double*)y, (const double*)b, G, n, s);
+    if (dim == 3)
+      return def_apply_t<3, double>((const double*)x, (double*)y, (const double*)b, G, (double*)cellbuf, n, s);
+    return def_apply_t<2, double>((const double*)x, (double*)y, (const double*)b, G, (double*)cellbuf, n, s);
   }
-  if (dim == 3) return def_apply_t<3, float>((const float*)x, (float*)y, (const float*)b, G, n, s);
-  return def_apply_t<2, float>((const float*)x, (float*)y, (const float*)b, G, n, s);
+  if (dim == 3) return def_apply_t<3, float>((const float*)x, (float*)y, (const float*)b, G, (float*)cellbuf, n, s);
+  return def_apply_t<2, float>((const float*)x, (float*)y, (const float*)b, G, (float*)cellbuf, n, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,8 +347,8 @@ struct DefGeo {
 };
 
 template <int DIM, typename T>
-__global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ u, int n, int colour, int np,
-                                 int n_iter, DefLevelT<T> lev, const T* __restrict__ dinv1, PatchParams<T> P) {
+__global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
+                                 DefLevelT<T> lev, const T* __restrict__ dinv1, PatchParams<T> P) {
   using S = PatchShape<DIM>;
   using DS = DefShape<DIM>;
   constexpr int SZT = S::SZT;
@@ -337,7 +358,7 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ u, int
   __shared__ T inv_a0[kMaxPatchesPerBlock];
   const int stride = DS::ELEMS + (n_iter > 1 ? 2 * SZT : 0);
   const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
-  patch_meta_init<DIM>(meta, np, n, colour);
+  patch_meta_init<DIM>(meta, np, n);
   __syncthreads();
   for (int g = threadIdx.x; g < np; g += blockDim.x) {  // p = 1: the vertex's inverse Q1 diagonal
     const int* v = meta[g].v;
@@ -356,8 +377,7 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ u, int
   geo.n = n;
   local_solve<DIM, T>(pb, geo, P, n_iter, DS::ELEMS);
   pfor<SZT>(np, [&](int g, int i) {
-    const PatchMeta& m = meta[g];
-    if (m.active) u[patch_node<DIM>(m, i, N1)] += P.omega_as * pb.at(g)[DT + i];
+    if (meta[g].active) dst[((int64_t)blockIdx.x * np + g) * SZT + i] = P.omega_as * pb.at(g)[DT + i];
   });
 }
 
@@ -372,14 +392,10 @@ static int patch_def_smem(int dim, int prec, int n_iter) {
 }
 
 template <int DIM, typename T>
-static cudaError_t patch_def_t(const T* r, T* u, int n, int colour, int np, int n_iter, const DefLevel& L,
+static cudaError_t patch_def_t(const T* r, T* dst, int n, int np, int n_iter, const DefLevel& L,
                                const PatchParamsHost& H, cudaStream_t st) {
   if (n < 2) return cudaSuccess;
-  const int cx = (colour & 1) ? n / 2 : (n - 1) / 2;
-  const int cy = ((colour >> 1) & 1) ? n / 2 : (n - 1) / 2;
-  const int cz = DIM == 3 ? (((colour >> 2) & 1) ? n / 2 : (n - 1) / 2) : 1;
-  const int64_t npatch = (int64_t)cx * cy * cz;
-  if (npatch == 0) return cudaSuccess;
+  const int64_t npatch = ipow(n - 1, DIM);
   if (np < 1 || np > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
   const int smem = np * patch_def_smem(DIM, sizeof(T) == 8 ? 0 : 1, n_iter);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
@@ -390,20 +406,20 @@ static cudaError_t patch_def_t(const T* r, T* u, int n, int colour, int np, int 
     lev.dinv[i] = (const T*)L.dinv[i];
   }
   const unsigned blocks = (unsigned)((npatch + np - 1) / np);
-  patch_def_kernel<DIM, T><<<blocks, threads, smem, st>>>(r, u, n, colour, np, n_iter, lev, (const T*)L.dinv1,
+  patch_def_kernel<DIM, T><<<blocks, threads, smem, st>>>(r, dst, n, np, n_iter, lev, (const T*)L.dinv1,
                                                           to_params<T>(H));
   g_launches += 1;
   return cudaGetLastError();
 }
 
-static cudaError_t patch_def(int dim, int prec, const void* r, void* u, int n, int colour, int np, int n_iter,
+static cudaError_t patch_def(int dim, int prec, const void* r, void* dst, int n, int np, int n_iter,
                              const DefLevel& L, const PatchParamsHost& P, cudaStream_t s) {
   if (prec == 0) {
-    if (dim == 3) return patch_def_t<3, double>((const double*)r, (double*)u, n, colour, np, n_iter, L, P, s);
-    return patch_def_t<2, double>((const double*)r, (double*)u, n, colour, np, n_iter, L, P, s);
+    if (dim == 3) return patch_def_t<3, double>((const double*)r, (double*)dst, n, np, n_iter, L, P, s);
+    return patch_def_t<2, double>((const double*)r, (double*)dst, n, np, n_iter, L, P, s);
   }
-  if (dim == 3) return patch_def_t<3, float>((const float*)r, (float*)u, n, colour, np, n_iter, L, P, s);
-  return patch_def_t<2, float>((const float*)r, (float*)u, n, colour, np, n_iter, L, P, s);
+  if (dim == 3) return patch_def_t<3, float>((const float*)r, (float*)dst, n, np, n_iter, L, P, s);
+  return patch_def_t<2, float>((const float*)r, (float*)dst, n, np, n_iter, L, P, s);
 }
 
 }  // namespace PMG_KNS

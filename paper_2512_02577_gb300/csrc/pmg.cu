@@ -109,6 +109,7 @@ struct Plan {
   };
   std::vector<LOff> lo;
   int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad, cx0, cy0;
+  int64_t pbuf = -1, cellbuf = -1;
   int64_t dtab_len = 0;
 };
 
@@ -194,6 +195,11 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   const int64_t N0 = ipow64((int64_t)P.K * P.n0 + 1, P.dim);
   P.cx0 = bump(cur, N0 * 8);  // unit vectors and operator columns of the coarse set-up
   P.cy0 = bump(cur, N0 * 8);
+  // per-patch corrections of one smoothing step (finest level; reused by the
+  // coarser ones) and, deformed, per-cell operator results (FP64 for the CG)
+  const int nf = cfg->n_cells;
+  P.pbuf = bump(cur, std::max<int64_t>(ipow64(std::max(nf - 1, 0), P.dim) * ipow64(2 * P.K - 1, P.dim), 1) * P.mg_es);
+  if (P.deformed) P.cellbuf = bump(cur, ipow64(nf, P.dim) * ipow64(P.K + 1, P.dim) * 8);
   P.total = cur;
   return PMG_OK;
 }
@@ -233,6 +239,8 @@ struct pmg_ctx {
   int* cidx = nullptr;
   void* ainv = nullptr;
   bool coarse_ready = false;
+  void* pbuf = nullptr;
+  void* cellbuf = nullptr;
   int ppc = 1;
   double omega_as = 0;
   double omega_j[4] = {1, 1, 1, 1};
@@ -277,7 +285,7 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   LevelData& L = c->lv[level];
   cudaError_t e;
   if (c->deformed) {
-    e = c->kt->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], L.n, c->stream);
+    e = c->kt->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cellbuf, L.n, c->stream);
   } else {
     void** t = prec == PMG_FP64 ? (void**)c->t64 : c->t_mg;
     e = c->kt->cart_apply(c->dim, prec, u, r, b, t[0], t[1], t[2], t[3], L.n, L.scale, c->stream);
@@ -286,8 +294,9 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   return PMG_OK;
 }
 
-// Patch corrections of one parity colour: u += omega_AS sum_{j in colour} Pi_j^T V_j Pi_j r.
-int patch_sweep_colour(pmg_ctx* c, int level, const void* r, void* u, int colour) {
+// Local solves of every patch of the level for the residual r, written to
+// the patch buffer as omega_AS d_j (one launch).
+int patch_solves(pmg_ctx* c, int level, const void* r) {
   LevelData& L = c->lv[level];
   const PatchParamsHost P = patch_params(c, level);
   cudaError_t e;
@@ -298,19 +307,21 @@ int patch_sweep_colour(pmg_ctx* c, int level, const void* r, void* u, int colour
       D.dinv[i] = L.dinv[i];
     }
     D.dinv1 = L.dinv1;
-    e = c->kt->patch_def(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+    e = c->kt->patch_def(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
   } else {
-    e = c->kt->patch_cart(c->dim, c->mgprec, r, u, L.n, colour, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
+    e = c->kt->patch_cart(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
                           c->stream);
   }
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
   return PMG_OK;
 }
 
-// One additive sweep's patch corrections: u += S r (all 2^d colours).
-int patch_sweep(pmg_ctx* c, int level, const void* r, void* u) {
-  for (int colour = 0; colour < (1 << c->dim); ++colour)
-    if (int rc = patch_sweep_colour(c, level, r, u, colour)) return rc;
+// One additive sweep's correction: u (+)= omega_AS sum_j Pi_j^T V_j Pi_j r
+// (add = false: u = that correction, the zero-initial-guess pre-smoothing).
+int patch_sweep(pmg_ctx* c, int level, const void* r, void* u, bool add) {
+  if (int rc = patch_solves(c, level, r)) return rc;
+  cudaError_t e = c->kt->patch_gather(c->dim, c->mgprec, c->pbuf, u, c->lv[level].n, add ? 1 : 0, c->stream);
+  if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch gather: ") + cudaGetErrorString(e));
   return PMG_OK;
 }
 
@@ -319,7 +330,7 @@ int smooth_level(pmg_ctx* c, int level, const void* b, void* u, int sweeps) {
   for (int s = 0; s < sweeps; ++s) {
     int rc = level_apply(c, level, c->mgprec, u, L.r, b);
     if (rc) return rc;
-    rc = patch_sweep(c, level, L.r, u);
+    rc = patch_sweep(c, level, L.r, u, true);
     if (rc) return rc;
   }
   return PMG_OK;
@@ -335,12 +346,12 @@ int vcycle_level(pmg_ctx* c, int level) {
     if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("coarse: ") + cudaGetErrorString(e));
     return PMG_OK;
   }
-  PMG_CUDA(cudaMemsetAsync(L.u, 0, es * L.N, c->stream));
+  (void)es;
   const int nu = c->cfg.smooth_steps;
   int rc;
   for (int s = 0; s < nu; ++s) {
     if (s == 0) {
-      rc = patch_sweep(c, level, L.b, L.u);  // zero guess: the residual is b
+      rc = patch_sweep(c, level, L.b, L.u, false);  // zero guess: the residual is b, u = S b
     } else {
       rc = smooth_level(c, level, L.b, L.u, 1);
     }
@@ -440,8 +451,8 @@ int precondition(pmg_ctx* c, const double* r, double* z) {
 
 // ---------------------------------------------------------------- autotuner
 // Patches per thread block of the smoother kernels, per (dim, degree, MG
-// precision, geometry, local cycles): every admissible value is timed on one
-// parity colour of the finest level (CUDA events, best of 3 after a warm-up)
+// precision, geometry, local cycles): every admissible value is timed on the
+// patch launch of the finest level (CUDA events, best of 3 after a warm-up)
 // and the fastest is kept for the process; with PMG_TUNE_FILE set, results
 // are also read from and appended to that file ("dim k prec geom cycles ppc"
 // per line).  Small meshes, whose launches are too short to time, use the
@@ -482,7 +493,9 @@ int admissible_ppc(const pmg_ctx* c, int ppc) {
   const int smem = c->deformed ? c->kt->patch_def_smem(c->dim, c->mgprec, c->cfg.local_cycles)
                                : c->kt->patch_smem(c->dim, c->mgprec, c->cfg.local_cycles);
   const int maxt = c->kt->patch_max_threads(c->dim, c->mgprec, c->deformed ? 1 : 0);
-  return ppc >= 1 && ppc <= 64 && (ppc * tpp + 31) / 32 * 32 <= std::min(1024, maxt) && ppc * smem <= kMaxDynSmem;
+  const int extra = c->deformed ? 0 : c->kt->patch_cart_extra_smem(c->dim, c->mgprec);
+  return ppc >= 1 && ppc <= 64 && (ppc * tpp + 31) / 32 * 32 <= std::min(1024, maxt) &&
+         ppc * smem + extra <= kMaxDynSmem;
 }
 
 int rule_ppc(const pmg_ctx* c) {
@@ -523,13 +536,16 @@ int choose_patches_per_block(pmg_ctx* c) {
   float best = 1e30f;
   int best_ppc = c->ppc;
   const int64_t before = g_launches.load();
+  const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
   for (int ppc = 1; ppc <= 64; ++ppc) {
     if (!admissible_ppc(c, ppc)) continue;
+    const int thr = ppc * tpp, padded = (thr + 31) / 32 * 32;
+    if (ppc > 2 && thr < 0.85 * padded) continue;  // warps with many idle lanes: not worth timing
     c->ppc = ppc;
     float tmin = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, c->stream);
-      int rc = patch_sweep_colour(c, c->L - 1, F.r, F.u, 0);
+      int rc = patch_solves(c, c->L - 1, F.r);
       cudaEventRecord(e1, c->stream);
       if (rc) {  // a launch the device rejects (resources): not a candidate
         cudaGetLastError();
@@ -592,6 +608,8 @@ int setup_context(pmg_ctx* c) {
   c->dtab_mg = c->mg32 ? (void*)c->dtab32 : (void*)c->dtab64;
   c->cidx = (int*)at(c, P.cidx);
   c->ainv = at(c, P.ainv);
+  c->pbuf = at(c, P.pbuf);
+  c->cellbuf = at(c, P.cellbuf);
 
   // coefficients and kernel attributes
   std::vector<double> coef(kMaxCoef, 0.0);
@@ -1003,6 +1021,40 @@ int pmg_synchronize(pmg_ctx* c) {
 }
 
 int64_t pmg_launch_count(void) { return g_launches.load(); }
+
+int pmg_smoother_phase_times(pmg_ctx* c, int level, int reps, double* ms) {
+  if (check_ctx(c) || !ms) return fail(PMG_ERR_ARG, "NULL argument");
+  if (level < 1 || level >= c->L) return fail(PMG_ERR_ARG, "smoothing level must be in 1..n_levels-1");
+  if (reps < 1) return fail(PMG_ERR_ARG, "reps < 1");
+  LevelData& L = c->lv[level];
+  cudaEvent_t ev[4];
+  for (auto& e : ev) PMG_CUDA(cudaEventCreate(&e));
+  double acc[3] = {0, 0, 0};
+  int rc = PMG_OK;
+  for (int it = 0; it <= reps && rc == PMG_OK; ++it) {  // iteration 0 warms up
+    cudaEventRecord(ev[0], c->stream);
+    rc = level_apply(c, level, c->mgprec, L.u, L.r, L.b);
+    cudaEventRecord(ev[1], c->stream);
+    if (!rc) rc = patch_solves(c, level, L.r);
+    cudaEventRecord(ev[2], c->stream);
+    if (!rc) {
+      cudaError_t e = c->kt->patch_gather(c->dim, c->mgprec, c->pbuf, L.u, L.n, 1, c->stream);
+      if (e != cudaSuccess) rc = fail(PMG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaEventRecord(ev[3], c->stream);
+    cudaEventSynchronize(ev[3]);
+    if (it > 0)
+      for (int k = 0; k < 3; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+        acc[k] += t;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+  return PMG_OK;
+}
 
 int pmg_patches_per_block(const pmg_ctx* c, int* ppc) {
   if (check_ctx(c) || !ppc) return fail(PMG_ERR_ARG, "NULL argument");

@@ -30,9 +30,12 @@ struct KernelTable {
   // y = A x (b == nullptr) or y = b - A x; Cartesian; t0..t3: scratch of N
   cudaError_t (*cart_apply)(int dim, int prec, const void* x, void* y, const void* b, void* t0, void* t1,
                             void* t2, void* t3, int n, double scale, cudaStream_t s);
-  // one parity colour of the Cartesian patch smoother
-  cudaError_t (*patch_cart)(int dim, int prec, const void* r, void* u, int n, int colour, int ppc, int n_iter,
+  // Cartesian patch smoother, every patch of the level: dst[patch][i] = omega_AS d_j[i]
+  cudaError_t (*patch_cart)(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                             const void* dinv, const PatchParamsHost& P, cudaStream_t s);
+  // u (+)= sum over the patches holding each node of dst (add = 0: u = sum)
+  cudaError_t (*patch_gather)(int dim, int prec, const void* dst, void* u, int n, int add, cudaStream_t s);
+  int (*patch_cart_extra_smem)(int dim, int prec);  // block shared bytes besides its patches
   int (*patch_threads)(int dim);                  // threads per patch
   int (*patch_smem)(int dim, int prec, int n_iter);  // shared bytes per patch
   // u_f += P u_c  /  r_c = P^T r_f  (nc = coarse cells per side); t0, t1 scratch of N_f
@@ -40,11 +43,12 @@ struct KernelTable {
                                cudaStream_t s);
   cudaError_t (*h_restrict)(int dim, int prec, const void* rf, void* rc, void* t0, void* t1, int nc,
                             cudaStream_t s);
-  // deformed geometry: y = A x or y = b - A x with stored G (float32)
-  cudaError_t (*def_apply)(int dim, int prec, const void* x, void* y, const void* b, const float* G, int n,
-                           cudaStream_t s);
-  // one colour of the deformed patch smoother
-  cudaError_t (*patch_def)(int dim, int prec, const void* r, void* u, int n, int colour, int ppc, int n_iter,
+  // deformed geometry: y = A x or y = b - A x with stored G (float32); cellbuf:
+  // n^d (K+1)^d scratch values
+  cudaError_t (*def_apply)(int dim, int prec, const void* x, void* y, const void* b, const float* G, void* cellbuf,
+                           int n, cudaStream_t s);
+  // deformed patch smoother, every patch of the level (output as patch_cart)
+  cudaError_t (*patch_def)(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                            const DefLevel& lev, const PatchParamsHost& P, cudaStream_t s);
   int (*patch_def_threads)(int dim);
   int (*patch_def_smem)(int dim, int prec, int n_iter);
