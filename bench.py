@@ -179,6 +179,124 @@ def cpu_baseline_entry(res):
                       % (res["dofs"], len(res["times"]))}
 
 
+# ----------------------------------------------------------------- extra sections
+HBM_GBS = 6794.8  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+
+
+def _timed_ms(torch, stream, flush, fn, reps=5):
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def extra_sections(p, torch, dev, stream, flush):
+    """Deformed 96^3 Q3 (24,137,569 DoFs, FP32 G_q, mixed precision) and a
+    bounded serving sample; reported beside the headline, outside its timing."""
+    out = {}
+    n, k = 96, 3
+    ctx = p.Context(p.make_config(dim=3, n_cells=n, degree=k, geometry=p.DEFORMED, mg_precision=p.FP32),
+                    stream=stream, device=dev)
+    N = ctx.num_dofs()
+    b = torch.empty(N, dtype=torch.float64, device=dev)
+    ctx.rhs_manufactured(b)
+    b32 = b.float()
+    y32 = torch.empty_like(b32)
+    x = torch.zeros_like(b)
+    t_apply32 = _timed_ms(torch, stream, flush, lambda: ctx.apply(b32, y32, prec=p.FP32))
+    t_apply64 = _timed_ms(torch, stream, flush, lambda: ctx.apply(b, x, prec=p.FP64), reps=3)
+    phases = ctx.smoother_phase_times(reps=3)
+    ctx.solve(b, x)
+    solves = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        solves.append(ctx.solve(b, x))
+    err = ctx.l2_error_manufactured(x)
+    ncell = n ** 3
+    g_bytes = ncell * (k + 1) ** 3 * 6 * 4
+    alg_bytes = 8 * N + g_bytes  # x read + y write (FP32) + G_q read
+    out["deformed_96_q3_mixed"] = {
+        "dofs": N, "solve_ms_p50": pct([s.time_ms for s in solves], 50), "iterations": solves[-1].iterations,
+        "rel_residual": solves[-1].rel_residual, "l2_error": err,
+        "apply_fp32_ms": t_apply32, "apply_fp64_ms": t_apply64,
+        "apply_fp32_roofline": {"bound": "hbm", "achieved": alg_bytes / (t_apply32 * 1e-3) / 1e9, "peak": HBM_GBS,
+                                "unit": "GB/s", "frac": alg_bytes / (t_apply32 * 1e-3) / 1e9 / HBM_GBS,
+                                "algorithmic_bytes": alg_bytes},
+        "smoother_phases_ms": {"residual": phases[0], "patch": phases[1], "gather": phases[2]},
+    }
+    ctx.close()
+    del b, b32, y32, x
+    from paper_2512_02577_gb300 import serve
+    from paper_2512_02577_gb300.inputs import serving_requests
+    reqs = serving_requests(n_requests=64, rate=50.0, n_hi=32)
+    _, summ = serve.run(reqs, precision=p.FP32, max_active=16)
+    out["serving_sample"] = dict(summ, workload="64 Poisson solves, Poisson arrivals 50/s, n in {8,16,32} "
+                                                "(log-uniform, snapped), k uniform 2..7, N(0,1) RHS, FP32 V-cycle, "
+                                                "FP64 CG, rtol 1e-8, 16 slots")
+    return out
+
+
+def degree_sweep():
+    """k = 1..8 on the unit cube: apply and sweep at n = round(200/k) (~8M
+    DoFs), FP64 and mixed solves on the nearest power-of-two mesh whose
+    coarse level stays small; N(0,1) right-hand side (seed 20251202 + k)."""
+    import torch
+    import paper_2512_02577_gb300 as p
+    from paper_2512_02577_gb300.inputs import random_vector
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rows = []
+    with torch.cuda.stream(stream):
+        for k in range(1, 9):
+            n = int(round(200.0 / k))
+            row = {"k": k, "n": n}
+            for prec in (p.FP64, p.FP32):
+                ctx = p.Context(p.make_config(dim=3, n_cells=n, degree=k, n_levels=1 if n % 2 else 2,
+                                              mg_precision=prec), stream=stream, device=dev)
+                N = ctx.num_dofs()
+                dt = torch.float64 if prec == p.FP64 else torch.float32
+                xv = torch.randn(N, dtype=dt, device=dev)
+                yv = torch.empty_like(xv)
+                ta = _timed_ms(torch, stream, flush, lambda: ctx.apply(xv, yv, prec=prec))
+                tag = "fp64" if prec == p.FP64 else "fp32"
+                row["dofs_apply"] = N
+                row["apply_%s_ms" % tag] = ta
+                row["apply_%s_gdofs" % tag] = N / ta / 1e6
+                if n % 2 == 0:
+                    ph = ctx.smoother_phase_times(reps=2)
+                    row["sweep_%s_ms" % tag] = sum(ph)
+                    row["sweep_%s_gdofs" % tag] = N / sum(ph) / 1e6
+                ctx.close()
+            ns = 2 ** int(round(__import__("math").log2(200.0 / k)))
+            row["n_solve"] = ns
+            for prec in (p.FP64, p.FP32):
+                ctx = p.Context(p.make_config(dim=3, n_cells=ns, degree=k, mg_precision=prec), stream=stream,
+                                device=dev)
+                b = torch.tensor(random_vector(3, ns, k, seed=20251202 + k), device=dev)
+                x = torch.zeros_like(b)
+                ctx.solve(b, x)
+                infos = [ctx.solve(b, x) for _ in range(2)]
+                tag = "fp64" if prec == p.FP64 else "mixed"
+                row["dofs_solve"] = ctx.num_dofs()
+                row["solve_%s_ms" % tag] = min(i.time_ms for i in infos)
+                row["iterations_%s" % tag] = infos[-1].iterations
+                row["rel_residual_%s" % tag] = infos[-1].rel_residual
+                ctx.close()
+            row["mixed_speedup"] = row["solve_fp64_ms"] / row["solve_mixed_ms"]
+            print(json.dumps(row), flush=True)
+            rows.append(row)
+    print(json.dumps({"degree_sweep": rows}))
+
+
 # ----------------------------------------------------------------- profiling
 def profile_region(region, n_def):
     """One NVTX range named 'profile' after warm-up, for
@@ -220,6 +338,21 @@ def profile_region(region, n_def):
             torch.cuda.nvtx.range_pop()
 
 
+# ----------------------------------------------------------------- ranks
+def reduce_over_ranks(local_ms, local_dofs, device=None):
+    """Replicas: the job's time is the slowest rank's, its work the sum of
+    all ranks' DoFs.  Single process: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms), float(local_dofs)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(local_dofs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 # ----------------------------------------------------------------- main
 def pct(xs, q):
     xs = sorted(xs)
@@ -239,12 +372,17 @@ def main():
     ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "deformed"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
     ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
+    ap.add_argument("--no-extras", action="store_true", help="skip the deformed and serving sections")
+    ap.add_argument("--sweep", action="store_true", help="degree sweep k = 1..8 at ~8M DoFs (separate JSON)")
     args = ap.parse_args()
     if args.oracle_child is not None:
         oracle_child(args.oracle_child)
         return
     if args.profile_region:
         profile_region(args.profile_region, args.profile_n)
+        return
+    if args.sweep:
+        degree_sweep()
         return
     args.warmup = max(args.warmup, 3)
 
@@ -329,13 +467,9 @@ def main():
             torch.distributed.barrier()
         clocks.stop()
         step_ms = [a.elapsed_time(z) for a, z in ev]
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms, total_dofs = reduce_over_ranks(sum(step_ms), N * args.steps, dev)
         ms_per_step = total_ms / args.steps
-        value = world * N * args.steps / (total_ms * 1e-3)
+        value = total_dofs / (total_ms * 1e-3)
 
         # ---- component timings (not part of value): apply, sweep, residual, solves
         def timed(fn, reps):
@@ -405,6 +539,7 @@ def main():
         for _ in range(args.steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t0) / args.steps
+        extra = {} if args.no_extras else extra_sections(p, torch, dev, stream, flush)
     if rank != 0:
         return
     line = {
@@ -437,6 +572,7 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    line.update(extra)
     print(json.dumps(line))
 
 

@@ -38,7 +38,7 @@ enum pmg_status {
   PMG_OK = 0,
   PMG_NOT_CONVERGED = 1,
   PMG_ERR_ARG = -1,          /* invalid argument (NULL pointer, bad level, bad size) */
-  PMG_ERR_UNSUPPORTED = -2,  /* dim not 2/3, degree not 1..8, coarse problem too large */
+  PMG_ERR_UNSUPPORTED = -2,  /* dim not 2/3, degree not 1..8; V-cycle/solve on a coarse level above 4096 free DoFs */
   PMG_ERR_OOM = -3,          /* device workspace could not be allocated / too small */
   PMG_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed */
   PMG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired */
@@ -80,6 +80,10 @@ typedef struct pmg_solve_info {
 /* Fill *cfg with defaults: 3D, n 8, k 2, automatic levels, Cartesian, FP64,
  * default damping, one local cycle, one smoothing step. */
 void pmg_config_default(pmg_config* cfg);
+
+/* Coarsest levels with more than 4096 free DoFs are accepted: such a context
+ * applies, computes residuals and smooths, while pmg_vcycle and pmg_solve
+ * return PMG_ERR_UNSUPPORTED. */
 
 /* Device bytes the context for *cfg needs (hierarchy vectors, geometry,
  * inverse diagonals, coarse inverse, scratch).  Allocates nothing; used by

@@ -101,7 +101,8 @@ struct Plan {
   int dim = 3, K = 2, nlev = 1, nplev = 1, n0 = 1, mg_es = 8;
   bool deformed = false, mg32 = false;
   std::vector<int> ns;
-  int nc = 0;  // free DoFs on the coarsest level
+  int nc = 0;  // free DoFs on the coarsest level (0 if above the dense limit)
+  bool coarse_ok = true;
   int64_t total = 0;
   // offsets
   struct LOff {
@@ -151,8 +152,10 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   for (int l = 0; l < L; ++l) P.ns[l] = P.n0 << l;
   const int64_t nc1 = (int64_t)P.K * P.n0 - 1;
   const int64_t nc = ipow64(std::max<int64_t>(nc1, 0), P.dim);
-  if (nc > kMaxCoarse) return fail(PMG_ERR_UNSUPPORTED, "coarsest level has more than 4096 free DoFs");
-  P.nc = (int)nc;
+  // a coarse problem above the dense limit leaves apply / residual / smooth
+  // usable; V-cycles and solves are then rejected
+  P.coarse_ok = nc <= kMaxCoarse;
+  P.nc = P.coarse_ok ? (int)nc : 0;
   const int ncomp = P.dim == 3 ? 6 : 3;
   int64_t cur = 0;
   P.lo.resize(L);
@@ -373,6 +376,8 @@ int vcycle_level(pmg_ctx* c, int level) {
 // pivoting), store the inverse in the MG precision.
 int ensure_coarse(pmg_ctx* c) {
   if (c->coarse_ready) return PMG_OK;
+  if (!c->plan.coarse_ok)
+    return fail(PMG_ERR_UNSUPPORTED, "coarsest level has more than 4096 free DoFs: no V-cycle or solve");
   LevelData& C = c->lv[0];
   const int N1 = C.N1;
   std::vector<int> idx;

@@ -37,7 +37,6 @@ def test_status_strings():
     (dict(dim=4), p.PMG_ERR_UNSUPPORTED),
     (dict(n_cells=0), p.PMG_ERR_ARG),
     (dict(n_cells=12, n_levels=4), p.PMG_ERR_UNSUPPORTED),   # 12 not divisible by 8
-    (dict(n_cells=5, degree=8), p.PMG_ERR_UNSUPPORTED),      # coarse (39)^3 > 4096
     (dict(local_cycles=0), p.PMG_ERR_ARG),
 ])
 def test_bytes_required_rejects(kw, code):
@@ -54,6 +53,12 @@ def test_bytes_required_grows_with_size():
     assert 0.5 * big < fp32 < 1.5 * big  # FP32 MG halves the hierarchy, keeps FP64 CG vectors
     # 3D n=32 Q4 (2.1M DoFs): a few hundred MB
     assert 1e8 < p.bytes_required(p.make_config(dim=3, n_cells=32, degree=4)) < 1e9
+
+
+def test_large_coarse_level_is_accepted_for_apply_only_contexts():
+    # 5 cells (odd): one level whose (39)^3 free DoFs exceed the dense coarse
+    # limit; the plan exists (apply/smooth), the V-cycle is refused at run time
+    assert p.bytes_required(p.make_config(n_cells=5, degree=8)) > 0
 
 
 def test_create_null_out_is_rejected():

@@ -435,3 +435,14 @@ def test_autotuned_patches_per_block_is_admissible():
     u1 = torch.zeros_like(b)
     ref.smooth(b, u1)
     assert torch.equal(u, u1)
+
+
+def test_vcycle_refused_above_dense_coarse_limit():
+    ctx = make_ctx(3, 5, 8)                  # single level, (39)^3 coarse DoFs
+    n = ctx.num_dofs()
+    x = to_dev(random_vector(3, 5, 8, seed=90))
+    y = torch.empty_like(x)
+    ctx.apply(x, y)                          # apply works
+    with pytest.raises(p.PmgError) as e:
+        ctx.vcycle(x, y)
+    assert e.value.code == p.PMG_ERR_UNSUPPORTED
