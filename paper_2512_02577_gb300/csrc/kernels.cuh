@@ -552,6 +552,13 @@ __device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n) 
   }
 }
 
+// Parity colour of a patch's vertex; patches of one colour have disjoint
+// interiors, so each node has at most one patch per colour.
+template <int DIM>
+__device__ __forceinline__ int patch_colour(const PatchMeta& m) {
+  return (m.v[0] & 1) | ((m.v[1] & 1) << 1) | (DIM == 3 ? ((m.v[2] & 1) << 2) : 0);
+}
+
 template <int DIM>
 __device__ __forceinline__ int64_t patch_node(const PatchMeta& m, int i, int N1) {
   constexpr int MT = mp(K);
@@ -582,45 +589,39 @@ __global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, 
   __syncthreads();
   const CartGeo<DIM, T> geo{sdinv, P.scale, T(1) / P.scale, P.inv_a0};
   local_solve<DIM, T>(pb, geo, P, n_iter, S::ELEMS);
+  const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   pfor<SZT>(np, [&](int g, int i) {
-    if (meta[g].active) dst[((int64_t)blockIdx.x * np + g) * SZT + i] = P.omega_as * pb.at(g)[DT + i];
+    const PatchMeta& m = meta[g];
+    if (m.active) dst[patch_colour<DIM>(m) * N + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
   });
 }
 
 // u (+)= sum over the patches whose interior holds the node of their
-// correction (patch buffer written by a patch kernel); boundary nodes get
-// no contribution.  Fixed summation order: patches by increasing vertex.
+// correction.  The patch kernels write the correction of a patch of colour c
+// at dst[c N + node] (N = nodes of the level); a node is covered by colour c
+// when, in every direction, the vertex of parity bit_d(c) among the one or
+// two vertices whose patch holds the node lies in 1..n-1.  Fixed order:
+// colours 0..2^d-1.  Boundary nodes get no contribution.
 template <int DIM, bool ADD, typename T>
 __global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ dst, T* __restrict__ u, int n) {
-  constexpr int MT = mp(K);
-  constexpr int SZT = ipow(MT, DIM);
   const int N1 = K * n + 1, nv = n - 1;
   const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-    int gd[3] = {(int)(t % N1), (int)((t / N1) % N1), DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0};
-    int vlo[3], vcnt[3];
-    bool any = true;
+    const int gd[3] = {(int)(t % N1), (int)((t / N1) % N1), DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0};
+    // per direction and parity: is there a vertex of that parity holding the node?
+    unsigned has[3] = {0u, 0u, 0u};
+#pragma unroll
     for (int d = 0; d < DIM; ++d) {
       const int g = gd[d], c = g / K, a = g - K * c;
-      int lo = a == 0 ? c : c, hi = a == 0 ? c : c + 1;  // vertices v with the node inside (v-1, v+1) cells
-      lo = lo < 1 ? 1 : lo;
-      hi = hi > nv ? nv : hi;
-      vlo[d] = lo;
-      vcnt[d] = hi - lo + 1;
-      if (vcnt[d] <= 0) any = false;
+      if (c >= 1 && c <= nv) has[d] |= 1u << (c & 1);
+      if (a != 0 && c + 1 >= 1 && c + 1 <= nv) has[d] |= 1u << ((c + 1) & 1);
     }
     T s = T(0);
-    if (any) {
-      const int cz = DIM == 3 ? vcnt[2] : 1;
-      for (int jz = 0; jz < cz; ++jz)
-        for (int jy = 0; jy < vcnt[1]; ++jy)
-          for (int jx = 0; jx < vcnt[0]; ++jx) {
-            const int vx = vlo[0] + jx, vy = vlo[1] + jy, vz = DIM == 3 ? vlo[2] + jz : 1;
-            const int ix = gd[0] - (K * (vx - 1) + 1), iy = gd[1] - (K * (vy - 1) + 1);
-            const int iz = DIM == 3 ? gd[2] - (K * (vz - 1) + 1) : 0;
-            const int64_t pid = (vx - 1) + (int64_t)nv * ((vy - 1) + (int64_t)nv * (DIM == 3 ? vz - 1 : 0));
-            s += dst[pid * SZT + ix + MT * (iy + MT * iz)];
-          }
+#pragma unroll
+    for (int col = 0; col < (1 << DIM); ++col) {
+      const bool cov = ((has[0] >> (col & 1)) & 1u) && ((has[1] >> ((col >> 1) & 1)) & 1u) &&
+                       (DIM == 2 || ((has[2] >> ((col >> 2) & 1)) & 1u));
+      if (cov) s += dst[col * N + t];
     }
     if (ADD) u[t] += s;
     else u[t] = s;

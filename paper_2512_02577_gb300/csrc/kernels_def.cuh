@@ -256,16 +256,21 @@ static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const vo
 // from the global degree-p diagonal of the level (a patch-interior DoF has
 // its whole support inside the patch, so diag(A_{j,p}) is that diagonal).
 // ---------------------------------------------------------------------------
+// Patch-level sum factorisation on the (2p+1)^d patch grid: per direction
+// the two cells' Gauss points (2(p+1)) are reached from the 2p+1 nodes by a
+// block-diagonal interpolation (each cell's (p+1) x (p+1) GLL->Gauss block,
+// sharing the centre node), gradients by block-diagonal collocation
+// derivatives, the q-op uses the stored G_q of the cell holding each point,
+// and the transposed steps sum the two cells' contributions at shared nodes.
 template <int DIM>
 struct DefShape {
   using PS = PatchShape<DIM>;
-  static constexpr int NCELL = 1 << DIM;
-  static constexpr int n1T = K + 1;
-  static constexpr int NPT = ipow(n1T, DIM);
-  static constexpr int XSZ = ipow(2 * K + 1, DIM);
-  static constexpr int LINES = NCELL * ipow(n1T, DIM - 1);  // lines of one top-level cell step, per patch
-  static constexpr int WORK = XSZ + NCELL * 5 * NPT;        // patch grid + 2^d cell tile sets
-  static constexpr int ELEMS = PS::ELEMS + WORK;
+  static constexpr int QT = 2 * (K + 1);                    // Gauss points per direction (top level)
+  static constexpr int BUF = ipow(QT, DIM);                 // >= (2K+1)^DIM
+  static constexpr int LINES = ipow(QT, DIM - 1);           // lines of the largest step, per patch
+  static constexpr int WORK = (DIM == 3 ? 4 : 3) * BUF;
+  template <typename T>
+  static constexpr int elems() { return PS::ELEMS + WORK; }
 };
 
 template <typename T>
@@ -274,8 +279,60 @@ struct DefLevelT {
   const T* dinv[4];
 };
 
-// Deformed patch geometry: patch vmult through the 2^d cells (§3.2.1);
-// inverse diagonals from the level's global degree-p diagonals.
+// Along axis AX of a tile with extents (EX, EY, EZ): src extent NI -> dst
+// extent NO.  OP 0: interpolation nodes -> points (NI = 2p+1, NO = 2(p+1));
+// OP 1: its transpose; OP 2: block-diagonal derivative (NI = NO = 2(p+1));
+// OP 3: its transpose.  ACC: dst += result.
+template <int DIM, int p, int AX, int OP, bool ACC, int EX, int EY, int EZ, typename T>
+__device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBlock<T>& pb, int src, int dst) {
+  constexpr int nq = p + 1, mf = 2 * p + 1, Q = 2 * nq;
+  constexpr int NI = (OP == 0) ? mf : (OP == 1 ? Q : Q);
+  constexpr int NO = (OP == 0) ? Q : (OP == 1 ? mf : Q);
+  constexpr int IX = AX == 0 ? NI : EX, IY = AX == 1 ? NI : EY, IZ = AX == 2 ? NI : EZ;
+  constexpr int OX = AX == 0 ? NO : EX, OY = AX == 1 ? NO : EY;
+  constexpr int SI = AX == 0 ? 1 : (AX == 1 ? IX : IX * IY);
+  constexpr int SO = AX == 0 ? 1 : (AX == 1 ? OX : OX * OY);
+  constexpr int NL = IX * IY * IZ / NI;
+  pfor<NL>(pb.np, [&](int g, int L) {
+    T* sm = pb.at(g);
+    const int bi = line_base<AX, IX, IY, IZ>(L);
+    const int bo = line_base<AX, OX, OY, (AX == 2 ? NO : EZ)>(L);
+    T x[NI], y[NO];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) x[j] = sm[src + bi + j * SI];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      T acc = T(0);
+      if constexpr (OP == 0) {  // point o of cell o / nq from nodes p c .. p c + p
+        const int c = o / nq, q = o % nq;
+#pragma unroll
+        for (int jj = 0; jj <= p; ++jj) acc += Sm[q * nq + jj] * x[p * c + jj];
+      } else if constexpr (OP == 1) {  // node o from the points of the cells holding it
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int jj = o - p * c;
+          if (jj >= 0 && jj <= p) {
+#pragma unroll
+            for (int q = 0; q < nq; ++q) acc += Sm[q * nq + jj] * x[c * nq + q];
+          }
+        }
+      } else if constexpr (OP == 2) {
+        const int c = o / nq, q = o % nq;
+#pragma unroll
+        for (int qq = 0; qq < nq; ++qq) acc += Dm[q * nq + qq] * x[c * nq + qq];
+      } else {
+        const int c = o / nq, q = o % nq;
+#pragma unroll
+        for (int qq = 0; qq < nq; ++qq) acc += Dm[qq * nq + q] * x[c * nq + qq];
+      }
+      if (ACC) sm[dst + bo + o * SO] += acc;
+      else sm[dst + bo + o * SO] = acc;
+    }
+  });
+}
+
+// Deformed patch geometry: patch vmult by patch-level sum factorisation
+// (§3.2.1); inverse diagonals from the level's global degree-p diagonals.
 template <int DIM, typename T>
 struct DefGeo {
   DefLevelT<T> lev;
@@ -297,50 +354,88 @@ struct DefGeo {
   template <int l>
   __device__ __forceinline__ void resid(const PBlock<T>& pb, int od, int orr, int oo) const {
     constexpr int p = plev(K, l);
-    constexpr int m = mp(p), mf = 2 * p + 1, n1 = p + 1;
-    constexpr int NP = ipow(n1, DIM);
-    constexpr int XS = ipow(mf, DIM);
-    constexpr int NCELL = 1 << DIM;
-    constexpr int X = PatchShape<DIM>::ELEMS;            // patch grid (zero on its boundary)
-    constexpr int CB = X + DefShape<DIM>::XSZ;           // cell tiles
-    // expand d to the full patch grid
-    pfor<XS>(pb.np, [&](int g, int i) {
+    constexpr int m = mp(p), mf = 2 * p + 1, nq = p + 1, Q = 2 * nq;
+    constexpr int NPc = ipow(nq, DIM);  // points per cell
+    constexpr int B = DefShape<DIM>::BUF;
+    constexpr int W = PatchShape<DIM>::ELEMS;
+    constexpr int B0 = W, B1 = W + B, B2 = W + 2 * B, B3 = W + 3 * B;
+    const T* Sm = coef<T>() + LAY.S[l];
+    const T* Dm = coef<T>() + LAY.Dq[l];
+    constexpr int MZ = DIM == 3 ? mf : 1, QZ = DIM == 3 ? Q : 1;
+    // expand d onto the patch grid (zero on its boundary) in B0: (mf, mf, MZ)
+    pfor<ipow(mf, DIM)>(pb.np, [&](int g, int i) {
       T* sm = pb.at(g);
       const int fx = i % mf, fy = (i / mf) % mf, fz = DIM == 3 ? i / (mf * mf) : 1;
       const bool in = fx > 0 && fx < mf - 1 && fy > 0 && fy < mf - 1 && (DIM == 2 || (fz > 0 && fz < mf - 1));
-      sm[X + i] = in ? sm[od + (fx - 1) + m * ((fy - 1) + m * (DIM == 3 ? fz - 1 : 0))] : T(0);
+      sm[B0 + i] = in ? sm[od + (fx - 1) + m * ((fy - 1) + m * (DIM == 3 ? fz - 1 : 0))] : T(0);
     });
     __syncthreads();
-    // distribute to the 2^d cells
-    pfor<NCELL * NP>(pb.np, [&](int g, int t) {
+    // values at the Gauss points: (mf,mf,MZ) -> (Q,mf,MZ) -> (Q,Q,MZ) -> (Q,Q,QZ)
+    patch_axis<DIM, p, 0, 0, false, mf, mf, MZ>(Sm, Dm, pb, B0, B1);
+    __syncthreads();
+    patch_axis<DIM, p, 1, 0, false, Q, mf, MZ>(Sm, Dm, pb, B1, B0);
+    __syncthreads();
+    if constexpr (DIM == 3) {
+      patch_axis<DIM, p, 2, 0, false, Q, Q, mf>(Sm, Dm, pb, B0, B1);
+      __syncthreads();
+    }
+    constexpr int U = DIM == 3 ? B1 : B0;  // values at the points
+    constexpr int GX = DIM == 3 ? B0 : B1, GY = B2, GZ = B3;
+    patch_axis<DIM, p, 0, 2, false, Q, Q, QZ>(Sm, Dm, pb, U, GX);
+    patch_axis<DIM, p, 1, 2, false, Q, Q, QZ>(Sm, Dm, pb, U, GY);
+    if constexpr (DIM == 3) patch_axis<DIM, p, 2, 2, false, Q, Q, QZ>(Sm, Dm, pb, U, GZ);
+    __syncthreads();
+    // q-op with the stored G_q of the cell holding each point; points visited
+    // cell by cell so that G_q reads are contiguous
+    pfor<(1 << DIM) * NPc>(pb.np, [&](int g, int t) {
       T* sm = pb.at(g);
-      const int c = t / NP, i = t - c * NP;
-      const int ox = c & 1, oy = (c >> 1) & 1, oz = DIM == 3 ? (c >> 2) & 1 : 0;
-      const int ax = i % n1, ay = (i / n1) % n1, az = DIM == 3 ? i / (n1 * n1) : 0;
-      sm[CB + c * 5 * NP + i] = sm[X + (p * ox + ax) + mf * ((p * oy + ay) + mf * (DIM == 3 ? p * oz + az : 0))];
+      const int c = t / NPc, pt = t - c * NPc;
+      const int px = pt % nq, py = (pt / nq) % nq, pz = DIM == 3 ? pt / (nq * nq) : 0;
+      const int qi = ((c & 1) * nq + px) + Q * ((((c >> 1) & 1) * nq + py) + Q * (DIM == 3 ? ((c >> 2) & 1) * nq + pz : 0));
+      const int* v = meta[g].v;
+      const int64_t cell = (v[0] - 1 + (c & 1)) +
+                           (int64_t)n * ((v[1] - 1 + ((c >> 1) & 1)) + (int64_t)n * (DIM == 3 ? v[2] - 1 + ((c >> 2) & 1) : 0));
+      const float* Gc = lev.G[l] + cell * ncomp<DIM>() * NPc + pt;
+      if constexpr (DIM == 3) {
+        const T g0 = sm[GX + qi], g1 = sm[GY + qi], g2 = sm[GZ + qi];
+        const T G00 = (T)Gc[0], G01 = (T)Gc[NPc], G02 = (T)Gc[2 * NPc];
+        const T G11 = (T)Gc[3 * NPc], G12 = (T)Gc[4 * NPc], G22 = (T)Gc[5 * NPc];
+        sm[GX + qi] = G00 * g0 + G01 * g1 + G02 * g2;
+        sm[GY + qi] = G01 * g0 + G11 * g1 + G12 * g2;
+        sm[GZ + qi] = G02 * g0 + G12 * g1 + G22 * g2;
+      } else {
+        const T g0 = sm[GX + qi], g1 = sm[GY + qi];
+        const T G00 = (T)Gc[0], G01 = (T)Gc[NPc], G11 = (T)Gc[2 * NPc];
+        sm[GX + qi] = G00 * g0 + G01 * g1;
+        sm[GY + qi] = G01 * g0 + G11 * g1;
+      }
     });
     __syncthreads();
-    auto tile = [&](int g, int c) { return pb.at(g) + CB + c * 5 * NP; };
-    auto gptr = [&](int g, int c) {
-      const int* v = meta[g].v;
-      const int cx = v[0] - 1 + (c & 1), cy = v[1] - 1 + ((c >> 1) & 1);
-      const int cz = DIM == 3 ? v[2] - 1 + ((c >> 2) & 1) : 0;
-      return lev.G[l] + (cx + (int64_t)n * (cy + (int64_t)n * cz)) * ncomp<DIM>() * NP;
-    };
-    cell_op<DIM, l, NCELL, T>(pb.np, tile, gptr);
-    // sum the cell results back onto the interior nodes: out = r - A d
+    // divergence back to the points, then to the nodes
+    patch_axis<DIM, p, 0, 3, false, Q, Q, QZ>(Sm, Dm, pb, GX, U);
+    __syncthreads();
+    patch_axis<DIM, p, 1, 3, true, Q, Q, QZ>(Sm, Dm, pb, GY, U);
+    __syncthreads();
+    if constexpr (DIM == 3) {
+      patch_axis<DIM, p, 2, 3, true, Q, Q, QZ>(Sm, Dm, pb, GZ, U);
+      __syncthreads();
+      patch_axis<DIM, p, 2, 1, false, Q, Q, Q>(Sm, Dm, pb, U, B0);   // (Q,Q,Q) -> (Q,Q,mf)
+      __syncthreads();
+      patch_axis<DIM, p, 1, 1, false, Q, Q, mf>(Sm, Dm, pb, B0, B2);  // -> (Q,mf,mf)
+      __syncthreads();
+      patch_axis<DIM, p, 0, 1, false, Q, mf, mf>(Sm, Dm, pb, B2, B0); // -> (mf,mf,mf)
+      __syncthreads();
+    } else {
+      patch_axis<DIM, p, 1, 1, false, Q, Q, 1>(Sm, Dm, pb, U, B2);    // (Q,Q) -> (Q,mf)
+      __syncthreads();
+      patch_axis<DIM, p, 0, 1, false, Q, mf, 1>(Sm, Dm, pb, B2, B1);  // -> (mf,mf)
+      __syncthreads();
+    }
+    constexpr int R = DIM == 3 ? B0 : B1;
     pfor<ipow(m, DIM)>(pb.np, [&](int g, int i) {
       T* sm = pb.at(g);
       const int fx = i % m + 1, fy = (i / m) % m + 1, fz = DIM == 3 ? i / (m * m) + 1 : 0;
-      T acc = T(0);
-#pragma unroll
-      for (int c = 0; c < NCELL; ++c) {
-        const int qx = c & 1, qy = (c >> 1) & 1, qz = DIM == 3 ? (c >> 2) & 1 : 0;
-        const int ax = fx - p * qx, ay = fy - p * qy, az = DIM == 3 ? fz - p * qz : 0;
-        if (ax < 0 || ax > p || ay < 0 || ay > p || az < 0 || az > p) continue;
-        acc += sm[CB + c * 5 * NP + ax + n1 * (ay + n1 * az)];
-      }
-      sm[oo + i] = sm[orr + i] - acc;
+      sm[oo + i] = sm[orr + i] - sm[R + fx + mf * (fy + mf * fz)];
     });
     __syncthreads();
   }
@@ -356,7 +451,8 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ PatchMeta meta[kMaxPatchesPerBlock];
   __shared__ T inv_a0[kMaxPatchesPerBlock];
-  const int stride = DS::ELEMS + (n_iter > 1 ? 2 * SZT : 0);
+  constexpr int EL = DS::template elems<T>();
+  const int stride = EL + (n_iter > 1 ? 2 * SZT : 0);
   const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
   patch_meta_init<DIM>(meta, np, n);
   __syncthreads();
@@ -375,9 +471,11 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
   geo.meta = meta;
   geo.inv_a0 = inv_a0;
   geo.n = n;
-  local_solve<DIM, T>(pb, geo, P, n_iter, DS::ELEMS);
+  local_solve<DIM, T>(pb, geo, P, n_iter, EL);
+  const int64_t NN = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   pfor<SZT>(np, [&](int g, int i) {
-    if (meta[g].active) dst[((int64_t)blockIdx.x * np + g) * SZT + i] = P.omega_as * pb.at(g)[DT + i];
+    const PatchMeta& m = meta[g];
+    if (m.active) dst[patch_colour<DIM>(m) * NN + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
   });
 }
 
@@ -386,8 +484,11 @@ static int patch_def_threads(int dim) { return dim == 3 ? DefShape<3>::LINES : D
 
 static int patch_def_smem(int dim, int prec, int n_iter) {
   const int es = prec == 0 ? 8 : 4;
-  const int elems = dim == 3 ? DefShape<3>::ELEMS + (n_iter > 1 ? 2 * PatchShape<3>::SZT : 0)
-                             : DefShape<2>::ELEMS + (n_iter > 1 ? 2 * PatchShape<2>::SZT : 0);
+  int elems;
+  if (dim == 3) elems = (prec == 0 ? DefShape<3>::elems<double>() : DefShape<3>::elems<float>()) +
+                        (n_iter > 1 ? 2 * PatchShape<3>::SZT : 0);
+  else elems = (prec == 0 ? DefShape<2>::elems<double>() : DefShape<2>::elems<float>()) +
+               (n_iter > 1 ? 2 * PatchShape<2>::SZT : 0);
   return elems * es;
 }
 

@@ -198,10 +198,11 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   const int64_t N0 = ipow64((int64_t)P.K * P.n0 + 1, P.dim);
   P.cx0 = bump(cur, N0 * 8);  // unit vectors and operator columns of the coarse set-up
   P.cy0 = bump(cur, N0 * 8);
-  // per-patch corrections of one smoothing step (finest level; reused by the
-  // coarser ones) and, deformed, per-cell operator results (FP64 for the CG)
+  // patch corrections of one smoothing step, one node-major vector per parity
+  // colour (finest level; reused by the coarser ones) and, deformed, per-cell
+  // operator results (FP64 for the CG)
   const int nf = cfg->n_cells;
-  P.pbuf = bump(cur, std::max<int64_t>(ipow64(std::max(nf - 1, 0), P.dim) * ipow64(2 * P.K - 1, P.dim), 1) * P.mg_es);
+  P.pbuf = bump(cur, (int64_t)(1 << P.dim) * ipow64((int64_t)P.K * nf + 1, P.dim) * P.mg_es);
   if (P.deformed) P.cellbuf = bump(cur, ipow64(nf, P.dim) * ipow64(P.K + 1, P.dim) * 8);
   P.total = cur;
   return PMG_OK;

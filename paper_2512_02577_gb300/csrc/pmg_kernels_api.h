@@ -30,7 +30,8 @@ struct KernelTable {
   // y = A x (b == nullptr) or y = b - A x; Cartesian; t0..t3: scratch of N
   cudaError_t (*cart_apply)(int dim, int prec, const void* x, void* y, const void* b, void* t0, void* t1,
                             void* t2, void* t3, int n, double scale, cudaStream_t s);
-  // Cartesian patch smoother, every patch of the level: dst[patch][i] = omega_AS d_j[i]
+  // Cartesian patch smoother, every patch of the level: omega_AS d_j written at
+  // dst[c N + node] for a patch of parity colour c (N nodes of the level)
   cudaError_t (*patch_cart)(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                             const void* dinv, const PatchParamsHost& P, cudaStream_t s);
   // u (+)= sum over the patches holding each node of dst (add = 0: u = sum)
