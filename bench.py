@@ -33,6 +33,10 @@ D, NCELL, K = 3, 32, 4
 ORACLE_N = 4          # bounded CPU sample: same degree and dimension, 4^3 cells (4,913 DoFs)
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (measured 1.255 with a project FMA probe)
 FP32_PEAK_TFLOPS = 78.5  # measured FP32 FMA (128 lanes x 152 SMs x 2 x ~2.0 GHz)
+# DRAM bytes (read + write) of one FP64 patch launch at 32^3 Q4, from the ncu
+# capture summarised in profiles/patch_cart_kernel_fp64_3d_q4.md (57.11 MB +
+# 54.63 MB); to be re-taken whenever patch_cart_kernel changes.
+PATCH64_TRAFFIC_BYTES = 111739648
 
 
 # ----------------------------------------------------------------- flop model
@@ -559,7 +563,7 @@ def main():
         "mixed_speedup_vs_fp64": pct(solve64, 50) / pct(solve32, 50),
         "roofline": {"kernel": "patch_cart_kernel<3,double> (all 29,791 patches of the finest level)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PATCH64_TRAFFIC_BYTES,
                      "flops_per_launch": flops_launch, "launch_ms": patch_launch_ms,
                      "peak_note": "nominal FP64 (measured FMA probe 1.255 TFLOP/s)"},
         "smoother_phases_ms": {"fp64": {"residual": phases[0], "patch": phases[1], "gather": phases[2]},

@@ -446,3 +446,45 @@ def test_vcycle_refused_above_dense_coarse_limit():
     with pytest.raises(p.PmgError) as e:
         ctx.vcycle(x, y)
     assert e.value.code == p.PMG_ERR_UNSUPPORTED
+
+
+def test_full_size_deformed_96_q3_apply_samples_and_mixed_solve():
+    # 3D deformed, 96^3 cells, Q3 (24,137,569 DoFs): the deformed benchmark
+    # configuration, FP32 V-cycle, FP64 CG and FP64 operator
+    d, n, k = 3, 96, 3
+    ctx = make_ctx(d, n, k, geom="deformed", prec=p.FP32)
+    m = fem.Mesh(d, n, k, "deformed", 0.05, geom_fp32=True)
+    N = m.n_dofs
+    assert N == 24137569
+    x = random_vector(d, n, k, seed=91)
+    y = torch.empty(N, dtype=torch.float64, device=DEV)
+    ctx.apply(to_dev(x), y)
+    rows = np.random.default_rng(92).integers(0, N, 60)
+    ref = _sampled_apply_rows(m, x, rows)
+    got = y.cpu().numpy()[rows]
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    b = torch.empty_like(y)
+    ctx.rhs_manufactured(b)
+    xs = torch.zeros_like(b)
+    info = ctx.solve(b, xs)
+    assert info.status == 0 and info.rel_residual <= 1e-8
+    Ax = torch.empty_like(xs)
+    ctx.apply(xs, Ax)
+    assert float(torch.linalg.norm(b - Ax) / torch.linalg.norm(b)) <= 2e-8
+    assert ctx.l2_error_manufactured(xs) < 1e-7
+
+
+def test_full_size_k8_apply_samples():
+    # degree 8 at 25^3 cells (8,120,601 DoFs), FP64 and FP32 operators
+    d, n, k = 3, 25, 8
+    ctx = make_ctx(d, n, k, L=1, prec=p.FP32)
+    m = fem.Mesh(d, n, k)
+    x = random_vector(d, n, k, seed=93)
+    rows = np.random.default_rng(94).integers(0, m.n_dofs, 40)
+    ref = _sampled_apply_rows(m, x, rows)
+    y = torch.empty(m.n_dofs, dtype=torch.float64, device=DEV)
+    ctx.apply(to_dev(x), y)
+    assert np.abs(y.cpu().numpy()[rows] - ref).max() <= 1e-11 * np.abs(ref).max()
+    y32 = torch.empty(m.n_dofs, dtype=torch.float32, device=DEV)
+    ctx.apply(to_dev(x, torch.float32), y32, prec=p.FP32)
+    assert np.abs(y32.cpu().double().numpy()[rows] - ref).max() <= 2e-5 * np.abs(ref).max()
