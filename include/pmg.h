@@ -52,6 +52,12 @@ enum pmg_geometry {
 
 enum pmg_precision { PMG_FP64 = 0, PMG_FP32 = 1 };
 
+/* Outer Krylov solver of pmg_solve (V-cycle as preconditioner). */
+enum pmg_outer {
+  PMG_OUTER_CG = 0,    /* preconditioned CG: needs the symmetric (full) local V-cycle */
+  PMG_OUTER_GMRES = 1  /* flexible right-preconditioned GMRES(gmres_restart), the paper's outer solver */
+};
+
 typedef struct pmg_ctx pmg_ctx;
 
 typedef struct pmg_config {
@@ -68,17 +74,25 @@ typedef struct pmg_config {
   int local_cycles;    /* N_iter of the local Richardson iteration (Algorithm 2), >= 1 */
   int smooth_steps;    /* pre- and post-smoothing sweeps per level, >= 1 */
   int patches_per_block; /* 0 = autotuned; else patches per thread block in the smoother */
+  int local_half;      /* 1: the local solver is the half V-cycle of §3.2.2 (post-smoothing dropped,
+                          one fine-level patch vmult instead of two; nonsymmetric, so outer_solver must
+                          be PMG_OUTER_GMRES, else PMG_ERR_UNSUPPORTED); 0: full V-cycle */
+  int outer_solver;    /* PMG_OUTER_CG (default) or PMG_OUTER_GMRES */
+  int gmres_restart;   /* GMRES cycle length m in 1..64 (default 30); the context then holds 2m + 1
+                          extra FP64 vectors of the finest level */
 } pmg_config;
 
 typedef struct pmg_solve_info {
-  int iterations;      /* CG iterations taken */
-  double rel_residual; /* ||b - A x||_2 / ||b||_2 of the recursively updated residual */
+  int iterations;      /* outer iterations taken (CG iterations or GMRES Arnoldi steps) */
+  double rel_residual; /* ||b - A x||_2 / ||b||_2: CG's recursively updated residual, or GMRES's
+                          Givens estimate of it */
   double time_ms;      /* wall time of the solve on the context's stream */
   int status;          /* PMG_OK or PMG_NOT_CONVERGED */
 } pmg_solve_info;
 
 /* Fill *cfg with defaults: 3D, n 8, k 2, automatic levels, Cartesian, FP64,
- * default damping, one local cycle, one smoothing step. */
+ * default damping, one full local V-cycle, one smoothing step, CG outer
+ * solver (GMRES restart length 30 if selected). */
 void pmg_config_default(pmg_config* cfg);
 
 /* Coarsest levels with more than 4096 free DoFs are accepted: such a context
@@ -126,8 +140,11 @@ int pmg_smooth(pmg_ctx* ctx, int level, int prec, const void* b, void* u, int sw
  * (double in and out; internally FP32 when mg_precision is PMG_FP32). */
 int pmg_vcycle(pmg_ctx* ctx, const double* r, double* z);
 
-/* Preconditioned CG (x_0 = 0, FP64 vectors and dots) with the V-cycle as
- * preconditioner until ||r||_2 <= rtol ||b||_2 or maxit iterations.
+/* Outer Krylov solve, x_0 = 0, FP64 vectors and dots, the V-cycle as
+ * preconditioner, until ||r||_2 <= rtol ||b||_2 or maxit iterations:
+ * preconditioned CG, or with outer_solver PMG_OUTER_GMRES flexible
+ * right-preconditioned GMRES(m) (Arnoldi with two classical Gram-Schmidt
+ * passes, Givens rotations on the device; the paper's outer solver, §3.2.2).
  * Synchronises the stream.  Returns PMG_OK or PMG_NOT_CONVERGED; *info may
  * be NULL. */
 int pmg_solve(pmg_ctx* ctx, const double* b, double* x, double rtol, int maxit, pmg_solve_info* info);

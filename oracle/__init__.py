@@ -20,7 +20,8 @@ paper (arXiv 2512.02577, "Multigrid p-Robustness at Jacobi Speeds"):
   (Algorithm 3) inside the local Richardson iteration (Algorithm 2), and the
   exact dense patch solve.
 * ``solver`` -- the additive vertex-patch smoother (Algorithm 1 with the
-  sequential update replaced by a sum), the geometric V-cycle and PCG.
+  sequential update replaced by a sum), the geometric V-cycle, PCG and
+  flexible GMRES (the outer solver for the half local V-cycle, §3.2.2).
 * ``constants`` -- the damping factors the paper leaves open (readings).
 
 All arithmetic is float64.  Where the deformed-geometry operator stores its

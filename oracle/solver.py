@@ -14,10 +14,14 @@ restriction R = P^T, recursion, prolongation P (the embedding), and an exact
 dense Cholesky solve on the coarsest level.  Pre-smoothing starts from a zero
 guess, so its residual is the right-hand side.
 
-Outer solver: preconditioned CG (the paper uses GMRES because its smoother
-is multiplicative; the additive smoother with the full, symmetric local
-V-cycle gives a symmetric preconditioner), x_0 = 0, stopping when
-||r||_2 <= rtol ||b||_2 on the free DoFs.
+Outer solvers, x_0 = 0, stopping when ||r||_2 <= rtol ||b||_2 on the free
+DoFs: preconditioned CG (the additive smoother with the full, symmetric
+local V-cycle gives a symmetric preconditioner) and GMRES (the paper's outer
+solver; needed once the local solver is the half V-cycle of §3.2.2, which
+drops post-smoothing and makes the preconditioner nonsymmetric).  GMRES is
+the flexible right-preconditioned form (restarted, Arnoldi with modified
+Gram-Schmidt, Givens rotations on the Hessenberg matrix); with a fixed
+preconditioner it is right-preconditioned GMRES.
 
 Parity of the iteration counts of this additive variant is unpinned by the
 paper (its Table 1 is for the multiplicative smoother with GMRES); the tests
@@ -148,10 +152,68 @@ def pcg(A, b, precond, rtol=1e-8, maxit=500):
     return x, it, hist
 
 
-def solve(h, b_int, rtol=1e-8, maxit=500):
-    """PCG on the finest level of hierarchy ``h`` with the V-cycle as
-    preconditioner; b and x on the free DoFs."""
+def gmres(A, b, precond, rtol=1e-8, maxit=500, restart=30):
+    """Flexible right-preconditioned GMRES(restart) from x_0 = 0; returns
+    (x, iterations, rel_residual history).  Each Arnoldi step stores
+    z_j = M^{-1} v_j, orthogonalises A z_j against v_0..v_j (modified
+    Gram-Schmidt), and updates the QR factorisation of the Hessenberg matrix
+    by one Givens rotation; |g_{j+1}| is then the residual norm of the
+    minimiser over span{z_0..z_j}.  The step stops when that norm is below
+    rtol ||b||, when maxit steps are done, or at the end of a cycle (then
+    x += Z y and the cycle restarts from the true residual)."""
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    hist = [1.0]
+    if nb == 0:
+        return x, 0, hist
+    it = 0
+    while True:
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta == 0 or it >= maxit:
+            return x, it, hist
+        V, Z = [r / beta], []
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        j = 0
+        while j < restart and it < maxit:
+            Z.append(precond(V[j]))
+            w = A @ Z[j]
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+            for i in range(j):          # earlier rotations on the new column
+                hi, hn = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * hi + sn[i] * hn
+                H[i + 1, j] = -sn[i] * hi + cs[i] * hn
+            rho = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j], H[j + 1, j] = rho, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j += 1
+            it += 1
+            hist.append(abs(g[j]) / nb)
+            if hist[-1] <= rtol:
+                break
+        y = sla.solve_triangular(H[:j, :j], g[:j])
+        for i in range(j):
+            x = x + y[i] * Z[i]
+        if hist[-1] <= rtol or it >= maxit:
+            return x, it, hist
+
+
+def solve(h, b_int, rtol=1e-8, maxit=500, outer="cg", restart=30):
+    """PCG (outer = "cg") or GMRES (outer = "gmres") on the finest level of
+    hierarchy ``h`` with the V-cycle as preconditioner; b and x on the free
+    DoFs."""
     fine = h.levels[-1]
+    if outer == "gmres":
+        return gmres(fine.A, b_int, h.vcycle, rtol, maxit, restart)
     return pcg(fine.A, b_int, h.vcycle, rtol, maxit)
 
 

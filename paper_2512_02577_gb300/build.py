@@ -1,9 +1,11 @@
 """Build the in-tree shared library ``libpmg.so`` for sm_103a.
 
-Every CUDA translation unit (one per polynomial degree, plus the runtime and
-vector kernels) is compiled by nvcc in parallel; the host set-up code by nvcc
-as C++.  Objects go to ``_build/``; the library is linked next to this file.
-An object is rebuilt when any source or header is newer than it.
+Every CUDA translation unit is compiled by nvcc in parallel: the runtime and
+vector kernels, and ``csrc/inst.cu`` once per kernel part -- each polynomial
+degree 1..8 x dimension 2, 3 x precision double, float, selected by -D flags
+-- so that no single unit dominates the build; the host set-up code by nvcc as
+C++.  Objects go to ``_build/``; the library is linked next to this file.  An
+object is rebuilt when any source or header is newer than it.
 """
 import concurrent.futures
 import glob
@@ -23,8 +25,17 @@ FLAGS = ["-std=c++17", "-O3", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompil
          "-I" + CSRC, "-I" + INCLUDE]
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+PART_SRC = os.path.join(CSRC, "inst.cu")
+DEGREES, DIMS, PRECS = range(1, 9), (2, 3), (0, 1)
+
+
+def _units():
+    """(source, object name, extra flags), heaviest kernel parts first."""
+    units = [(PART_SRC, "inst_k%d_d%d_p%d.o" % (k, d, p), ["-DPMG_K=%d" % k, "-DPMG_DIM=%d" % d, "-DPMG_PREC=%d" % p])
+             for k in reversed(DEGREES) for d in reversed(DIMS) for p in PRECS]
+    others = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    units += [(s, os.path.basename(s) + ".o", []) for s in others if s != PART_SRC]
+    return units
 
 
 def _headers():
@@ -39,8 +50,8 @@ def _stale(obj, src, newest_header):
     return os.path.getmtime(src) > t or newest_header > t
 
 
-def _compile(src, obj, verbose):
-    cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+def _compile(src, obj, extra, verbose):
+    cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -52,18 +63,17 @@ def _compile(src, obj, verbose):
 def build(verbose=False, jobs=None):
     """Compile (incrementally) and link libpmg.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
-    srcs = _sources()
     newest_header = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     objs, todo = [], []
-    for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s) + ".o")
+    for s, name, extra in _units():
+        o = os.path.join(BUILD, name)
         objs.append(o)
         if _stale(o, s, newest_header):
-            todo.append((s, o))
+            todo.append((s, o, extra))
     jobs = jobs or min(len(todo) or 1, os.cpu_count() or 4)
     if todo:
         with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as ex:
-            futs = [ex.submit(_compile, s, o, verbose) for s, o in todo]
+            futs = [ex.submit(_compile, s, o, extra, verbose) for s, o, extra in todo]
             for f in futs:
                 f.result()
     if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):

@@ -1,11 +1,21 @@
-// Launch wrappers for one degree K (PMG_K) and the table that exposes them.
-// Each inst_k<K>.cu defines PMG_K and PMG_KNS, then includes this file.
+// Launch wrappers for one part of the kernel library -- degree K (PMG_K),
+// dimension PMG_DIM, precision PMG_PREC (0 = double, 1 = float) -- and the
+// table that exposes them.  inst.cu defines the part's namespace and table
+// name from those three macros and includes this file; every wrapper checks
+// that the (dim, prec) it is asked for is its own.
 #pragma once
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "kernels_def.cuh"
 
 namespace pmg {
 namespace PMG_KNS {
+
+using TP = std::conditional_t<PMG_PREC == 0, double, float>;
+constexpr int DP = PMG_DIM;
+
+static bool mine(int dim, int prec) { return dim == DP && prec == PMG_PREC; }
 
 static cudaError_t upload(const double* coef) {
   const int n = LAY.total;
@@ -40,18 +50,9 @@ static cudaError_t cart_apply_t(const T* x, T* y, const T* b, T* t0, T* t1, T* t
 
 static cudaError_t cart_apply(int dim, int prec, const void* x, void* y, const void* b, void* t0, void* t1,
                               void* t2, void* t3, int n, double scale, cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3)
-      return cart_apply_t<3, double>((const double*)x, (double*)y, (const double*)b, (double*)t0, (double*)t1,
-                                     (double*)t2, (double*)t3, n, scale, s);
-    return cart_apply_t<2, double>((const double*)x, (double*)y, (const double*)b, (double*)t0, (double*)t1,
-                                   (double*)t2, (double*)t3, n, scale, s);
-  }
-  if (dim == 3)
-    return cart_apply_t<3, float>((const float*)x, (float*)y, (const float*)b, (float*)t0, (float*)t1,
-                                  (float*)t2, (float*)t3, n, (float)scale, s);
-  return cart_apply_t<2, float>((const float*)x, (float*)y, (const float*)b, (float*)t0, (float*)t1,
-                                (float*)t2, (float*)t3, n, (float)scale, s);
+  if (!mine(dim, prec)) return cudaErrorInvalidValue;
+  return cart_apply_t<DP, TP>((const TP*)x, (TP*)y, (const TP*)b, (TP*)t0, (TP*)t1, (TP*)t2, (TP*)t3, n, (TP)scale,
+                              s);
 }
 
 static int patch_threads(int dim) { return dim == 3 ? PatchShape<3>::TPP : PatchShape<2>::TPP; }
@@ -80,7 +81,8 @@ static cudaError_t patch_cart_t(const T* r, T* dst, int n, int ppc, int n_iter, 
   if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
   const int64_t np = ipow(n - 1, DIM);
   const int64_t blocks = (np + ppc - 1) / ppc;
-  const int threads = std::min(1024, (ppc * S::TPP + 31) / 32 * 32);
+  const int threads = std::min(256, (ppc * S::TPP + 31) / 32 * 32);
+  if (ppc * S::TPP > 256) return cudaErrorInvalidConfiguration;
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const int smem = ppc * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
@@ -92,13 +94,8 @@ static cudaError_t patch_cart_t(const T* r, T* dst, int n, int ppc, int n_iter, 
 
 static cudaError_t patch_cart(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                               const void* dinv, const PatchParamsHost& P, cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3)
-      return patch_cart_t<3, double>((const double*)r, (double*)dst, n, ppc, n_iter, (const double*)dinv, P, s);
-    return patch_cart_t<2, double>((const double*)r, (double*)dst, n, ppc, n_iter, (const double*)dinv, P, s);
-  }
-  if (dim == 3) return patch_cart_t<3, float>((const float*)r, (float*)dst, n, ppc, n_iter, (const float*)dinv, P, s);
-  return patch_cart_t<2, float>((const float*)r, (float*)dst, n, ppc, n_iter, (const float*)dinv, P, s);
+  if (!mine(dim, prec)) return cudaErrorInvalidValue;
+  return patch_cart_t<DP, TP>((const TP*)r, (TP*)dst, n, ppc, n_iter, (const TP*)dinv, P, s);
 }
 
 // u (+)= the summed patch corrections held in dst (add = 0: u = sum)
@@ -112,12 +109,8 @@ static cudaError_t patch_gather_t(const T* dst, T* u, int n, int add, cudaStream
 }
 
 static cudaError_t patch_gather(int dim, int prec, const void* dst, void* u, int n, int add, cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3) return patch_gather_t<3, double>((const double*)dst, (double*)u, n, add, s);
-    return patch_gather_t<2, double>((const double*)dst, (double*)u, n, add, s);
-  }
-  if (dim == 3) return patch_gather_t<3, float>((const float*)dst, (float*)u, n, add, s);
-  return patch_gather_t<2, float>((const float*)dst, (float*)u, n, add, s);
+  if (!mine(dim, prec)) return cudaErrorInvalidValue;
+  return patch_gather_t<DP, TP>((const TP*)dst, (TP*)u, n, add, s);
 }
 
 template <int DIM, typename T>
@@ -156,22 +149,14 @@ static cudaError_t h_restrict_t(const T* rf, T* rc, T* t0, T* t1, int nc, cudaSt
 
 static cudaError_t h_prolong_add(int dim, int prec, const void* uc, void* uf, void* t0, void* t1, int nc,
                                  cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3) return h_prolong_t<3, double>((const double*)uc, (double*)uf, (double*)t0, (double*)t1, nc, s);
-    return h_prolong_t<2, double>((const double*)uc, (double*)uf, (double*)t0, (double*)t1, nc, s);
-  }
-  if (dim == 3) return h_prolong_t<3, float>((const float*)uc, (float*)uf, (float*)t0, (float*)t1, nc, s);
-  return h_prolong_t<2, float>((const float*)uc, (float*)uf, (float*)t0, (float*)t1, nc, s);
+  if (!mine(dim, prec)) return cudaErrorInvalidValue;
+  return h_prolong_t<DP, TP>((const TP*)uc, (TP*)uf, (TP*)t0, (TP*)t1, nc, s);
 }
 
 static cudaError_t h_restrict(int dim, int prec, const void* rf, void* rc, void* t0, void* t1, int nc,
                               cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3) return h_restrict_t<3, double>((const double*)rf, (double*)rc, (double*)t0, (double*)t1, nc, s);
-    return h_restrict_t<2, double>((const double*)rf, (double*)rc, (double*)t0, (double*)t1, nc, s);
-  }
-  if (dim == 3) return h_restrict_t<3, float>((const float*)rf, (float*)rc, (float*)t0, (float*)t1, nc, s);
-  return h_restrict_t<2, float>((const float*)rf, (float*)rc, (float*)t0, (float*)t1, nc, s);
+  if (!mine(dim, prec)) return cudaErrorInvalidValue;
+  return h_restrict_t<DP, TP>((const TP*)rf, (TP*)rc, (TP*)t0, (TP*)t1, nc, s);
 }
 
 // Opt every kernel of this degree into the largest dynamic shared memory the
@@ -182,7 +167,10 @@ static cudaError_t allow_smem(Kern k, int optin) {
   cudaFuncAttributes a;
   cudaError_t e = cudaFuncGetAttributes(&a, k);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  // prefer the largest shared-memory carve-out: these kernels live in it
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 static int max_threads_of(const void* k) {
@@ -195,16 +183,9 @@ static int max_threads_of(const void* k) {
 }
 
 static int patch_max_threads(int dim, int prec, int deformed) {
-  if (deformed) {
-    if (prec == 0) return dim == 3 ? max_threads_of((const void*)patch_def_kernel<3, double>)
-                                   : max_threads_of((const void*)patch_def_kernel<2, double>);
-    return dim == 3 ? max_threads_of((const void*)patch_def_kernel<3, float>)
-                    : max_threads_of((const void*)patch_def_kernel<2, float>);
-  }
-  if (prec == 0) return dim == 3 ? max_threads_of((const void*)patch_cart_kernel<3, double>)
-                                 : max_threads_of((const void*)patch_cart_kernel<2, double>);
-  return dim == 3 ? max_threads_of((const void*)patch_cart_kernel<3, float>)
-                  : max_threads_of((const void*)patch_cart_kernel<2, float>);
+  if (!mine(dim, prec)) return 0;
+  return deformed ? max_threads_of((const void*)patch_def_kernel<DP, TP>)
+                  : max_threads_of((const void*)patch_cart_kernel<DP, TP>);
 }
 
 static cudaError_t prepare() {
@@ -214,18 +195,9 @@ static cudaError_t prepare() {
   if (e != cudaSuccess) return e;
   cudaError_t r = cudaSuccess;
   auto acc = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
-  acc(allow_smem(patch_cart_kernel<2, double>, optin));
-  acc(allow_smem(patch_cart_kernel<3, double>, optin));
-  acc(allow_smem(patch_cart_kernel<2, float>, optin));
-  acc(allow_smem(patch_cart_kernel<3, float>, optin));
-  acc(allow_smem(patch_def_kernel<2, double>, optin));
-  acc(allow_smem(patch_def_kernel<3, double>, optin));
-  acc(allow_smem(patch_def_kernel<2, float>, optin));
-  acc(allow_smem(patch_def_kernel<3, float>, optin));
-  acc(allow_smem(def_cell_kernel<2, double>, optin));
-  acc(allow_smem(def_cell_kernel<3, double>, optin));
-  acc(allow_smem(def_cell_kernel<2, float>, optin));
-  acc(allow_smem(def_cell_kernel<3, float>, optin));
+  acc(allow_smem(patch_cart_kernel<DP, TP>, optin));
+  acc(allow_smem(patch_def_kernel<DP, TP>, optin));
+  acc(allow_smem(def_cell_kernel<DP, TP>, optin));
   return r;
 }
 
@@ -234,6 +206,8 @@ static cudaError_t prepare() {
 const KernelTable* PMG_TABLE_FN() {
   static KernelTable t = {
       PMG_K,
+      PMG_DIM,
+      PMG_PREC,
       PMG_KNS::prepare,
       PMG_KNS::upload,
       PMG_KNS::cart_apply,

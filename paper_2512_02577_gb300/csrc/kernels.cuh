@@ -459,9 +459,10 @@ __device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst)
   }
 }
 
-// Algorithm 3 (full V-cycle) on p-level l for the residuals r_l of all
-// patches of the block, results in d_l; level 0 (p = 1) is the exact 1x1
-// solve (§3.2).
+// Algorithm 3 on p-level l for the residuals r_l of all patches of the
+// block, results in d_l; level 0 (p = 1) is the exact 1x1 solve (§3.2).
+// Full V-cycle, or with P.half the half V-cycle of §3.2.2 (pre-smoothing,
+// coarse correction, no post-smoothing).
 template <int DIM, int l, typename T, class Geo>
 __device__ void pvcycle(const PBlock<T>& pb, const Geo& geo, const PatchParams<T>& P) {
   using S = PatchShape<DIM>;
@@ -484,6 +485,7 @@ __device__ void pvcycle(const PBlock<T>& pb, const Geo& geo, const PatchParams<T
     restrict_p<DIM, l>(pb, S::off_r(l - 1));               // restrict
     pvcycle<DIM, l - 1, T>(pb, geo, P);                    // recurse
     prolong_p<DIM, l>(pb, S::off_d(l - 1), D);             // prolongate, add
+    if (P.half) return;  // half V-cycle (§3.2.2): no post-smoothing (uniform per block)
     geo.template resid<l>(pb, D, R, 0);                   // residual
     pfor<SZ>(pb.np, [&](int g, int i) {  // post-smoothing
       T* sm = pb.at(g);
@@ -567,9 +569,16 @@ __device__ __forceinline__ int64_t patch_node(const PatchMeta& m, int i, int N1)
 }
 
 // Cartesian patches: gather r_j, Algorithm 2/3, write omega_AS d_j.
+// At most 256 threads per block: every degree's patch lines fit (at most 225
+// per patch).  For moderate degrees, ask for three blocks per SM (registers
+// <= 85) so that 24 warps keep the FP64 pipe fed; longer lines need more
+// registers than that without spilling.
+constexpr int kPatchMinBlocks = K <= 4 ? 3 : 1;
+
 template <int DIM, typename T>
-__global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
-                                  const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
+__global__ void __launch_bounds__(256, kPatchMinBlocks)
+    patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
+                      const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
   using S = PatchShape<DIM>;
   constexpr int SZT = S::SZT;
   constexpr int RT = S::off_r(S::L - 1), DT = S::off_d(S::L - 1);
@@ -587,7 +596,7 @@ __global__ void patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, 
     pb.at(g)[RT + i] = m.active ? r[patch_node<DIM>(m, i, N1)] : T(0);
   });
   __syncthreads();
-  const CartGeo<DIM, T> geo{sdinv, P.scale, T(1) / P.scale, P.inv_a0};
+  const CartGeo<DIM, T> geo{sdinv, P.scale, P.inv_scale, P.inv_a0};
   local_solve<DIM, T>(pb, geo, P, n_iter, S::ELEMS);
   const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   pfor<SZT>(np, [&](int g, int i) {
@@ -721,6 +730,8 @@ static PatchParams<T> to_params(const PatchParamsHost& H) {
   P.omega_as = (T)H.omega_as;
   for (int i = 0; i < 4; ++i) P.omega[i] = (T)H.omega[i];
   P.inv_a0 = (T)H.inv_a0;
+  P.inv_scale = (T)(1.0 / H.scale);
+  P.half = H.half;
   return P;
 }
 

@@ -9,6 +9,7 @@
 // accumulate without atomics and in a fixed order.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 namespace pmg {
 namespace PMG_KNS {
@@ -239,13 +240,9 @@ static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, T* 
 
 static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const void* b, const float* G, void* cellbuf,
                              int n, cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3)
-      return def_apply_t<3, double>((const double*)x, (double*)y, (const double*)b, G, (double*)cellbuf, n, s);
-    return def_apply_t<2, double>((const double*)x, (double*)y, (const double*)b, G, (double*)cellbuf, n, s);
-  }
-  if (dim == 3) return def_apply_t<3, float>((const float*)x, (float*)y, (const float*)b, G, (float*)cellbuf, n, s);
-  return def_apply_t<2, float>((const float*)x, (float*)y, (const float*)b, G, (float*)cellbuf, n, s);
+  if (dim != PMG_DIM || prec != PMG_PREC) return cudaErrorInvalidValue;
+  using TP = std::conditional_t<PMG_PREC == 0, double, float>;
+  return def_apply_t<PMG_DIM, TP>((const TP*)x, (TP*)y, (const TP*)b, G, (TP*)cellbuf, n, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -515,12 +512,9 @@ static cudaError_t patch_def_t(const T* r, T* dst, int n, int np, int n_iter, co
 
 static cudaError_t patch_def(int dim, int prec, const void* r, void* dst, int n, int np, int n_iter,
                              const DefLevel& L, const PatchParamsHost& P, cudaStream_t s) {
-  if (prec == 0) {
-    if (dim == 3) return patch_def_t<3, double>((const double*)r, (double*)dst, n, np, n_iter, L, P, s);
-    return patch_def_t<2, double>((const double*)r, (double*)dst, n, np, n_iter, L, P, s);
-  }
-  if (dim == 3) return patch_def_t<3, float>((const float*)r, (float*)dst, n, np, n_iter, L, P, s);
-  return patch_def_t<2, float>((const float*)r, (float*)dst, n, np, n_iter, L, P, s);
+  if (dim != PMG_DIM || prec != PMG_PREC) return cudaErrorInvalidValue;
+  using TP = std::conditional_t<PMG_PREC == 0, double, float>;
+  return patch_def_t<PMG_DIM, TP>((const TP*)r, (TP*)dst, n, np, n_iter, L, P, s);
 }
 
 }  // namespace PMG_KNS

@@ -25,7 +25,7 @@
 #include "setup.h"
 
 namespace pmg {
-const KernelTable* kernel_table(int K);
+const KernelTable* kernel_table(int K, int dim, int prec);
 void set_last_error(const std::string& msg);
 }  // namespace pmg
 
@@ -38,7 +38,7 @@ static __device__ __align__(256) double g_apply_scratch[4 * kMaxDofs];
 struct DeviceState {
   bool ready = false;
   double* scratch = nullptr;  // device address of g_apply_scratch on this device
-  bool coef[9] = {};
+  bool coef[9][2] = {};  // by degree and dimension
 };
 
 constexpr int kMaxDevices = 64;
@@ -67,7 +67,7 @@ extern "C" int pmg_apply_cartesian_noalloc(int dim, int n_cells, int degree, con
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(PMG_ERR_UNSUPPORTED, "device ordinal above 63");
-  const pmg::KernelTable* kt = pmg::kernel_table(degree);
+  const pmg::KernelTable* kt = pmg::kernel_table(degree, dim, 0);
   double* scratch = nullptr;
   {
     // first call on this device (and first call for this degree): resolve the
@@ -81,13 +81,13 @@ extern "C" int pmg_apply_cartesian_noalloc(int dim, int n_cells, int degree, con
       s.scratch = (double*)ptr;
       s.ready = true;
     }
-    if (!s.coef[degree]) {
+    if (!s.coef[degree][dim - 2]) {
       std::vector<double> coef(pmg::kMaxCoef, 0.0);
       pmg::host::fill_coefficients(degree, coef.data());
       e = kt->prepare();
       if (e == cudaSuccess) e = kt->upload(coef.data());
       if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("coefficient upload: ") + cudaGetErrorString(e));
-      s.coef[degree] = true;
+      s.coef[degree][dim - 2] = true;
     }
     scratch = s.scratch;
   }

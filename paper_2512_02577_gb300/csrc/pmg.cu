@@ -27,27 +27,30 @@
 #include "vec.h"
 
 namespace pmg {
-const KernelTable* kernel_table_k1();
-const KernelTable* kernel_table_k2();
-const KernelTable* kernel_table_k3();
-const KernelTable* kernel_table_k4();
-const KernelTable* kernel_table_k5();
-const KernelTable* kernel_table_k6();
-const KernelTable* kernel_table_k7();
-const KernelTable* kernel_table_k8();
+#define PMG_DECLARE_PARTS(k)                    \
+  const KernelTable* kernel_table_k##k##_d2_p0(); \
+  const KernelTable* kernel_table_k##k##_d2_p1(); \
+  const KernelTable* kernel_table_k##k##_d3_p0(); \
+  const KernelTable* kernel_table_k##k##_d3_p1();
+PMG_DECLARE_PARTS(1)
+PMG_DECLARE_PARTS(2)
+PMG_DECLARE_PARTS(3)
+PMG_DECLARE_PARTS(4)
+PMG_DECLARE_PARTS(5)
+PMG_DECLARE_PARTS(6)
+PMG_DECLARE_PARTS(7)
+PMG_DECLARE_PARTS(8)
+#undef PMG_DECLARE_PARTS
 
-const KernelTable* kernel_table(int K) {
-  switch (K) {
-    case 1: return kernel_table_k1();
-    case 2: return kernel_table_k2();
-    case 3: return kernel_table_k3();
-    case 4: return kernel_table_k4();
-    case 5: return kernel_table_k5();
-    case 6: return kernel_table_k6();
-    case 7: return kernel_table_k7();
-    case 8: return kernel_table_k8();
-    default: return nullptr;
-  }
+const KernelTable* kernel_table(int K, int dim, int prec) {
+  using Fn = const KernelTable* (*)();
+#define PMG_PARTS(k) {{kernel_table_k##k##_d2_p0, kernel_table_k##k##_d2_p1}, \
+                      {kernel_table_k##k##_d3_p0, kernel_table_k##k##_d3_p1}}
+  static const Fn parts[8][2][2] = {PMG_PARTS(1), PMG_PARTS(2), PMG_PARTS(3), PMG_PARTS(4),
+                                    PMG_PARTS(5), PMG_PARTS(6), PMG_PARTS(7), PMG_PARTS(8)};
+#undef PMG_PARTS
+  if (K < 1 || K > 8 || dim < 2 || dim > 3 || prec < 0 || prec > 1) return nullptr;
+  return parts[K - 1][dim - 2][prec]();
 }
 }  // namespace pmg
 
@@ -112,6 +115,10 @@ struct Plan {
   int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad, cx0, cy0;
   int64_t pbuf = -1, cellbuf = -1;
   int64_t dtab_len = 0;
+  // flexible GMRES (outer_solver GMRES): basis v_0..v_m, z_0..z_{m-1},
+  // Hessenberg (m+1) x m, small state, multi-dot partials
+  int m = 0;
+  int64_t gv = -1, gz = -1, gh = -1, gs = -1, gpart = -1;
 };
 
 int64_t bump(int64_t& cur, int64_t bytes) {
@@ -129,6 +136,13 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_ARG, "unknown geometry");
   if (cfg->mg_precision != PMG_FP64 && cfg->mg_precision != PMG_FP32) return fail(PMG_ERR_ARG, "unknown precision");
   if (cfg->local_cycles < 1 || cfg->smooth_steps < 1) return fail(PMG_ERR_ARG, "local_cycles, smooth_steps >= 1");
+  if (cfg->local_half != 0 && cfg->local_half != 1) return fail(PMG_ERR_ARG, "local_half must be 0 or 1");
+  if (cfg->outer_solver != PMG_OUTER_CG && cfg->outer_solver != PMG_OUTER_GMRES)
+    return fail(PMG_ERR_ARG, "unknown outer_solver");
+  if (cfg->outer_solver == PMG_OUTER_GMRES && (cfg->gmres_restart < 1 || cfg->gmres_restart > kMaxKrylov))
+    return fail(PMG_ERR_ARG, "gmres_restart must be in 1..64");
+  if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
+    return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
   P.K = cfg->degree;
   P.deformed = cfg->geometry == PMG_GEOM_DEFORMED;
@@ -183,6 +197,14 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   for (int i = 0; i < 4; ++i) P.t64[i] = bump(cur, NF * 8);
   for (int i = 0; i < 4; ++i) P.t_mg[i] = P.mg32 ? bump(cur, NF * 4) : P.t64[i];
   for (int i = 0; i < 6; ++i) P.cg[i] = bump(cur, NF * 8);
+  if (cfg->outer_solver == PMG_OUTER_GMRES) {
+    P.m = cfg->gmres_restart;
+    P.gv = bump(cur, (P.m + 1) * NF * 8);
+    P.gz = bump(cur, P.m * NF * 8);
+    P.gh = bump(cur, (int64_t)(P.m + 1) * P.m * 8);
+    P.gs = bump(cur, GmresState::size(P.m) * 8);
+    P.gpart = bump(cur, (int64_t)(P.m + 1) * kDotBlocks * 8);
+  }
   P.scal = bump(cur, S_COUNT * 8);
   P.partial = bump(cur, kDotBlocks * 8 * 2);
   P.dtab_len = 0;
@@ -214,6 +236,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
 struct SolveState {
   int phase = 0;
   int it = 0, maxit = 0, status = 0;
+  int gj = 0;  // GMRES: Arnoldi steps taken in the current cycle
   double rtol = 0, nb = 0, rel = 0, time_ms = 0;
   double* x_out = nullptr;
   bool x_host = false;
@@ -227,7 +250,8 @@ struct pmg_ctx {
   int mgprec = PMG_FP64;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  const KernelTable* kt = nullptr;
+  const KernelTable* kt[2] = {};  // kernel parts of (K, dim), by precision
+  const KernelTable* km() const { return kt[mgprec]; }  // the multigrid precision's part
   std::vector<LevelData> lv;
   char* ws = nullptr;
   bool own_ws = false;
@@ -236,6 +260,10 @@ struct pmg_ctx {
   double *cg_x = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *cg_z = nullptr, *cg_b = nullptr;
   double* scal = nullptr;
   double* partial = nullptr;
+  bool gmres = false;  // outer solver: flexible GMRES (else PCG)
+  int gm = 0;          // GMRES restart length
+  double *gv = nullptr, *gz = nullptr, *gh = nullptr, *gs = nullptr, *gpart = nullptr;
+  int64_t gld = 0;     // stride of the GMRES basis columns
   double* host_scal = nullptr;  // pinned
   void* dtab_mg = nullptr;
   double* dtab64 = nullptr;
@@ -264,6 +292,7 @@ PatchParamsHost patch_params(const pmg_ctx* c, int level) {
   P.omega_as = c->omega_as;
   for (int i = 0; i < 4; ++i) P.omega[i] = c->omega_j[i];
   P.inv_a0 = c->lv[level].inv_a0;
+  P.half = c->cfg.local_half;
   return P;
 }
 
@@ -289,10 +318,10 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   LevelData& L = c->lv[level];
   cudaError_t e;
   if (c->deformed) {
-    e = c->kt->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cellbuf, L.n, c->stream);
+    e = c->kt[prec]->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cellbuf, L.n, c->stream);
   } else {
     void** t = prec == PMG_FP64 ? (void**)c->t64 : c->t_mg;
-    e = c->kt->cart_apply(c->dim, prec, u, r, b, t[0], t[1], t[2], t[3], L.n, L.scale, c->stream);
+    e = c->kt[prec]->cart_apply(c->dim, prec, u, r, b, t[0], t[1], t[2], t[3], L.n, L.scale, c->stream);
   }
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("apply: ") + cudaGetErrorString(e));
   return PMG_OK;
@@ -311,9 +340,9 @@ int patch_solves(pmg_ctx* c, int level, const void* r) {
       D.dinv[i] = L.dinv[i];
     }
     D.dinv1 = L.dinv1;
-    e = c->kt->patch_def(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+    e = c->km()->patch_def(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
   } else {
-    e = c->kt->patch_cart(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
+    e = c->km()->patch_cart(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
                           c->stream);
   }
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
@@ -324,7 +353,7 @@ int patch_solves(pmg_ctx* c, int level, const void* r) {
 // (add = false: u = that correction, the zero-initial-guess pre-smoothing).
 int patch_sweep(pmg_ctx* c, int level, const void* r, void* u, bool add) {
   if (int rc = patch_solves(c, level, r)) return rc;
-  cudaError_t e = c->kt->patch_gather(c->dim, c->mgprec, c->pbuf, u, c->lv[level].n, add ? 1 : 0, c->stream);
+  cudaError_t e = c->km()->patch_gather(c->dim, c->mgprec, c->pbuf, u, c->lv[level].n, add ? 1 : 0, c->stream);
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch gather: ") + cudaGetErrorString(e));
   return PMG_OK;
 }
@@ -363,10 +392,10 @@ int vcycle_level(pmg_ctx* c, int level) {
   }
   if ((rc = level_apply(c, level, c->mgprec, L.u, L.r, L.b))) return rc;
   LevelData& C = c->lv[level - 1];
-  cudaError_t e = c->kt->h_restrict(c->dim, c->mgprec, L.r, C.b, c->t_mg[0], c->t_mg[1], C.n, c->stream);
+  cudaError_t e = c->km()->h_restrict(c->dim, c->mgprec, L.r, C.b, c->t_mg[0], c->t_mg[1], C.n, c->stream);
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("restrict: ") + cudaGetErrorString(e));
   if ((rc = vcycle_level(c, level - 1))) return rc;
-  e = c->kt->h_prolong_add(c->dim, c->mgprec, C.u, L.u, c->t_mg[0], c->t_mg[1], C.n, c->stream);
+  e = c->km()->h_prolong_add(c->dim, c->mgprec, C.u, L.u, c->t_mg[0], c->t_mg[1], C.n, c->stream);
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("prolongate: ") + cudaGetErrorString(e));
   return smooth_level(c, level, L.b, L.u, nu);
 }
@@ -495,17 +524,17 @@ void tune_file_append_locked(const TuneKey& key, int ppc) {
 }
 
 int admissible_ppc(const pmg_ctx* c, int ppc) {
-  const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
-  const int smem = c->deformed ? c->kt->patch_def_smem(c->dim, c->mgprec, c->cfg.local_cycles)
-                               : c->kt->patch_smem(c->dim, c->mgprec, c->cfg.local_cycles);
-  const int maxt = c->kt->patch_max_threads(c->dim, c->mgprec, c->deformed ? 1 : 0);
-  const int extra = c->deformed ? 0 : c->kt->patch_cart_extra_smem(c->dim, c->mgprec);
+  const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
+  const int smem = c->deformed ? c->km()->patch_def_smem(c->dim, c->mgprec, c->cfg.local_cycles)
+                               : c->km()->patch_smem(c->dim, c->mgprec, c->cfg.local_cycles);
+  const int maxt = c->km()->patch_max_threads(c->dim, c->mgprec, c->deformed ? 1 : 0);
+  const int extra = c->deformed ? 0 : c->km()->patch_cart_extra_smem(c->dim, c->mgprec);
   return ppc >= 1 && ppc <= 64 && (ppc * tpp + 31) / 32 * 32 <= std::min(1024, maxt) &&
          ppc * smem + extra <= kMaxDynSmem;
 }
 
 int rule_ppc(const pmg_ctx* c) {
-  const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
+  const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
   int ppc = std::max(1, 256 / tpp);
   while (ppc > 1 && !admissible_ppc(c, ppc)) --ppc;
   return ppc;
@@ -542,7 +571,7 @@ int choose_patches_per_block(pmg_ctx* c) {
   float best = 1e30f;
   int best_ppc = c->ppc;
   const int64_t before = g_launches.load();
-  const int tpp = c->deformed ? c->kt->patch_def_threads(c->dim) : c->kt->patch_threads(c->dim);
+  const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
   for (int ppc = 1; ppc <= 64; ++ppc) {
     if (!admissible_ppc(c, ppc)) continue;
     const int thr = ppc * tpp, padded = (thr + 31) / 32 * 32;
@@ -605,6 +634,16 @@ int setup_context(pmg_ctx* c) {
     c->t64[i] = (double*)at(c, P.t64[i]);
     c->t_mg[i] = at(c, P.t_mg[i]);
   }
+  if (P.m > 0) {
+    c->gmres = true;
+    c->gm = P.m;
+    c->gld = c->lv[c->L - 1].N;
+    c->gv = (double*)at(c, P.gv);
+    c->gz = (double*)at(c, P.gz);
+    c->gh = (double*)at(c, P.gh);
+    c->gs = (double*)at(c, P.gs);
+    c->gpart = (double*)at(c, P.gpart);
+  }
   double** cg[6] = {&c->cg_x, &c->cg_r, &c->cg_p, &c->cg_Ap, &c->cg_z, &c->cg_b};
   for (int i = 0; i < 6; ++i) *cg[i] = (double*)at(c, P.cg[i]);
   c->scal = (double*)at(c, P.scal);
@@ -620,8 +659,10 @@ int setup_context(pmg_ctx* c) {
   // coefficients and kernel attributes
   std::vector<double> coef(kMaxCoef, 0.0);
   host::fill_coefficients(c->K, coef.data());
-  PMG_CUDA(c->kt->prepare());
-  PMG_CUDA(c->kt->upload(coef.data()));
+  for (const KernelTable* t : c->kt) {
+    PMG_CUDA(t->prepare());
+    PMG_CUDA(t->upload(coef.data()));
+  }
 
   // damping
   const pmg_config& cf = c->cfg;
@@ -710,6 +751,9 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->local_cycles = 1;
   cfg->smooth_steps = 1;
   cfg->patches_per_block = 0;
+  cfg->local_half = 0;
+  cfg->outer_solver = PMG_OUTER_CG;
+  cfg->gmres_restart = 30;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {
@@ -749,7 +793,8 @@ int pmg_create(const pmg_config* cfg, void* stream, void* workspace, int64_t wor
     }
     c->own_stream = true;
   }
-  c->kt = kernel_table(c->K);
+  c->kt[0] = kernel_table(c->K, c->dim, PMG_FP64);
+  c->kt[1] = kernel_table(c->K, c->dim, PMG_FP32);
   if (workspace) {
     if (workspace_bytes < c->plan.total) {
       delete c;
@@ -864,6 +909,64 @@ static int enqueue_iteration(pmg_ctx* c) {
   return PMG_OK;
 }
 
+// ---------------------------------------------------------------- GMRES
+// Flexible right-preconditioned GMRES(m) (the paper's outer solver, needed
+// with the half local V-cycle, §3.2.2): each step z_j = B v_j (V-cycle),
+// w = A z_j, two classical Gram-Schmidt passes against v_0..v_j (one
+// multi-dot and one multi-axpy each), ||w||, the Givens update of the
+// Hessenberg column on the device, v_{j+1} = w / ||w||; the host reads only
+// the residual estimate |g_{j+1}| while the next step's V-cycle is already
+// enqueued.  At convergence, maxit or the end of a cycle, x += Z y; a new
+// cycle restarts from the true residual b - A x.
+
+// v_0 = r / ||r|| (r: first cycle b, else b - A x) and z_0 = B v_0
+static int gmres_cycle_start(pmg_ctx* c, bool first) {
+  const int64_t N = c->lv[c->L - 1].N;
+  cudaStream_t s = c->stream;
+  double* nrm2 = c->gs + GmresState::nrm2(c->gm);
+  if (first) {
+    PMG_CUDA(cudaMemcpyAsync(nrm2, c->scal + S_BB, 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    if (int rc = level_apply(c, c->L - 1, PMG_FP64, c->cg_x, c->cg_r, c->cg_b)) return rc;
+    PMG_CUDA(dot(c->cg_r, c->cg_r, N, c->partial, nrm2, s));
+  }
+  PMG_CUDA(gmres_start(c->gs, nrm2, c->gm, c->cg_r, c->gv, N, s));
+  c->sv.gj = 0;
+  return precondition(c, c->gv, c->gz);
+}
+
+// Arnoldi step j = sv.gj (z_j already enqueued); records ev_rr after the
+// residual estimate's copy, then enqueues z_{j+1} if the cycle has room.
+static int gmres_enqueue_step(pmg_ctx* c) {
+  const int64_t N = c->lv[c->L - 1].N, ld = c->gld;
+  cudaStream_t s = c->stream;
+  const int j = c->sv.gj, m = c->gm;
+  double* w = c->gv + (j + 1) * ld;
+  double* hcol = c->gh + (int64_t)j * (m + 1);
+  double* h2 = c->gs + GmresState::h2(m);
+  double* nrm2 = c->gs + GmresState::nrm2(m);
+  if (int rc = level_apply(c, c->L - 1, PMG_FP64, c->gz + j * ld, w, nullptr)) return rc;
+  PMG_CUDA(multi_dot(c->gv, ld, j + 1, w, N, c->gpart, hcol, s));
+  PMG_CUDA(multi_axpy(w, c->gv, ld, j + 1, hcol, -1.0, N, s));
+  PMG_CUDA(multi_dot(c->gv, ld, j + 1, w, N, c->gpart, h2, s));
+  PMG_CUDA(multi_axpy(w, c->gv, ld, j + 1, h2, -1.0, N, s));
+  PMG_CUDA(dot(w, w, N, c->partial, nrm2, s));
+  PMG_CUDA(gmres_givens(c->gh, c->gs, nrm2, j, m, w, N, s));
+  PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_RR, c->gs + GmresState::est(m), 8, cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaEventRecord(c->ev_rr, s));
+  ++c->sv.it;
+  c->sv.gj = j + 1;
+  if (j + 1 < m) return precondition(c, w, c->gz + (j + 1) * ld);
+  return PMG_OK;
+}
+
+// x += Z y over the steps of the current cycle
+static int gmres_update_x(pmg_ctx* c) {
+  const int64_t N = c->lv[c->L - 1].N;
+  PMG_CUDA(gmres_update(c->gh, c->gs, c->sv.gj, c->gm, c->gz, c->gld, c->cg_x, N, c->stream));
+  return PMG_OK;
+}
+
 static int solve_start(pmg_ctx* c, const double* b, bool b_host, double rtol, int maxit) {
   const int64_t N = c->lv[c->L - 1].N;
   cudaStream_t s = c->stream;
@@ -877,6 +980,13 @@ static int solve_start(pmg_ctx* c, const double* b, bool b_host, double rtol, in
   PMG_CUDA(dot(c->cg_r, c->cg_r, N, c->partial, c->scal + S_BB, s));
   PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_BB, c->scal + S_BB, 8, cudaMemcpyDeviceToHost, s));
   PMG_CUDA(cudaEventRecord(c->ev_rr, s));
+  if (c->gmres) {
+    // b is kept for the residuals of restarted cycles
+    PMG_CUDA(cudaMemcpyAsync(c->cg_b, c->cg_r, 8 * N, cudaMemcpyDeviceToDevice, s));
+    if (int rc = gmres_cycle_start(c, true)) return rc;
+    c->sv.phase = SP_WAIT_BB;
+    return PMG_OK;
+  }
   if (int rc = precondition(c, c->cg_r, c->cg_z)) return rc;
   PMG_CUDA(dot(c->cg_r, c->cg_z, N, c->partial, c->scal + S_RZ, s));
   PMG_CUDA(cudaMemcpyAsync(c->cg_p, c->cg_z, 8 * N, cudaMemcpyDeviceToDevice, s));
@@ -887,6 +997,9 @@ static int solve_start(pmg_ctx* c, const double* b, bool b_host, double rtol, in
 static int solve_finish(pmg_ctx* c, int status) {
   const int64_t N = c->lv[c->L - 1].N;
   c->sv.status = status;
+  if (c->gmres && c->sv.gj > 0) {
+    if (int rc = gmres_update_x(c)) return rc;
+  }
   PMG_CUDA(cudaEventRecord(c->ev1, c->stream));
   if (c->sv.x_out) {
     PMG_CUDA(cudaMemcpyAsync(c->sv.x_out, c->cg_x, 8 * N,
@@ -931,8 +1044,9 @@ static int solve_progress(pmg_ctx* c, bool block, int* state) {
       }
       c->sv.rel = 1.0;
     } else {
-      c->sv.rel = std::sqrt(std::max(c->host_scal[S_RR], 0.0)) / c->sv.nb;
-      if (!(c->sv.rel == c->sv.rel)) return fail(PMG_ERR_STATE, "CG breakdown (NaN residual)");
+      c->sv.rel = c->gmres ? c->host_scal[S_RR] / c->sv.nb
+                           : std::sqrt(std::max(c->host_scal[S_RR], 0.0)) / c->sv.nb;
+      if (!(c->sv.rel == c->sv.rel)) return fail(PMG_ERR_STATE, "solver breakdown (NaN residual)");
       if (c->sv.rel <= c->sv.rtol) {
         if (int rc = solve_finish(c, PMG_OK)) return rc;
         continue;
@@ -942,7 +1056,15 @@ static int solve_progress(pmg_ctx* c, bool block, int* state) {
       if (int rc = solve_finish(c, PMG_NOT_CONVERGED)) return rc;
       continue;
     }
-    if (int rc = enqueue_iteration(c)) return rc;
+    if (c->gmres) {
+      if (c->sv.gj == c->gm) {  // end of a cycle: update x and restart
+        if (int rc = gmres_update_x(c)) return rc;
+        if (int rc = gmres_cycle_start(c, false)) return rc;
+      }
+      if (int rc = gmres_enqueue_step(c)) return rc;
+    } else {
+      if (int rc = enqueue_iteration(c)) return rc;
+    }
     c->sv.phase = SP_WAIT_RR;
   }
 }
@@ -1044,7 +1166,7 @@ int pmg_smoother_phase_times(pmg_ctx* c, int level, int reps, double* ms) {
     if (!rc) rc = patch_solves(c, level, L.r);
     cudaEventRecord(ev[2], c->stream);
     if (!rc) {
-      cudaError_t e = c->kt->patch_gather(c->dim, c->mgprec, c->pbuf, L.u, L.n, 1, c->stream);
+      cudaError_t e = c->km()->patch_gather(c->dim, c->mgprec, c->pbuf, L.u, L.n, 1, c->stream);
       if (e != cudaSuccess) rc = fail(PMG_ERR_CUDA, cudaGetErrorString(e));
     }
     cudaEventRecord(ev[3], c->stream);

@@ -94,6 +94,8 @@ struct PatchParams {
   T omega_as;     // additive-Schwarz damping
   T omega[4];     // Jacobi damping per p-level
   T inv_a0;       // 1 / A_{j,1} on Cartesian meshes (uniform)
+  T inv_scale;    // 1 / scale
+  int half;       // 1: half local V-cycle (post-smoothing dropped, §3.2.2)
 };
 
 }  // namespace pmg

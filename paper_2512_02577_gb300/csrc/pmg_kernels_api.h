@@ -1,7 +1,11 @@
-// Per-degree table of kernel launchers, filled by inst_k<K>.cu.  Host code
-// (pmg.cu) dispatches on the degree k through kernel_table(k); every entry
-// enqueues on the given stream and returns the launch's cudaError_t.
+// Table of kernel launchers of one part of the library -- degree k, dimension
+// d, precision -- filled by inst.cu compiled for that part.  Host code
+// (pmg.cu) looks a part up through kernel_table(k, d, prec); every entry
+// enqueues on the given stream and returns the launch's cudaError_t, and
+// rejects (cudaErrorInvalidValue) a (dim, prec) that is not its part's.
 // Precision flag: 0 = double, 1 = float (element type of every vector).
+// Each part has its own constant-memory copy of the degree's coefficients:
+// upload() fills that copy.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -14,6 +18,7 @@ struct PatchParamsHost {
   double omega_as;
   double omega[4];
   double inv_a0;     // 1 / A_{j,1} (Cartesian)
+  int half;          // 1: half local V-cycle (no post-smoothing, §3.2.2)
 };
 
 // Deformed-geometry arrays of one mesh level (device pointers).
@@ -25,6 +30,8 @@ struct DefLevel {
 
 struct KernelTable {
   int K;
+  int dim;
+  int prec;
   cudaError_t (*prepare)();
   cudaError_t (*upload)(const double* coef);
   // y = A x (b == nullptr) or y = b - A x; Cartesian; t0..t3: scratch of N
@@ -57,6 +64,7 @@ struct KernelTable {
   int (*patch_max_threads)(int dim, int prec, int deformed);
 };
 
-const KernelTable* kernel_table(int K);
+// nullptr when k, dim or prec is out of range
+const KernelTable* kernel_table(int K, int dim, int prec);
 
 }  // namespace pmg

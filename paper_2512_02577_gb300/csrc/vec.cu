@@ -110,6 +110,148 @@ cudaError_t cg_update_p(double* p, const double* z, int64_t n, double* s, int nu
 // Flexible (Polak-Ribiere) variant: s[num] = r.z_new - r_old.z_new computed
 // by the caller; identical structure.
 
+// ------------------------------------------------------------ GMRES
+// Flexible right-preconditioned GMRES (the outer solver of the half local
+// V-cycle, §3.2.2).  The Krylov basis v_0..v_m and the preconditioned
+// vectors z_0..z_{m-1} are FP64 columns of length n with stride ld; the
+// Hessenberg matrix H is column-major with leading dimension m + 1.  The
+// small state lives in one device array (GmresState offsets) so the host
+// reads one number per step: the residual estimate |g_{j+1}|.
+
+// partial[i * kDotBlocks + b] = block b's slice of v_i . w, i = blockIdx.y
+__global__ void __launch_bounds__(256) multi_dot_partial_kernel(const double* __restrict__ V, int64_t ld,
+                                                                const double* __restrict__ w, int64_t n,
+                                                                double* __restrict__ partial) {
+  const double* v = V + (int64_t)blockIdx.y * ld;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += v[i] * w[i];
+  block_store_sum(s, partial + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// out[i] = sum of the kDotBlocks partials of vector i, fixed order (block i)
+__global__ void __launch_bounds__(256) multi_sum_kernel(const double* __restrict__ partial, int nb,
+                                                        double* __restrict__ out) {
+  const double* p = partial + (int64_t)blockIdx.x * nb;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += p[i];
+  block_store_sum(s, out + blockIdx.x);
+}
+
+cudaError_t multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* partial,
+                      double* out, cudaStream_t st) {
+  if (nv < 1 || nv > kMaxKrylov + 1) return cudaErrorInvalidValue;
+  multi_dot_partial_kernel<<<dim3(kDotBlocks, nv), 256, 0, st>>>(V, ld, w, n, partial);
+  multi_sum_kernel<<<nv, 256, 0, st>>>(partial, kDotBlocks, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// w += sgn sum_{i < nv} c_i v_i (coefficients staged in shared memory)
+__global__ void __launch_bounds__(256) multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V,
+                                                         int64_t ld, int nv, const double* __restrict__ c,
+                                                         double sgn, int64_t n) {
+  __shared__ double cs[kMaxKrylov + 1];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = sgn * c[i];
+  __syncthreads();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[k];
+    for (int i = 0; i < nv; ++i) acc += cs[i] * V[i * ld + k];
+    w[k] = acc;
+  }
+}
+
+cudaError_t multi_axpy(double* w, const double* V, int64_t ld, int nv, const double* c, double sgn, int64_t n,
+                       cudaStream_t st) {
+  if (nv < 1 || nv > kMaxKrylov + 1) return cudaErrorInvalidValue;
+  multi_axpy_kernel<<<grid_for(n, 256), 256, 0, st>>>(w, V, ld, nv, c, sgn, n);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// Start of a cycle: beta = sqrt(nrm2[0]); g = beta e_1; S[INV] = 1 / beta (0 if beta = 0)
+__global__ void gmres_start_kernel(double* __restrict__ S, const double* __restrict__ nrm2, int m) {
+  const double beta = sqrt(fmax(nrm2[0], 0.0));
+  double* g = S + GmresState::g(m);
+  g[0] = beta;
+  for (int i = 1; i <= m; ++i) g[i] = 0.0;
+  S[GmresState::inv(m)] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// Step j: H(:, j) += h2 (second Gram-Schmidt pass), H(j+1, j) = ||w||, the
+// earlier rotations on the column, a new rotation zeroing H(j+1, j), and
+// g updated; S[EST] = |g_{j+1}|, S[INV] = 1 / ||w|| (0 on breakdown).
+__global__ void gmres_givens_kernel(double* __restrict__ H, double* __restrict__ S, const double* __restrict__ nrm2,
+                                    int j, int m) {
+  double* h = H + (int64_t)j * (m + 1);
+  const double* h2 = S + GmresState::h2(m);
+  double* cs = S + GmresState::cs(m);
+  double* sn = S + GmresState::sn(m);
+  double* g = S + GmresState::g(m);
+  for (int i = 0; i <= j; ++i) h[i] += h2[i];
+  const double hn = sqrt(fmax(nrm2[0], 0.0));
+  h[j + 1] = hn;
+  S[GmresState::inv(m)] = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double a = h[i], b = h[i + 1];
+    h[i] = cs[i] * a + sn[i] * b;
+    h[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double rho = hypot(h[j], h[j + 1]);
+  const double c = rho > 0.0 ? h[j] / rho : 1.0, s = rho > 0.0 ? h[j + 1] / rho : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  h[j] = rho;
+  h[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  S[GmresState::est(m)] = fabs(g[j + 1]);
+}
+
+// dst = src * S[INV]
+__global__ void __launch_bounds__(256) scale_by_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                                       const double* __restrict__ f, int64_t n) {
+  const double a = *f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = a * src[i];
+}
+
+// y = R^{-1} g(0:k) with R the leading k x k upper triangle of the rotated H
+__global__ void gmres_backsolve_kernel(const double* __restrict__ H, double* __restrict__ S, int k, int m) {
+  const double* g = S + GmresState::g(m);
+  double* y = S + GmresState::y(m);
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int c = i + 1; c < k; ++c) t -= H[(int64_t)c * (m + 1) + i] * y[c];
+    const double d = H[(int64_t)i * (m + 1) + i];
+    y[i] = d != 0.0 ? t / d : 0.0;
+  }
+}
+
+cudaError_t gmres_start(double* S, const double* nrm2, int m, const double* r, double* v0, int64_t n,
+                        cudaStream_t st) {
+  gmres_start_kernel<<<1, 1, 0, st>>>(S, nrm2, m);
+  scale_by_kernel<<<grid_for(n, 256), 256, 0, st>>>(v0, r, S + GmresState::inv(m), n);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_givens(double* H, double* S, const double* nrm2, int j, int m, double* v, int64_t n,
+                         cudaStream_t st) {
+  gmres_givens_kernel<<<1, 1, 0, st>>>(H, S, nrm2, j, m);
+  scale_by_kernel<<<grid_for(n, 256), 256, 0, st>>>(v, v, S + GmresState::inv(m), n);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_update(const double* H, double* S, int k, int m, const double* Z, int64_t ld, double* x, int64_t n,
+                         cudaStream_t st) {
+  if (k < 1) return cudaSuccess;
+  gmres_backsolve_kernel<<<1, 1, 0, st>>>(H, S, k, m);
+  g_launches += 1;
+  return multi_axpy(x, Z, ld, k, S + GmresState::y(m), 1.0, n, st);
+}
+
 // ------------------------------------------------------------ casts
 __global__ void d2f_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -27,6 +27,38 @@ cudaError_t cg_update_xr(double* x, double* r, const double* p, const double* Ap
                          int num, int den, double* partial, double* rr_out, cudaStream_t st);
 cudaError_t cg_update_p(double* p, const double* z, int64_t n, double* s, int num, int den, int first,
                         cudaStream_t st);
+// ---- flexible GMRES (outer solver for the half local V-cycle)
+constexpr int kMaxKrylov = 64;  // largest restart length
+// Offsets of the small GMRES state in its device array (restart length m).
+struct GmresState {
+  static constexpr int cs(int m) { return 0; }
+  static constexpr int sn(int m) { return m; }
+  static constexpr int g(int m) { return 2 * m; }            // m + 1 entries
+  static constexpr int y(int m) { return 3 * m + 1; }        // m entries
+  static constexpr int h2(int m) { return 4 * m + 1; }       // m + 1 entries
+  static constexpr int inv(int m) { return 5 * m + 2; }
+  static constexpr int est(int m) { return 5 * m + 3; }
+  static constexpr int nrm2(int m) { return 5 * m + 4; }
+  static constexpr int size(int m) { return 5 * m + 5; }
+};
+// out[i] = v_i . w for i < nv (v_i = V + i ld), deterministic two-pass;
+// partial: nv * kDotBlocks doubles
+cudaError_t multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* partial,
+                      double* out, cudaStream_t st);
+// w += sgn sum_{i < nv} c_i v_i  (c on the device)
+cudaError_t multi_axpy(double* w, const double* V, int64_t ld, int nv, const double* c, double sgn, int64_t n,
+                       cudaStream_t st);
+// cycle start: beta = sqrt(*nrm2), g = beta e_1, v0 = r / beta
+cudaError_t gmres_start(double* S, const double* nrm2, int m, const double* r, double* v0, int64_t n,
+                        cudaStream_t st);
+// Arnoldi step j after orthogonalisation: Givens update of H(:, j) and g,
+// S[est] = |g_{j+1}|, then v = v / ||v|| (||v||^2 in *nrm2)
+cudaError_t gmres_givens(double* H, double* S, const double* nrm2, int j, int m, double* v, int64_t n,
+                         cudaStream_t st);
+// x += Z y with y = R^{-1} g over the first k steps of the cycle
+cudaError_t gmres_update(const double* H, double* S, int k, int m, const double* Z, int64_t ld, double* x, int64_t n,
+                         cudaStream_t st);
+
 cudaError_t cast_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
 cudaError_t cast_f2d(const float* a, double* b, int64_t n, cudaStream_t st);
 cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, const void* b, void* u, int64_t N,

@@ -38,6 +38,11 @@ def test_status_strings():
     (dict(n_cells=0), p.PMG_ERR_ARG),
     (dict(n_cells=12, n_levels=4), p.PMG_ERR_UNSUPPORTED),   # 12 not divisible by 8
     (dict(local_cycles=0), p.PMG_ERR_ARG),
+    (dict(local_half=1, outer_solver=p.OUTER_CG), p.PMG_ERR_UNSUPPORTED),  # nonsymmetric under CG
+    (dict(local_half=2), p.PMG_ERR_ARG),
+    (dict(outer_solver=p.OUTER_GMRES, gmres_restart=0), p.PMG_ERR_ARG),
+    (dict(outer_solver=p.OUTER_GMRES, gmres_restart=65), p.PMG_ERR_ARG),
+    (dict(outer_solver=7), p.PMG_ERR_ARG),
 ])
 def test_bytes_required_rejects(kw, code):
     with pytest.raises(p.PmgError) as e:
@@ -53,6 +58,18 @@ def test_bytes_required_grows_with_size():
     assert 0.5 * big < fp32 < 1.5 * big  # FP32 MG halves the hierarchy, keeps FP64 CG vectors
     # 3D n=32 Q4 (2.1M DoFs): a few hundred MB
     assert 1e8 < p.bytes_required(p.make_config(dim=3, n_cells=32, degree=4)) < 1e9
+
+
+def test_gmres_workspace_holds_its_krylov_vectors():
+    # 2m + 1 extra FP64 vectors of the finest grid (plus small state)
+    cg = p.bytes_required(p.make_config(dim=3, n_cells=16, degree=2))
+    for m in (1, 10, 30):
+        gm = p.bytes_required(p.make_config(dim=3, n_cells=16, degree=2, local_half=1, gmres_restart=m))
+        small = gm - cg - (2 * m + 1) * 33 ** 3 * 8   # Hessenberg, state, multi-dot partials
+        assert 0 <= small <= (m + 1) * (320 + m) * 8 + 2048
+    # local_half selects GMRES by default in the binding
+    assert p.make_config(local_half=1).outer_solver == p.OUTER_GMRES
+    assert p.make_config().outer_solver == p.OUTER_CG
 
 
 def test_large_coarse_level_is_accepted_for_apply_only_contexts():

@@ -361,3 +361,103 @@ def test_l2_convergence_rate(d, k, ns, geom):
     e = [_l2_error(d, n, k, geom) for n in ns]
     rate = math.log(e[-2] / e[-1], 2)
     assert abs(rate - (k + 1)) < 0.2, (e, rate)
+
+
+# ---------------------------------------------------------------- half V-cycle, GMRES
+def _vcycle_closed_form(ps, full):
+    """The local V-cycle as a matrix, by the recursion of Algorithm 3 written
+    as products: with M = omega D^{-1} and C = T B_{l-1} T^T, pre-smoothing
+    and coarse correction give X = M + C (I - A M); the full cycle adds
+    post-smoothing, B = X + M (I - A X); the half cycle stops at X."""
+    B = np.linalg.inv(ps.A[0])
+    for l in range(1, len(ps.levels)):
+        A = ps.A[l]
+        M = np.diag(ps.omega[l] * ps.Dinv[l])
+        C = ps.T[l] @ B @ ps.T[l].T
+        I = np.eye(A.shape[0])
+        X = M + C @ (I - A @ M)
+        B = X + M @ (I - A @ X) if full else X
+    return B
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (2, 7), (3, 3), (3, 4)])
+@pytest.mark.parametrize("full", [True, False])
+def test_local_vcycle_equals_closed_form(d, k, full):
+    ps = _solver(d, k)
+    n = ps.A[-1].shape[0]
+    V = np.column_stack([ps.local_solve(e, full=full) for e in np.eye(n)])
+    B = _vcycle_closed_form(ps, full)
+    np.testing.assert_allclose(V, B, atol=1e-12 * np.abs(B).max())
+    if not full:
+        # dropping post-smoothing makes the local solver nonsymmetric
+        assert np.abs(V - V.T).max() > 1e-6 * np.abs(V).max()
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (3, 4)])
+def test_two_half_vcycles_are_richardson_on_the_half_cycle(d, k):
+    # Algorithm 2 with N_iter = 2: d = B r + B (r - A B r) = (2B - B A B) r
+    ps = _solver(d, k)
+    n = ps.A[-1].shape[0]
+    B = _vcycle_closed_form(ps, False)
+    V2 = np.column_stack([ps.local_solve(e, n_iter=2, full=False) for e in np.eye(n)])
+    np.testing.assert_allclose(V2, 2 * B - B @ ps.A[-1] @ B, atol=1e-12 * np.abs(V2).max())
+
+
+def _nonsymmetric_system(n=24, seed=9):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.5
+    M = np.eye(n) + 0.1 * rng.standard_normal((n, n))     # a fixed nonsymmetric preconditioner
+    b = rng.standard_normal(n)
+    return A, M, b
+
+
+def test_gmres_reaches_direct_solution():
+    A, M, b = _nonsymmetric_system()
+    x, it, hist = solver.gmres(A, b, lambda v: M @ v, rtol=1e-13, maxit=100, restart=50)
+    assert it <= len(b)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-10)
+    assert np.linalg.norm(b - A @ x) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 5])
+def test_gmres_minimises_the_residual_over_the_krylov_space(j):
+    # x_j = M K y with K = [b, (AM) b, ..., (AM)^{j-1} b] and y the least
+    # squares minimiser of ||b - A M K y||: brute force with lstsq
+    A, M, b = _nonsymmetric_system()
+    x, it, hist = solver.gmres(A, b, lambda v: M @ v, rtol=0.0, maxit=j, restart=30)
+    assert it == j
+    K = np.column_stack([np.linalg.matrix_power(A @ M, i) @ b for i in range(j)])
+    y = np.linalg.lstsq(A @ M @ K, b, rcond=None)[0]
+    best = np.linalg.norm(b - A @ M @ K @ y)
+    res = np.linalg.norm(b - A @ x)
+    np.testing.assert_allclose(res, best, rtol=1e-9)
+    # the Givens estimate is the true residual; the history never increases
+    np.testing.assert_allclose(hist[-1] * np.linalg.norm(b), res, rtol=1e-9)
+    assert all(h1 <= h0 * (1 + 1e-12) for h0, h1 in zip(hist, hist[1:]))
+
+
+def test_gmres_restart_one_is_minimal_residual_step():
+    # GMRES(1), one step: x = alpha M b with alpha = <AMb, b> / <AMb, AMb>
+    A, M, b = _nonsymmetric_system()
+    x, it, _ = solver.gmres(A, b, lambda v: M @ v, rtol=0.0, maxit=1, restart=1)
+    w = A @ M @ b
+    np.testing.assert_allclose(x, (w @ b) / (w @ w) * (M @ b), rtol=1e-12)
+    # restarted cycles still converge on this well-conditioned system
+    x, it, _ = solver.gmres(A, b, lambda v: M @ v, rtol=1e-10, maxit=400, restart=3)
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+
+
+@pytest.mark.parametrize("d,n,k,L", [(2, 8, 3, 3), (3, 4, 3, 2)])
+def test_gmres_with_half_vcycle_matches_direct_solve(d, n, k, L):
+    m = fem.Mesh(d, n, k)
+    h = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d), full_vcycle=False)
+    fine = h.levels[-1]
+    b = np.random.default_rng(2).standard_normal(fine.A.shape[0])
+    x, it, hist = solver.solve(h, b, rtol=1e-10, outer="gmres")
+    ref = solver.direct_solve(fine.A, b)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-8
+    assert np.linalg.norm(b - fine.A @ x) <= 1.0001e-10 * np.linalg.norm(b)
+    # §3.2.2: the half cycle costs a few more outer iterations than the full one
+    hf = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d))
+    _, it_full, _ = solver.solve(hf, b, rtol=1e-10, outer="gmres")
+    assert it_full <= it <= it_full + 6
