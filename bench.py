@@ -255,16 +255,21 @@ def extra_sections(p, torch, dev, stream, flush):
 
 
 def outer_solver_section(p, torch, dev, stream, flush):
-    """3D 32^3 Q4 manufactured problem: full local V-cycle with CG and with
-    GMRES, and the half local V-cycle (§3.2.2) with GMRES, FP64 and mixed;
-    median of 3 solves (L2 flushed before each) and the smoother's patch
-    launch time."""
+    """3D 32^3 Q4 manufactured problem: additive smoother with the full
+    local V-cycle under CG and GMRES and with the half local V-cycle (§3.2.2)
+    under GMRES; multiplicative smoother (Algorithm 1, colour by colour) with
+    the full cycle under CG and the half cycle under GMRES (the paper's
+    configuration); FP64 and mixed; median of 3 solves (L2 flushed before
+    each) and the smoother's patch launch time (all patches)."""
     res = {}
     for prec, pname in ((p.FP64, "fp64"), (p.FP32, "mixed")):
-        for half, outer, name in ((0, p.OUTER_CG, "full_cg"), (0, p.OUTER_GMRES, "full_gmres"),
-                                  (1, p.OUTER_GMRES, "half_gmres")):
+        for sm, half, outer, name in ((p.ADDITIVE, 0, p.OUTER_CG, "full_cg"),
+                                      (p.ADDITIVE, 0, p.OUTER_GMRES, "full_gmres"),
+                                      (p.ADDITIVE, 1, p.OUTER_GMRES, "half_gmres"),
+                                      (p.MULTIPLICATIVE, 0, p.OUTER_CG, "mult_full_cg"),
+                                      (p.MULTIPLICATIVE, 1, p.OUTER_GMRES, "mult_half_gmres")):
             ctx = p.Context(p.make_config(dim=3, n_cells=32, degree=4, mg_precision=prec, local_half=half,
-                                          outer_solver=outer), stream=stream, device=dev)
+                                          outer_solver=outer, smoother=sm), stream=stream, device=dev)
             b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
             ctx.rhs_manufactured(b)
             x = torch.zeros_like(b)

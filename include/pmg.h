@@ -52,6 +52,15 @@ enum pmg_geometry {
 
 enum pmg_precision { PMG_FP64 = 0, PMG_FP32 = 1 };
 
+/* Vertex-patch smoother (§2.1). */
+enum pmg_smoother {
+  PMG_SMOOTHER_ADDITIVE = 0,       /* u += omega_patch sum_j Pi_j^T d_j, all patches from one residual */
+  PMG_SMOOTHER_MULTIPLICATIVE = 1  /* Algorithm 1: patches in turn, each from the current residual; run
+                                      colour by colour over the 2^d vertex-parity colours (forward in
+                                      pre-smoothing and pmg_smooth, backward in post-smoothing, so the
+                                      V-cycle stays symmetric); no damping */
+};
+
 /* Outer Krylov solver of pmg_solve (V-cycle as preconditioner). */
 enum pmg_outer {
   PMG_OUTER_CG = 0,    /* preconditioned CG: needs the symmetric (full) local V-cycle */
@@ -80,6 +89,7 @@ typedef struct pmg_config {
   int outer_solver;    /* PMG_OUTER_CG (default) or PMG_OUTER_GMRES */
   int gmres_restart;   /* GMRES cycle length m in 1..64 (default 30); the context then holds 2m + 1
                           extra FP64 vectors of the finest level */
+  int smoother;        /* PMG_SMOOTHER_ADDITIVE (default) or PMG_SMOOTHER_MULTIPLICATIVE */
 } pmg_config;
 
 typedef struct pmg_solve_info {
@@ -130,10 +140,14 @@ int pmg_apply(pmg_ctx* ctx, int level, int prec, const void* x, void* y);
 /* r = b - A_level u (the "evaluate" step of Algorithm 1, here global). */
 int pmg_residual(pmg_ctx* ctx, int level, int prec, const void* b, const void* u, void* r);
 
-/* `sweeps` additive vertex-patch sweeps on `level` >= 1:
+/* `sweeps` vertex-patch sweeps on `level` >= 1 with the configured smoother:
+ * additive,
  *   u <- u + omega_AS sum_j Pi_j^T LocalSolve_j(Pi_j (b - A u)),
- * the patch update of Algorithm 1 summed over all patches, with LocalSolve
- * = Algorithm 2 around the full p-multigrid V-cycle of Algorithm 3. */
+ * the patch update of Algorithm 1 summed over all patches; or
+ * multiplicative, Algorithm 1 itself (per parity colour: r = b - A u, then
+ * u += Pi_j^T LocalSolve_j(Pi_j r) for every patch of the colour), colours in
+ * increasing order.  LocalSolve = Algorithm 2 around the p-multigrid V-cycle
+ * of Algorithm 3 (full, or half with local_half). */
 int pmg_smooth(pmg_ctx* ctx, int level, int prec, const void* b, void* u, int sweeps);
 
 /* One geometric V-cycle on the finest level from a zero guess: z = B r

@@ -9,6 +9,17 @@ where LocalSolve is Algorithm 2 around Algorithm 3 (``patch.PatchSolver``).
 The sum is accumulated colour by colour (the 2^d parities of the vertex
 index), lexicographically within a colour; the order changes only rounding.
 
+Multiplicative smoother (Algorithm 1 as printed): patches one after the
+other, each computing its residual from the current u.  Patches of one
+parity colour have disjoint interiors, and no patch's closure meets the
+interior of another patch of its colour, so updating a whole colour from
+one residual is the same as visiting its patches one by one: a sweep is
+the sequential Algorithm 1 in colour-major order (colours 0..2^d-1 forward;
+post-smoothing visits them backward, so the V-cycle stays symmetric).
+The paper colours patches so that no two of a colour share any DoF; the
+parity colouring is the weaker condition that suffices here, because a
+patch writes only its interior.
+
 V-cycle (§2, Eq. (1)-(4)): one pre- and one post-smoothing sweep, residual,
 restriction R = P^T, recursion, prolongation P (the embedding), and an exact
 dense Cholesky solve on the coarsest level.  Pre-smoothing starts from a zero
@@ -47,7 +58,7 @@ class Level:
     """One mesh level: assembled A_l on the free DoFs and its patches."""
 
     def __init__(self, mesh, omega_jacobi, omega_patch, n_iter=1, full_vcycle=True,
-                 with_patches=True):
+                 with_patches=True, multiplicative=False):
         self.mesh = mesh
         self.A = assemble(mesh)
         self.I = mesh.interior_index()
@@ -56,6 +67,7 @@ class Level:
         self.omega_patch = omega_patch
         self.n_iter = n_iter
         self.full = full_vcycle
+        self.multiplicative = multiplicative
         self.patches = []
         if with_patches:
             verts = interior_vertices(mesh)
@@ -72,11 +84,39 @@ class Level:
             c[idx] += ps.local_solve(r[idx], self.n_iter, self.full)
         return self.omega_patch * c
 
+    def mult_sweep(self, b, u, forward=True):
+        """One multiplicative sweep (Algorithm 1), colour by colour: per
+        colour the residual b - A u, then every patch of the colour adds its
+        local solve to its interior DoFs (no damping)."""
+        u = u.copy()
+        colours = range(1 << self.mesh.d)
+        for c in (colours if forward else reversed(colours)):
+            r = b - self.A @ u
+            for v, idx, ps in self.patches:
+                if colour_of(v) == c:
+                    u[idx] += ps.local_solve(r[idx], self.n_iter, self.full)
+        return u
+
+    def mult_sweep_sequential(self, b, u, forward=True):
+        """Algorithm 1 literally: patch after patch in colour-major order,
+        each residual from the u its predecessor left (test reference for
+        ``mult_sweep``)."""
+        u = u.copy()
+        order = self.patches if forward else self.patches[::-1]
+        for v, idx, ps in order:
+            r = b - self.A @ u
+            u[idx] += ps.local_solve(r[idx], self.n_iter, self.full)
+        return u
+
     def smooth(self, b, u, sweeps=1):
-        """``sweeps`` additive sweeps u <- u + S (b - A u)."""
+        """``sweeps`` sweeps: additive u <- u + S (b - A u), or forward
+        multiplicative sweeps."""
         u = u.copy()
         for _ in range(sweeps):
-            u = u + self.smooth_correction(b - self.A @ u)
+            if self.multiplicative:
+                u = self.mult_sweep(b, u)
+            else:
+                u = u + self.smooth_correction(b - self.A @ u)
         return u
 
 
@@ -84,7 +124,7 @@ class Hierarchy:
     """Geometric hierarchy n_l = n_0 2^l, l = 0..L (finest last)."""
 
     def __init__(self, mesh, n_levels, omega_jacobi, omega_patch, n_iter=1,
-                 full_vcycle=True, smooth_steps=1):
+                 full_vcycle=True, smooth_steps=1, multiplicative=False):
         ns = [mesh.n]
         for _ in range(n_levels - 1):
             if ns[-1] % 2:
@@ -94,7 +134,8 @@ class Hierarchy:
         self.levels = []
         for l, n in enumerate(ns):
             self.levels.append(Level(mesh.with_level(n=n), omega_jacobi, omega_patch,
-                                     n_iter, full_vcycle, with_patches=(l > 0)))
+                                     n_iter, full_vcycle, with_patches=(l > 0),
+                                     multiplicative=multiplicative))
         self.P = [None] + [prolongation(self.levels[l - 1].mesh) for l in range(1, len(ns))]
         A0 = self.levels[0].A.toarray()
         self.coarse = sla.cho_factor(A0) if A0.size else None
@@ -113,13 +154,19 @@ class Hierarchy:
         lev = self.levels[l]
         u = np.zeros_like(b)
         for s in range(self.smooth_steps):
-            # the first pre-smoothing residual is b itself (zero guess)
-            r = b if s == 0 else b - lev.A @ u
-            u = u + lev.smooth_correction(r)
+            if lev.multiplicative:
+                u = lev.mult_sweep(b, u, forward=True)
+            else:
+                # the first pre-smoothing residual is b itself (zero guess)
+                r = b if s == 0 else b - lev.A @ u
+                u = u + lev.smooth_correction(r)
         r = b - lev.A @ u
         u = u + self.P[l] @ self.vcycle(self.P[l].T @ r, l - 1)
         for _ in range(self.smooth_steps):
-            u = u + lev.smooth_correction(b - lev.A @ u)
+            if lev.multiplicative:
+                u = lev.mult_sweep(b, u, forward=False)
+            else:
+                u = u + lev.smooth_correction(b - lev.A @ u)
         return u
 
 

@@ -25,6 +25,7 @@ PMG_ERR_STATE = -6
 CARTESIAN, DEFORMED = 0, 1
 FP64, FP32 = 0, 1
 OUTER_CG, OUTER_GMRES = 0, 1
+ADDITIVE, MULTIPLICATIVE = 0, 1
 
 # Every entry point declared in include/pmg.h.
 EXPORTED = [
@@ -53,6 +54,7 @@ class Config(ctypes.Structure):
         ("omega_jacobi", ctypes.c_double * 4), ("local_cycles", ctypes.c_int),
         ("smooth_steps", ctypes.c_int), ("patches_per_block", ctypes.c_int),
         ("local_half", ctypes.c_int), ("outer_solver", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+        ("smoother", ctypes.c_int),
     ]
 
 
@@ -122,7 +124,8 @@ def _check(code):
 
 def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, deform_amp=0.05,
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
-                smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30):
+                smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
+                smoother=ADDITIVE):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -137,6 +140,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.local_half = local_half
     c.outer_solver = (OUTER_GMRES if local_half else OUTER_CG) if outer_solver is None else outer_solver
     c.gmres_restart = gmres_restart
+    c.smoother = smoother
     return c
 
 

@@ -77,12 +77,12 @@ template <int DIM, typename T>
 static cudaError_t patch_cart_t(const T* r, T* dst, int n, int ppc, int n_iter, const T* dinv,
                                 const PatchParamsHost& H, cudaStream_t st) {
   using S = PatchShape<DIM>;
-  if (n < 2) return cudaSuccess;  // no interior vertex, no patch
+  const int64_t np = patch_count(DIM, n, H.colour);
+  if (np == 0) return cudaSuccess;  // no interior vertex (of this colour), no patch
   if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
-  const int64_t np = ipow(n - 1, DIM);
   const int64_t blocks = (np + ppc - 1) / ppc;
-  const int threads = std::min(256, (ppc * S::TPP + 31) / 32 * 32);
-  if (ppc * S::TPP > 256) return cudaErrorInvalidConfiguration;
+  // more patch lines than threads is fine: every step loops over its lines
+  const int threads = std::min(kPatchMaxThreads, (ppc * S::TPP + 31) / 32 * 32);
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const int smem = ppc * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;

@@ -535,20 +535,26 @@ struct PatchMeta {
   int active;
 };
 
+// Patch pid of the launch: lexicographic (x fastest) over all interior
+// vertices (colour < 0) or over those of parity colour `colour` (vertex
+// index 2 i + 1 for an odd parity bit, 2 i + 2 for an even one).
 template <int DIM>
-__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n) {
-  const int nv = n - 1;
-  const int64_t npatch = DIM == 3 ? (int64_t)nv * nv * nv : (int64_t)nv * nv;
+__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n, int colour) {
+  const int c0 = patch_count_1d(n, colour, 0), c1 = patch_count_1d(n, colour, 1);
+  const int64_t npatch = patch_count(DIM, n, colour);
+  const int step = colour < 0 ? 1 : 2;
+  const int b0 = colour < 0 || (colour & 1) ? 1 : 2, b1 = colour < 0 || ((colour >> 1) & 1) ? 1 : 2;
+  const int b2 = colour < 0 || ((colour >> 2) & 1) ? 1 : 2;
   for (int g = threadIdx.x; g < np; g += blockDim.x) {
     const int64_t pid = (int64_t)blockIdx.x * np + g;
     PatchMeta m;
     m.active = pid < npatch;
     int64_t t = m.active ? pid : 0;
-    m.v[0] = (int)(t % nv) + 1;
-    t /= nv;
-    m.v[1] = (int)(t % nv) + 1;
-    t /= nv;
-    m.v[2] = DIM == 3 ? (int)t + 1 : 0;
+    m.v[0] = b0 + step * (int)(t % c0);
+    t /= c0;
+    m.v[1] = b1 + step * (int)(t % c1);
+    t /= c1;
+    m.v[2] = DIM == 3 ? b2 + step * (int)t : 0;
     for (int d = 0; d < 3; ++d) m.g0[d] = (d < DIM) ? K * (m.v[d] - 1) + 1 : 0;
     meta[g] = m;
   }
@@ -568,15 +574,23 @@ __device__ __forceinline__ int64_t patch_node(const PatchMeta& m, int i, int N1)
   return (int64_t)(m.g0[0] + ix) + (int64_t)N1 * ((m.g0[1] + iy) + (int64_t)N1 * (m.g0[2] + iz));
 }
 
-// Cartesian patches: gather r_j, Algorithm 2/3, write omega_AS d_j.
-// At most 256 threads per block: every degree's patch lines fit (at most 225
-// per patch).  For moderate degrees, ask for three blocks per SM (registers
-// <= 85) so that 24 warps keep the FP64 pipe fed; longer lines need more
-// registers than that without spilling.
-constexpr int kPatchMinBlocks = K <= 4 ? 3 : 1;
+// Cartesian patches: gather r_j, Algorithm 2/3, write omega_AS d_j
+// (additive), or add d_j to u for the patches of one colour (multiplicative).
+// Degrees up to 4: at most 256 threads per block and three blocks per SM
+// (registers <= 85), so that 24 warps keep the FP64 pipe fed.  Higher
+// degrees need more registers per line than that without spilling and run
+// fastest with the compiler's own choice (measured: bounding k = 7 to 256
+// threads made its FP32 launch 40% slower).
+#if PMG_K <= 4
+#define PMG_PATCH_BOUNDS __launch_bounds__(256, 3)
+constexpr int kPatchMaxThreads = 256;
+#else
+#define PMG_PATCH_BOUNDS
+constexpr int kPatchMaxThreads = 1024;
+#endif
 
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256, kPatchMinBlocks)
+__global__ void PMG_PATCH_BOUNDS
     patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
                       const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
   using S = PatchShape<DIM>;
@@ -588,7 +602,7 @@ __global__ void __launch_bounds__(256, kPatchMinBlocks)
   const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
   T* sdinv = reinterpret_cast<T*>(smraw) + np * stride;  // inverse-diagonal tables of all p-levels
   for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
-  patch_meta_init<DIM>(meta, np, n);
+  patch_meta_init<DIM>(meta, np, n, P.colour);
   __syncthreads();
   const int N1 = K * n + 1;
   pfor<SZT>(np, [&](int g, int i) {  // gather r_j = Pi_j r
@@ -601,7 +615,9 @@ __global__ void __launch_bounds__(256, kPatchMinBlocks)
   const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   pfor<SZT>(np, [&](int g, int i) {
     const PatchMeta& m = meta[g];
-    if (m.active) dst[patch_colour<DIM>(m) * N + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
+    if (!m.active) return;
+    if (P.colour < 0) dst[patch_colour<DIM>(m) * N + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
+    else dst[patch_node<DIM>(m, i, N1)] += pb.at(g)[DT + i];  // one patch of the colour per node
   });
 }
 
@@ -732,6 +748,7 @@ static PatchParams<T> to_params(const PatchParamsHost& H) {
   P.inv_a0 = (T)H.inv_a0;
   P.inv_scale = (T)(1.0 / H.scale);
   P.half = H.half;
+  P.colour = H.colour;
   return P;
 }
 

@@ -451,7 +451,7 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
   constexpr int EL = DS::template elems<T>();
   const int stride = EL + (n_iter > 1 ? 2 * SZT : 0);
   const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
-  patch_meta_init<DIM>(meta, np, n);
+  patch_meta_init<DIM>(meta, np, n, P.colour);
   __syncthreads();
   for (int g = threadIdx.x; g < np; g += blockDim.x) {  // p = 1: the vertex's inverse Q1 diagonal
     const int* v = meta[g].v;
@@ -472,7 +472,9 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
   const int64_t NN = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   pfor<SZT>(np, [&](int g, int i) {
     const PatchMeta& m = meta[g];
-    if (m.active) dst[patch_colour<DIM>(m) * NN + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
+    if (!m.active) return;
+    if (P.colour < 0) dst[patch_colour<DIM>(m) * NN + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
+    else dst[patch_node<DIM>(m, i, N1)] += pb.at(g)[DT + i];  // one patch of the colour per node
   });
 }
 
@@ -492,8 +494,8 @@ static int patch_def_smem(int dim, int prec, int n_iter) {
 template <int DIM, typename T>
 static cudaError_t patch_def_t(const T* r, T* dst, int n, int np, int n_iter, const DefLevel& L,
                                const PatchParamsHost& H, cudaStream_t st) {
-  if (n < 2) return cudaSuccess;
-  const int64_t npatch = ipow(n - 1, DIM);
+  const int64_t npatch = patch_count(DIM, n, H.colour);
+  if (npatch == 0) return cudaSuccess;
   if (np < 1 || np > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
   const int smem = np * patch_def_smem(DIM, sizeof(T) == 8 ? 0 : 1, n_iter);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;

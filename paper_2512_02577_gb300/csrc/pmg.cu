@@ -141,6 +141,8 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_ARG, "unknown outer_solver");
   if (cfg->outer_solver == PMG_OUTER_GMRES && (cfg->gmres_restart < 1 || cfg->gmres_restart > kMaxKrylov))
     return fail(PMG_ERR_ARG, "gmres_restart must be in 1..64");
+  if (cfg->smoother != PMG_SMOOTHER_ADDITIVE && cfg->smoother != PMG_SMOOTHER_MULTIPLICATIVE)
+    return fail(PMG_ERR_ARG, "unknown smoother");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
     return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
@@ -293,6 +295,7 @@ PatchParamsHost patch_params(const pmg_ctx* c, int level) {
   for (int i = 0; i < 4; ++i) P.omega[i] = c->omega_j[i];
   P.inv_a0 = c->lv[level].inv_a0;
   P.half = c->cfg.local_half;
+  P.colour = -1;
   return P;
 }
 
@@ -329,9 +332,11 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
 
 // Local solves of every patch of the level for the residual r, written to
 // the patch buffer as omega_AS d_j (one launch).
-int patch_solves(pmg_ctx* c, int level, const void* r) {
+int patch_solves(pmg_ctx* c, int level, const void* r, int colour = -1, void* u = nullptr) {
   LevelData& L = c->lv[level];
-  const PatchParamsHost P = patch_params(c, level);
+  PatchParamsHost P = patch_params(c, level);
+  P.colour = colour;
+  void* dst = colour < 0 ? c->pbuf : u;
   cudaError_t e;
   if (c->deformed) {
     DefLevel D{};
@@ -340,10 +345,9 @@ int patch_solves(pmg_ctx* c, int level, const void* r) {
       D.dinv[i] = L.dinv[i];
     }
     D.dinv1 = L.dinv1;
-    e = c->km()->patch_def(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+    e = c->km()->patch_def(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
   } else {
-    e = c->km()->patch_cart(c->dim, c->mgprec, r, c->pbuf, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
-                          c->stream);
+    e = c->km()->patch_cart(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P, c->stream);
   }
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
   return PMG_OK;
@@ -358,8 +362,35 @@ int patch_sweep(pmg_ctx* c, int level, const void* r, void* u, bool add) {
   return PMG_OK;
 }
 
-int smooth_level(pmg_ctx* c, int level, const void* b, void* u, int sweeps) {
+// One multiplicative sweep (Algorithm 1) colour by colour: per parity colour
+// the residual r = b - A u, then every patch of the colour adds its local
+// solve to u (patches of a colour have disjoint interiors and none reads
+// another's interior, so this is the sequential patch loop in colour-major
+// order).  zero_guess: u starts at 0 and the first residual is b.
+int mult_sweep(pmg_ctx* c, int level, const void* b, void* u, bool forward, bool zero_guess) {
   LevelData& L = c->lv[level];
+  const int nc = 1 << c->dim;
+  const size_t es = c->mg32 ? 4 : 8;
+  if (zero_guess) PMG_CUDA(cudaMemsetAsync(u, 0, es * L.N, c->stream));
+  for (int i = 0; i < nc; ++i) {
+    const int colour = forward ? i : nc - 1 - i;
+    const void* r = b;
+    if (!(zero_guess && i == 0)) {
+      if (int rc = level_apply(c, level, c->mgprec, u, L.r, b)) return rc;
+      r = L.r;
+    }
+    if (int rc = patch_solves(c, level, r, colour, u)) return rc;
+  }
+  return PMG_OK;
+}
+
+int smooth_level(pmg_ctx* c, int level, const void* b, void* u, int sweeps, bool forward = true) {
+  LevelData& L = c->lv[level];
+  if (c->cfg.smoother == PMG_SMOOTHER_MULTIPLICATIVE) {
+    for (int s = 0; s < sweeps; ++s)
+      if (int rc = mult_sweep(c, level, b, u, forward, false)) return rc;
+    return PMG_OK;
+  }
   for (int s = 0; s < sweeps; ++s) {
     int rc = level_apply(c, level, c->mgprec, u, L.r, b);
     if (rc) return rc;
@@ -383,7 +414,9 @@ int vcycle_level(pmg_ctx* c, int level) {
   const int nu = c->cfg.smooth_steps;
   int rc;
   for (int s = 0; s < nu; ++s) {
-    if (s == 0) {
+    if (c->cfg.smoother == PMG_SMOOTHER_MULTIPLICATIVE) {
+      rc = mult_sweep(c, level, L.b, L.u, true, s == 0);  // forward colours
+    } else if (s == 0) {
       rc = patch_sweep(c, level, L.b, L.u, false);  // zero guess: the residual is b, u = S b
     } else {
       rc = smooth_level(c, level, L.b, L.u, 1);
@@ -397,7 +430,8 @@ int vcycle_level(pmg_ctx* c, int level) {
   if ((rc = vcycle_level(c, level - 1))) return rc;
   e = c->km()->h_prolong_add(c->dim, c->mgprec, C.u, L.u, c->t_mg[0], c->t_mg[1], C.n, c->stream);
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("prolongate: ") + cudaGetErrorString(e));
-  return smooth_level(c, level, L.b, L.u, nu);
+  // post-smoothing visits the colours backward: the V-cycle stays symmetric
+  return smooth_level(c, level, L.b, L.u, nu, false);
 }
 
 // Coarsest level, set up before the first V-cycle: assemble A_0 on the free
@@ -754,6 +788,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->local_half = 0;
   cfg->outer_solver = PMG_OUTER_CG;
   cfg->gmres_restart = 30;
+  cfg->smoother = PMG_SMOOTHER_ADDITIVE;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {

@@ -96,6 +96,20 @@ struct PatchParams {
   T inv_a0;       // 1 / A_{j,1} on Cartesian meshes (uniform)
   T inv_scale;    // 1 / scale
   int half;       // 1: half local V-cycle (post-smoothing dropped, §3.2.2)
+  int colour;     // -1: all patches (additive); c >= 0: patches of parity colour c
 };
+
+// Interior vertices (patches) of a level with n cells per side: all (n-1)^d,
+// or those of parity colour c (bit d of c = parity of the d-th vertex index;
+// odd indices 1, 3, ... number n / 2, even ones 2, 4, ... (n - 1) / 2).
+__host__ __device__ inline int patch_count_1d(int n, int colour, int d) {
+  if (colour < 0) return n - 1;
+  return ((colour >> d) & 1) ? n / 2 : (n - 1) / 2;
+}
+__host__ __device__ inline int64_t patch_count(int dim, int n, int colour) {
+  int64_t c = 1;
+  for (int d = 0; d < dim; ++d) c *= patch_count_1d(n, colour, d);
+  return n < 2 ? 0 : c;
+}
 
 }  // namespace pmg

@@ -19,6 +19,9 @@ struct PatchParamsHost {
   double omega[4];
   double inv_a0;     // 1 / A_{j,1} (Cartesian)
   int half;          // 1: half local V-cycle (no post-smoothing, §3.2.2)
+  int colour;        // -1: every patch, additive output (omega_AS d_j per colour
+                     // vector); c >= 0: only the patches of parity colour c,
+                     // u += d_j added straight into dst (multiplicative sweep)
 };
 
 // Deformed-geometry arrays of one mesh level (device pointers).

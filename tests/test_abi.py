@@ -43,6 +43,7 @@ def test_status_strings():
     (dict(outer_solver=p.OUTER_GMRES, gmres_restart=0), p.PMG_ERR_ARG),
     (dict(outer_solver=p.OUTER_GMRES, gmres_restart=65), p.PMG_ERR_ARG),
     (dict(outer_solver=7), p.PMG_ERR_ARG),
+    (dict(smoother=2), p.PMG_ERR_ARG),
 ])
 def test_bytes_required_rejects(kw, code):
     with pytest.raises(p.PmgError) as e:

@@ -461,3 +461,62 @@ def test_gmres_with_half_vcycle_matches_direct_solve(d, n, k, L):
     hf = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d))
     _, it_full, _ = solver.solve(hf, b, rtol=1e-10, outer="gmres")
     assert it_full <= it <= it_full + 6
+
+
+# ---------------------------------------------------------------- multiplicative smoother
+@pytest.mark.parametrize("d,n,k", [(2, 6, 2), (2, 5, 3), (3, 4, 2)])
+@pytest.mark.parametrize("forward", [True, False])
+def test_colour_sweep_equals_sequential_patch_loop(d, n, k, forward):
+    # Algorithm 1 visited patch by patch (residual recomputed after every
+    # patch) equals the colour-by-colour update
+    m = fem.Mesh(d, n, k)
+    lev = solver.Level(m, constants.omega_jacobi(d, k), constants.omega_patch(d), multiplicative=True)
+    rng = np.random.default_rng(8)
+    b, u = rng.standard_normal(len(lev.I)), rng.standard_normal(len(lev.I))
+    np.testing.assert_allclose(lev.mult_sweep(b, u, forward), lev.mult_sweep_sequential(b, u, forward),
+                               atol=1e-12 * np.abs(u).max())
+
+
+def test_multiplicative_sweep_with_exact_solves_is_a_product_of_projections():
+    # exact local solves: each patch step is u <- u + P_j (x - u) with the
+    # A-orthogonal projection P_j = Pi_j^T A_j^{-1} Pi_j A, so the error
+    # e = x - u never grows in the energy norm and the sweep equals the
+    # product of (I - P_j) applied to e, patch by patch
+    d, n, k = 2, 4, 3
+    m = fem.Mesh(d, n, k)
+    lev = solver.Level(m, constants.omega_jacobi(d, k), constants.omega_patch(d), multiplicative=True)
+    A = lev.A.toarray()
+    N = A.shape[0]
+    for _, idx, ps in lev.patches:
+        ps.local_solve = lambda r, n_iter=1, full=True, ps=ps: ps.exact_solve(r)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(N)
+    b = A @ x
+    u = lev.mult_sweep(b, np.zeros(N))
+    e = x.copy()
+    for _, idx, ps in lev.patches:
+        Pj = np.zeros((N, N))
+        Pj[np.ix_(idx, idx)] = np.linalg.inv(A[np.ix_(idx, idx)])
+        e = e - Pj @ A @ e
+    np.testing.assert_allclose(x - u, e, atol=1e-10 * np.abs(x).max())
+    assert (x - u) @ A @ (x - u) < x @ A @ x
+
+
+@pytest.mark.parametrize("d,n,k,L", [(2, 8, 3, 3), (3, 4, 2, 2)])
+def test_multiplicative_vcycle_symmetric_and_cg_converges(d, n, k, L):
+    m = fem.Mesh(d, n, k)
+    h = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d), multiplicative=True)
+    fine = h.levels[-1]
+    N = fine.A.shape[0]
+    rng = np.random.default_rng(5)
+    cols = rng.standard_normal((N, 6))
+    Bc = np.column_stack([h.vcycle(c) for c in cols.T])
+    # forward pre- and backward post-smoothing: <B x, y> = <x, B y>
+    np.testing.assert_allclose(cols.T @ Bc, (cols.T @ Bc).T, atol=1e-11 * np.abs(Bc).max())
+    b = rng.standard_normal(N)
+    x, it, _ = solver.solve(h, b, rtol=1e-10)
+    np.testing.assert_allclose(x, solver.direct_solve(fine.A, b), rtol=1e-7, atol=1e-9)
+    # the multiplicative smoother needs no more iterations than the additive one
+    ha = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d))
+    _, it_add, _ = solver.solve(ha, b, rtol=1e-10)
+    assert it <= it_add
