@@ -34,9 +34,9 @@ ORACLE_N = 4          # bounded CPU sample: same degree and dimension, 4^3 cells
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (measured 1.255 with a project FMA probe)
 FP32_PEAK_TFLOPS = 78.5  # measured FP32 FMA (128 lanes x 152 SMs x 2 x ~2.0 GHz)
 # DRAM bytes (read + write) of one FP64 patch launch at 32^3 Q4, from the ncu
-# capture summarised in profiles/patch_cart_kernel_fp64_3d_q4.md (57.11 MB +
-# 54.63 MB); to be re-taken whenever patch_cart_kernel changes.
-PATCH64_TRAFFIC_BYTES = 111739648
+# capture summarised in profiles/patch_cart_kernel_fp64_3d_q4.md (57.21 MB +
+# 54.93 MB); to be re-taken whenever patch_cart_kernel changes.
+PATCH64_TRAFFIC_BYTES = 112135168
 
 
 # ----------------------------------------------------------------- flop model
@@ -239,6 +239,7 @@ def extra_sections(p, torch, dev, stream, flush):
     ctx.close()
     del b, b32, y32, x
     out["outer_solvers_32_q4"] = outer_solver_section(p, torch, dev, stream, flush)
+    out["distorted_64_q3_mixed"] = distorted_section(p, torch, dev, stream, flush)
     from paper_2512_02577_gb300 import serve
     from paper_2512_02577_gb300.inputs import serving_requests
     reqs = serving_requests(n_requests=64, rate=50.0, n_hi=32)
@@ -252,6 +253,43 @@ def extra_sections(p, torch, dev, stream, flush):
     _, summ = serve.run(reqs, precision=p.FP32, max_active=16)
     out["serving_sample_warm"] = dict(summ, workload=workload, process="warm")
     return out
+
+
+def distorted_section(p, torch, dev, stream, flush):
+    """Randomly distorted 3D 64^3 Q3 mesh (7,189,057 DoFs; every interior
+    vertex moved by 0.25 h in a random direction, seed 2512), mixed
+    precision: additive smoother with the full local cycle under CG and with
+    the half cycle under GMRES; median of 3 solves (L2 flushed before each),
+    plus the stored-G_q FP32 apply."""
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    n, k, delta = 64, 3, 0.25
+    disp = vertex_displacements(3, n, delta, 2512)
+    res = {"delta": delta}
+    for half, outer, name in ((0, p.OUTER_CG, "full_cg"), (1, p.OUTER_GMRES, "half_gmres")):
+        ctx = p.Context(p.make_config(dim=3, n_cells=n, degree=k, geometry=p.DISTORTED, vertex_disp=disp,
+                                      mg_precision=p.FP32, local_half=half, outer_solver=outer),
+                        stream=stream, device=dev)
+        b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
+        ctx.rhs_manufactured(b)
+        x = torch.zeros_like(b)
+        ctx.solve(b, x)
+        infos = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            infos.append(ctx.solve(b, x))
+        res[name] = {"solve_ms_p50": pct([i.time_ms for i in infos], 50), "iterations": infos[-1].iterations,
+                     "rel_residual": infos[-1].rel_residual, "l2_error": ctx.l2_error_manufactured(x),
+                     "smoother_phases_ms": dict(zip(("residual", "patch", "gather"),
+                                                    ctx.smoother_phase_times(reps=3)))}
+        if name == "full_cg":
+            b32, y32 = b.float(), torch.empty(ctx.num_dofs(), dtype=torch.float32, device=dev)
+            res["dofs"] = ctx.num_dofs()
+            res["apply_fp32_ms"] = _timed_ms(torch, stream, flush, lambda: ctx.apply(b32, y32, prec=p.FP32))
+            del b32, y32
+        ctx.close()
+        del b, x
+    return res
 
 
 def outer_solver_section(p, torch, dev, stream, flush):

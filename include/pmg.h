@@ -47,7 +47,11 @@ enum pmg_status {
 
 enum pmg_geometry {
   PMG_GEOM_CARTESIAN = 0,   /* x = X on the uniform mesh */
-  PMG_GEOM_DEFORMED = 1     /* x = X + a prod_i sin(2 pi X_i) (1,..,1), analytic */
+  PMG_GEOM_DEFORMED = 1,    /* x = X + a prod_i sin(2 pi X_i) (1,..,1), analytic */
+  PMG_GEOM_DISTORTED = 2    /* randomly distorted mesh (§3.2.2, §4): the finest mesh's vertices moved by
+                               vertex_disp, every cell of every level the trilinear (2D: bilinear) image
+                               of its displaced corners; a coarse vertex is the fine vertex at the same
+                               grid position (levels nested topologically, Eq. (2) transfers unchanged) */
 };
 
 enum pmg_precision { PMG_FP64 = 0, PMG_FP32 = 1 };
@@ -90,6 +94,11 @@ typedef struct pmg_config {
   int gmres_restart;   /* GMRES cycle length m in 1..64 (default 30); the context then holds 2m + 1
                           extra FP64 vectors of the finest level */
   int smoother;        /* PMG_SMOOTHER_ADDITIVE (default) or PMG_SMOOTHER_MULTIPLICATIVE */
+  const double* vertex_disp; /* PMG_GEOM_DISTORTED only (else ignored): HOST array of the displacements
+                          of the finest mesh's (n_cells + 1)^d vertices, d doubles per vertex, vertices
+                          lexicographic with x fastest; boundary vertices must have zero normal
+                          displacement for the domain to stay the unit square/cube, and no cell may
+                          be inverted.  Read by pmg_create only (copied); the caller keeps ownership */
 } pmg_config;
 
 typedef struct pmg_solve_info {

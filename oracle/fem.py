@@ -15,6 +15,12 @@ quadrature points (§4 uses deformed meshes; this analytic map is the reading
 for the smoothly deformed configuration).  F is the identity on the boundary,
 so the domain stays the unit cube, and since F is one global map, coarse
 spaces are exactly nested in fine ones (§2: topological nestedness).
+Or a randomly distorted mesh (§3.2.2, §4): the vertices of the finest mesh
+displaced (an input array), every cell of every level the trilinear
+(bilinear in 2D) image of the reference cell spanned by its displaced
+corners; a coarse vertex is the fine vertex at the same grid position, so
+the levels are nested topologically but not geometrically (the transfers
+stay the reference embedding, Eq. (2)).
 """
 import itertools
 
@@ -30,19 +36,24 @@ class Mesh:
     geometry ('cartesian' or 'deformed' with amplitude ``amp``), and whether
     the stored quadrature-point tensors are rounded to float32."""
 
-    def __init__(self, d, n, k, geometry="cartesian", amp=0.05, geom_fp32=False):
+    def __init__(self, d, n, k, geometry="cartesian", amp=0.05, geom_fp32=False, disp=None, n_fine=None):
         if d not in (2, 3):
             raise ValueError("d in {2, 3}")
         self.d, self.n, self.k = d, n, k
         self.geometry = geometry
         self.amp = amp
+        # distorted: displacements of the finest mesh's (n_fine + 1)^d vertices
+        self.disp = None if disp is None else np.asarray(disp, dtype=np.float64)
+        self.n_fine = n if n_fine is None else n_fine
+        if geometry == "distorted" and (self.disp is None or self.n_fine % n):
+            raise ValueError("distorted geometry needs fine-vertex displacements and n | n_fine")
         self.geom_fp32 = bool(geom_fp32) and geometry != "cartesian"
         self.h = 1.0 / n
         self.n1 = k * n + 1
 
     def with_level(self, n=None, k=None):
         return Mesh(self.d, self.n if n is None else n, self.k if k is None else k,
-                    self.geometry, self.amp, self.geom_fp32)
+                    self.geometry, self.amp, self.geom_fp32, self.disp, self.n_fine)
 
     @property
     def n_dofs(self):
@@ -88,6 +99,8 @@ class Mesh:
         if self.geometry == "cartesian":
             J = np.broadcast_to(np.eye(d), X.shape[:-1] + (d, d)).copy()
             return X.copy(), J
+        if self.geometry == "distorted":
+            return self._trilinear_map(X)
         s = np.sin(2 * np.pi * X)
         c = np.cos(2 * np.pi * X)
         prod = np.prod(s, axis=-1)
@@ -101,6 +114,39 @@ class Mesh:
             # dF_i / dX_j = delta_ij + a 2 pi cos(2 pi X_j) prod_{m != j} sin(2 pi X_m)
             J[..., :, j] += self.amp * 2 * np.pi * c[..., j][..., None] * others[..., None]
         return x, J
+
+    def vertex_position(self, v):
+        """Physical position of vertex v (integer index per direction) of this
+        level: the reference position plus the displacement of the fine
+        vertex at the same place."""
+        stride = self.n_fine // self.n
+        vf = [vi * stride for vi in v]
+        flat = sum(vf[m] * (self.n_fine + 1) ** m for m in range(self.d))
+        return np.asarray(v, dtype=np.float64) / self.n + self.disp[flat]
+
+    def _trilinear_map(self, X):
+        """x(X) and dx/dX for the trilinear cells: in cell c (the one holding
+        X; the map is continuous across cells), xi = n X - c in [0, 1]^d and
+        x = sum over the 2^d corners s of prod_m N_{s_m}(xi_m) P_{c+s} with
+        N_0(t) = 1 - t, N_1(t) = t; dx/dX = n dx/dxi.  All points at once."""
+        d = self.d
+        shape = X.shape[:-1]
+        Xf = X.reshape(-1, d)
+        c = np.minimum(np.floor(Xf * self.n).astype(np.int64), self.n - 1)
+        xi = Xf * self.n - c
+        stride = self.n_fine // self.n
+        x = np.zeros_like(Xf)
+        J = np.zeros((Xf.shape[0], d, d))
+        for s in itertools.product(*([(0, 1)] * d)):
+            v = c + np.array(s)
+            flat = sum(v[:, m] * stride * (self.n_fine + 1) ** m for m in range(d))
+            P = v / self.n + self.disp[flat]                  # displaced corner positions
+            N = [xi[:, m] if s[m] else 1.0 - xi[:, m] for m in range(d)]
+            x += np.prod(N, axis=0)[:, None] * P
+            for j in range(d):
+                g = self.n * (1.0 if s[j] else -1.0) * np.prod([N[m] for m in range(d) if m != j], axis=0)
+                J[:, :, j] += g[:, None] * P
+        return x.reshape(shape + (d,)), J.reshape(shape + (d, d))
 
     def cell_quadrature(self, c, nq):
         """Reference tensor Gauss points of cell c: returns (X points (Q, d),

@@ -9,6 +9,8 @@ raises: there is no fallback implementation.
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -22,7 +24,7 @@ PMG_ERR_OOM = -3
 PMG_ERR_CUDA = -4
 PMG_ERR_DEVICE_TIMEOUT = -5
 PMG_ERR_STATE = -6
-CARTESIAN, DEFORMED = 0, 1
+CARTESIAN, DEFORMED, DISTORTED = 0, 1, 2
 FP64, FP32 = 0, 1
 OUTER_CG, OUTER_GMRES = 0, 1
 ADDITIVE, MULTIPLICATIVE = 0, 1
@@ -54,7 +56,7 @@ class Config(ctypes.Structure):
         ("omega_jacobi", ctypes.c_double * 4), ("local_cycles", ctypes.c_int),
         ("smooth_steps", ctypes.c_int), ("patches_per_block", ctypes.c_int),
         ("local_half", ctypes.c_int), ("outer_solver", ctypes.c_int), ("gmres_restart", ctypes.c_int),
-        ("smoother", ctypes.c_int),
+        ("smoother", ctypes.c_int), ("vertex_disp", ctypes.c_void_p),
     ]
 
 
@@ -125,7 +127,7 @@ def _check(code):
 def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, deform_amp=0.05,
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
                 smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
-                smoother=ADDITIVE):
+                smoother=ADDITIVE, vertex_disp=None):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -141,6 +143,14 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.outer_solver = (OUTER_GMRES if local_half else OUTER_CG) if outer_solver is None else outer_solver
     c.gmres_restart = gmres_restart
     c.smoother = smoother
+    if vertex_disp is not None:
+        # ((n+1)^d, d) float64 displacements of the finest mesh's vertices;
+        # the config keeps a reference so the array outlives it
+        d = np.ascontiguousarray(vertex_disp, dtype=np.float64)
+        if d.shape != ((n_cells + 1) ** dim, dim):
+            raise ValueError("vertex_disp must have shape ((n_cells + 1)^dim, dim)")
+        c._vertex_disp_ref = d
+        c.vertex_disp = d.ctypes.data
     return c
 
 

@@ -114,6 +114,7 @@ struct Plan {
   std::vector<LOff> lo;
   int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad, cx0, cy0;
   int64_t pbuf = -1, cellbuf = -1;
+  int64_t verts = -1;  // distorted: positions of the finest mesh's vertices
   int64_t dtab_len = 0;
   // flexible GMRES (outer_solver GMRES): basis v_0..v_m, z_0..z_{m-1},
   // Hessenberg (m+1) x m, small state, multi-dot partials
@@ -132,8 +133,11 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   if (cfg->dim != 2 && cfg->dim != 3) return fail(PMG_ERR_UNSUPPORTED, "dim must be 2 or 3");
   if (cfg->degree < 1 || cfg->degree > 8) return fail(PMG_ERR_UNSUPPORTED, "degree must be in 1..8");
   if (cfg->n_cells < 1) return fail(PMG_ERR_ARG, "n_cells must be >= 1");
-  if (cfg->geometry != PMG_GEOM_CARTESIAN && cfg->geometry != PMG_GEOM_DEFORMED)
+  if (cfg->geometry != PMG_GEOM_CARTESIAN && cfg->geometry != PMG_GEOM_DEFORMED &&
+      cfg->geometry != PMG_GEOM_DISTORTED)
     return fail(PMG_ERR_ARG, "unknown geometry");
+  if (cfg->geometry == PMG_GEOM_DISTORTED && !cfg->vertex_disp)
+    return fail(PMG_ERR_ARG, "distorted geometry needs vertex_disp");
   if (cfg->mg_precision != PMG_FP64 && cfg->mg_precision != PMG_FP32) return fail(PMG_ERR_ARG, "unknown precision");
   if (cfg->local_cycles < 1 || cfg->smooth_steps < 1) return fail(PMG_ERR_ARG, "local_cycles, smooth_steps >= 1");
   if (cfg->local_half != 0 && cfg->local_half != 1) return fail(PMG_ERR_ARG, "local_half must be 0 or 1");
@@ -147,7 +151,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
   P.K = cfg->degree;
-  P.deformed = cfg->geometry == PMG_GEOM_DEFORMED;
+  P.deformed = cfg->geometry != PMG_GEOM_CARTESIAN;  // general geometry: stored G_q
   P.mg32 = cfg->mg_precision == PMG_FP32;
   P.mg_es = P.mg32 ? 4 : 8;
   P.nplev = nlev(P.K);
@@ -227,6 +231,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   // operator results (FP64 for the CG)
   const int nf = cfg->n_cells;
   P.pbuf = bump(cur, (int64_t)(1 << P.dim) * ipow64((int64_t)P.K * nf + 1, P.dim) * P.mg_es);
+  if (cfg->geometry == PMG_GEOM_DISTORTED) P.verts = bump(cur, ipow64(nf + 1, P.dim) * P.dim * 8);
   if (P.deformed) P.cellbuf = bump(cur, ipow64(nf, P.dim) * ipow64(P.K + 1, P.dim) * 8);
   P.total = cur;
   return PMG_OK;
@@ -275,6 +280,7 @@ struct pmg_ctx {
   bool coarse_ready = false;
   void* pbuf = nullptr;
   void* cellbuf = nullptr;
+  double* verts = nullptr;  // distorted geometry: finest-mesh vertex positions
   int ppc = 1;
   double omega_as = 0;
   double omega_j[4] = {1, 1, 1, 1};
@@ -297,6 +303,15 @@ PatchParamsHost patch_params(const pmg_ctx* c, int level) {
   P.half = c->cfg.local_half;
   P.colour = -1;
   return P;
+}
+
+GeomDesc geom_desc(const pmg_ctx* c) {
+  GeomDesc g{};
+  g.kind = c->cfg.geometry == PMG_GEOM_DISTORTED ? 2 : (c->deformed ? 1 : 0);
+  g.amp = c->cfg.deform_amp;
+  g.verts = c->verts;
+  g.n_fine = c->lv[c->L - 1].n;
+  return g;
 }
 
 QuadTab make_tab(int p, int nq) {
@@ -689,6 +704,7 @@ int setup_context(pmg_ctx* c) {
   c->ainv = at(c, P.ainv);
   c->pbuf = at(c, P.pbuf);
   c->cellbuf = at(c, P.cellbuf);
+  c->verts = (double*)at(c, P.verts);
 
   // coefficients and kernel attributes
   std::vector<double> coef(kMaxCoef, 0.0);
@@ -738,12 +754,27 @@ int setup_context(pmg_ctx* c) {
 
   // deformed geometry: G_q per level and p-level, inverse diagonals
   if (c->deformed) {
+    if (c->verts) {
+      // vertex positions of the finest mesh: reference position + displacement
+      const int nf = c->lv[c->L - 1].n, nv = nf + 1;
+      const int64_t NV = ipow64(nv, c->dim);
+      std::vector<double> pos((size_t)(NV * c->dim));
+      for (int64_t v = 0; v < NV; ++v) {
+        int64_t t = v;
+        for (int m = 0; m < c->dim; ++m) {
+          pos[v * c->dim + m] = (double)(t % nv) / nf + cf.vertex_disp[v * c->dim + m];
+          t /= nv;
+        }
+      }
+      PMG_CUDA(cudaMemcpyAsync(c->verts, pos.data(), 8 * pos.size(), cudaMemcpyHostToDevice, c->stream));
+      PMG_CUDA(cudaStreamSynchronize(c->stream));
+    }
     for (int l = 0; l < c->L; ++l) {
       LevelData& D = c->lv[l];
       for (int pl = 0; pl < c->nplev; ++pl) {
         if (!D.G[pl]) continue;
         const int p = plev(c->K, pl);
-        PMG_CUDA(compute_geometry(c->dim, D.n, p, cf.deform_amp, make_tab(p, p + 1), D.G[pl], c->stream));
+        PMG_CUDA(compute_geometry(c->dim, D.n, p, geom_desc(c), make_tab(p, p + 1), D.G[pl], c->stream));
         if (D.dinv[pl])
           PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, p, make_tab(p, p + 1), D.G[pl], c->t64[0], D.dinv[pl],
                                             c->mgprec, c->stream));
@@ -789,6 +820,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->outer_solver = PMG_OUTER_CG;
   cfg->gmres_restart = 30;
   cfg->smoother = PMG_SMOOTHER_ADDITIVE;
+  cfg->vertex_disp = nullptr;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {
@@ -1161,7 +1193,7 @@ int pmg_solve_progress(pmg_ctx* c, int* done, pmg_solve_info* info) {
 int pmg_rhs_manufactured(pmg_ctx* c, double* b) {
   if (check_ctx(c) || !b) return fail(PMG_ERR_ARG, "NULL argument");
   LevelData& F = c->lv[c->L - 1];
-  PMG_CUDA(rhs_manufactured(c->dim, F.n, c->K, c->cfg.deform_amp, c->deformed ? 1 : 0, make_tab(c->K, c->K + 1), b,
+  PMG_CUDA(rhs_manufactured(c->dim, F.n, c->K, geom_desc(c), make_tab(c->K, c->K + 1), b,
                             c->stream));
   return PMG_OK;
 }
@@ -1169,7 +1201,7 @@ int pmg_rhs_manufactured(pmg_ctx* c, double* b) {
 int pmg_l2_error_manufactured(pmg_ctx* c, const double* x, double* err) {
   if (check_ctx(c) || !x || !err) return fail(PMG_ERR_ARG, "NULL argument");
   LevelData& F = c->lv[c->L - 1];
-  PMG_CUDA(l2_error_partials(c->dim, F.n, c->K, c->cfg.deform_amp, c->deformed ? 1 : 0, make_tab(c->K, c->K + 3), x,
+  PMG_CUDA(l2_error_partials(c->dim, F.n, c->K, geom_desc(c), make_tab(c->K, c->K + 3), x,
                              c->partial, c->scal + S_TMP, c->stream));
   PMG_CUDA(cudaMemcpyAsync(c->host_scal + S_TMP, c->scal + S_TMP, 8, cudaMemcpyDeviceToHost, c->stream));
   PMG_CUDA(cudaStreamSynchronize(c->stream));

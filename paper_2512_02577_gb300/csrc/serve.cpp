@@ -37,11 +37,14 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int>;
+// contexts are reused only for the same configuration (a distorted mesh: the
+// same displacement array, by address)
+using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, const double*>;
 
 Key key_of(const pmg_config& c) {
   return Key(c.dim, c.n_cells, c.degree, c.mg_precision, c.geometry, c.n_levels, c.local_cycles, c.smooth_steps,
-             c.local_half, c.outer_solver, c.outer_solver == PMG_OUTER_GMRES ? c.gmres_restart : 0, c.smoother);
+             c.local_half, c.outer_solver, c.outer_solver == PMG_OUTER_GMRES ? c.gmres_restart : 0, c.smoother,
+             c.geometry == PMG_GEOM_DISTORTED ? c.vertex_disp : nullptr);
 }
 
 struct Slot {

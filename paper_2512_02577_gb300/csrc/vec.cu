@@ -403,8 +403,58 @@ __device__ void map_point(int dim, double a, const double* X, double* x, double 
   }
 }
 
+// Trilinear (bilinear in 2D) cell c of a level with n cells per side, corners
+// at the displaced vertices: with xi = n X - c, x = sum over corners s of
+// prod_m N_{s_m}(xi_m) P_{c+s} (N_0 = 1 - t, N_1 = t), dx/dX = n dx/dxi.
+__device__ void map_trilinear(int dim, const GeomDesc& g, int n, const int* c, const double* X, double* x,
+                              double J[3][3]) {
+  const int stride = g.n_fine / n, nv = g.n_fine + 1;
+  double xi[3];
+  for (int m = 0; m < dim; ++m) {
+    xi[m] = n * X[m] - c[m];
+    x[m] = 0.0;
+    for (int j = 0; j < dim; ++j) J[m][j] = 0.0;
+  }
+  for (int s = 0; s < (1 << dim); ++s) {
+    int64_t flat = 0, mul = 1;
+    double N[3], dN[3];
+    for (int m = 0; m < dim; ++m) {
+      const int bit = (s >> m) & 1;
+      flat += mul * (int64_t)((c[m] + bit) * stride);
+      mul *= nv;
+      N[m] = bit ? xi[m] : 1.0 - xi[m];
+      dN[m] = bit ? 1.0 : -1.0;
+    }
+    const double* P = g.verts + flat * dim;
+    double w = 1.0;
+    for (int m = 0; m < dim; ++m) w *= N[m];
+    for (int i = 0; i < dim; ++i) x[i] += w * P[i];
+    for (int j = 0; j < dim; ++j) {
+      double gj = n * dN[j];
+      for (int m = 0; m < dim; ++m)
+        if (m != j) gj *= N[m];
+      for (int i = 0; i < dim; ++i) J[i][j] += gj * P[i];
+    }
+  }
+}
+
+// x = F(X) and J = dF/dX for the level's geometry (cell c holds X)
+__device__ void map_geo(int dim, const GeomDesc& g, int n, const int* c, const double* X, double* x,
+                        double J[3][3]) {
+  if (g.kind == 2) {
+    map_trilinear(dim, g, n, c, X, x, J);
+  } else if (g.kind == 1) {
+    map_point(dim, g.amp, X, x, J);
+  } else {
+    for (int i = 0; i < dim; ++i) {
+      x[i] = X[i];
+      for (int j = 0; j < dim; ++j) J[i][j] = i == j ? 1.0 : 0.0;
+    }
+  }
+}
+
 // G[cell][comp][q] = w_q det J J^{-1} J^{-T} with J = dF/dX h, rounded to float.
-__global__ void geometry_kernel(int dim, int n, int p, double amp, QuadTab tab, float* __restrict__ G) {
+__global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab, float* __restrict__ G) {
   const int nq = p + 1;
   const int NP = dim == 3 ? nq * nq * nq : nq * nq;
   const int nc = dim == 3 ? 6 : 3;
@@ -422,7 +472,7 @@ __global__ void geometry_kernel(int dim, int n, int p, double amp, QuadTab tab, 
       X[m] = h * (cidx[m] + tab.x[qi[m]]);
       w *= tab.w[qi[m]];
     }
-    map_point(dim, amp, X, x, J);
+    map_geo(dim, geo, n, cidx, X, x, J);
     for (int i = 0; i < dim; ++i)
       for (int j = 0; j < dim; ++j) J[i][j] *= h;
     double Gq[3][3];
@@ -473,10 +523,11 @@ __global__ void geometry_kernel(int dim, int n, int p, double amp, QuadTab tab, 
   }
 }
 
-cudaError_t compute_geometry(int dim, int n, int p, double amp, const QuadTab& tab, float* G, cudaStream_t st) {
+cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G,
+                             cudaStream_t st) {
   const int nq = p + 1;
   const int64_t work = (dim == 3 ? (int64_t)n * n * n * nq * nq * nq : (int64_t)n * n * nq * nq);
-  geometry_kernel<<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, amp, tab, G);
+  geometry_kernel<<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, geo, tab, G);
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -558,8 +609,7 @@ cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, 
 
 // ------------------------------------------------------------ RHS, L2 error
 // b_a += sum_q f(F(X_q)) phi_a(xi_q) w_q det J_q  for one colour of cells
-__global__ void rhs_kernel(int dim, int n, int K, double amp, int deformed, QuadTab tab, double* __restrict__ b,
-                           int colour) {
+__global__ void rhs_kernel(int dim, int n, int K, GeomDesc geo, QuadTab tab, double* __restrict__ b, int colour) {
   const int n1 = K + 1;
   const int NP = dim == 3 ? n1 * n1 * n1 : n1 * n1;
   const int nq = tab.nq;
@@ -593,8 +643,8 @@ __global__ void rhs_kernel(int dim, int n, int K, double amp, int deformed, Quad
         phi *= tab.V[qi[m] * 12 + ai[m]];
       }
       double det;
-      if (deformed) {
-        map_point(dim, amp, X, x, J);
+      if (geo.kind != 0) {
+        map_geo(dim, geo, n, cc, X, x, J);
         if (dim == 3)
           det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
@@ -615,7 +665,7 @@ __global__ void rhs_kernel(int dim, int n, int K, double amp, int deformed, Quad
   }
 }
 
-cudaError_t rhs_manufactured(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, double* b,
+cudaError_t rhs_manufactured(int dim, int n, int K, const GeomDesc& geo, const QuadTab& tab, double* b,
                              cudaStream_t st) {
   const int N1 = K * n + 1;
   const int64_t N = dim == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
@@ -624,14 +674,14 @@ cudaError_t rhs_manufactured(int dim, int n, int K, double amp, int deformed, co
   const int NP = dim == 3 ? (K + 1) * (K + 1) * (K + 1) : (K + 1) * (K + 1);
   for (int colour = 0; colour < (1 << dim); ++colour) {
     const int64_t work = (dim == 3 ? (int64_t)n * n * n : (int64_t)n * n) / (1 << dim) * NP + NP * 8;
-    rhs_kernel<<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, K, amp, deformed, tab, b, colour);
+    rhs_kernel<<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, K, geo, tab, b, colour);
     g_launches += 1;
   }
   return cudaGetLastError();
 }
 
 // per-block partial of sum over cells of sum_q (u_h - u)^2 w det J
-__global__ void __launch_bounds__(256) l2err_kernel(int dim, int n, int K, double amp, int deformed, QuadTab tab,
+__global__ void __launch_bounds__(256) l2err_kernel(int dim, int n, int K, GeomDesc geo, QuadTab tab,
                                                     const double* __restrict__ xv, double* __restrict__ partial) {
   const int n1 = K + 1;
   const int nq = tab.nq;
@@ -653,8 +703,8 @@ __global__ void __launch_bounds__(256) l2err_kernel(int dim, int n, int K, doubl
       w *= tab.w[qi[m]];
     }
     double det;
-    if (deformed) {
-      map_point(dim, amp, X, x, J);
+    if (geo.kind != 0) {
+      map_geo(dim, geo, n, cc, X, x, J);
       if (dim == 3)
         det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
@@ -682,9 +732,9 @@ __global__ void __launch_bounds__(256) l2err_kernel(int dim, int n, int K, doubl
   block_store_sum(acc, partial + blockIdx.x);
 }
 
-cudaError_t l2_error_partials(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, const double* x,
+cudaError_t l2_error_partials(int dim, int n, int K, const GeomDesc& geo, const QuadTab& tab, const double* x,
                               double* partial, double* out, cudaStream_t st) {
-  l2err_kernel<<<kDotBlocks, 256, 0, st>>>(dim, n, K, amp, deformed, tab, x, partial);
+  l2err_kernel<<<kDotBlocks, 256, 0, st>>>(dim, n, K, geo, tab, x, partial);
   sum_partials_kernel<<<1, 256, 0, st>>>(partial, kDotBlocks, out);
   g_launches += 2;
   return cudaGetLastError();

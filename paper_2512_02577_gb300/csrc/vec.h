@@ -70,12 +70,23 @@ cudaError_t coarse_gather_row(const double* y, const int* idx, int nc, double* A
 // positive.  row, col: nc scratch each.
 cudaError_t coarse_invert(double* A, int nc, double* row, double* col, int* bad, void* out, int prec,
                           cudaStream_t st);
-cudaError_t compute_geometry(int dim, int n, int p, double amp, const QuadTab& tab, float* G, cudaStream_t st);
+// Geometry of a level: kind 0 Cartesian, 1 the analytic deformation with
+// amplitude amp, 2 trilinear cells spanned by displaced vertices (verts:
+// device array of the finest mesh's (n_fine + 1)^d vertex positions, dim
+// doubles each, x fastest; a level with n cells takes every (n_fine / n)-th).
+struct GeomDesc {
+  int kind;
+  double amp;
+  const double* verts;
+  int n_fine;
+};
+cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G,
+                             cudaStream_t st);
 cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
                                      void* inv, int prec, cudaStream_t st);
-cudaError_t rhs_manufactured(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, double* b,
+cudaError_t rhs_manufactured(int dim, int n, int K, const GeomDesc& geo, const QuadTab& tab, double* b,
                              cudaStream_t st);
-cudaError_t l2_error_partials(int dim, int n, int K, double amp, int deformed, const QuadTab& tab, const double* x,
+cudaError_t l2_error_partials(int dim, int n, int K, const GeomDesc& geo, const QuadTab& tab, const double* x,
                               double* partial, double* out, cudaStream_t st);
 
 }  // namespace pmg

@@ -43,3 +43,21 @@ def serving_requests(n_requests=256, rate=50.0, arrival_seed=7, size_seed=11, rh
     ks = rs.integers(k_lo, k_hi + 1, n_requests)
     return [dict(id=i, t_arrival=float(t[i]), n=int(ns[i]), k=int(ks[i]), rhs_seed=rhs_seed0 + i)
             for i in range(n_requests)]
+
+
+def vertex_displacements(dim, n, delta, seed):
+    """Random mesh distortion of §3.2.2 / §4: every interior vertex of the
+    n^d mesh of the unit square/cube moves by delta h_v in a random direction
+    (uniform on the sphere: a normalised N(0, I) draw), h_v = 1/n being the
+    shortest edge at the vertex; boundary vertices stay.  Returns
+    ((n+1)^d, dim) float64, vertices lexicographic with x fastest."""
+    rng = np.random.default_rng(seed)
+    nv = (n + 1) ** dim
+    g = rng.standard_normal((nv, dim))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    idx = np.arange(nv)
+    interior = np.ones(nv, dtype=bool)
+    for d in range(dim):
+        c = (idx // (n + 1) ** d) % (n + 1)
+        interior &= (c > 0) & (c < n)
+    return np.where(interior[:, None], g * (delta / n), 0.0)

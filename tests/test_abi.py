@@ -44,6 +44,7 @@ def test_status_strings():
     (dict(outer_solver=p.OUTER_GMRES, gmres_restart=65), p.PMG_ERR_ARG),
     (dict(outer_solver=7), p.PMG_ERR_ARG),
     (dict(smoother=2), p.PMG_ERR_ARG),
+    (dict(geometry=p.DISTORTED), p.PMG_ERR_ARG),            # no vertex displacements
 ])
 def test_bytes_required_rejects(kw, code):
     with pytest.raises(p.PmgError) as e:
@@ -83,3 +84,13 @@ def test_create_null_out_is_rejected():
     lib = p.load_library()
     cfg = p.make_config()
     assert lib.pmg_create(ctypes.byref(cfg), None, None, 0, None) == p.PMG_ERR_ARG
+
+
+def test_distorted_config_keeps_its_displacements():
+    import numpy as np
+    d = np.zeros((5 ** 3, 3))
+    cfg = p.make_config(dim=3, n_cells=4, degree=2, geometry=p.DISTORTED, vertex_disp=d)
+    assert cfg.vertex_disp == cfg._vertex_disp_ref.ctypes.data
+    assert p.bytes_required(cfg) > p.bytes_required(p.make_config(dim=3, n_cells=4, degree=2, geometry=p.DEFORMED))
+    with pytest.raises(ValueError):
+        p.make_config(dim=3, n_cells=4, degree=2, geometry=p.DISTORTED, vertex_disp=np.zeros((10, 3)))

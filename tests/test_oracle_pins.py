@@ -520,3 +520,74 @@ def test_multiplicative_vcycle_symmetric_and_cg_converges(d, n, k, L):
     ha = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d))
     _, it_add, _ = solver.solve(ha, b, rtol=1e-10)
     assert it <= it_add
+
+
+# ---------------------------------------------------------------- randomly distorted meshes
+def _distorted(d, n, k, delta=0.25, seed=17):
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    return fem.Mesh(d, n, k, "distorted", disp=vertex_displacements(d, n, delta, seed))
+
+
+def test_displacements_recipe():
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    D = vertex_displacements(3, 4, 0.3, 5)
+    assert D.shape == (125, 3)
+    norms = np.linalg.norm(D, axis=1)
+    v = np.arange(125)
+    inner = np.all([((v // 5 ** m) % 5 > 0) & ((v // 5 ** m) % 5 < 4) for m in range(3)], axis=0)
+    np.testing.assert_allclose(norms[inner], 0.3 / 4, rtol=1e-14)
+    assert np.all(norms[~inner] == 0)
+
+
+@pytest.mark.parametrize("d,k", [(2, 1), (2, 3), (3, 1), (3, 2)])
+def test_distorted_volume_and_linear_energy(d, k):
+    # the trilinear cells tile the unit cube: sum w det J = 1 exactly (det J
+    # is a polynomial the (k+1)-point rule integrates exactly), and u = x_1
+    # lies in V_h (x is trilinear in the reference coordinates), so
+    # a(u, u) = |Omega| = 1
+    m = _distorted(d, 3, k)
+    vol = 0.0
+    for c in m.cells():
+        _, X, w = m.cell_quadrature(c, k + 1)
+        _, DF = m.map_and_jacobian(X)
+        vol += np.sum(w * np.linalg.det(DF * m.h))
+    assert abs(vol - 1) < 1e-13
+    Af = fem.assemble_full(m)
+    u = fem.dof_coordinates(m)[:, 0]
+    assert abs(u @ (Af @ u) - 1) < 1e-12
+    assert np.abs(Af @ np.ones(Af.shape[0])).max() < 1e-12 * abs(Af).max()
+    assert abs(Af - Af.T).max() < 1e-14 * abs(Af).max()
+
+
+def test_distorted_map_is_continuous_and_zero_distortion_is_cartesian():
+    m = _distorted(3, 4, 2)
+    # a point on the face x = 1/2 between two cells: both cells' maps agree
+    X = np.array([0.5, 0.3, 0.6])
+    left = m._trilinear_map(X[None, :] - [1e-15, 0, 0])[0][0]
+    right = m._trilinear_map(X[None, :] + [1e-15, 0, 0])[0][0]
+    np.testing.assert_allclose(left, right, atol=1e-12)
+    # corners land on the displaced vertices
+    x, _ = m.map_and_jacobian(np.array([[0.25, 0.5, 0.75]]))
+    np.testing.assert_allclose(x[0], m.vertex_position((1, 2, 3)), atol=1e-15)
+    m0 = fem.Mesh(3, 3, 2, "distorted", disp=np.zeros((64, 3)))
+    A0, A = fem.assemble(m0), fem.assemble(fem.Mesh(3, 3, 2))
+    assert abs(A0 - A).max() < 1e-13 * abs(A).max()
+
+
+def test_distorted_coarse_levels_use_the_fine_vertices():
+    m = _distorted(2, 8, 2)
+    mc = m.with_level(n=2)
+    # coarse vertex (1, 1) is fine vertex (4, 4)
+    np.testing.assert_allclose(mc.vertex_position((1, 1)), m.vertex_position((4, 4)), atol=0)
+
+
+@pytest.mark.parametrize("outer,half", [("cg", False), ("gmres", True)])
+def test_distorted_solve_matches_direct(outer, half):
+    m = _distorted(2, 8, 3, delta=0.3)
+    h = solver.Hierarchy(m, 3, constants.omega_jacobi(2, 3), constants.omega_patch(2), full_vcycle=not half)
+    fine = h.levels[-1]
+    b = fem.rhs_manufactured(m)[m.interior_index()]
+    x, it, hist = solver.solve(h, b, rtol=1e-10, outer=outer)
+    assert it < 40
+    xs = solver.direct_solve(fine.A, b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
