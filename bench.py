@@ -141,9 +141,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_child(seconds):
+def oracle_child(seconds, n_steps=0):
     """Runs in a fresh single-threaded process: time the oracle's step
-    (apply + sweep + PCG solve) on the bounded sample, set-up excluded."""
+    (apply + sweep + PCG solve) on the bounded sample, set-up excluded;
+    exactly n_steps steps if n_steps > 0, else for about ``seconds``."""
     import numpy as np
     from oracle import constants, fem, solver
     m = fem.Mesh(D, ORACLE_N, K)
@@ -156,7 +157,7 @@ def oracle_child(seconds):
     fine = h.levels[-1]
     times = []
     t_end = time.time() + seconds
-    while time.time() < t_end or len(times) < 3:
+    while (len(times) < n_steps) if n_steps > 0 else (time.time() < t_end or len(times) < 3):
         t0 = time.perf_counter()
         fine.A @ b
         fine.smooth(b, np.zeros_like(b))
@@ -165,10 +166,11 @@ def oracle_child(seconds):
     print(json.dumps({"dofs": m.n_dofs, "times": times, "iterations": it}))
 
 
-def run_oracle(seconds):
+def run_oracle(seconds, n_steps=0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(seconds)],
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(seconds),
+                        "--oracle-steps", str(n_steps)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle child failed:\n" + r.stderr[-2000:])
@@ -450,6 +452,7 @@ def main():
     ap.add_argument("--oracle-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-child", type=float, default=None)
+    ap.add_argument("--oracle-steps", type=int, default=0)
     ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "deformed"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
     ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
@@ -457,7 +460,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="degree sweep k = 1..8 at ~8M DoFs (separate JSON)")
     args = ap.parse_args()
     if args.oracle_child is not None:
-        oracle_child(args.oracle_child)
+        oracle_child(args.oracle_child, args.oracle_steps)
         return
     if args.profile_region:
         profile_region(args.profile_region, args.profile_n)
@@ -474,8 +477,9 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        res = run_oracle(max(args.oracle_seconds, 1.0) * (args.steps + args.warmup) / max(args.steps, 1))
-        times = res["times"][args.warmup:] or res["times"]
+        # exactly W untimed + K timed oracle steps, each on the bounded sample
+        res = run_oracle(0.0, n_steps=args.warmup + max(args.steps, 1))
+        times = res["times"][args.warmup:]
         t = statistics.median(times)
         value = res["dofs"] / t
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": args.gpus,
