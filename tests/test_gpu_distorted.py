@@ -117,3 +117,23 @@ def test_distortion_costs_a_few_iterations():
     x = torch.zeros_like(b)
     assert abs(cart.solve(b, x).iterations - its[0]) <= 1
 
+
+
+def test_distorted_fp32_apply_and_block_packing():
+    d, n, k = 3, 4, 3
+    m = mesh_for(d, n, k)
+    A = fem.assemble(m)
+    x = random_vector(d, n, k, seed=94)
+    ctx = ctx_for(d, n, k, L=2, prec=p.FP32)
+    y = torch.empty(m.n_dofs, dtype=torch.float32, device=DEV)
+    ctx.apply(to_dev(x, torch.float32), y, prec=p.FP32)
+    assert rel(y.cpu().double().numpy()[m.interior_index()], A @ x[m.interior_index()]) < 2e-5
+    # every admissible block packing gives bitwise the same sweep
+    b = to_dev(random_vector(d, n, k, seed=95), torch.float32)
+    outs = []
+    for ppc in (1, 2, 5):
+        c = ctx_for(d, n, k, L=2, prec=p.FP32, patches_per_block=ppc)
+        u = torch.zeros_like(b)
+        c.smooth(b, u)
+        outs.append(u)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])

@@ -169,3 +169,18 @@ def test_gmres_through_the_server_matches_direct_solve():
     assert res["state"] == 2 and res["iterations"] == info.iterations
     assert torch.equal(xh, x.cpu())
     srv.close()
+
+
+def test_gmres_restart_one_matches_oracle():
+    # GMRES(1): one minimal-residual step per cycle, restarted from b - A x
+    d, n, k, L = 2, 8, 2, 3
+    ctx = make_ctx(d, n, k, L=L, outer_solver=p.OUTER_GMRES, gmres_restart=1)
+    h = hier(d, n, k, L, "cartesian", True)
+    fine = h.levels[-1]
+    b_ref = random_vector(d, n, k, seed=66)
+    x = torch.zeros(fine.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    info = ctx.solve(to_dev(b_ref), x, rtol=1e-8, maxit=300)
+    x_ref, it_ref, _ = solver.gmres(fine.A, b_ref[fine.I], h.vcycle, rtol=1e-8, maxit=300, restart=1)
+    assert info.status == 0
+    assert abs(info.iterations - it_ref) <= 1, (info.iterations, it_ref)
+    assert rel(x.cpu().numpy(), full(fine, x_ref)) < 1e-6

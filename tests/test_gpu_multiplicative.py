@@ -121,3 +121,24 @@ def test_multiplicative_needs_fewer_iterations_than_additive():
         x = torch.zeros_like(b)
         its[sm] = ctx.solve(b, x).iterations
     assert its[p.MULTIPLICATIVE] < its[p.ADDITIVE], its
+
+
+def test_multiplicative_two_half_cycles_and_deformed_2d_vcycle():
+    # N_iter = 2 around the half local cycle inside the multiplicative sweep
+    d, n, k = 3, 4, 3
+    ctx = make_ctx(d, n, k, L=2, smoother=p.MULTIPLICATIVE, local_half=1, local_cycles=2)
+    m = fem.Mesh(d, n, k, "cartesian", 0.05, geom_fp32=True)
+    lev = solver.Level(m, constants.omega_jacobi(d, k), constants.omega_patch(d), n_iter=2, full_vcycle=False,
+                       multiplicative=True)
+    b = random_vector(d, n, k, seed=76)
+    u = torch.zeros(m.n_dofs, dtype=torch.float64, device=DEV)
+    ctx.smooth(to_dev(b), u)
+    assert rel(u.cpu().numpy(), full(lev, lev.smooth(b[lev.I], np.zeros(len(lev.I))))) < 1e-11
+    # 2D deformed V-cycle
+    ctx2 = make_ctx(2, 8, 3, L=0, geom="deformed", smoother=p.MULTIPLICATIVE)
+    h = mult_hier(2, 8, 3, n_levels_auto(8), "deformed")
+    fine = h.levels[-1]
+    r = random_vector(2, 8, 3, seed=77)
+    z = torch.empty(fine.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    ctx2.vcycle(to_dev(r), z)
+    assert rel(z.cpu().numpy(), full(fine, h.vcycle(r[fine.I]))) < 1e-11

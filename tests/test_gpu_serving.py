@@ -78,3 +78,34 @@ def test_concurrent_requests_overlap():
     recs1, _ = serve.run(reqs, precision=p.FP32, max_active=1)
     order = sorted(recs1, key=lambda r: r["t_start"])
     assert all(a["t_done"] <= b["t_start"] + 1e-6 for a, b in zip(order, order[1:]))
+
+
+def test_mixed_method_stream_same_alone_and_in_the_mix():
+    # requests with different smoothers, local cycles, outer solvers and
+    # geometries in one stream: each result equals its solve alone
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    disp = vertex_displacements(3, 8, 0.2, 7)
+    cfgs = [p.make_config(dim=3, n_cells=8, degree=3, mg_precision=p.FP32),
+            p.make_config(dim=3, n_cells=8, degree=3, mg_precision=p.FP32, smoother=p.MULTIPLICATIVE),
+            p.make_config(dim=3, n_cells=8, degree=2, mg_precision=p.FP32, local_half=1),
+            p.make_config(dim=3, n_cells=8, degree=2, geometry=p.DISTORTED, vertex_disp=disp,
+                          mg_precision=p.FP32, local_half=1, smoother=p.MULTIPLICATIVE),
+            p.make_config(dim=3, n_cells=4, degree=4, geometry=p.DEFORMED)]
+    srv = p.Server(0, 5)
+    jobs = []
+    for i, cfg in enumerate(cfgs):
+        b = serve._rhs(3, cfg.n_cells, cfg.degree, 700 + i)
+        x = torch.zeros_like(b).pin_memory()
+        jobs.append((cfg, b, x, srv.submit(cfg, b, x)))
+    while any(srv.result(j[3])["state"] < 2 for j in jobs):
+        srv.poll()
+    for cfg, b, x, rid in jobs:
+        res = srv.result(rid)
+        assert res["state"] == 2 and res["rel_residual"] <= 1e-8
+        ctx = p.Context(cfg, device="cuda:0")
+        xa = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda:0")
+        info = ctx.solve(b.cuda(), xa)
+        assert info.iterations == res["iterations"]
+        assert torch.equal(xa.cpu(), x)
+        ctx.close()
+    srv.close()
