@@ -38,7 +38,10 @@ enum pmg_status {
   PMG_OK = 0,
   PMG_NOT_CONVERGED = 1,
   PMG_ERR_ARG = -1,          /* invalid argument (NULL pointer, bad level, bad size) */
-  PMG_ERR_UNSUPPORTED = -2,  /* dim not 2/3, degree not 1..8; V-cycle/solve on a coarse level above 4096 free DoFs */
+  PMG_ERR_UNSUPPORTED = -2,  /* dim not 2/3, degree not 1..8; V-cycle/solve on a coarse level above 4096 free DoFs;
+                                pmg_create when one patch's local p-multigrid does not fit in a block's shared
+                                memory (3D FP64: deformed/distorted k = 8, deformed/distorted k = 7 with
+                                local_cycles >= 2, Cartesian k = 8 with local_cycles >= 2) */
   PMG_ERR_OOM = -3,          /* device workspace could not be allocated / too small */
   PMG_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed */
   PMG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired */
