@@ -260,16 +260,18 @@ def extra_sections(p, torch, dev, stream, flush):
 def distorted_section(p, torch, dev, stream, flush):
     """Randomly distorted 3D 64^3 Q3 mesh (7,189,057 DoFs; every interior
     vertex moved by 0.25 h in a random direction, seed 2512), mixed
-    precision: additive smoother with the full local cycle under CG and with
-    the half cycle under GMRES; median of 3 solves (L2 flushed before each),
-    plus the stored-G_q FP32 apply."""
+    precision: additive and multiplicative smoothers, each with the full
+    local cycle under CG and with the half cycle under GMRES; median of 3
+    solves (L2 flushed before each), plus the stored-G_q FP32 apply."""
     from paper_2512_02577_gb300.inputs import vertex_displacements
     n, k, delta = 64, 3, 0.25
     disp = vertex_displacements(3, n, delta, 2512)
     res = {"delta": delta}
-    for half, outer, name in ((0, p.OUTER_CG, "full_cg"), (1, p.OUTER_GMRES, "half_gmres")):
+    for sm, half, outer, name in ((p.ADDITIVE, 0, p.OUTER_CG, "full_cg"), (p.ADDITIVE, 1, p.OUTER_GMRES, "half_gmres"),
+                                  (p.MULTIPLICATIVE, 0, p.OUTER_CG, "mult_full_cg"),
+                                  (p.MULTIPLICATIVE, 1, p.OUTER_GMRES, "mult_half_gmres")):
         ctx = p.Context(p.make_config(dim=3, n_cells=n, degree=k, geometry=p.DISTORTED, vertex_disp=disp,
-                                      mg_precision=p.FP32, local_half=half, outer_solver=outer),
+                                      mg_precision=p.FP32, local_half=half, outer_solver=outer, smoother=sm),
                         stream=stream, device=dev)
         b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
         ctx.rhs_manufactured(b)

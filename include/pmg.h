@@ -100,8 +100,9 @@ typedef struct pmg_config {
   const double* vertex_disp; /* PMG_GEOM_DISTORTED only (else ignored): HOST array of the displacements
                           of the finest mesh's (n_cells + 1)^d vertices, d doubles per vertex, vertices
                           lexicographic with x fastest; boundary vertices must have zero normal
-                          displacement for the domain to stay the unit square/cube, and no cell may
-                          be inverted.  Read by pmg_create only (copied); the caller keeps ownership */
+                          displacement for the domain to stay the unit square/cube.  pmg_create
+                          returns PMG_ERR_ARG if a cell is inverted (det J <= 0 at a quadrature
+                          point).  Read by pmg_create only (copied); the caller keeps ownership */
 } pmg_config;
 
 typedef struct pmg_solve_info {

@@ -754,6 +754,8 @@ int setup_context(pmg_ctx* c) {
 
   // deformed geometry: G_q per level and p-level, inverse diagonals
   if (c->deformed) {
+    int* geobad = (int*)at(c, c->plan.gjbad);  // free until the coarse set-up
+    PMG_CUDA(cudaMemsetAsync(geobad, 0, sizeof(int), c->stream));
     if (c->verts) {
       // vertex positions of the finest mesh: reference position + displacement
       const int nf = c->lv[c->L - 1].n, nv = nf + 1;
@@ -774,7 +776,7 @@ int setup_context(pmg_ctx* c) {
       for (int pl = 0; pl < c->nplev; ++pl) {
         if (!D.G[pl]) continue;
         const int p = plev(c->K, pl);
-        PMG_CUDA(compute_geometry(c->dim, D.n, p, geom_desc(c), make_tab(p, p + 1), D.G[pl], c->stream));
+        PMG_CUDA(compute_geometry(c->dim, D.n, p, geom_desc(c), make_tab(p, p + 1), D.G[pl], geobad, c->stream));
         if (D.dinv[pl])
           PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, p, make_tab(p, p + 1), D.G[pl], c->t64[0], D.dinv[pl],
                                             c->mgprec, c->stream));
@@ -783,7 +785,10 @@ int setup_context(pmg_ctx* c) {
         PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, 1, make_tab(1, 2), D.G[0], c->t64[0], D.dinv1, c->mgprec,
                                           c->stream));
     }
+    int bad = 0;
+    PMG_CUDA(cudaMemcpyAsync(&bad, geobad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PMG_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) return fail(PMG_ERR_ARG, "inverted cell: det J <= 0 at a quadrature point of the mesh");
   }
 
   // patches per block: the autotuned value (or the caller's)

@@ -454,7 +454,8 @@ __device__ void map_geo(int dim, const GeomDesc& g, int n, const int* c, const d
 }
 
 // G[cell][comp][q] = w_q det J J^{-1} J^{-T} with J = dF/dX h, rounded to float.
-__global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab, float* __restrict__ G) {
+__global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab, float* __restrict__ G,
+                                int* __restrict__ bad) {
   const int nq = p + 1;
   const int NP = dim == 3 ? nq * nq * nq : nq * nq;
   const int nc = dim == 3 ? 6 : 3;
@@ -481,6 +482,7 @@ __global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab
       const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
       const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
       const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      if (!(det > 0.0)) atomicOr(bad, 1);
       double inv[3][3];
       inv[0][0] = c00 / det;
       inv[1][0] = c01 / det;
@@ -499,6 +501,7 @@ __global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab
         }
     } else {
       const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      if (!(det > 0.0)) atomicOr(bad, 1);
       double inv[2][2];
       inv[0][0] = J[1][1] / det;
       inv[0][1] = -J[0][1] / det;
@@ -523,11 +526,11 @@ __global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab
   }
 }
 
-cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G,
+cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G, int* bad,
                              cudaStream_t st) {
   const int nq = p + 1;
   const int64_t work = (dim == 3 ? (int64_t)n * n * n * nq * nq * nq : (int64_t)n * n * nq * nq);
-  geometry_kernel<<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, geo, tab, G);
+  geometry_kernel<<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, geo, tab, G, bad);
   g_launches += 1;
   return cudaGetLastError();
 }

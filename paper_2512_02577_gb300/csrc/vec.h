@@ -80,7 +80,8 @@ struct GeomDesc {
   const double* verts;
   int n_fine;
 };
-cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G,
+// *bad |= 1 where a cell's det J <= 0 at a quadrature point (inverted cell)
+cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G, int* bad,
                              cudaStream_t st);
 cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
                                      void* inv, int prec, cudaStream_t st);

@@ -137,3 +137,15 @@ def test_distorted_fp32_apply_and_block_packing():
         c.smooth(b, u)
         outs.append(u)
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_inverted_cell_is_rejected():
+    # vertex (1, 1) of a 4 x 4 mesh pushed 1.5 h past its neighbour: the
+    # cells around it fold over (det J < 0), and pmg_create says so
+    n = 4
+    d = np.zeros(((n + 1) ** 2, 2))
+    d[1 + (n + 1) * 1] = [1.5 / n, 1.5 / n]
+    cfg = p.make_config(dim=2, n_cells=n, degree=2, geometry=p.DISTORTED, vertex_disp=d)
+    with pytest.raises(p.PmgError) as e:
+        p.Context(cfg, device=DEV)
+    assert e.value.code == p.PMG_ERR_ARG and "inverted" in str(e.value)
