@@ -535,16 +535,20 @@ int precondition(pmg_ctx* c, const double* r, double* z) {
 
 // ---------------------------------------------------------------- autotuner
 // Patches per thread block of the smoother kernels, per (dim, degree, MG
-// precision, geometry, local cycles): every admissible value is timed on the
-// patch launch of the finest level (CUDA events, best of 3 after a warm-up)
-// and the fastest is kept for the process; with PMG_TUNE_FILE set, results
-// are also read from and appended to that file ("dim k prec geom cycles ppc"
-// per line).  Small meshes, whose launches are too short to time, use the
-// rule "about 256 threads per block" without caching it.
+// precision, geometry, local cycles, smoother): every admissible value is
+// timed on the patch launches of one finest-level sweep -- the one launch
+// over all patches (additive) or the 2^d colour launches (multiplicative,
+// each over an eighth of the patches in 3D, where the last wave matters) --
+// with CUDA events, best of 3 after a warm-up, and the fastest is kept for
+// the process; with PMG_TUNE_FILE set, results are also read from and
+// appended to that file ("dim k prec geom cycles smoother ppc" per line).
+// Small meshes, whose launches are too short to time, use the rule "about
+// 256 threads per block" without caching it.
 struct TuneKey {
-  int dim, K, prec, geom, cycles;
+  int dim, K, prec, geom, cycles, smoother;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dim, K, prec, geom, cycles) < std::tie(o.dim, o.K, o.prec, o.geom, o.cycles);
+    return std::tie(dim, K, prec, geom, cycles, smoother) <
+           std::tie(o.dim, o.K, o.prec, o.geom, o.cycles, o.smoother);
   }
 };
 std::mutex g_tune_mu;
@@ -558,8 +562,9 @@ void tune_file_read_locked() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int d, k, pr, ge, cy, ppc;
-  while (std::fscanf(f, "%d %d %d %d %d %d", &d, &k, &pr, &ge, &cy, &ppc) == 6) g_tune[{d, k, pr, ge, cy}] = ppc;
+  int d, k, pr, ge, cy, sm, ppc;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d", &d, &k, &pr, &ge, &cy, &sm, &ppc) == 7)
+    g_tune[{d, k, pr, ge, cy, sm}] = ppc;
   std::fclose(f);
 }
 
@@ -568,7 +573,7 @@ void tune_file_append_locked(const TuneKey& key, int ppc) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %d\n", key.dim, key.K, key.prec, key.geom, key.cycles, ppc);
+  std::fprintf(f, "%d %d %d %d %d %d %d\n", key.dim, key.K, key.prec, key.geom, key.cycles, key.smoother, ppc);
   std::fclose(f);
 }
 
@@ -601,7 +606,8 @@ int choose_patches_per_block(pmg_ctx* c) {
   LevelData& F = c->lv[c->L - 1];
   const int64_t patches = ipow64(std::max(F.n - 1, 0), c->dim);
   if (c->K == 1 || patches < 4096) return PMG_OK;
-  const TuneKey key{c->dim, c->K, c->mgprec, c->deformed ? 1 : 0, cf.local_cycles};
+  const bool mult = cf.smoother == PMG_SMOOTHER_MULTIPLICATIVE;
+  const TuneKey key{c->dim, c->K, c->mgprec, c->deformed ? 1 : 0, cf.local_cycles, mult ? 1 : 0};
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_file_read_locked();
@@ -629,7 +635,12 @@ int choose_patches_per_block(pmg_ctx* c) {
     float tmin = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, c->stream);
-      int rc = patch_solves(c, c->L - 1, F.r);
+      int rc = PMG_OK;
+      if (mult) {
+        for (int col = 0; col < (1 << c->dim) && !rc; ++col) rc = patch_solves(c, c->L - 1, F.r, col, F.u);
+      } else {
+        rc = patch_solves(c, c->L - 1, F.r);
+      }
       cudaEventRecord(e1, c->stream);
       if (rc) {  // a launch the device rejects (resources): not a candidate
         cudaGetLastError();
