@@ -263,7 +263,7 @@ template <int DIM>
 struct DefShape {
   using PS = PatchShape<DIM>;
   static constexpr int QT = 2 * (K + 1);                    // Gauss points per direction (top level)
-  static constexpr int BUF = ipow(QT, DIM);                 // >= (2K+1)^DIM
+  static constexpr int BUF = tpitch(QT) * ipow(QT, DIM - 1);  // padded (QT)^DIM tile, >= (2K+1)^DIM
   static constexpr int LINES = ipow(QT, DIM - 1);           // lines of the largest step, per patch
   static constexpr int WORK = (DIM == 3 ? 4 : 3) * BUF;
   template <typename T>
@@ -279,7 +279,11 @@ struct DefLevelT {
 // Along axis AX of a tile with extents (EX, EY, EZ): src extent NI -> dst
 // extent NO.  OP 0: interpolation nodes -> points (NI = 2p+1, NO = 2(p+1));
 // OP 1: its transpose; OP 2: block-diagonal derivative (NI = NO = 2(p+1));
-// OP 3: its transpose.  ACC: dst += result.
+// OP 3: its transpose.  ACC: dst += result.  A tile with x extent e is
+// stored with row pitch tpitch(e) (odd) and plane pitch tpitch(e) * (y
+// extent): with the even point counts 2(p+1) an unpadded tile would put the
+// lines of a warp on a few banks (x lines 2(p+1) apart, y lines
+// 4(p+1)^2 apart).
 template <int DIM, int p, int AX, int OP, bool ACC, int EX, int EY, int EZ, typename T>
 __device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBlock<T>& pb, int src, int dst) {
   constexpr int nq = p + 1, mf = 2 * p + 1, Q = 2 * nq;
@@ -287,13 +291,27 @@ __device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBloc
   constexpr int NO = (OP == 0) ? Q : (OP == 1 ? mf : Q);
   constexpr int IX = AX == 0 ? NI : EX, IY = AX == 1 ? NI : EY, IZ = AX == 2 ? NI : EZ;
   constexpr int OX = AX == 0 ? NO : EX, OY = AX == 1 ? NO : EY;
-  constexpr int SI = AX == 0 ? 1 : (AX == 1 ? IX : IX * IY);
-  constexpr int SO = AX == 0 ? 1 : (AX == 1 ? OX : OX * OY);
+  constexpr int RXI = tpitch(IX), RYI = RXI * IY;  // input row / plane pitch
+  constexpr int RXO = tpitch(OX), RYO = RXO * OY;  // output row / plane pitch
+  constexpr int SI = AX == 0 ? 1 : (AX == 1 ? RXI : RYI);
+  constexpr int SO = AX == 0 ? 1 : (AX == 1 ? RXO : RYO);
   constexpr int NL = IX * IY * IZ / NI;
   pfor<NL>(pb.np, [&](int g, int L) {
     T* sm = pb.at(g);
-    const int bi = line_base<AX, IX, IY, IZ>(L);
-    const int bo = line_base<AX, OX, OY, (AX == 2 ? NO : EZ)>(L);
+    int bi, bo;
+    if constexpr (AX == 0) {  // line (y, z)
+      const int y = L % IY, z = L / IY;
+      bi = RXI * y + RYI * z;
+      bo = RXO * y + RYO * z;
+    } else if constexpr (AX == 1) {  // line (x, z)
+      const int x = L % IX, z = L / IX;
+      bi = x + RYI * z;
+      bo = x + RYO * z;
+    } else {  // line (x, y)
+      const int x = L % IX, y = L / IX;
+      bi = x + RXI * y;
+      bo = x + RXO * y;
+    }
     T x[NI], y[NO];
 #pragma unroll
     for (int j = 0; j < NI; ++j) x[j] = sm[src + bi + j * SI];
@@ -388,7 +406,9 @@ struct DefGeo {
       T* sm = pb.at(g);
       const int c = t / NPc, pt = t - c * NPc;
       const int px = pt % nq, py = (pt / nq) % nq, pz = DIM == 3 ? pt / (nq * nq) : 0;
-      const int qi = ((c & 1) * nq + px) + Q * ((((c >> 1) & 1) * nq + py) + Q * (DIM == 3 ? ((c >> 2) & 1) * nq + pz : 0));
+      const int qx = (c & 1) * nq + px, qy = ((c >> 1) & 1) * nq + py;
+      const int qz = DIM == 3 ? ((c >> 2) & 1) * nq + pz : 0;
+      const int qi = qx + tpitch(Q) * (qy + Q * qz);  // padded (Q, Q, QZ) tile
       const int* v = meta[g].v;
       const int64_t cell = (v[0] - 1 + (c & 1)) +
                            (int64_t)n * ((v[1] - 1 + ((c >> 1) & 1)) + (int64_t)n * (DIM == 3 ? v[2] - 1 + ((c >> 2) & 1) : 0));

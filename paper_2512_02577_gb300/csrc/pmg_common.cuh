@@ -23,6 +23,10 @@ __host__ __device__ constexpr int plev(int K, int l) {
 }
 // Patch-interior points per direction at degree p.
 __host__ __device__ constexpr int mp(int p) { return 2 * p - 1; }
+// Row pitch of a shared-memory tile whose rows hold e values: e rounded up
+// to odd, so that rows (and planes of an even number of rows) start on
+// different banks.
+__host__ __device__ constexpr int tpitch(int e) { return e | 1; }
 
 // Patch-interior node i (0..2p-2) of degree p: 0 = strictly in the first
 // cell, 1 = the patch centre (shared), 2 = strictly in the second cell.
