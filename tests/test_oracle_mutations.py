@@ -83,3 +83,97 @@ def test_wrong_transfer_breaks_galerkin_identity(monkeypatch):
     Tbad = Tbad * 0.9
     assert np.abs(T.T @ Ap @ T - Aq).max() < 1e-12 * np.abs(Aq).max()
     assert np.abs(Tbad.T @ Ap @ Tbad - Aq).max() > 1e-3 * np.abs(Aq).max()
+
+
+def _nonsymmetric(n=20, seed=4):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.5
+    M = np.eye(n) + 0.1 * rng.standard_normal((n, n))
+    return A, M, rng.standard_normal(n)
+
+
+def test_wrong_givens_sign_breaks_minimal_residual(monkeypatch):
+    # planted: g_{j+1} = +sn g_j (the rotated right-hand side with the wrong
+    # sign); the least-squares optimality pin must notice
+    A, M, b = _nonsymmetric()
+    j = 4
+    K = np.column_stack([np.linalg.matrix_power(A @ M, i) @ b for i in range(j)])
+    y = np.linalg.lstsq(A @ M @ K, b, rcond=None)[0]
+    best = np.linalg.norm(b - A @ M @ K @ y)
+    x, _, _ = solver.gmres(A, b, lambda v: M @ v, rtol=0.0, maxit=j, restart=30)
+    assert abs(np.linalg.norm(b - A @ x) - best) < 1e-9 * best
+    orig_hypot = np.hypot
+
+    def wrong_gmres(A, b, precond, rtol=1e-8, maxit=500, restart=30):
+        # the oracle's loop with one planted sign, written out for the test
+        x = np.zeros_like(b)
+        r = b.copy()
+        beta = np.linalg.norm(r)
+        V, Z = [r / beta], []
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        for jj in range(maxit):
+            Z.append(precond(V[jj]))
+            w = A @ Z[jj]
+            for i in range(jj + 1):
+                H[i, jj] = w @ V[i]
+                w = w - H[i, jj] * V[i]
+            H[jj + 1, jj] = np.linalg.norm(w)
+            V.append(w / H[jj + 1, jj])
+            for i in range(jj):
+                hi, hn = H[i, jj], H[i + 1, jj]
+                H[i, jj] = cs[i] * hi + sn[i] * hn
+                H[i + 1, jj] = -sn[i] * hi + cs[i] * hn
+            rho = orig_hypot(H[jj, jj], H[jj + 1, jj])
+            cs[jj], sn[jj] = H[jj, jj] / rho, H[jj + 1, jj] / rho
+            H[jj, jj], H[jj + 1, jj] = rho, 0.0
+            g[jj + 1] = +sn[jj] * g[jj]                 # planted: sign
+            g[jj] = cs[jj] * g[jj]
+        yy = np.linalg.solve(np.triu(H[:maxit, :maxit]), g[:maxit])
+        return x + sum(yy[i] * Z[i] for i in range(maxit)), maxit, None
+
+    xw, _, _ = wrong_gmres(A, b, lambda v: M @ v, maxit=j)
+    assert np.linalg.norm(b - A @ xw) > best * (1 + 1e-6)
+
+
+def test_missing_residual_update_breaks_sequential_equivalence(monkeypatch):
+    # planted: every colour reuses the residual of the first one (no update
+    # between colours); the pin against the patch-by-patch loop must notice
+    m = fem.Mesh(2, 6, 2)
+    lev = solver.Level(m, constants.omega_jacobi(2, 2), constants.omega_patch(2), multiplicative=True)
+    rng = np.random.default_rng(1)
+    b, u = rng.standard_normal(len(lev.I)), rng.standard_normal(len(lev.I))
+    ref = lev.mult_sweep_sequential(b, u)
+    r = b - lev.A @ u
+    wrong = u.copy()
+    for c in range(4):
+        for v, idx, ps in lev.patches:
+            if solver.colour_of(v) == c:
+                wrong[idx] += ps.local_solve(r[idx])
+    np.testing.assert_allclose(lev.mult_sweep(b, u), ref, atol=1e-12 * np.abs(u).max())
+    assert np.abs(wrong - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_swapped_trilinear_shape_functions_break_volume(monkeypatch):
+    # planted: N_0 and N_1 exchanged in the trilinear map; the exact-volume
+    # and linear-energy pins must notice
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    m = fem.Mesh(2, 3, 2, "distorted", disp=vertex_displacements(2, 3, 0.25, 17))
+    orig = fem.Mesh._trilinear_map
+
+    def swapped(self, X):
+        Xs = X.copy()
+        c = np.minimum(np.floor(Xs * self.n), self.n - 1)
+        Xs = (c + 1.0 - (Xs * self.n - c)) / self.n    # xi -> 1 - xi in every cell
+        return orig(self, Xs)
+
+    def energy():
+        Af = fem.assemble_full(m)
+        u = fem.dof_coordinates(m)[:, 0]
+        return u @ (Af @ u)
+
+    assert abs(energy() - 1) < 1e-12
+    monkeypatch.setattr(fem.Mesh, "_trilinear_map", swapped)
+    assert abs(energy() - 1) > 1e-6
