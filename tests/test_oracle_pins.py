@@ -591,3 +591,17 @@ def test_distorted_solve_matches_direct(outer, half):
     assert it < 40
     xs = solver.direct_solve(fine.A, b)
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+
+
+def test_multiplicative_half_cycle_gmres_matches_direct_solve():
+    # the paper's configuration (Algorithm 1 sweeps, half local V-cycle,
+    # GMRES) on a distorted mesh reaches the sparse direct solution
+    m = _distorted(2, 8, 3, delta=0.25)
+    h = solver.Hierarchy(m, 3, constants.omega_jacobi(2, 3), constants.omega_patch(2), full_vcycle=False,
+                         multiplicative=True)
+    fine = h.levels[-1]
+    b = fem.rhs_manufactured(m)[m.interior_index()]
+    x, it, _ = solver.solve(h, b, rtol=1e-10, outer="gmres")
+    xs = solver.direct_solve(fine.A, b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+    assert it < 20
