@@ -576,12 +576,13 @@ __device__ __forceinline__ int64_t patch_node(const PatchMeta& m, int i, int N1)
 
 // Cartesian patches: gather r_j, Algorithm 2/3, write omega_AS d_j
 // (additive), or add d_j to u for the patches of one colour (multiplicative).
-// Degrees up to 4: at most 256 threads per block and three blocks per SM
-// (registers <= 85), so that 24 warps keep the FP64 pipe fed.  Higher
-// degrees need more registers per line than that without spilling and run
-// fastest with the compiler's own choice (measured: bounding k = 7 to 256
-// threads made its FP32 launch 40% slower).
-#if PMG_K <= 4
+// FP64, degrees up to 4: at most 256 threads per block and three blocks per
+// SM (registers <= 85), so that 24 warps keep the FP64 pipe fed.  Higher
+// degrees need more registers per line than that without spilling, and the
+// FP32 kernels (40 registers, shared-memory bound) run fastest with the
+// compiler's own choice and larger blocks (measured: bounding k = 7 to 256
+// threads made its FP32 launch 40% slower, k = 4 FP32 3% slower).
+#if PMG_K <= 4 && PMG_PREC == 0
 #define PMG_PATCH_BOUNDS __launch_bounds__(256, 3)
 constexpr int kPatchMaxThreads = 256;
 #else
