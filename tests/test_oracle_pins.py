@@ -605,3 +605,27 @@ def test_multiplicative_half_cycle_gmres_matches_direct_solve():
     xs = solver.direct_solve(fine.A, b)
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
     assert it < 20
+
+
+def test_gmres_is_flexible():
+    # a preconditioner that changes every step (M_0, M_1, M_0, ...): the
+    # iterate still minimises ||b - A x|| over span{z_0..z_{j-1}}, the
+    # stored preconditioned vectors (least squares on the explicit Z)
+    A, M, b = _nonsymmetric_system()
+    rng = np.random.default_rng(12)
+    M2 = np.eye(len(b)) + 0.2 * rng.standard_normal(M.shape)
+    calls, Z = [0], []
+
+    def varying(v):
+        z = (M if calls[0] % 2 == 0 else M2) @ v
+        calls[0] += 1
+        Z.append(z)
+        return z
+
+    j = 5
+    x, it, _ = solver.gmres(A, b, varying, rtol=0.0, maxit=j, restart=30)
+    assert it == j and len(Z) == j
+    Zm = np.column_stack(Z)
+    y = np.linalg.lstsq(A @ Zm, b, rcond=None)[0]
+    np.testing.assert_allclose(np.linalg.norm(b - A @ x), np.linalg.norm(b - A @ Zm @ y), rtol=1e-9)
+    np.testing.assert_allclose(x, Zm @ y, rtol=1e-8, atol=1e-12)
