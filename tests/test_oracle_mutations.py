@@ -92,7 +92,7 @@ def _nonsymmetric(n=20, seed=4):
     return A, M, rng.standard_normal(n)
 
 
-def test_wrong_givens_sign_breaks_minimal_residual(monkeypatch):
+def test_wrong_givens_sign_breaks_minimal_residual():
     # planted: g_{j+1} = +sn g_j (the rotated right-hand side with the wrong
     # sign); the least-squares optimality pin must notice
     A, M, b = _nonsymmetric()
@@ -102,7 +102,6 @@ def test_wrong_givens_sign_breaks_minimal_residual(monkeypatch):
     best = np.linalg.norm(b - A @ M @ K @ y)
     x, _, _ = solver.gmres(A, b, lambda v: M @ v, rtol=0.0, maxit=j, restart=30)
     assert abs(np.linalg.norm(b - A @ x) - best) < 1e-9 * best
-    orig_hypot = np.hypot
 
     def wrong_gmres(A, b, precond, rtol=1e-8, maxit=500, restart=30):
         # the oracle's loop with one planted sign, written out for the test
@@ -126,7 +125,7 @@ def test_wrong_givens_sign_breaks_minimal_residual(monkeypatch):
                 hi, hn = H[i, jj], H[i + 1, jj]
                 H[i, jj] = cs[i] * hi + sn[i] * hn
                 H[i + 1, jj] = -sn[i] * hi + cs[i] * hn
-            rho = orig_hypot(H[jj, jj], H[jj + 1, jj])
+            rho = np.hypot(H[jj, jj], H[jj + 1, jj])
             cs[jj], sn[jj] = H[jj, jj] / rho, H[jj + 1, jj] / rho
             H[jj, jj], H[jj + 1, jj] = rho, 0.0
             g[jj + 1] = +sn[jj] * g[jj]                 # planted: sign
@@ -138,7 +137,7 @@ def test_wrong_givens_sign_breaks_minimal_residual(monkeypatch):
     assert np.linalg.norm(b - A @ xw) > best * (1 + 1e-6)
 
 
-def test_missing_residual_update_breaks_sequential_equivalence(monkeypatch):
+def test_missing_residual_update_breaks_sequential_equivalence():
     # planted: every colour reuses the residual of the first one (no update
     # between colours); the pin against the patch-by-patch loop must notice
     m = fem.Mesh(2, 6, 2)
