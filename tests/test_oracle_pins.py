@@ -629,3 +629,19 @@ def test_gmres_is_flexible():
     y = np.linalg.lstsq(A @ Zm, b, rcond=None)[0]
     np.testing.assert_allclose(np.linalg.norm(b - A @ x), np.linalg.norm(b - A @ Zm @ y), rtol=1e-9)
     np.testing.assert_allclose(x, Zm @ y, rtol=1e-8, atol=1e-12)
+
+
+def test_table1_fixture_is_consistent():
+    # the transcribed Table 1 has 16 rows (2 dims x 2 degrees x 4 local
+    # solvers) of 4 counts, and the orderings the GPU test asserts hold for
+    # the printed numbers themselves
+    rows = golden_rows("table1_gmres_iterations.txt")
+    assert len(rows) == 16 and all(len(r) == 7 for r in rows)
+    t = {(int(r[0]), int(r[1]), r[2]): [int(v) for v in r[3:]] for r in rows}
+    for dim in (2, 3):
+        for k in (3, 7):
+            for i in range(4):
+                assert t[(dim, k, "25V")][i] <= t[(dim, k, "1V")][i] <= t[(dim, k, "1H")][i]
+                assert t[(dim, k, "2H")][i] <= t[(dim, k, "1H")][i]
+            for s in ("1V", "1H", "2H", "25V"):
+                assert all(b >= a for a, b in zip(t[(dim, k, s)], t[(dim, k, s)][1:]))
