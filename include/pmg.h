@@ -213,7 +213,8 @@ int64_t pmg_launch_count(void);
 
 /* Patches per thread block the smoother kernels of this context use: the
  * config's value, or the autotuned one (timed per dimension, degree,
- * precision, geometry and local cycles on the finest level; cached for the
+ * precision, geometry, local cycles and smoother on the finest level's
+ * patch launches of one sweep; cached for the
  * process and, if the environment variable PMG_TUNE_FILE names a file, in
  * that file). */
 int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
@@ -235,8 +236,11 @@ const char* pmg_last_error(void);
  * copies -- tolerance, iteration cap); pmg_server_poll never blocks: it
  * admits queued requests in arrival order while fewer than max_active run
  * and the request's pmg_bytes_required fits in the budget (idle resident
- * contexts with the same dim/n/degree/precision/geometry/levels/cycles are
- * reused; least-recently-used idle contexts are evicted to make room),
+ * contexts with the same configuration -- dim, n, degree, precision,
+ * geometry, levels, local cycles, smoothing steps, half cycle, smoother,
+ * outer solver and restart, and for a distorted mesh the same displacement
+ * array -- are reused; least-recently-used idle contexts are evicted to
+ * make room),
  * advances every running solve (pmg_solve_progress) and retires finished
  * ones.  Each resident context has its own stream, so the kernels of
  * concurrent requests overlap on the device.  One host thread drives a
@@ -270,7 +274,8 @@ int pmg_server_stats(const pmg_server* server, int64_t* used_bytes, int* residen
  * vectors) is a file-scope device array of 4 x PMG_NOALLOC_MAX_DOFS doubles
  * (64 MiB) that every GPU loading the library holds until exit.  The first
  * call on a device (and the first for each degree) resolves that array's
- * address and loads the degree's 1D matrices into constant memory, which
+ * address and loads the degree's 1D matrices into constant memory (once per
+ * degree and dimension), which
  * synchronises: make it before any stream capture.  All calls share the
  * array; calls that overlap on the GPU race on it.  Grids above
  * PMG_NOALLOC_MAX_DOFS are rejected with PMG_ERR_UNSUPPORTED. */
