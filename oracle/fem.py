@@ -22,6 +22,7 @@ corners; a coarse vertex is the fine vertex at the same grid position, so
 the levels are nested topologically but not geometrically (the transfers
 stay the reference embedding, Eq. (2)).
 """
+import functools
 import itertools
 
 import numpy as np
@@ -173,6 +174,7 @@ class Mesh:
         return G
 
 
+@functools.lru_cache(maxsize=None)
 def _tensor_basis(k, nq, d):
     """Values and reference gradients of the tensor Q_k basis at the tensor
     Gauss points: Phi (Q, n_loc) and Grad (d, Q, n_loc), x fastest."""
@@ -194,7 +196,10 @@ def _tensor_basis(k, nq, d):
         mats = list(mats)
         mats[i] = D
         Grad.append(kron_list(mats))
-    return Phi, np.array(Grad)
+    Grad = np.array(Grad)
+    Phi.flags.writeable = False  # memoised: shared by every cell
+    Grad.flags.writeable = False
+    return Phi, Grad
 
 
 def element_stiffness(mesh, c, k=None):

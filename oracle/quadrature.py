@@ -6,13 +6,24 @@ the node set nor the rule.  Reading taken: Lagrange polynomials on the k+1
 Gauss-Lobatto (GLL) points, and the (k+1)-point Gauss-Legendre rule, on every
 p-level with p in place of k.
 
+The rules are memoised (read-only arrays): the mesh code asks for the same
+rule once per cell.
+
 Pinned by tests against closed forms (k=2 nodes {0, 1/2, 1}; 2-point Gauss
 1/2 -+ 1/(2 sqrt 3)), sum of weights = 1, exact integration of x^m for
 m <= 2n-1, and agreement with numpy's leggauss.
 """
+import functools
+
 import numpy as np
 
 _LD = np.longdouble
+
+
+def _frozen(*arrays):
+    for a in arrays:
+        a.flags.writeable = False
+    return arrays if len(arrays) > 1 else arrays[0]
 
 
 def _legendre(n, x):
@@ -26,6 +37,7 @@ def _legendre(n, x):
     return p1, p0
 
 
+@functools.lru_cache(maxsize=None)
 def gauss_legendre(n):
     """n-point Gauss-Legendre rule on [0, 1]: (points, weights), ascending.
 
@@ -49,9 +61,10 @@ def gauss_legendre(n):
     w = 2 / ((1 - x * x) * dp * dp)
     order = np.argsort(x)
     x, w = x[order], w[order]
-    return np.asarray((x + 1) / 2, dtype=np.float64), np.asarray(w / 2, dtype=np.float64)
+    return _frozen(np.asarray((x + 1) / 2, dtype=np.float64), np.asarray(w / 2, dtype=np.float64))
 
 
+@functools.lru_cache(maxsize=None)
 def gauss_lobatto_nodes(k):
     """The k+1 Gauss-Lobatto points on [0, 1] (endpoints included), ascending.
 
@@ -63,7 +76,7 @@ def gauss_lobatto_nodes(k):
     if k < 1:
         raise ValueError("k >= 1")
     if k == 1:
-        return np.array([0.0, 1.0])
+        return _frozen(np.array([0.0, 1.0]))
     i = np.arange(1, k, dtype=_LD)
     x = -np.cos(_LD(np.pi) * i / k)
     for _ in range(100):
@@ -76,7 +89,7 @@ def gauss_lobatto_nodes(k):
             break
     x = np.sort(x)
     full = np.concatenate([[_LD(-1)], x, [_LD(1)]])
-    return np.asarray((full + 1) / 2, dtype=np.float64)
+    return _frozen(np.asarray((full + 1) / 2, dtype=np.float64))
 
 
 def lagrange_values(nodes, x):

@@ -176,3 +176,39 @@ def test_swapped_trilinear_shape_functions_break_volume(monkeypatch):
     assert abs(energy() - 1) < 1e-12
     monkeypatch.setattr(fem.Mesh, "_trilinear_map", swapped)
     assert abs(energy() - 1) > 1e-6
+
+
+def test_eigenvalues_of_a_instead_of_the_jacobi_scaled_patch_break_the_damping_pins():
+    # planted: lambda_max of A_{j,p} itself instead of D^{-1/2} A_{j,p} D^{-1/2}
+    from tests.test_oracle_pins import lambda_bounds_hold
+
+    def wrong(d, p):
+        A = patch.patch_matrix(fem.Mesh(d, 2, p), (1,) * d, p)
+        return float(np.linalg.eigvalsh(A)[-1])
+
+    cases = [(2, 2), (2, 5), (3, 2), (3, 3), (3, 4)]
+    assert all(lambda_bounds_hold(constants.lambda_max_jacobi(d, p), d, p) for d, p in cases)
+    assert not any(lambda_bounds_hold(wrong(d, p), d, p) for d, p in cases)
+
+
+def test_patch_closure_instead_of_interior_breaks_the_damping_pins():
+    # planted: all (2p+1)^d nodes of the 2^d patch cells (Neumann patch
+    # matrix with the patch boundary kept) instead of the (2p-1)^d interior
+    import itertools
+    from tests.test_oracle_pins import lambda_bounds_hold
+
+    def wrong(d, p):
+        m = fem.Mesh(d, 2, p)
+        nf = 2 * p + 1
+        A = np.zeros((nf ** d, nf ** d))
+        for off in itertools.product(*([range(2)] * d)):
+            Ke = fem.element_stiffness(m, off, p)
+            loc = np.zeros(1, dtype=np.int64)
+            for dd in range(d):
+                g = p * off[dd] + np.arange(p + 1)
+                loc = (loc[None, :] + nf ** dd * g[:, None]).reshape(-1)
+            A[np.ix_(loc, loc)] += Ke
+        s = 1.0 / np.sqrt(np.diag(A))
+        return float(np.linalg.eigvalsh(s[:, None] * A * s[None, :])[-1])
+
+    assert not any(lambda_bounds_hold(wrong(d, p), d, p) for d, p in [(2, 3), (3, 2), (3, 3)])

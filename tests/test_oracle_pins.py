@@ -645,3 +645,78 @@ def test_table1_fixture_is_consistent():
                 assert t[(dim, k, "2H")][i] <= t[(dim, k, "1H")][i]
             for s in ("1V", "1H", "2H", "25V"):
                 assert all(b >= a for a, b in zip(t[(dim, k, s)], t[(dim, k, s)][1:]))
+
+
+# ------------------------------------------------------------ Jacobi damping
+# lambda_max(D^{-1} A_{j,p}) on the unit Cartesian patch is what the omega_J
+# reading (4 / (3 lambda_max)) rests on.  Pinned by bounds that the
+# mathematics fixes and by a textbook construction, not by re-running the
+# oracle's eigen-solve.
+def _patch_and_diag(d, p):
+    A = patch.patch_matrix(fem.Mesh(d, 2, p), (1,) * d, p)
+    return A, np.diag(A).copy()
+
+
+def _power_rayleigh(A, D, iters=3000):
+    """Power iteration on D^{-1} A (own loop) and the generalised Rayleigh
+    quotient v^T A v / v^T D v of its last iterate: a lower bound of
+    lambda_max(D^{-1} A) for any v, equal to it once converged."""
+    v = np.cos(2.1 * np.arange(A.shape[0])) + 0.3
+    for _ in range(iters):
+        w = (A @ v) / D
+        v = w / np.linalg.norm(w)
+    return float(v @ (A @ v)) / float(v @ (D * v))
+
+
+def lambda_bounds_hold(lam, d, p):
+    """Rayleigh lower bound <= lambda <= Gershgorin bound of D^{-1} A, and
+    lambda within 1e-9 of the converged power-iteration quotient."""
+    A, D = _patch_and_diag(d, p)
+    R = _power_rayleigh(A, D)
+    G = float(np.max(np.abs(A).sum(axis=1) / D))
+    return R <= lam * (1 + 1e-12) and lam <= G and abs(lam - R) <= 1e-9 * lam
+
+
+@pytest.mark.parametrize("d,p", [(2, 2), (2, 3), (2, 5), (2, 8), (3, 2), (3, 3), (3, 4), (3, 5)])
+def test_lambda_max_jacobi_between_rayleigh_and_gershgorin(d, p):
+    assert lambda_bounds_hold(constants.lambda_max_jacobi(d, p), d, p)
+
+
+def _q2_patch_1d():
+    """1D Q2 (nodes 0, 1/2, 1) element stiffness and exact mass on a unit
+    cell, textbook values, assembled over two cells and restricted to the
+    three patch-interior nodes (mid-point, centre vertex, mid-point)."""
+    Ke = np.array([[7., -8., 1.], [-8., 16., -8.], [1., -8., 7.]]) / 3.0
+    Me = np.array([[4., 2., -1.], [2., 16., 2.], [-1., 2., 4.]]) / 30.0
+    K, M = np.zeros((5, 5)), np.zeros((5, 5))
+    for c in (0, 2):
+        K[c:c + 3, c:c + 3] += Ke
+        M[c:c + 3, c:c + 3] += Me
+    return K[1:4, 1:4], M[1:4, 1:4]
+
+
+def test_q2_textbook_patch_matrices():
+    # the typed element matrices: K annihilates constants, M integrates 1 to 1,
+    # and the 1D patch has lambda_max(D^{-1} K) = 1 + 2/sqrt(7) in closed form
+    Ke = np.array([[7., -8., 1.], [-8., 16., -8.], [1., -8., 7.]]) / 3.0
+    Me = np.array([[4., 2., -1.], [2., 16., 2.], [-1., 2., 4.]]) / 30.0
+    assert np.abs(Ke.sum(axis=1)).max() < 1e-15 and abs(Me.sum() - 1.0) < 1e-15
+    K, _ = _q2_patch_1d()
+    s = 1.0 / np.sqrt(np.diag(K))
+    assert abs(np.linalg.eigvalsh(s[:, None] * K * s[None, :])[-1] - (1 + 2 / np.sqrt(7))) < 1e-14
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_lambda_max_jacobi_q2_equals_textbook_kronecker_patch(d):
+    # A_{j,2} = sum_dir (K on dir, M elsewhere) from the textbook 1D matrices
+    # (the cell size scales A uniformly, so D^{-1} A does not depend on it)
+    K, M = _q2_patch_1d()
+    A = np.zeros((3 ** d, 3 ** d))
+    for direction in range(d):
+        term = np.ones((1, 1))
+        for ax in reversed(range(d)):          # x fastest: the x factor is the last kron
+            term = np.kron(term, K if ax == direction else M)
+        A += term
+    s = 1.0 / np.sqrt(np.diag(A))
+    lam = np.linalg.eigvalsh(s[:, None] * A * s[None, :])[-1]
+    assert abs(constants.lambda_max_jacobi(d, 2) - lam) <= 1e-12 * lam
