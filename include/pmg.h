@@ -153,7 +153,11 @@ int pmg_apply(pmg_ctx* ctx, int level, int prec, const void* x, void* y);
 /* r = b - A_level u (the "evaluate" step of Algorithm 1, here global). */
 int pmg_residual(pmg_ctx* ctx, int level, int prec, const void* b, const void* u, void* r);
 
-/* `sweeps` vertex-patch sweeps on `level` >= 1 with the configured smoother:
+/* `sweeps` vertex-patch sweeps on `level` with the configured smoother.  The
+ * level must have patches (n >= 2 cells per side) and smoother data: every
+ * level but the coarsest of a deformed or distorted hierarchy (Cartesian
+ * patch operators need no stored data; a single-level context is smoothable
+ * on its one level); PMG_ERR_ARG otherwise.  The smoother is
  * additive,
  *   u <- u + omega_AS sum_j Pi_j^T LocalSolve_j(Pi_j (b - A u)),
  * the patch update of Algorithm 1 summed over all patches; or
@@ -219,6 +223,20 @@ int64_t pmg_launch_count(void);
  * that file). */
 int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
 
+/* The damping a context runs with: omega_AS of the additive smoother and the
+ * local Jacobi damping omega_J per p-level (omega_jacobi[4], index 0 = the
+ * p = 1 level, unused and 1; entries beyond the context's p-levels are 1).
+ * The config's values where it gives them (> 0), else the defaults below. */
+int pmg_damping(const pmg_ctx* ctx, double* omega_patch, double* omega_jacobi);
+
+/* Default damping for (dim, degree), without a context or a GPU (host
+ * arithmetic only).  The paper gives no damping (§2.2, §3.2 name a damped
+ * Jacobi smoother; its smoother is multiplicative and needs no omega_AS), so
+ * these are readings: omega_AS = 1.5 / 2^d (a free DoF lies in at most 2^d
+ * patch interiors), omega_J(p) = 4 / (3 lambda_max(D^-1 A_{j,p})) on the
+ * Cartesian patch of degree p (scale invariant), lambda_max by Lanczos. */
+int pmg_default_damping(int dim, int degree, double* omega_patch, double* omega_jacobi);
+
 /* Instrumentation: mean device times (ms, CUDA events on the context's
  * stream) of the three phases of one smoothing step on `level`, over `reps`
  * repetitions after one warm-up, on the level's own vectors: ms[0] residual
@@ -235,12 +253,14 @@ const char* pmg_last_error(void);
  * of pmg_num_dofs(finest) doubles each -- pinned memory for overlapping
  * copies -- tolerance, iteration cap); pmg_server_poll never blocks: it
  * admits queued requests in arrival order while fewer than max_active run
- * and the request's pmg_bytes_required fits in the budget (idle resident
- * contexts with the same configuration -- dim, n, degree, precision,
- * geometry, levels, local cycles, smoothing steps, half cycle, smoother,
- * outer solver and restart, and for a distorted mesh the same displacement
- * array -- are reused; least-recently-used idle contexts are evicted to
- * make room),
+ * and the request's pmg_bytes_required fits in the budget (an idle resident
+ * context is reused when the request's configuration would build the same
+ * operator and preconditioner: every pmg_config field pmg_create reads -- dim,
+ * n, degree, levels, precision, geometry and, for the deformed geometry, its
+ * amplitude, damping (all values <= 0 count as "default"), local cycles,
+ * smoothing steps, half cycle, smoother, outer solver and restart, patches
+ * per block -- and for a distorted mesh the same displacement values;
+ * least-recently-used idle contexts are evicted to make room),
  * advances every running solve (pmg_solve_progress) and retires finished
  * ones.  Each resident context has its own stream, so the kernels of
  * concurrent requests overlap on the device.  One host thread drives a
@@ -248,7 +268,10 @@ const char* pmg_last_error(void);
 typedef struct pmg_server pmg_server;
 int pmg_server_create(int64_t memory_budget_bytes, int max_active, pmg_server** out);
 int pmg_server_destroy(pmg_server* server);
-/* PMG_ERR_OOM if the request can never fit in the budget. */
+/* PMG_ERR_OOM if the request can never fit in the budget.  The config is
+ * copied, and for a distorted mesh so are its vertex displacements: the
+ * caller may free cfg and cfg->vertex_disp on return.  b_host and x_host must
+ * stay valid until the request is done. */
 int pmg_server_submit(pmg_server* server, const pmg_config* cfg, const double* b_host, double* x_host, double rtol,
                       int maxit, int64_t* request_id);
 int pmg_server_poll(pmg_server* server, int* n_running, int* n_queued);
@@ -257,6 +280,11 @@ int pmg_server_poll(pmg_server* server, int* n_running, int* n_queued);
  * steady clock: submission, admission, completion. */
 int pmg_server_result(pmg_server* server, int64_t request_id, int* state, pmg_solve_info* info, double* t_submit,
                       double* t_start, double* t_done);
+/* Forget a finished (done or failed) request: its id becomes unknown.  The
+ * server keeps every request until it is released or the server destroyed,
+ * so a long-running driver releases each request once it has read the
+ * result.  PMG_ERR_STATE while the request is queued or running. */
+int pmg_server_release(pmg_server* server, int64_t request_id);
 int pmg_server_stats(const pmg_server* server, int64_t* used_bytes, int* resident_contexts,
                      int64_t* created_contexts);
 
@@ -278,7 +306,9 @@ int pmg_server_stats(const pmg_server* server, int64_t* used_bytes, int* residen
  * degree and dimension), which
  * synchronises: make it before any stream capture.  All calls share the
  * array; calls that overlap on the GPU race on it.  Grids above
- * PMG_NOALLOC_MAX_DOFS are rejected with PMG_ERR_UNSUPPORTED. */
+ * PMG_NOALLOC_MAX_DOFS are rejected with PMG_ERR_UNSUPPORTED.  x, y and the
+ * stream must belong to the calling thread's current device: the scratch
+ * array, the constant-memory upload and the launch all use that device. */
 int pmg_apply_cartesian_noalloc(int dim, int n_cells, int degree, const double* x, double* y, void* stream);
 
 #ifdef __cplusplus

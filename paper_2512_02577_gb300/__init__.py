@@ -37,7 +37,7 @@ EXPORTED = [
     "pmg_launch_count", "pmg_status_string", "pmg_last_error", "pmg_apply_cartesian_noalloc",
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
-    "pmg_smoother_phase_times",
+    "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -109,6 +109,9 @@ def load_library(path=LIB_PATH):
                                      ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_server_stats": (cint, [vp, ctypes.POINTER(i64), ctypes.POINTER(cint), ctypes.POINTER(i64)]),
         "pmg_smoother_phase_times": (cint, [vp, cint, cint, ctypes.POINTER(dbl)]),
+        "pmg_damping": (cint, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "pmg_default_damping": (cint, [cint, cint, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "pmg_server_release": (cint, [vp, i64]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -167,12 +170,28 @@ def launch_count():
 
 def apply_cartesian_noalloc(dim, n_cells, degree, x, y, stream=None):
     """y = A x (FP64, Cartesian) through the allocation-free entry point, for
-    callers that cannot allocate device memory; see include/pmg.h."""
+    callers that cannot allocate device memory; see include/pmg.h.  x and y
+    must be on one device; the call runs with that device current, on
+    ``stream`` (default: that device's current stream)."""
     lib = load_library()
     n = (degree * n_cells + 1) ** dim
-    sh = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-    _check(lib.pmg_apply_cartesian_noalloc(dim, n_cells, degree, _ptr(x, torch.float64, n),
-                                           _ptr(y, torch.float64, n), ctypes.c_void_p(sh or None)))
+    px, py = _ptr(x, torch.float64, n), _ptr(y, torch.float64, n)
+    if x.device != y.device:
+        raise ValueError("x and y must be on the same device, got %s and %s" % (x.device, y.device))
+    if stream is not None and stream.device != x.device:
+        raise ValueError("stream is on %s, the vectors on %s" % (stream.device, x.device))
+    with torch.cuda.device(x.device):
+        sh = (stream if stream is not None else torch.cuda.current_stream(x.device)).cuda_stream
+        _check(lib.pmg_apply_cartesian_noalloc(dim, n_cells, degree, px, py, ctypes.c_void_p(sh or None)))
+
+
+def default_damping(dim, degree):
+    """(omega_patch, [omega_J per p-level]) the library uses when a config
+    leaves the damping at its default; host arithmetic, no GPU needed."""
+    lib = load_library()
+    wp, wj = ctypes.c_double(), (ctypes.c_double * 4)()
+    _check(lib.pmg_default_damping(dim, degree, ctypes.byref(wp), wj))
+    return wp.value, list(wj)
 
 
 def _ptr(t, dtype, n):
@@ -282,6 +301,12 @@ class Context:
         _check(_lib.pmg_smoother_phase_times(self.handle, level, reps, out))
         return tuple(out)
 
+    def damping(self):
+        """(omega_patch, [omega_J per p-level]) this context runs with."""
+        wp, wj = ctypes.c_double(), (ctypes.c_double * 4)()
+        _check(_lib.pmg_damping(self.handle, ctypes.byref(wp), wj))
+        return wp.value, list(wj)
+
     def patches_per_block(self):
         n = ctypes.c_int()
         _check(_lib.pmg_patches_per_block(self.handle, ctypes.byref(n)))
@@ -329,6 +354,11 @@ class Server:
         return dict(state=st.value, code=code, iterations=info.iterations, rel_residual=info.rel_residual,
                     device_ms=info.time_ms, status=info.status, t_submit=ts.value, t_start=ta.value,
                     t_done=td.value)
+
+    def release(self, rid):
+        """Forget a finished request (its buffers may then be reused)."""
+        _check(_lib.pmg_server_release(self.handle, rid))
+        self._keep.pop(rid, None)
 
     def stats(self):
         used, res, created = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()

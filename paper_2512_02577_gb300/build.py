@@ -5,11 +5,13 @@ vector kernels, and ``csrc/inst.cu`` once per kernel part -- each polynomial
 degree 1..8 x dimension 2, 3 x precision double, float, selected by -D flags
 -- so that no single unit dominates the build; the host set-up code by nvcc as
 C++.  Objects go to ``_build/``; the library is linked next to this file.  An
-object is rebuilt when any source or header is newer than it.
+object is rebuilt when its source or a header it includes (transitively) is
+newer than it.
 """
 import concurrent.futures
 import glob
 import os
+import re
 import subprocess
 import sys
 
@@ -38,16 +40,31 @@ def _units():
     return units
 
 
-def _headers():
-    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        glob.glob(os.path.join(INCLUDE, "*.h"))
+_INCLUDE_RE = re.compile(r'^\s*#\s*include\s*"([^"]+)"', re.M)
 
 
-def _stale(obj, src, newest_header):
+def _includes(path, seen=None):
+    """Every project header that ``path`` includes, transitively (quoted
+    includes resolved next to the including file, then in include/)."""
+    seen = set() if seen is None else seen
+    with open(path) as f:
+        text = f.read()
+    for name in _INCLUDE_RE.findall(text):
+        for base in (os.path.dirname(path), INCLUDE):
+            h = os.path.normpath(os.path.join(base, name))
+            if os.path.exists(h):
+                if h not in seen:
+                    seen.add(h)
+                    _includes(h, seen)
+                break
+    return seen
+
+
+def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    return os.path.getmtime(src) > t or newest_header > t
+    return any(os.path.getmtime(f) > t for f in [src] + sorted(_includes(src)))
 
 
 def _compile(src, obj, extra, verbose):
@@ -63,12 +80,11 @@ def _compile(src, obj, extra, verbose):
 def build(verbose=False, jobs=None):
     """Compile (incrementally) and link libpmg.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
-    newest_header = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     objs, todo = [], []
     for s, name, extra in _units():
         o = os.path.join(BUILD, name)
         objs.append(o)
-        if _stale(o, s, newest_header):
+        if _stale(o, s):
             todo.append((s, o, extra))
     jobs = jobs or min(len(todo) or 1, os.cpu_count() or 4)
     if todo:

@@ -67,6 +67,18 @@ extern "C" int pmg_apply_cartesian_noalloc(int dim, int n_cells, int degree, con
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(PMG_ERR_UNSUPPORTED, "device ordinal above 63");
+  // the vectors must live on this device (a pointer of another device, or a
+  // host pointer, would be dereferenced by kernels running here)
+  for (const void* v : {(const void*)x, (const void*)y}) {
+    cudaPointerAttributes a{};
+    e = cudaPointerGetAttributes(&a, v);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PMG_ERR_ARG, std::string("cudaPointerGetAttributes: ") + cudaGetErrorString(e));
+    }
+    if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+      return fail(PMG_ERR_ARG, "x and y must be device memory of the current device (" + std::to_string(dev) + ")");
+  }
   const pmg::KernelTable* kt = pmg::kernel_table(degree, dim, 0);
   double* scratch = nullptr;
   {

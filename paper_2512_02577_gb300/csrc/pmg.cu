@@ -189,14 +189,17 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     for (int i = 0; i < 4; ++i) o.G[i] = o.dinv[i] = -1;
     o.dinv1 = -1;
     if (P.deformed) {
+      // smoother data on every level that is smoothed: all but the coarsest
+      // of a hierarchy, and the only level of a single-level context
+      const bool smoothed = l > 0 || L == 1;
       for (int pl = 0; pl < P.nplev; ++pl) {
         const int p = plev(P.K, pl);
         const bool top = pl == P.nplev - 1;
-        if (!top && l == 0) continue;  // coarsest level: only the operator itself
+        if (!top && !smoothed) continue;  // coarsest level: only the operator itself
         o.G[pl] = bump(cur, ipow64(nl, P.dim) * ipow64(p + 1, P.dim) * ncomp * 4);
-        if (l > 0 && pl > 0) o.dinv[pl] = bump(cur, ipow64((int64_t)p * nl + 1, P.dim) * P.mg_es);
+        if (smoothed && pl > 0) o.dinv[pl] = bump(cur, ipow64((int64_t)p * nl + 1, P.dim) * P.mg_es);
       }
-      if (l > 0) o.dinv1 = bump(cur, ipow64(nl + 1, P.dim) * P.mg_es);
+      if (smoothed) o.dinv1 = bump(cur, ipow64(nl + 1, P.dim) * P.mg_es);
     }
   }
   const int64_t NF = ipow64((int64_t)P.K * cfg->n_cells + 1, P.dim);
@@ -669,6 +672,10 @@ int choose_patches_per_block(pmg_ctx* c) {
 
 int check_ctx(const pmg_ctx* c) { return c ? PMG_OK : fail(PMG_ERR_ARG, "context is NULL"); }
 
+// omega_AS reading: theta / 2^d with theta = 1.5 (every free DoF lies in at
+// most 2^d patch interiors)
+double default_omega_patch(int dim) { return 1.5 / (1 << dim); }
+
 int setup_context(pmg_ctx* c) {
   const Plan& P = c->plan;
   c->lv.resize(c->L);
@@ -727,7 +734,7 @@ int setup_context(pmg_ctx* c) {
 
   // damping
   const pmg_config& cf = c->cfg;
-  c->omega_as = cf.omega_patch > 0 ? cf.omega_patch : 1.5 / (1 << c->dim);
+  c->omega_as = cf.omega_patch > 0 ? cf.omega_patch : default_omega_patch(c->dim);
   for (int l = 0; l < 4; ++l) {
     if (l < c->nplev && l > 0)
       c->omega_j[l] = cf.omega_jacobi[l] > 0 ? cf.omega_jacobi[l]
@@ -956,9 +963,21 @@ int pmg_residual(pmg_ctx* c, int level, int prec, const void* b, const void* u, 
   return level_apply(c, level, prec, u, r, b);
 }
 
+// A level can be smoothed when it has patches (n >= 2) and its smoother
+// data: every level but the coarsest of a hierarchy, the coarsest too when
+// Cartesian (the patch operators need no stored data), and the only level of
+// a single-level context.
+static int check_smooth_level(const pmg_ctx* c, int level) {
+  if (level < 0 || level >= c->L) return fail(PMG_ERR_ARG, "level out of range");
+  if (c->lv[level].n < 2) return fail(PMG_ERR_ARG, "level has no interior vertex (n < 2): no patches to smooth");
+  if (level == 0 && c->L > 1 && c->deformed)
+    return fail(PMG_ERR_ARG, "the coarsest level of a deformed hierarchy holds no smoother data");
+  return PMG_OK;
+}
+
 int pmg_smooth(pmg_ctx* c, int level, int prec, const void* b, void* u, int sweeps) {
   if (check_ctx(c) || !b || !u) return fail(PMG_ERR_ARG, "NULL argument");
-  if (level < 1 || level >= c->L) return fail(PMG_ERR_ARG, "smoothing level must be in 1..n_levels-1");
+  if (int rc = check_smooth_level(c, level)) return rc;
   if (prec != c->mgprec) return fail(PMG_ERR_ARG, "smoother precision must equal mg_precision");
   if (sweeps < 0) return fail(PMG_ERR_ARG, "sweeps < 0");
   return smooth_level(c, level, b, u, sweeps);
@@ -1235,7 +1254,7 @@ int64_t pmg_launch_count(void) { return g_launches.load(); }
 
 int pmg_smoother_phase_times(pmg_ctx* c, int level, int reps, double* ms) {
   if (check_ctx(c) || !ms) return fail(PMG_ERR_ARG, "NULL argument");
-  if (level < 1 || level >= c->L) return fail(PMG_ERR_ARG, "smoothing level must be in 1..n_levels-1");
+  if (int rc = check_smooth_level(c, level)) return rc;
   if (reps < 1) return fail(PMG_ERR_ARG, "reps < 1");
   LevelData& L = c->lv[level];
   cudaEvent_t ev[4];
@@ -1264,6 +1283,24 @@ int pmg_smoother_phase_times(pmg_ctx* c, int level, int reps, double* ms) {
   for (auto& e : ev) cudaEventDestroy(e);
   if (rc) return rc;
   for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+  return PMG_OK;
+}
+
+int pmg_default_damping(int dim, int degree, double* omega_patch, double* omega_jacobi) {
+  if (dim != 2 && dim != 3) return fail(PMG_ERR_UNSUPPORTED, "dim must be 2 or 3");
+  if (degree < 1 || degree > 8) return fail(PMG_ERR_UNSUPPORTED, "degree must be in 1..8");
+  if (!omega_patch || !omega_jacobi) return fail(PMG_ERR_ARG, "NULL argument");
+  *omega_patch = default_omega_patch(dim);
+  const int np = nlev(degree);
+  for (int l = 0; l < 4; ++l)
+    omega_jacobi[l] = (l > 0 && l < np) ? host::default_omega_jacobi(dim, plev(degree, l)) : 1.0;
+  return PMG_OK;
+}
+
+int pmg_damping(const pmg_ctx* c, double* omega_patch, double* omega_jacobi) {
+  if (check_ctx(c) || !omega_patch || !omega_jacobi) return fail(PMG_ERR_ARG, "NULL argument");
+  *omega_patch = c->omega_as;
+  for (int l = 0; l < 4; ++l) omega_jacobi[l] = c->omega_j[l];
   return PMG_OK;
 }
 

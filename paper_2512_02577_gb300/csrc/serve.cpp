@@ -5,8 +5,8 @@
 // by pmg_server_submit.  pmg_server_poll, which never blocks, (1) admits
 // queued requests in arrival order while a slot is free and the request's
 // context fits in the device-memory budget -- reusing an idle resident
-// context with the same (dim, n, degree, precision, geometry, levels) when
-// one exists, evicting least-recently-used idle contexts otherwise -- (2)
+// context built from the same configuration when one exists (key_of),
+// evicting least-recently-used idle contexts otherwise -- (2)
 // advances every running solve as far as its completed device work allows
 // (pmg_solve_progress: each CG iteration enqueues its V-cycle, captured as a
 // CUDA graph, before the host reads the residual), and (3) retires solves
@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <cstdint>
 #include <deque>
 #include <map>
 #include <string>
@@ -37,20 +38,74 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-// contexts are reused only for the same configuration (a distorted mesh: the
-// same displacement array, by address)
-using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, const double*>;
+// A resident context is reused only for a request whose configuration would
+// build the same operator and preconditioner: every pmg_config field that
+// pmg_create reads, with the damping as given (<= 0 means "default", so all
+// non-positive values are one key), the deformation amplitude when the
+// geometry uses it, and for a distorted mesh the displacement CONTENTS
+// (copied at submit; compared by a 64-bit FNV-1a hash and then exactly).
+struct Key {
+  int dim = 0, n_cells = 0, degree = 0, mg_precision = 0, geometry = 0, n_levels = 0, local_cycles = 0,
+      smooth_steps = 0, local_half = 0, outer_solver = 0, gmres_restart = 0, smoother = 0, patches_per_block = 0;
+  double deform_amp = 0, omega_patch = 0, omega_jacobi[4] = {0, 0, 0, 0};
+  uint64_t disp_hash = 0;
+  const std::vector<double>* disp = nullptr;  // the request's own copy (distorted only)
 
-Key key_of(const pmg_config& c) {
-  return Key(c.dim, c.n_cells, c.degree, c.mg_precision, c.geometry, c.n_levels, c.local_cycles, c.smooth_steps,
-             c.local_half, c.outer_solver, c.outer_solver == PMG_OUTER_GMRES ? c.gmres_restart : 0, c.smoother,
-             c.geometry == PMG_GEOM_DISTORTED ? c.vertex_disp : nullptr);
+  bool operator==(const Key& o) const {
+    if (std::tie(dim, n_cells, degree, mg_precision, geometry, n_levels, local_cycles, smooth_steps, local_half,
+                 outer_solver, gmres_restart, smoother, patches_per_block, deform_amp, omega_patch, disp_hash) !=
+        std::tie(o.dim, o.n_cells, o.degree, o.mg_precision, o.geometry, o.n_levels, o.local_cycles,
+                 o.smooth_steps, o.local_half, o.outer_solver, o.gmres_restart, o.smoother, o.patches_per_block,
+                 o.deform_amp, o.omega_patch, o.disp_hash))
+      return false;
+    for (int i = 0; i < 4; ++i)
+      if (omega_jacobi[i] != o.omega_jacobi[i]) return false;
+    if ((disp == nullptr) != (o.disp == nullptr)) return false;
+    return !disp || *disp == *o.disp;
+  }
+};
+
+uint64_t fnv1a(const std::vector<double>& v) {
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
+  for (size_t i = 0; i < v.size() * sizeof(double); ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// disp: the request's copy of the displacements (distorted geometry), else null
+Key key_of(const pmg_config& c, const std::vector<double>* disp) {
+  Key k;
+  k.dim = c.dim;
+  k.n_cells = c.n_cells;
+  k.degree = c.degree;
+  k.mg_precision = c.mg_precision;
+  k.geometry = c.geometry;
+  k.n_levels = c.n_levels;
+  k.local_cycles = c.local_cycles;
+  k.smooth_steps = c.smooth_steps;
+  k.local_half = c.local_half;
+  k.outer_solver = c.outer_solver;
+  k.gmres_restart = c.outer_solver == PMG_OUTER_GMRES ? c.gmres_restart : 0;
+  k.smoother = c.smoother;
+  k.patches_per_block = c.patches_per_block;
+  k.deform_amp = c.geometry == PMG_GEOM_DEFORMED ? c.deform_amp : 0.0;
+  k.omega_patch = c.omega_patch > 0 ? c.omega_patch : 0.0;
+  for (int i = 0; i < 4; ++i) k.omega_jacobi[i] = c.omega_jacobi[i] > 0 ? c.omega_jacobi[i] : 0.0;
+  if (c.geometry == PMG_GEOM_DISTORTED && disp) {
+    k.disp = disp;
+    k.disp_hash = fnv1a(*disp);
+  }
+  return k;
 }
 
 struct Slot {
   pmg_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   Key key;
+  std::vector<double> disp;  // the displacements the context was built from (distorted geometry)
   int64_t bytes = 0;
   bool busy = false;
   int64_t last_used = 0;
@@ -59,6 +114,7 @@ struct Slot {
 struct Request {
   int64_t id = 0;
   pmg_config cfg{};
+  std::vector<double> disp;  // copy of cfg.vertex_disp taken at submit (distorted geometry)
   const double* b = nullptr;
   double* x = nullptr;
   double rtol = 1e-8;
@@ -107,7 +163,7 @@ void destroy_slot(pmg_server* s, Slot* sl) {
 // device's free memory allow.  nullptr if r must wait.
 Slot* acquire_slot(pmg_server* s, Request* r, int* err) {
   *err = PMG_OK;
-  const Key k = key_of(r->cfg);
+  const Key k = key_of(r->cfg, r->cfg.geometry == PMG_GEOM_DISTORTED ? &r->disp : nullptr);
   for (Slot* sl : s->slots)
     if (!sl->busy && sl->key == k) return sl;
   while (s->used + r->bytes > s->budget) {
@@ -138,7 +194,8 @@ Slot* acquire_slot(pmg_server* s, Request* r, int* err) {
     *err = rc;
     return nullptr;
   }
-  sl->key = k;
+  sl->disp = r->disp;  // the slot's key refers to its own copy
+  sl->key = key_of(r->cfg, r->cfg.geometry == PMG_GEOM_DISTORTED ? &sl->disp : nullptr);
   sl->bytes = r->bytes;
   s->used += r->bytes;
   s->slots.push_back(sl);
@@ -192,6 +249,14 @@ int pmg_server_submit(pmg_server* s, const pmg_config* cfg, const double* b_host
   Request* r = new Request();
   r->id = s->next_id++;
   r->cfg = *cfg;
+  if (cfg->geometry == PMG_GEOM_DISTORTED && cfg->vertex_disp) {
+    // the request owns its displacements from here on: the caller's array
+    // may be freed or reused before the request is admitted
+    int64_t nv = 1;
+    for (int d = 0; d < cfg->dim; ++d) nv *= cfg->n_cells + 1;
+    r->disp.assign(cfg->vertex_disp, cfg->vertex_disp + nv * cfg->dim);
+    r->cfg.vertex_disp = r->disp.data();
+  }
   r->b = b_host;
   r->x = x_host;
   r->rtol = rtol;
@@ -268,6 +333,16 @@ int pmg_server_result(pmg_server* s, int64_t id, int* state, pmg_solve_info* inf
   if (t_start) *t_start = r->t_start;
   if (t_done) *t_done = r->t_done;
   return r->state == 3 ? r->status : PMG_OK;
+}
+
+int pmg_server_release(pmg_server* s, int64_t id) {
+  if (!s) return fail(PMG_ERR_ARG, "NULL server");
+  auto it = s->requests.find(id);
+  if (it == s->requests.end()) return fail(PMG_ERR_ARG, "unknown request id");
+  if (it->second->state < 2) return fail(PMG_ERR_STATE, "request is still queued or running");
+  delete it->second;
+  s->requests.erase(it);
+  return PMG_OK;
 }
 
 int pmg_server_stats(const pmg_server* s, int64_t* used_bytes, int* resident_contexts, int64_t* created_contexts) {

@@ -58,6 +58,7 @@ def run(requests, dim=3, precision=FP32, geometry=CARTESIAN, max_active=8, budge
                             queue_s=res["t_start"] - res["t_submit"], t_start=res["t_start"],
                             t_done=res["t_done"], state=res["state"],
                             iterations=res["iterations"], rel_residual=res["rel_residual"], x=x))
+        server.release(ids[i])
     stats = server.stats()
     server.close()
     lat = np.array([rec["latency_s"] for rec in records])

@@ -1,6 +1,7 @@
 """CUDA path vs the CPU oracle, through the C ABI.
 
-Tolerances (relative 2-norm unless stated):
+Tolerances (each check bounds both the relative 2-norm ||a - b|| / ||b|| and
+the element-wise max|a - b| / max|b|, see tests/parity.py):
   FP64 operator apply / residual       1e-12
   FP64 smoother sweep / V-cycle        1e-11  (summation order differs)
   FP32 apply / sweep / V-cycle         2e-5 vs the oracle's FP64
@@ -24,9 +25,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def rel(a, b):
-    nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+from tests.parity import rel  # noqa: E402  (max of norm-relative and element-wise error)
 
 
 def make_ctx(d, n, k, L=0, geom="cartesian", prec=p.FP64, **kw):

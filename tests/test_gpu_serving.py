@@ -109,3 +109,74 @@ def test_mixed_method_stream_same_alone_and_in_the_mix():
         assert torch.equal(xa.cpu(), x)
         ctx.close()
     srv.close()
+
+
+def test_reuse_key_separates_amplitude_damping_and_displacements():
+    # One slot, so each request finds the previous one's context idle: a
+    # context may be reused only when it builds the same operator and
+    # preconditioner.  Requests differ only in the deformation amplitude,
+    # the damping, or the displacement values (the caller overwrites its
+    # displacement array after the first submit); the last repeats the first
+    # and reuses its context.
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    d, n, k = 3, 4, 3
+    disp = vertex_displacements(d, n, 0.2, 21)
+    disp_b = vertex_displacements(d, n, 0.2, 22)
+    base = dict(dim=d, n_cells=n, degree=k, mg_precision=p.FP32)
+    cfgs = [p.make_config(geometry=p.DEFORMED, deform_amp=0.05, **base),
+            p.make_config(geometry=p.DEFORMED, deform_amp=0.1, **base),
+            p.make_config(**base),
+            p.make_config(omega_patch=0.12, **base),
+            p.make_config(omega_jacobi=[1.0, 0.6], **base)]
+    srv = p.Server(0, 1)
+    jobs = []
+
+    def submit(cfg, seed):
+        b = serve._rhs(d, n, k, seed)
+        x = torch.zeros_like(b).pin_memory()
+        jobs.append((b, x, srv.submit(cfg, b, x)))
+
+    for i, cfg in enumerate(cfgs):
+        submit(cfg, 900 + i)
+    arr = np.array(disp)                               # the caller's buffer
+    cfg_a = p.make_config(geometry=p.DISTORTED, vertex_disp=arr, **base)
+    cfg_a.vertex_disp = arr.ctypes.data                 # point at the buffer itself, not a copy
+    submit(cfg_a, 905)
+    arr[:] = disp_b                                     # reused before the request was admitted
+    submit(cfg_a, 906)
+    submit(cfgs[0], 907)
+    while any(srv.result(j[2])["state"] < 2 for j in jobs):
+        srv.poll()
+    assert srv.stats()["created_contexts"] == 7
+    solo_cfgs = cfgs + [p.make_config(geometry=p.DISTORTED, vertex_disp=disp, **base),
+                        p.make_config(geometry=p.DISTORTED, vertex_disp=disp_b, **base), cfgs[0]]
+    xs = []
+    for cfg, (b, x, rid) in zip(solo_cfgs, jobs):
+        res = srv.result(rid)
+        assert res["state"] == 2 and res["rel_residual"] <= 1e-8
+        ctx = p.Context(cfg, device="cuda:0")
+        xa = torch.zeros(ctx.num_dofs(), dtype=torch.float64, device="cuda:0")
+        info = ctx.solve(b.cuda(), xa)
+        assert info.iterations == res["iterations"]
+        assert torch.equal(xa.cpu(), x)
+        ctx.close()
+        srv.release(rid)
+        xs.append(x)
+    assert srv.result(jobs[0][2])["code"] == p.PMG_ERR_ARG   # released: unknown id
+    assert not torch.equal(xs[0], xs[1]) and not torch.equal(xs[2], xs[3]) and not torch.equal(xs[5], xs[6])
+    srv.close()
+
+
+def test_release_refuses_a_running_request():
+    srv = p.Server(0, 1)
+    cfg = p.make_config(dim=3, n_cells=8, degree=2)
+    b = serve._rhs(3, 8, 2, 1)
+    x = torch.zeros_like(b).pin_memory()
+    rid = srv.submit(cfg, b, x)
+    with pytest.raises(p.PmgError) as e:
+        srv.release(rid)                                # still queued
+    assert e.value.code == p.PMG_ERR_STATE
+    while srv.result(rid)["state"] < 2:
+        srv.poll()
+    srv.release(rid)
+    srv.close()

@@ -22,8 +22,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def rel(a, b):
-    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+from tests.parity import rel  # noqa: E402  (max of norm-relative and element-wise error)
 
 
 @pytest.mark.parametrize("d,n,k", [(3, 8, 3), (2, 16, 2), (3, 24, 5), (3, 4, 8), (2, 5, 1)])
