@@ -74,6 +74,18 @@ enum pmg_outer {
   PMG_OUTER_GMRES = 1  /* flexible right-preconditioned GMRES(gmres_restart), the paper's outer solver */
 };
 
+/* Layout of the patches of one thread block in shared memory (the smoother's
+ * local solves, §3.2).  Both give bitwise the same results. */
+enum pmg_patch_layout {
+  PMG_PATCH_AUTO = 0,         /* autotuned (or patch-major when patches_per_block > 0) */
+  PMG_PATCH_MAJOR = 1,        /* each patch's vectors contiguous, patches_per_block patches per block */
+  PMG_PATCH_INTERLEAVED = 2   /* Cartesian only: a fixed number of patches per block (16 where shared
+                                 memory allows, fewer at high degree) stored element-major, one patch
+                                 per lane group, for conflict-free shared-memory access; when it is the
+                                 autotuner's choice, levels with fewer patches than one such block per
+                                 SM use the patch-major layout, when the config's, every level uses it */
+};
+
 typedef struct pmg_ctx pmg_ctx;
 
 typedef struct pmg_config {
@@ -89,7 +101,7 @@ typedef struct pmg_config {
                              <= 0 selects 4 / (3 lambda_max(D^-1 A_{j,p})) of the Cartesian patch */
   int local_cycles;    /* N_iter of the local Richardson iteration (Algorithm 2), >= 1 */
   int smooth_steps;    /* pre- and post-smoothing sweeps per level, >= 1 */
-  int patches_per_block; /* 0 = autotuned; else patches per thread block in the smoother */
+  int patches_per_block; /* patch-major layout: patches per thread block in the smoother, 0 = autotuned */
   int local_half;      /* 1: the local solver is the half V-cycle of §3.2.2 (post-smoothing dropped,
                           one fine-level patch vmult instead of two; nonsymmetric, so outer_solver must
                           be PMG_OUTER_GMRES, else PMG_ERR_UNSUPPORTED); 0: full V-cycle */
@@ -103,6 +115,10 @@ typedef struct pmg_config {
                           displacement for the domain to stay the unit square/cube.  pmg_create
                           returns PMG_ERR_ARG if a cell is inverted (det J <= 0 at a quadrature
                           point).  Read by pmg_create only (copied); the caller keeps ownership */
+  int patch_layout;    /* shared-memory layout of the smoother's patch kernel (enum pmg_patch_layout):
+                          PMG_PATCH_AUTO (default) = timed at creation among the admissible layouts and
+                          block shapes; PMG_PATCH_MAJOR or PMG_PATCH_INTERLEAVED to fix the layout */
+  int patch_threads;   /* PMG_PATCH_INTERLEAVED: threads per block (multiple of 32), 0 = autotuned */
 } pmg_config;
 
 typedef struct pmg_solve_info {
@@ -215,13 +231,18 @@ int pmg_synchronize(pmg_ctx* ctx);
  * nodes). */
 int64_t pmg_launch_count(void);
 
-/* Patches per thread block the smoother kernels of this context use: the
- * config's value, or the autotuned one (timed per dimension, degree,
- * precision, geometry, local cycles and smoother on the finest level's
- * patch launches of one sweep; cached for the
- * process and, if the environment variable PMG_TUNE_FILE names a file, in
- * that file). */
+/* Patches per thread block the smoother kernels of this context use on the
+ * finest level: the config's value, or the autotuned one (layout and block
+ * shape timed per dimension, degree, precision, geometry, local cycles,
+ * smoother and finest n on the finest level's patch launches of one sweep;
+ * cached for the process and, if the environment variable PMG_TUNE_FILE
+ * names a file, in that file). */
 int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
+
+/* The patch-kernel layout of a context's finest level (enum
+ * pmg_patch_layout, never AUTO), its patches per block and threads per
+ * block, as chosen by the config or the autotuner. */
+int pmg_patch_layout(const pmg_ctx* ctx, int* layout, int* patches_per_block, int* threads);
 
 /* The damping a context runs with: omega_AS of the additive smoother and the
  * local Jacobi damping omega_J per p-level (omega_jacobi[4], index 0 = the

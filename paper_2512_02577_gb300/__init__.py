@@ -28,6 +28,7 @@ CARTESIAN, DEFORMED, DISTORTED = 0, 1, 2
 FP64, FP32 = 0, 1
 OUTER_CG, OUTER_GMRES = 0, 1
 ADDITIVE, MULTIPLICATIVE = 0, 1
+PATCH_AUTO, PATCH_MAJOR, PATCH_INTERLEAVED = 0, 1, 2
 
 # Every entry point declared in include/pmg.h.
 EXPORTED = [
@@ -37,7 +38,7 @@ EXPORTED = [
     "pmg_launch_count", "pmg_status_string", "pmg_last_error", "pmg_apply_cartesian_noalloc",
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
-    "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release",
+    "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release", "pmg_patch_layout",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -57,6 +58,7 @@ class Config(ctypes.Structure):
         ("smooth_steps", ctypes.c_int), ("patches_per_block", ctypes.c_int),
         ("local_half", ctypes.c_int), ("outer_solver", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("smoother", ctypes.c_int), ("vertex_disp", ctypes.c_void_p),
+        ("patch_layout", ctypes.c_int), ("patch_threads", ctypes.c_int),
     ]
 
 
@@ -112,6 +114,7 @@ def load_library(path=LIB_PATH):
         "pmg_damping": (cint, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_default_damping": (cint, [cint, cint, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_server_release": (cint, [vp, i64]),
+        "pmg_patch_layout": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -130,7 +133,7 @@ def _check(code):
 def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, deform_amp=0.05,
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
                 smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
-                smoother=ADDITIVE, vertex_disp=None):
+                smoother=ADDITIVE, vertex_disp=None, patch_layout=PATCH_AUTO, patch_threads=0):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -146,6 +149,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.outer_solver = (OUTER_GMRES if local_half else OUTER_CG) if outer_solver is None else outer_solver
     c.gmres_restart = gmres_restart
     c.smoother = smoother
+    c.patch_layout, c.patch_threads = patch_layout, patch_threads
     if vertex_disp is not None:
         # ((n+1)^d, d) float64 displacements of the finest mesh's vertices;
         # the config keeps a reference so the array outlives it
@@ -306,6 +310,12 @@ class Context:
         wp, wj = ctypes.c_double(), (ctypes.c_double * 4)()
         _check(_lib.pmg_damping(self.handle, ctypes.byref(wp), wj))
         return wp.value, list(wj)
+
+    def patch_layout(self):
+        """(layout, patches per block, threads per block) of the finest level."""
+        lay, ppc, thr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.pmg_patch_layout(self.handle, ctypes.byref(lay), ctypes.byref(ppc), ctypes.byref(thr)))
+        return lay.value, ppc.value, thr.value
 
     def patches_per_block(self):
         n = ctypes.c_int()

@@ -98,6 +98,37 @@ static cudaError_t patch_cart(int dim, int prec, const void* r, void* dst, int n
   return patch_cart_t<DP, TP>((const TP*)r, (TP*)dst, n, ppc, n_iter, (const TP*)dinv, P, s);
 }
 
+// Interleaved layout: patches per block of this part's interleaved kernel
+// for n_iter local cycles, or 0 when it has none or they do not fit.
+static int patch_il_of(int dim, int prec, int n_iter) {
+  if (!mine(dim, prec)) return 0;
+  constexpr int il = patch_il<DP, TP>();
+  if (il == 0) return 0;
+  const int smem = il * patch_smem(dim, prec, n_iter) + patch_cart_extra_smem(dim, prec);
+  return smem <= kMaxDynSmem ? il : 0;
+}
+
+template <int DIM, typename T>
+static cudaError_t patch_cart_il_t(const T* r, T* dst, int n, int threads, int n_iter, const T* dinv,
+                                   const PatchParamsHost& H, cudaStream_t st) {
+  const int64_t np = patch_count(DIM, n, H.colour);
+  if (np == 0) return cudaSuccess;
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int il = patch_il_of(DIM, prec, n_iter);
+  if (il == 0 || threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
+  const int smem = il * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
+  patch_cart_il_kernel<DIM, T><<<(unsigned)((np + il - 1) / il), threads, smem, st>>>(r, dst, n, n_iter, dinv,
+                                                                                   dinv_len(DIM), to_params<T>(H));
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+static cudaError_t patch_cart_il(int dim, int prec, const void* r, void* dst, int n, int threads, int n_iter,
+                                 const void* dinv, const PatchParamsHost& P, cudaStream_t s) {
+  if (!mine(dim, prec)) return cudaErrorInvalidValue;
+  return patch_cart_il_t<DP, TP>((const TP*)r, (TP*)dst, n, threads, n_iter, (const TP*)dinv, P, s);
+}
+
 // u (+)= the summed patch corrections held in dst (add = 0: u = sum)
 template <int DIM, typename T>
 static cudaError_t patch_gather_t(const T* dst, T* u, int n, int add, cudaStream_t st) {
@@ -188,6 +219,11 @@ static int patch_max_threads(int dim, int prec, int deformed) {
                   : max_threads_of((const void*)patch_cart_kernel<DP, TP>);
 }
 
+static int patch_il_max_threads(int dim, int prec) {
+  if (!mine(dim, prec) || patch_il<DP, TP>() == 0) return 0;
+  return max_threads_of((const void*)patch_cart_il_kernel<DP, TP>);
+}
+
 static cudaError_t prepare() {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -196,6 +232,7 @@ static cudaError_t prepare() {
   cudaError_t r = cudaSuccess;
   auto acc = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
   acc(allow_smem(patch_cart_kernel<DP, TP>, optin));
+  if (patch_il<DP, TP>() > 0) acc(allow_smem(patch_cart_il_kernel<DP, TP>, optin));
   acc(allow_smem(patch_def_kernel<DP, TP>, optin));
   acc(allow_smem(def_cell_kernel<DP, TP>, optin));
   return r;
@@ -223,6 +260,9 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::patch_def_threads,
       PMG_KNS::patch_def_smem,
       PMG_KNS::patch_max_threads,
+      PMG_KNS::patch_il_of,
+      PMG_KNS::patch_cart_il,
+      PMG_KNS::patch_il_max_threads,
   };
   return &t;
 }

@@ -185,22 +185,52 @@ __device__ __forceinline__ int line_base(int L) {
   else return L;
 }
 
-// Shared memory of the patches of one block.
-template <typename T>
+// Shared memory of the patches of one block, in one of two layouts.
+//   IL = 0: patch-major; patch g's elements at base + g * stride (np patches).
+//   IL > 0: element-major, IL patches interleaved; element e of patch g at
+//           base[e * IL + g] (np = IL).  Work items are mapped patch-fastest,
+//           so a warp's lanes hold IL patches at 32 / IL consecutive items.
+//           Every tile of the patch has odd row and plane pitches (2p - 1 is
+//           odd), so consecutive lines start at addresses of alternating
+//           parity: with IL = 16 an FP32 warp access touches 32 distinct
+//           banks and an FP64 one two 128-byte rows -- no bank conflicts,
+//           whatever the line direction (the lanes of the paper's SIMD
+//           vectorisation across cells, here across patches).
+template <typename T, int IL_>
 struct PBlock {
+  using value_type = T;
+  static constexpr int IL = IL_;
   T* base;
   int stride;  // elements per patch
   int np;      // patches in the block
-  __device__ __forceinline__ T* at(int g) const { return base + g * stride; }
+  struct Ref {
+    T* p;
+    __device__ __forceinline__ T& operator[](int e) const { return p[IL ? e * IL : e]; }
+  };
+  __device__ __forceinline__ Ref at(int g) const { return Ref{IL ? base + g : base + g * stride}; }
 };
 
 // for every (g, i), g < np, i < COUNT, spread over the block's threads
 template <int COUNT, class F>
-__device__ __forceinline__ void pfor(int np, F&& f) {
+__device__ __forceinline__ void pfor_n(int np, F&& f) {
   const int total = np * COUNT;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int g = t / COUNT;
     f(g, t - g * COUNT);
+  }
+}
+
+// the same over the patches of a PBlock, in its layout's item order
+template <int COUNT, class PB, class F>
+__device__ __forceinline__ void pfor(const PB& pb, F&& f) {
+  if constexpr (PB::IL == 0) {
+    pfor_n<COUNT>(pb.np, f);
+  } else {
+    constexpr int total = PB::IL * COUNT;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int i = t / PB::IL;
+      f(t - i * PB::IL, i);
+    }
   }
 }
 
@@ -238,8 +268,8 @@ struct CartGeo {
 
   // out = r - A_l d for every patch of the block (offsets within a patch;
   // out may be t0 = offset 0; d and r distinct from t0, t1)
-  template <int l>
-  __device__ __forceinline__ void resid(const PBlock<T>& pb, int od, int orr, int oo) const {
+  template <int l, class PB>
+  __device__ __forceinline__ void resid(const PB& pb, int od, int orr, int oo) const {
     constexpr int p = plev(K, l);
     constexpr int m = mp(p);
     constexpr int SZT = PatchShape<DIM>::SZT;
@@ -247,8 +277,8 @@ struct CartGeo {
     const T* KP = coef<T>() + LAY.KP[l];
     const T s = scale;
     if constexpr (DIM == 3) {
-      pfor<m * m>(pb.np, [&](int g, int L) {
-        T* sm = pb.at(g);
+      pfor<m * m>(pb, [&](int g, int L) {
+        auto sm = pb.at(g);
         const int b = line_base<0, m, m, m>(L);
         T x[m], y0[m], y1[m];
 #pragma unroll
@@ -259,8 +289,8 @@ struct CartGeo {
         for (int i = 0; i < m; ++i) { sm[b + i] = y0[i]; sm[SZT + b + i] = y1[i]; }
       });
       __syncthreads();
-      pfor<m * m>(pb.np, [&](int g, int L) {
-        T* sm = pb.at(g);
+      pfor<m * m>(pb, [&](int g, int L) {
+        auto sm = pb.at(g);
         const int b = line_base<1, m, m, m>(L);
         T a[m], c[m], y0[m], y1[m], y2[m];
 #pragma unroll
@@ -272,8 +302,8 @@ struct CartGeo {
         for (int i = 0; i < m; ++i) { sm[b + i * m] = y0[i]; sm[SZT + b + i * m] = y1[i] + y2[i]; }
       });
       __syncthreads();
-      pfor<m * m>(pb.np, [&](int g, int L) {
-        T* sm = pb.at(g);
+      pfor<m * m>(pb, [&](int g, int L) {
+        auto sm = pb.at(g);
         const int b = line_base<2, m, m, m>(L);
         T a[m], c[m], y1[m], y2[m];
 #pragma unroll
@@ -285,8 +315,8 @@ struct CartGeo {
       });
       __syncthreads();
     } else {
-      pfor<m>(pb.np, [&](int g, int L) {
-        T* sm = pb.at(g);
+      pfor<m>(pb, [&](int g, int L) {
+        auto sm = pb.at(g);
         const int b = line_base<0, m, m, 1>(L);
         T x[m], y0[m], y1[m];
 #pragma unroll
@@ -297,8 +327,8 @@ struct CartGeo {
         for (int i = 0; i < m; ++i) { sm[b + i] = y0[i]; sm[SZT + b + i] = y1[i]; }
       });
       __syncthreads();
-      pfor<m>(pb.np, [&](int g, int L) {
-        T* sm = pb.at(g);
+      pfor<m>(pb, [&](int g, int L) {
+        auto sm = pb.at(g);
         const int b = line_base<1, m, m, 1>(L);
         T a[m], c[m], y1[m], y2[m];
 #pragma unroll
@@ -315,16 +345,17 @@ struct CartGeo {
 
 // Restriction: level l-1 residual at `dst` = T_l^T (level-l vector in t0),
 // using t1 (and t0 again in 3D) as intermediates.
-template <int DIM, int l, typename T>
-__device__ __forceinline__ void restrict_p(const PBlock<T>& pb, int dst) {
+template <int DIM, int l, class PB>
+__device__ __forceinline__ void restrict_p(const PB& pb, int dst) {
+  using T = typename PB::value_type;
   constexpr int pf = plev(K, l), pc = plev(K, l - 1);
   constexpr int m = mp(pf), mc = mp(pc);
   constexpr int SZT = PatchShape<DIM>::SZT;
   constexpr int EZ = DIM == 3 ? m : 1;
   const T* Tr = coef<T>() + LAY.Tr[l];  // m x mc, row-major
   // x: (m, m, EZ) in t0 -> (mc, m, EZ) in t1
-  pfor<m * EZ>(pb.np, [&](int g, int L) {
-    T* sm = pb.at(g);
+  pfor<m * EZ>(pb, [&](int g, int L) {
+    auto sm = pb.at(g);
     const int bi = line_base<0, m, m, EZ>(L), bo = line_base<0, mc, m, EZ>(L);
     T x[m];
 #pragma unroll
@@ -341,8 +372,8 @@ __device__ __forceinline__ void restrict_p(const PBlock<T>& pb, int dst) {
   __syncthreads();
   // y: (mc, m, EZ) in t1 -> (mc, mc, EZ) in t0 (2D: directly into dst)
   const int ydst = DIM == 3 ? 0 : dst;
-  pfor<mc * EZ>(pb.np, [&](int g, int L) {
-    T* sm = pb.at(g);
+  pfor<mc * EZ>(pb, [&](int g, int L) {
+    auto sm = pb.at(g);
     const int bi = line_base<1, mc, m, EZ>(L), bo = line_base<1, mc, mc, EZ>(L);
     T x[m];
 #pragma unroll
@@ -358,8 +389,8 @@ __device__ __forceinline__ void restrict_p(const PBlock<T>& pb, int dst) {
   });
   __syncthreads();
   if constexpr (DIM == 3) {
-    pfor<mc * mc>(pb.np, [&](int g, int L) {
-      T* sm = pb.at(g);
+    pfor<mc * mc>(pb, [&](int g, int L) {
+      auto sm = pb.at(g);
       const int bi = line_base<2, mc, mc, m>(L), bo = line_base<2, mc, mc, mc>(L);
       T x[m];
 #pragma unroll
@@ -379,16 +410,17 @@ __device__ __forceinline__ void restrict_p(const PBlock<T>& pb, int dst) {
 
 // Prolongation: level-l vector at `dst` += T_l (level l-1 vector at `src`),
 // using t0, t1.
-template <int DIM, int l, typename T>
-__device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst) {
+template <int DIM, int l, class PB>
+__device__ __forceinline__ void prolong_p(const PB& pb, int src, int dst) {
+  using T = typename PB::value_type;
   constexpr int pf = plev(K, l), pc = plev(K, l - 1);
   constexpr int m = mp(pf), mc = mp(pc);
   constexpr int SZT = PatchShape<DIM>::SZT;
   constexpr int EZC = DIM == 3 ? mc : 1;
   const T* Tr = coef<T>() + LAY.Tr[l];
   // x: (mc, mc, EZC) -> (m, mc, EZC) in t0
-  pfor<mc * EZC>(pb.np, [&](int g, int L) {
-    T* sm = pb.at(g);
+  pfor<mc * EZC>(pb, [&](int g, int L) {
+    auto sm = pb.at(g);
     const int bi = line_base<0, mc, mc, EZC>(L), bo = line_base<0, m, mc, EZC>(L);
     T x[mc];
 #pragma unroll
@@ -405,8 +437,8 @@ __device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst)
   __syncthreads();
   if constexpr (DIM == 3) {
     // y: (m, mc, mc) in t0 -> (m, m, mc) in t1
-    pfor<m * mc>(pb.np, [&](int g, int L) {
-      T* sm = pb.at(g);
+    pfor<m * mc>(pb, [&](int g, int L) {
+      auto sm = pb.at(g);
       const int bi = line_base<1, m, mc, mc>(L), bo = line_base<1, m, m, mc>(L);
       T x[mc];
 #pragma unroll
@@ -422,8 +454,8 @@ __device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst)
     });
     __syncthreads();
     // z: (m, m, mc) in t1 -> (m, m, m) added into dst
-    pfor<m * m>(pb.np, [&](int g, int L) {
-      T* sm = pb.at(g);
+    pfor<m * m>(pb, [&](int g, int L) {
+      auto sm = pb.at(g);
       const int bi = line_base<2, m, m, mc>(L), bo = line_base<2, m, m, m>(L);
       T x[mc];
 #pragma unroll
@@ -440,8 +472,8 @@ __device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst)
     __syncthreads();
   } else {
     // y: (m, mc) in t0 -> (m, m) added into dst
-    pfor<m>(pb.np, [&](int g, int L) {
-      T* sm = pb.at(g);
+    pfor<m>(pb, [&](int g, int L) {
+      auto sm = pb.at(g);
       const int bi = line_base<1, m, mc, 1>(L), bo = line_base<1, m, m, 1>(L);
       T x[mc];
 #pragma unroll
@@ -463,12 +495,13 @@ __device__ __forceinline__ void prolong_p(const PBlock<T>& pb, int src, int dst)
 // block, results in d_l; level 0 (p = 1) is the exact 1x1 solve (§3.2).
 // Full V-cycle, or with P.half the half V-cycle of §3.2.2 (pre-smoothing,
 // coarse correction, no post-smoothing).
-template <int DIM, int l, typename T, class Geo>
-__device__ void pvcycle(const PBlock<T>& pb, const Geo& geo, const PatchParams<T>& P) {
+template <int DIM, int l, class PB, class Geo>
+__device__ void pvcycle(const PB& pb, const Geo& geo, const PatchParams<typename PB::value_type>& P) {
+  using T = typename PB::value_type;
   using S = PatchShape<DIM>;
   if constexpr (l == 0) {
-    pfor<1>(pb.np, [&](int g, int) {
-      T* sm = pb.at(g);
+    pfor<1>(pb, [&](int g, int) {
+      auto sm = pb.at(g);
       sm[S::off_d(0)] = sm[S::off_r(0)] * geo.a0inv(g);
     });
     __syncthreads();
@@ -476,19 +509,19 @@ __device__ void pvcycle(const PBlock<T>& pb, const Geo& geo, const PatchParams<T
     constexpr int SZ = S::SZ(l);
     constexpr int R = S::off_r(l), D = S::off_d(l);
     const T om = P.omega[l];
-    pfor<SZ>(pb.np, [&](int g, int i) {  // pre-smoothing (zero initial guess)
-      T* sm = pb.at(g);
+    pfor<SZ>(pb, [&](int g, int i) {  // pre-smoothing (zero initial guess)
+      auto sm = pb.at(g);
       sm[D + i] = om * geo.dinv_at(g, l, i) * sm[R + i];
     });
     __syncthreads();
     geo.template resid<l>(pb, D, R, 0);                   // residual into t0
     restrict_p<DIM, l>(pb, S::off_r(l - 1));               // restrict
-    pvcycle<DIM, l - 1, T>(pb, geo, P);                    // recurse
+    pvcycle<DIM, l - 1>(pb, geo, P);                    // recurse
     prolong_p<DIM, l>(pb, S::off_d(l - 1), D);             // prolongate, add
     if (P.half) return;  // half V-cycle (§3.2.2): no post-smoothing (uniform per block)
     geo.template resid<l>(pb, D, R, 0);                   // residual
-    pfor<SZ>(pb.np, [&](int g, int i) {  // post-smoothing
-      T* sm = pb.at(g);
+    pfor<SZ>(pb, [&](int g, int i) {  // post-smoothing
+      auto sm = pb.at(g);
       sm[D + i] += om * geo.dinv_at(g, l, i) * sm[i];
     });
     __syncthreads();
@@ -497,29 +530,30 @@ __device__ void pvcycle(const PBlock<T>& pb, const Geo& geo, const PatchParams<T
 
 // Algorithm 2 around Algorithm 3 for every patch of the block: the top-level
 // residual in r_top on entry, the correction in d_top on exit.
-template <int DIM, typename T, class Geo>
-__device__ __forceinline__ void local_solve(const PBlock<T>& pb, const Geo& geo, const PatchParams<T>& P,
-                                            int n_iter, int extra) {
+template <int DIM, class PB, class Geo>
+__device__ __forceinline__ void local_solve(const PB& pb, const Geo& geo,
+                                            const PatchParams<typename PB::value_type>& P, int n_iter, int extra) {
+  using T = typename PB::value_type;
   using S = PatchShape<DIM>;
   constexpr int L = S::L, SZT = S::SZT;
   constexpr int RT = S::off_r(L - 1), DT = S::off_d(L - 1);
   if (n_iter <= 1) {
-    pvcycle<DIM, L - 1, T>(pb, geo, P);
+    pvcycle<DIM, L - 1>(pb, geo, P);
     return;
   }
   const int RJ = extra, DS = extra + SZT;  // keep r_j and the running correction
-  pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[RJ + i] = sm[RT + i]; });
+  pfor<SZT>(pb, [&](int g, int i) { auto sm = pb.at(g); sm[RJ + i] = sm[RT + i]; });
   __syncthreads();
-  pvcycle<DIM, L - 1, T>(pb, geo, P);
-  pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[DS + i] = sm[DT + i]; });
+  pvcycle<DIM, L - 1>(pb, geo, P);
+  pfor<SZT>(pb, [&](int g, int i) { auto sm = pb.at(g); sm[DS + i] = sm[DT + i]; });
   __syncthreads();
   for (int it = 1; it < n_iter; ++it) {
     geo.template resid<L - 1>(pb, DS, RJ, RT);
-    pvcycle<DIM, L - 1, T>(pb, geo, P);
-    pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[DS + i] += sm[DT + i]; });
+    pvcycle<DIM, L - 1>(pb, geo, P);
+    pfor<SZT>(pb, [&](int g, int i) { auto sm = pb.at(g); sm[DS + i] += sm[DT + i]; });
     __syncthreads();
   }
-  pfor<SZT>(pb.np, [&](int g, int i) { T* sm = pb.at(g); sm[DT + i] = sm[DS + i]; });
+  pfor<SZT>(pb, [&](int g, int i) { auto sm = pb.at(g); sm[DT + i] = sm[DS + i]; });
   __syncthreads();
 }
 
@@ -590,36 +624,80 @@ constexpr int kPatchMaxThreads = 256;
 constexpr int kPatchMaxThreads = 1024;
 #endif
 
+// Interleave width of this part's interleaved patch kernel: the largest
+// power of two up to 16 whose block of patches (one local V-cycle each,
+// N_iter = 1) fits the shared memory a block may request, or 0 (no
+// interleaved kernel; 3D FP64 k = 8).
 template <int DIM, typename T>
-__global__ void PMG_PATCH_BOUNDS
-    patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
-                      const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
+constexpr int patch_il() {
+  constexpr int per_patch = PatchShape<DIM>::ELEMS * (int)sizeof(T);
+  int il = 16;
+  while (il > 1 && il * per_patch > kMaxDynSmem - 8 * 1024) il /= 2;
+  return il > 1 ? il : 0;
+}
+
+// Body of the Cartesian patch kernels: gather r_j, Algorithm 2/3, write
+// omega_AS d_j (additive), or add d_j to u for the patches of one colour
+// (multiplicative).  IL: layout of the block's patches (PBlock).
+template <int DIM, typename T, int IL>
+__device__ __forceinline__ void patch_cart_body(const T* __restrict__ r, T* __restrict__ dst, int n, int np,
+                                                int n_iter, const T* __restrict__ dinv, int dinv_len,
+                                                const PatchParams<T>& P) {
   using S = PatchShape<DIM>;
   constexpr int SZT = S::SZT;
   constexpr int RT = S::off_r(S::L - 1), DT = S::off_d(S::L - 1);
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ PatchMeta meta[kMaxPatchesPerBlock];
   const int stride = S::ELEMS + (n_iter > 1 ? 2 * SZT : 0);
-  const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
+  const PBlock<T, IL> pb{reinterpret_cast<T*>(smraw), stride, np};
   T* sdinv = reinterpret_cast<T*>(smraw) + np * stride;  // inverse-diagonal tables of all p-levels
   for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
   patch_meta_init<DIM>(meta, np, n, P.colour);
   __syncthreads();
   const int N1 = K * n + 1;
-  pfor<SZT>(np, [&](int g, int i) {  // gather r_j = Pi_j r
+  pfor<SZT>(pb, [&](int g, int i) {  // gather r_j = Pi_j r
     const PatchMeta& m = meta[g];
     pb.at(g)[RT + i] = m.active ? r[patch_node<DIM>(m, i, N1)] : T(0);
   });
   __syncthreads();
   const CartGeo<DIM, T> geo{sdinv, P.scale, P.inv_scale, P.inv_a0};
-  local_solve<DIM, T>(pb, geo, P, n_iter, S::ELEMS);
+  local_solve<DIM>(pb, geo, P, n_iter, S::ELEMS);
   const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
-  pfor<SZT>(np, [&](int g, int i) {
+  pfor<SZT>(pb, [&](int g, int i) {
     const PatchMeta& m = meta[g];
     if (!m.active) return;
     if (P.colour < 0) dst[patch_colour<DIM>(m) * N + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];
     else dst[patch_node<DIM>(m, i, N1)] += pb.at(g)[DT + i];  // one patch of the colour per node
   });
+}
+
+// Patch-major layout, np patches per block.  FP64, degrees up to 4: at most
+// 256 threads per block and three blocks per SM (registers <= 85), so that
+// 24 warps keep the FP64 pipe fed.  Higher degrees need more registers per
+// line than that without spilling, and the FP32 kernels (40 registers) run
+// fastest with the compiler's own choice and larger blocks (measured:
+// bounding k = 7 to 256 threads made its FP32 launch 40% slower, k = 4 FP32
+// 3% slower).
+template <int DIM, typename T>
+__global__ void PMG_PATCH_BOUNDS
+    patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
+                      const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
+  patch_cart_body<DIM, T, 0>(r, dst, n, np, n_iter, dinv, dinv_len, P);
+}
+
+// Interleaved layout, patch_il() patches per block (np = IL): conflict-free
+// shared-memory accesses; the thread count is the autotuner's choice.
+#if PMG_PREC == 0
+#define PMG_PATCH_IL_BOUNDS __launch_bounds__(768, 1)
+#else
+#define PMG_PATCH_IL_BOUNDS
+#endif
+template <int DIM, typename T>
+__global__ void PMG_PATCH_IL_BOUNDS
+    patch_cart_il_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int n_iter,
+                         const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
+  constexpr int IL = patch_il<DIM, T>() > 0 ? patch_il<DIM, T>() : 1;
+  patch_cart_body<DIM, T, IL>(r, dst, n, IL, n_iter, dinv, dinv_len, P);
 }
 
 // u (+)= sum over the patches whose interior holds the node of their

@@ -39,7 +39,7 @@ __device__ __forceinline__ void tiles_axis(const T* C, int ng, const Tile& tile,
   constexpr int EZ = DIM == 3 ? n : 1;
   constexpr int nl = n * EZ;
   constexpr int st = AX == 0 ? 1 : (AX == 1 ? n : n * n);
-  pfor<NC * nl>(ng, [&](int g, int t) {
+  pfor_n<NC * nl>(ng, [&](int g, int t) {
     const int c = t / nl, L = t - c * nl;
     T* A = tile(g, c);
     const int b = line_base<AX, n, n, EZ>(L);
@@ -77,7 +77,7 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
     tiles_axis<3, n1, NC, 1, false, false>(Dm, ng, tile, A1, B1);
     tiles_axis<3, n1, NC, 2, false, false>(Dm, ng, tile, A1, B2);
     __syncthreads();
-    pfor<NC * NP>(ng, [&](int g, int t) {
+    pfor_n<NC * NP>(ng, [&](int g, int t) {
       const int c = t / NP, q = t - c * NP;
       T* A = tile(g, c);
       const float* Gc = gptr(g, c);
@@ -109,7 +109,7 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
     tiles_axis<2, n1, NC, 0, false, false>(Dm, ng, tile, A0, B0);
     tiles_axis<2, n1, NC, 1, false, false>(Dm, ng, tile, A0, B1);
     __syncthreads();
-    pfor<NC * NP>(ng, [&](int g, int t) {
+    pfor_n<NC * NP>(ng, [&](int g, int t) {
       const int c = t / NP, q = t - c * NP;
       T* A = tile(g, c);
       const float* Gc = gptr(g, c);
@@ -127,7 +127,7 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
     __syncthreads();
     tiles_axis<2, n1, NC, 0, true, false>(Sm, ng, tile, A0, A1);
     __syncthreads();
-    pfor<NC * NP>(ng, [&](int g, int t) {
+    pfor_n<NC * NP>(ng, [&](int g, int t) {
       const int c = t / NP, q = t - c * NP;
       T* A = tile(g, c);
       A[A0 + q] = A[A1 + q];
@@ -162,7 +162,7 @@ __global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ cellout
   __syncthreads();
   const int N1 = K * n + 1;
   auto tile = [&](int g, int) { return base + g * 5 * NP; };
-  pfor<NP>(cpb, [&](int g, int i) {
+  pfor_n<NP>(cpb, [&](int g, int i) {
     const int ax = i % n1, ay = (i / n1) % n1, az = DIM == 3 ? i / (n1 * n1) : 0;
     const int gx = K * cell_of[g][0] + ax, gy = K * cell_of[g][1] + ay, gz = K * cell_of[g][2] + az;
     const bool bnd = gx == 0 || gx == N1 - 1 || gy == 0 || gy == N1 - 1 || (DIM == 3 && (gz == 0 || gz == N1 - 1));
@@ -174,7 +174,7 @@ __global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ cellout
     return G + cell * ncomp<DIM>() * NP;
   };
   cell_op<DIM, l, 1, T>(cpb, tile, gptr);
-  pfor<NP>(cpb, [&](int g, int i) {
+  pfor_n<NP>(cpb, [&](int g, int i) {
     if (cell_of[g][3]) cellout[((int64_t)blockIdx.x * cpb + g) * NP + i] = tile(g, 0)[i];
   });
 }
@@ -285,7 +285,7 @@ struct DefLevelT {
 // lines of a warp on a few banks (x lines 2(p+1) apart, y lines
 // 4(p+1)^2 apart).
 template <int DIM, int p, int AX, int OP, bool ACC, int EX, int EY, int EZ, typename T>
-__device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBlock<T>& pb, int src, int dst) {
+__device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBlock<T, 0>& pb, int src, int dst) {
   constexpr int nq = p + 1, mf = 2 * p + 1, Q = 2 * nq;
   constexpr int NI = (OP == 0) ? mf : (OP == 1 ? Q : Q);
   constexpr int NO = (OP == 0) ? Q : (OP == 1 ? mf : Q);
@@ -296,8 +296,8 @@ __device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBloc
   constexpr int SI = AX == 0 ? 1 : (AX == 1 ? RXI : RYI);
   constexpr int SO = AX == 0 ? 1 : (AX == 1 ? RXO : RYO);
   constexpr int NL = IX * IY * IZ / NI;
-  pfor<NL>(pb.np, [&](int g, int L) {
-    T* sm = pb.at(g);
+  pfor<NL>(pb, [&](int g, int L) {
+    auto sm = pb.at(g);
     int bi, bo;
     if constexpr (AX == 0) {  // line (y, z)
       const int y = L % IY, z = L / IY;
@@ -366,8 +366,8 @@ struct DefGeo {
   }
   __device__ __forceinline__ T a0inv(int g) const { return inv_a0[g]; }
 
-  template <int l>
-  __device__ __forceinline__ void resid(const PBlock<T>& pb, int od, int orr, int oo) const {
+  template <int l, class PB>
+  __device__ __forceinline__ void resid(const PB& pb, int od, int orr, int oo) const {
     constexpr int p = plev(K, l);
     constexpr int m = mp(p), mf = 2 * p + 1, nq = p + 1, Q = 2 * nq;
     constexpr int NPc = ipow(nq, DIM);  // points per cell
@@ -378,8 +378,8 @@ struct DefGeo {
     const T* Dm = coef<T>() + LAY.Dq[l];
     constexpr int MZ = DIM == 3 ? mf : 1, QZ = DIM == 3 ? Q : 1;
     // expand d onto the patch grid (zero on its boundary) in B0: (mf, mf, MZ)
-    pfor<ipow(mf, DIM)>(pb.np, [&](int g, int i) {
-      T* sm = pb.at(g);
+    pfor<ipow(mf, DIM)>(pb, [&](int g, int i) {
+      auto sm = pb.at(g);
       const int fx = i % mf, fy = (i / mf) % mf, fz = DIM == 3 ? i / (mf * mf) : 1;
       const bool in = fx > 0 && fx < mf - 1 && fy > 0 && fy < mf - 1 && (DIM == 2 || (fz > 0 && fz < mf - 1));
       sm[B0 + i] = in ? sm[od + (fx - 1) + m * ((fy - 1) + m * (DIM == 3 ? fz - 1 : 0))] : T(0);
@@ -402,8 +402,8 @@ struct DefGeo {
     __syncthreads();
     // q-op with the stored G_q of the cell holding each point; points visited
     // cell by cell so that G_q reads are contiguous
-    pfor<(1 << DIM) * NPc>(pb.np, [&](int g, int t) {
-      T* sm = pb.at(g);
+    pfor<(1 << DIM) * NPc>(pb, [&](int g, int t) {
+      auto sm = pb.at(g);
       const int c = t / NPc, pt = t - c * NPc;
       const int px = pt % nq, py = (pt / nq) % nq, pz = DIM == 3 ? pt / (nq * nq) : 0;
       const int qx = (c & 1) * nq + px, qy = ((c >> 1) & 1) * nq + py;
@@ -449,8 +449,8 @@ struct DefGeo {
       __syncthreads();
     }
     constexpr int R = DIM == 3 ? B0 : B1;
-    pfor<ipow(m, DIM)>(pb.np, [&](int g, int i) {
-      T* sm = pb.at(g);
+    pfor<ipow(m, DIM)>(pb, [&](int g, int i) {
+      auto sm = pb.at(g);
       const int fx = i % m + 1, fy = (i / m) % m + 1, fz = DIM == 3 ? i / (m * m) + 1 : 0;
       sm[oo + i] = sm[orr + i] - sm[R + fx + mf * (fy + mf * fz)];
     });
@@ -470,7 +470,7 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
   __shared__ T inv_a0[kMaxPatchesPerBlock];
   constexpr int EL = DS::template elems<T>();
   const int stride = EL + (n_iter > 1 ? 2 * SZT : 0);
-  const PBlock<T> pb{reinterpret_cast<T*>(smraw), stride, np};
+  const PBlock<T, 0> pb{reinterpret_cast<T*>(smraw), stride, np};
   patch_meta_init<DIM>(meta, np, n, P.colour);
   __syncthreads();
   for (int g = threadIdx.x; g < np; g += blockDim.x) {  // p = 1: the vertex's inverse Q1 diagonal
@@ -478,7 +478,7 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
     inv_a0[g] = dinv1[v[0] + (int64_t)(n + 1) * (v[1] + (int64_t)(n + 1) * v[2])];
   }
   const int N1 = K * n + 1;
-  pfor<SZT>(np, [&](int g, int i) {
+  pfor<SZT>(pb, [&](int g, int i) {
     const PatchMeta& m = meta[g];
     pb.at(g)[RT + i] = m.active ? r[patch_node<DIM>(m, i, N1)] : T(0);
   });
@@ -488,9 +488,9 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
   geo.meta = meta;
   geo.inv_a0 = inv_a0;
   geo.n = n;
-  local_solve<DIM, T>(pb, geo, P, n_iter, EL);
+  local_solve<DIM>(pb, geo, P, n_iter, EL);
   const int64_t NN = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
-  pfor<SZT>(np, [&](int g, int i) {
+  pfor<SZT>(pb, [&](int g, int i) {
     const PatchMeta& m = meta[g];
     if (!m.active) return;
     if (P.colour < 0) dst[patch_colour<DIM>(m) * NN + patch_node<DIM>(m, i, N1)] = P.omega_as * pb.at(g)[DT + i];

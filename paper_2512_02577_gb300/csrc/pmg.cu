@@ -78,6 +78,7 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 constexpr int kMaxCoarse = 4096;
+constexpr int kNumSMs = 152;  // GB300
 constexpr int64_t kAlign = 256;
 
 enum Scal { S_RZ = 0, S_PAP = 1, S_RR = 2, S_RZN = 3, S_BB = 4, S_TMP = 5, S_COUNT = 16 };
@@ -147,6 +148,11 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_ARG, "gmres_restart must be in 1..64");
   if (cfg->smoother != PMG_SMOOTHER_ADDITIVE && cfg->smoother != PMG_SMOOTHER_MULTIPLICATIVE)
     return fail(PMG_ERR_ARG, "unknown smoother");
+  if (cfg->patch_layout != PMG_PATCH_AUTO && cfg->patch_layout != PMG_PATCH_MAJOR &&
+      cfg->patch_layout != PMG_PATCH_INTERLEAVED)
+    return fail(PMG_ERR_ARG, "unknown patch_layout");
+  if (cfg->patches_per_block < 0 || cfg->patch_threads < 0)
+    return fail(PMG_ERR_ARG, "patches_per_block, patch_threads >= 0");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
     return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
@@ -284,7 +290,8 @@ struct pmg_ctx {
   void* pbuf = nullptr;
   void* cellbuf = nullptr;
   double* verts = nullptr;  // distorted geometry: finest-mesh vertex positions
-  int ppc = 1;
+  int ppc = 1;          // patch-major layout: patches per block
+  int il_threads = 0;   // > 0: interleaved layout (Cartesian), threads per block
   double omega_as = 0;
   double omega_j[4] = {1, 1, 1, 1};
   cudaGraphExec_t vgraph = nullptr;
@@ -348,6 +355,17 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   return PMG_OK;
 }
 
+// The interleaved layout puts IL patches in one block: on levels with fewer
+// than one such block per SM it would leave SMs idle, so when it was chosen
+// by the autotuner those levels (the coarse ones) keep the patch-major
+// layout with its smaller blocks.
+bool use_interleaved(const pmg_ctx* c, int level, int colour) {
+  if (c->il_threads <= 0) return false;
+  if (c->cfg.patch_layout == PMG_PATCH_INTERLEAVED) return true;  // the caller's choice: every level
+  const int il = c->km()->patch_il(c->dim, c->mgprec, c->cfg.local_cycles);
+  return patch_count(c->dim, c->lv[level].n, colour) >= (int64_t)kNumSMs * il;
+}
+
 // Local solves of every patch of the level for the residual r, written to
 // the patch buffer as omega_AS d_j (one launch).
 int patch_solves(pmg_ctx* c, int level, const void* r, int colour = -1, void* u = nullptr) {
@@ -364,6 +382,9 @@ int patch_solves(pmg_ctx* c, int level, const void* r, int colour = -1, void* u 
     }
     D.dinv1 = L.dinv1;
     e = c->km()->patch_def(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
+  } else if (use_interleaved(c, level, colour)) {
+    e = c->km()->patch_cart_il(c->dim, c->mgprec, r, dst, L.n, c->il_threads, c->cfg.local_cycles, c->dtab_mg, P,
+                               c->stream);
   } else {
     e = c->km()->patch_cart(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P, c->stream);
   }
@@ -537,25 +558,31 @@ int precondition(pmg_ctx* c, const double* r, double* z) {
 }
 
 // ---------------------------------------------------------------- autotuner
-// Patches per thread block of the smoother kernels, per (dim, degree, MG
-// precision, geometry, local cycles, smoother): every admissible value is
-// timed on the patch launches of one finest-level sweep -- the one launch
-// over all patches (additive) or the 2^d colour launches (multiplicative,
-// each over an eighth of the patches in 3D, where the last wave matters) --
-// with CUDA events, best of 3 after a warm-up, and the fastest is kept for
-// the process; with PMG_TUNE_FILE set, results are also read from and
-// appended to that file ("dim k prec geom cycles smoother ppc" per line).
-// Small meshes, whose launches are too short to time, use the rule "about
-// 256 threads per block" without caching it.
+// Shared-memory layout and block shape of the smoother's patch kernel, per
+// (dim, degree, MG precision, geometry, local cycles, smoother, finest n):
+// the patch-major layout with 1..64 patches per block, and (Cartesian) the
+// interleaved layout with 128..1024 threads per block.  Every admissible
+// candidate is timed on the patch launches of one finest-level sweep -- the
+// one launch over all patches (additive) or the 2^d colour launches
+// (multiplicative, each over an eighth of the patches in 3D, where the last
+// wave matters) -- with CUDA events, best of 3 after a warm-up, and the
+// fastest is kept for the process; with PMG_TUNE_FILE set, results are also
+// read from and appended to that file ("dim k prec geom cycles smoother n
+// layout ppc threads" per line).  Small meshes, whose launches are too short
+// to time, use a rule (interleaved with 256 threads where available, else
+// about 256 threads of patch-major patches) without caching it.
 struct TuneKey {
-  int dim, K, prec, geom, cycles, smoother;
+  int dim, K, prec, geom, cycles, smoother, n;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dim, K, prec, geom, cycles, smoother) <
-           std::tie(o.dim, o.K, o.prec, o.geom, o.cycles, o.smoother);
+    return std::tie(dim, K, prec, geom, cycles, smoother, n) <
+           std::tie(o.dim, o.K, o.prec, o.geom, o.cycles, o.smoother, o.n);
   }
 };
+struct TuneVal {
+  int layout, ppc, threads;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;
+std::map<TuneKey, TuneVal> g_tune;
 bool g_tune_file_read = false;
 
 void tune_file_read_locked() {
@@ -565,18 +592,24 @@ void tune_file_read_locked() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int d, k, pr, ge, cy, sm, ppc;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d", &d, &k, &pr, &ge, &cy, &sm, &ppc) == 7)
-    g_tune[{d, k, pr, ge, cy, sm}] = ppc;
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    TuneKey k{};
+    TuneVal v{};
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &k.dim, &k.K, &k.prec, &k.geom, &k.cycles, &k.smoother,
+                    &k.n, &v.layout, &v.ppc, &v.threads) == 10)
+      g_tune[k] = v;
+  }
   std::fclose(f);
 }
 
-void tune_file_append_locked(const TuneKey& key, int ppc) {
+void tune_file_append_locked(const TuneKey& k, const TuneVal& v) {
   const char* path = std::getenv("PMG_TUNE_FILE");
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %d %d\n", key.dim, key.K, key.prec, key.geom, key.cycles, key.smoother, ppc);
+  std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", k.dim, k.K, k.prec, k.geom, k.cycles, k.smoother, k.n, v.layout,
+               v.ppc, v.threads);
   std::fclose(f);
 }
 
@@ -590,6 +623,12 @@ int admissible_ppc(const pmg_ctx* c, int ppc) {
          ppc * smem + extra <= kMaxDynSmem;
 }
 
+// the interleaved layout exists for this context and admits `threads`
+int admissible_il(const pmg_ctx* c, int threads) {
+  if (c->deformed || c->km()->patch_il(c->dim, c->mgprec, c->cfg.local_cycles) == 0) return 0;
+  return threads >= 32 && threads % 32 == 0 && threads <= c->km()->patch_il_max_threads(c->dim, c->mgprec);
+}
+
 int rule_ppc(const pmg_ctx* c) {
   const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
   int ppc = std::max(1, 256 / tpp);
@@ -597,29 +636,64 @@ int rule_ppc(const pmg_ctx* c) {
   return ppc;
 }
 
-int choose_patches_per_block(pmg_ctx* c) {
+void set_layout(pmg_ctx* c, const TuneVal& v) {
+  c->ppc = v.ppc;
+  c->il_threads = v.layout == PMG_PATCH_INTERLEAVED ? v.threads : 0;
+}
+
+int choose_patch_layout(pmg_ctx* c) {
   const pmg_config& cf = c->cfg;
   if (!admissible_ppc(c, 1)) return fail(PMG_ERR_UNSUPPORTED, "patch does not fit in shared memory for this degree");
-  if (cf.patches_per_block > 0) {
+  int layout = cf.patch_layout;
+  if (layout == PMG_PATCH_AUTO && cf.patches_per_block > 0) layout = PMG_PATCH_MAJOR;
+  if (layout == PMG_PATCH_INTERLEAVED && !admissible_il(c, 32))
+    return fail(PMG_ERR_UNSUPPORTED, "no interleaved patch layout for this configuration (deformed geometry, or "
+                                     "the interleaved patches do not fit in shared memory)");
+  c->ppc = rule_ppc(c);
+  c->il_threads = 0;
+  if (layout == PMG_PATCH_MAJOR && cf.patches_per_block > 0) {
     if (!admissible_ppc(c, cf.patches_per_block)) return fail(PMG_ERR_ARG, "patches_per_block not admissible");
     c->ppc = cf.patches_per_block;
     return PMG_OK;
   }
-  c->ppc = rule_ppc(c);
+  if (layout == PMG_PATCH_INTERLEAVED && cf.patch_threads > 0) {
+    if (!admissible_il(c, cf.patch_threads)) return fail(PMG_ERR_ARG, "patch_threads not admissible");
+    c->il_threads = cf.patch_threads;
+    return PMG_OK;
+  }
+  const bool try_major = layout != PMG_PATCH_INTERLEAVED;
+  const bool try_il = layout != PMG_PATCH_MAJOR && admissible_il(c, 256);
+  if (try_il) c->il_threads = 256;  // rule for meshes too small to time
   LevelData& F = c->lv[c->L - 1];
   const int64_t patches = ipow64(std::max(F.n - 1, 0), c->dim);
   if (c->K == 1 || patches < 4096) return PMG_OK;
   const bool mult = cf.smoother == PMG_SMOOTHER_MULTIPLICATIVE;
-  const TuneKey key{c->dim, c->K, c->mgprec, c->deformed ? 1 : 0, cf.local_cycles, mult ? 1 : 0};
+  const TuneKey key{c->dim, c->K, c->mgprec, c->deformed ? 1 : 0, cf.local_cycles, mult ? 1 : 0, F.n};
+  auto valid = [&](const TuneVal& v) {
+    return v.layout == PMG_PATCH_INTERLEAVED ? try_il && admissible_il(c, v.threads)
+                                             : try_major && admissible_ppc(c, v.ppc);
+  };
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_file_read_locked();
     auto it = g_tune.find(key);
-    if (it != g_tune.end() && admissible_ppc(c, it->second)) {
-      c->ppc = it->second;
+    if (it != g_tune.end() && valid(it->second)) {
+      set_layout(c, it->second);
       return PMG_OK;
     }
   }
+  std::vector<TuneVal> cand;
+  const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
+  if (try_major)
+    for (int ppc = 1; ppc <= 64; ++ppc) {
+      if (!admissible_ppc(c, ppc)) continue;
+      const int thr = ppc * tpp, padded = (thr + 31) / 32 * 32;
+      if (ppc > 2 && thr < 0.85 * padded) continue;  // warps with many idle lanes: not worth timing
+      cand.push_back({PMG_PATCH_MAJOR, ppc, 0});
+    }
+  if (try_il)
+    for (int t : {128, 192, 256, 320, 384, 448, 512, 640, 768, 896, 1024})
+      if (admissible_il(c, t)) cand.push_back({PMG_PATCH_INTERLEAVED, c->ppc, t});
   const size_t es = c->mg32 ? 4 : 8;
   PMG_CUDA(cudaMemsetAsync(F.r, 0, es * F.N, c->stream));
   PMG_CUDA(cudaMemsetAsync(F.u, 0, es * F.N, c->stream));
@@ -627,14 +701,10 @@ int choose_patches_per_block(pmg_ctx* c) {
   PMG_CUDA(cudaEventCreate(&e0));
   PMG_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_ppc = c->ppc;
+  TuneVal best_v{c->il_threads > 0 ? PMG_PATCH_INTERLEAVED : PMG_PATCH_MAJOR, c->ppc, c->il_threads};
   const int64_t before = g_launches.load();
-  const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
-  for (int ppc = 1; ppc <= 64; ++ppc) {
-    if (!admissible_ppc(c, ppc)) continue;
-    const int thr = ppc * tpp, padded = (thr + 31) / 32 * 32;
-    if (ppc > 2 && thr < 0.85 * padded) continue;  // warps with many idle lanes: not worth timing
-    c->ppc = ppc;
+  for (const TuneVal& v : cand) {
+    set_layout(c, v);
     float tmin = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, c->stream);
@@ -657,16 +727,16 @@ int choose_patches_per_block(pmg_ctx* c) {
     }
     if (tmin < best * 0.995f) {
       best = tmin;
-      best_ppc = ppc;
+      best_v = v;
     }
   }
   g_launches -= g_launches.load() - before;  // tuning launches are not the caller's work
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->ppc = best_ppc;
+  set_layout(c, best_v);
   std::lock_guard<std::mutex> g(g_tune_mu);
-  g_tune[key] = best_ppc;
-  tune_file_append_locked(key, best_ppc);
+  g_tune[key] = best_v;
+  tune_file_append_locked(key, best_v);
   return PMG_OK;
 }
 
@@ -809,8 +879,8 @@ int setup_context(pmg_ctx* c) {
     if (bad) return fail(PMG_ERR_ARG, "inverted cell: det J <= 0 at a quadrature point of the mesh");
   }
 
-  // patches per block: the autotuned value (or the caller's)
-  if (int rc = choose_patches_per_block(c)) return rc;
+  // patch-kernel layout and block shape: the autotuned choice (or the caller's)
+  if (int rc = choose_patch_layout(c)) return rc;
 
   PMG_CUDA(cudaMallocHost((void**)&c->host_scal, 8 * S_COUNT));
   PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
@@ -844,6 +914,8 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->gmres_restart = 30;
   cfg->smoother = PMG_SMOOTHER_ADDITIVE;
   cfg->vertex_disp = nullptr;
+  cfg->patch_layout = PMG_PATCH_AUTO;
+  cfg->patch_threads = 0;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {
@@ -1306,7 +1378,22 @@ int pmg_damping(const pmg_ctx* c, double* omega_patch, double* omega_jacobi) {
 
 int pmg_patches_per_block(const pmg_ctx* c, int* ppc) {
   if (check_ctx(c) || !ppc) return fail(PMG_ERR_ARG, "NULL argument");
-  *ppc = c->ppc;
+  *ppc = c->il_threads > 0 ? c->km()->patch_il(c->dim, c->mgprec, c->cfg.local_cycles) : c->ppc;
+  return PMG_OK;
+}
+
+int pmg_patch_layout(const pmg_ctx* c, int* layout, int* patches_per_block, int* threads) {
+  if (check_ctx(c) || !layout || !patches_per_block || !threads) return fail(PMG_ERR_ARG, "NULL argument");
+  if (c->il_threads > 0) {
+    *layout = PMG_PATCH_INTERLEAVED;
+    *patches_per_block = c->km()->patch_il(c->dim, c->mgprec, c->cfg.local_cycles);
+    *threads = c->il_threads;
+  } else {
+    const int tpp = c->deformed ? c->km()->patch_def_threads(c->dim) : c->km()->patch_threads(c->dim);
+    *layout = PMG_PATCH_MAJOR;
+    *patches_per_block = c->ppc;
+    *threads = std::min(1024, (c->ppc * tpp + 31) / 32 * 32);
+  }
   return PMG_OK;
 }
 

@@ -65,6 +65,14 @@ struct KernelTable {
   int (*patch_def_smem)(int dim, int prec, int n_iter);
   // largest block the patch kernel can launch with (registers included)
   int (*patch_max_threads)(int dim, int prec, int deformed);
+  // Cartesian patch smoother with the interleaved shared-memory layout (IL
+  // patches per block, element-major): IL for n_iter local cycles (0: no
+  // such kernel, or it does not fit); launch with `threads` per block (a
+  // multiple of 32); same output as patch_cart; largest admissible threads
+  int (*patch_il)(int dim, int prec, int n_iter);
+  cudaError_t (*patch_cart_il)(int dim, int prec, const void* r, void* dst, int n, int threads, int n_iter,
+                               const void* dinv, const PatchParamsHost& P, cudaStream_t s);
+  int (*patch_il_max_threads)(int dim, int prec);
 };
 
 // nullptr when k, dim or prec is out of range

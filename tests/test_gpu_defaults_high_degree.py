@@ -178,3 +178,68 @@ def test_coarsest_level_smoothing_rules():
     dctx = p.Context(p.make_config(dim=3, n_cells=6, degree=2, geometry=p.DEFORMED), device=DEV)
     with pytest.raises(p.PmgError):
         dctx.smooth(b, u, level=0)
+
+
+# ------------------------------------------------------------ interleaved patch layout
+@pytest.mark.parametrize("d,n,k,prec", [(3, 4, 2, p.FP32), (3, 4, 4, p.FP32), (3, 4, 4, p.FP64), (3, 4, 6, p.FP32),
+                                        (3, 4, 7, p.FP32), (3, 3, 8, p.FP32), (2, 8, 3, p.FP32), (2, 8, 5, p.FP64)])
+def test_interleaved_layout_sweep_and_vcycle_match_oracle(d, n, k, prec):
+    # the interleaved shared-memory layout forced on every level
+    L = 1 if n % 2 else 0
+    ctx = ctx_default(d, n, k, L=L, prec=prec, patch_layout=p.PATCH_INTERLEAVED, patch_threads=256)
+    lay, ppc, thr = ctx.patch_layout()
+    assert lay == p.PATCH_INTERLEAVED and thr == 256 and ppc in (2, 4, 8, 16)
+    dt = torch.float64 if prec == p.FP64 else torch.float32
+    if L == 1:
+        fine, h = oracle_level(d, n, k, "cartesian"), None
+    else:
+        h = hier(d, n, k)
+        fine = h.levels[-1]
+    b = random_vector(d, n, k, seed=371 + k)
+    u0 = random_vector(d, n, k, seed=372 + k)
+    u = to_dev(u0, dt)
+    ctx.smooth(to_dev(b, dt), u, level=-1, sweeps=1)
+    assert rel(u, full(fine, fine.smooth(b[fine.I], u0[fine.I], sweeps=1))) < _tol(prec)
+    if h is not None:
+        z = torch.empty(fine.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        ctx.vcycle(to_dev(b), z)
+        assert rel(z, full(fine, h.vcycle(b[fine.I]))) < _tol(prec)
+
+
+@pytest.mark.parametrize("k,prec", [(2, p.FP32), (3, p.FP32), (4, p.FP32), (4, p.FP64), (5, p.FP32), (7, p.FP32)])
+def test_interleaved_and_patch_major_layouts_are_bitwise_equal(k, prec):
+    # same per-patch arithmetic in both layouts: identical sweeps, V-cycles
+    # and multiplicative colour sweeps, at every admissible block shape
+    d, n = 3, 16 if k <= 4 else 8
+    dt = torch.float64 if prec == p.FP64 else torch.float32
+    b = to_dev(random_vector(d, n, k, seed=381), dt)
+    r = to_dev(random_vector(d, n, k, seed=382))
+    outs = []
+    for lay, ppc, thr in ((p.PATCH_MAJOR, 1, 0), (p.PATCH_MAJOR, 3, 0), (p.PATCH_INTERLEAVED, 0, 128),
+                          (p.PATCH_INTERLEAVED, 0, 416), (p.PATCH_INTERLEAVED, 0, 768)):
+        for sm in (p.ADDITIVE, p.MULTIPLICATIVE):
+            try:
+                ctx = ctx_default(d, n, k, prec=prec, patch_layout=lay, patches_per_block=ppc, patch_threads=thr,
+                                  smoother=sm)
+            except p.PmgError as e:             # block shape above the kernel's limit
+                assert e.code == p.PMG_ERR_ARG and thr > 0
+                continue
+            u = torch.zeros_like(b)
+            ctx.smooth(b, u)
+            z = torch.empty_like(r)
+            ctx.vcycle(r, z)
+            outs.append((sm, u, z))
+            ctx.close()
+    for sm in (p.ADDITIVE, p.MULTIPLICATIVE):
+        got = [(u, z) for s, u, z in outs if s == sm]
+        assert len(got) >= 3
+        for u, z in got[1:]:
+            assert torch.equal(u, got[0][0]) and torch.equal(z, got[0][1])
+
+
+def test_autotuner_considers_the_interleaved_layout():
+    ctx = ctx_default(3, 32, 4, prec=p.FP32)       # 29,791 patches: timed
+    lay, ppc, thr = ctx.patch_layout()
+    assert lay in (p.PATCH_MAJOR, p.PATCH_INTERLEAVED) and ppc >= 1 and thr % 32 == 0
+    with pytest.raises(p.PmgError):                 # no interleaved layout for deformed meshes
+        ctx_default(3, 4, 2, geometry=p.DEFORMED, patch_layout=p.PATCH_INTERLEAVED)
