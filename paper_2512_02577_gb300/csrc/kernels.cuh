@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "pmg_common.cuh"
+#include "coef_tables.h"
 #include "pmg_kernels_api.h"
 #include "vec.h"
 
@@ -24,6 +25,16 @@ constexpr CoefLayout LAY = coef_layout(K);
 
 static __constant__ double c_coef64[kMaxCoef];
 static __constant__ float c_coef32[kMaxCoef];
+
+// The same coefficient block as compile-time tables (generated at build time
+// from the host set-up, coef_tables.h).  Every contraction whose indices are
+// known after unrolling reads these: the compiler folds the entries into the
+// arithmetic instead of loading them for every line.  Reads with run-time
+// indices (the h-transfer passes) use the constant-memory copy above.
+#define PMG_TAB_(prec, k) PMG_COEF##prec##_K##k
+#define PMG_TAB(prec, k) PMG_TAB_(prec, k)
+static __device__ constexpr double c_tab64[] = PMG_TAB(64, PMG_K);
+static __device__ constexpr float c_tab32[] = PMG_TAB(32, PMG_K);
 
 static inline int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
@@ -39,6 +50,13 @@ template <>
 __device__ __forceinline__ const double* coef<double>() { return c_coef64; }
 template <>
 __device__ __forceinline__ const float* coef<float>() { return c_coef32; }
+
+template <typename T>
+__device__ __forceinline__ const T* ctab();
+template <>
+__device__ __forceinline__ const double* ctab<double>() { return c_tab64; }
+template <>
+__device__ __forceinline__ const float* ctab<float>() { return c_tab32; }
 
 // ===========================================================================
 // Cartesian operator A = s * sum_dir (K on dir, M elsewhere), applied by one
@@ -59,7 +77,7 @@ __global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, cons
   const int N1 = K * n + 1;
   const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
   const int64_t total = (int64_t)(n + 1) * lines;
-  const T* C = coef<T>();
+  const T* C = ctab<T>();
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int c, p, q;
@@ -266,23 +284,47 @@ struct CartGeo {
   __device__ __forceinline__ T dinv_at(int, int l, int i) const { return dinv[dinv_off(l) + i] * inv_scale; }
   __device__ __forceinline__ T a0inv(int) const { return inv_a0; }
 
-  // out = r - A_l d for every patch of the block (offsets within a patch;
-  // out may be t0 = offset 0; d and r distinct from t0, t1)
-  template <int l, class PB>
-  __device__ __forceinline__ void resid(const PB& pb, int od, int orr, int oo) const {
+  // The Jacobi steps of Algorithm 3 fold into the line passes of the
+  // residual (no separate pointwise pass over the patch):
+  //   MODE 0: out = r - A_l d;
+  //   MODE 1: d = om D^-1 r first (pre-smoothing from a zero guess, written
+  //           to d by the first pass), then out = r - A_l d;
+  //   MODE 2: d += om D^-1 (r - A_l d) (post-smoothing; out not written).
+  // Offsets within a patch; out may be t0 = offset 0; d and r distinct from
+  // t0, t1.
+  static constexpr bool kFusedSmoothing = true;
+  template <int l, int MODE = 0, class PB>
+  __device__ __forceinline__ void resid(const PB& pb, int od, int orr, int oo, T om = T(0)) const {
     constexpr int p = plev(K, l);
     constexpr int m = mp(p);
     constexpr int SZT = PatchShape<DIM>::SZT;
-    const T* MP = coef<T>() + LAY.MP[l];
-    const T* KP = coef<T>() + LAY.KP[l];
+    const T* MP = ctab<T>() + LAY.MP[l];
+    const T* KP = ctab<T>() + LAY.KP[l];
     const T s = scale;
+    // first pass, along x: x = d (MODE 1: computed from r and stored)
+    auto first = [&](auto sm, int b, T* x) {
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        if constexpr (MODE == 1) {
+          const T v = om * dinv_at(0, l, b + j) * sm[orr + b + j];
+          sm[od + b + j] = v;
+          x[j] = v;
+        } else {
+          x[j] = sm[od + b + j];
+        }
+      }
+    };
+    // last pass: the residual t_e at patch element e
+    auto last = [&](auto sm, int e, T t) {
+      if constexpr (MODE == 2) sm[od + e] += om * dinv_at(0, l, e) * t;
+      else sm[oo + e] = t;
+    };
     if constexpr (DIM == 3) {
       pfor<m * m>(pb, [&](int g, int L) {
         auto sm = pb.at(g);
         const int b = line_base<0, m, m, m>(L);
         T x[m], y0[m], y1[m];
-#pragma unroll
-        for (int j = 0; j < m; ++j) x[j] = sm[od + b + j];
+        first(sm, b, x);
         pmv<p>(MP, x, y0);
         pmv<p>(KP, x, y1);
 #pragma unroll
@@ -311,7 +353,7 @@ struct CartGeo {
         pmv<p>(KP, a, y1);
         pmv<p>(MP, c, y2);
 #pragma unroll
-        for (int i = 0; i < m; ++i) sm[oo + b + i * m * m] = sm[orr + b + i * m * m] - s * (y1[i] + y2[i]);
+        for (int i = 0; i < m; ++i) last(sm, b + i * m * m, sm[orr + b + i * m * m] - s * (y1[i] + y2[i]));
       });
       __syncthreads();
     } else {
@@ -319,8 +361,7 @@ struct CartGeo {
         auto sm = pb.at(g);
         const int b = line_base<0, m, m, 1>(L);
         T x[m], y0[m], y1[m];
-#pragma unroll
-        for (int j = 0; j < m; ++j) x[j] = sm[od + b + j];
+        first(sm, b, x);
         pmv<p>(MP, x, y0);
         pmv<p>(KP, x, y1);
 #pragma unroll
@@ -336,7 +377,7 @@ struct CartGeo {
         pmv<p>(KP, a, y1);
         pmv<p>(MP, c, y2);
 #pragma unroll
-        for (int i = 0; i < m; ++i) sm[oo + b + i * m] = sm[orr + b + i * m] - s * (y1[i] + y2[i]);
+        for (int i = 0; i < m; ++i) last(sm, b + i * m, sm[orr + b + i * m] - s * (y1[i] + y2[i]));
       });
       __syncthreads();
     }
@@ -352,7 +393,7 @@ __device__ __forceinline__ void restrict_p(const PB& pb, int dst) {
   constexpr int m = mp(pf), mc = mp(pc);
   constexpr int SZT = PatchShape<DIM>::SZT;
   constexpr int EZ = DIM == 3 ? m : 1;
-  const T* Tr = coef<T>() + LAY.Tr[l];  // m x mc, row-major
+  const T* Tr = ctab<T>() + LAY.Tr[l];  // m x mc, row-major
   // x: (m, m, EZ) in t0 -> (mc, m, EZ) in t1
   pfor<m * EZ>(pb, [&](int g, int L) {
     auto sm = pb.at(g);
@@ -417,7 +458,7 @@ __device__ __forceinline__ void prolong_p(const PB& pb, int src, int dst) {
   constexpr int m = mp(pf), mc = mp(pc);
   constexpr int SZT = PatchShape<DIM>::SZT;
   constexpr int EZC = DIM == 3 ? mc : 1;
-  const T* Tr = coef<T>() + LAY.Tr[l];
+  const T* Tr = ctab<T>() + LAY.Tr[l];
   // x: (mc, mc, EZC) -> (m, mc, EZC) in t0
   pfor<mc * EZC>(pb, [&](int g, int L) {
     auto sm = pb.at(g);
@@ -509,22 +550,30 @@ __device__ void pvcycle(const PB& pb, const Geo& geo, const PatchParams<typename
     constexpr int SZ = S::SZ(l);
     constexpr int R = S::off_r(l), D = S::off_d(l);
     const T om = P.omega[l];
-    pfor<SZ>(pb, [&](int g, int i) {  // pre-smoothing (zero initial guess)
-      auto sm = pb.at(g);
-      sm[D + i] = om * geo.dinv_at(g, l, i) * sm[R + i];
-    });
-    __syncthreads();
-    geo.template resid<l>(pb, D, R, 0);                   // residual into t0
-    restrict_p<DIM, l>(pb, S::off_r(l - 1));               // restrict
-    pvcycle<DIM, l - 1>(pb, geo, P);                    // recurse
-    prolong_p<DIM, l>(pb, S::off_d(l - 1), D);             // prolongate, add
+    if constexpr (Geo::kFusedSmoothing) {
+      geo.template resid<l, 1>(pb, D, R, 0, om);  // pre-smoothing (zero guess) + residual into t0
+    } else {
+      pfor<SZ>(pb, [&](int g, int i) {  // pre-smoothing (zero initial guess)
+        auto sm = pb.at(g);
+        sm[D + i] = om * geo.dinv_at(g, l, i) * sm[R + i];
+      });
+      __syncthreads();
+      geo.template resid<l>(pb, D, R, 0);  // residual into t0
+    }
+    restrict_p<DIM, l>(pb, S::off_r(l - 1));    // restrict
+    pvcycle<DIM, l - 1>(pb, geo, P);            // recurse
+    prolong_p<DIM, l>(pb, S::off_d(l - 1), D);  // prolongate, add
     if (P.half) return;  // half V-cycle (§3.2.2): no post-smoothing (uniform per block)
-    geo.template resid<l>(pb, D, R, 0);                   // residual
-    pfor<SZ>(pb, [&](int g, int i) {  // post-smoothing
-      auto sm = pb.at(g);
-      sm[D + i] += om * geo.dinv_at(g, l, i) * sm[i];
-    });
-    __syncthreads();
+    if constexpr (Geo::kFusedSmoothing) {
+      geo.template resid<l, 2>(pb, D, R, 0, om);  // residual + post-smoothing
+    } else {
+      geo.template resid<l>(pb, D, R, 0);  // residual
+      pfor<SZ>(pb, [&](int g, int i) {     // post-smoothing
+        auto sm = pb.at(g);
+        sm[D + i] += om * geo.dinv_at(g, l, i) * sm[i];
+      });
+      __syncthreads();
+    }
   }
 }
 

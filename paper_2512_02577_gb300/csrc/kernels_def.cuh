@@ -64,8 +64,8 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
   constexpr int n1 = p + 1;
   constexpr int NP = ipow(n1, DIM);
   constexpr int A0 = 0, A1 = NP, B0 = 2 * NP, B1 = 3 * NP, B2 = 4 * NP;
-  const T* Sm = coef<T>() + LAY.S[l];
-  const T* Dm = coef<T>() + LAY.Dq[l];
+  const T* Sm = ctab<T>() + LAY.S[l];
+  const T* Dm = ctab<T>() + LAY.Dq[l];
   if constexpr (DIM == 3) {
     tiles_axis<3, n1, NC, 0, false, false>(Sm, ng, tile, A0, A1);
     __syncthreads();
@@ -366,6 +366,8 @@ struct DefGeo {
   }
   __device__ __forceinline__ T a0inv(int g) const { return inv_a0[g]; }
 
+  static constexpr bool kFusedSmoothing = false;  // Jacobi steps as separate pointwise passes
+
   template <int l, class PB>
   __device__ __forceinline__ void resid(const PB& pb, int od, int orr, int oo) const {
     constexpr int p = plev(K, l);
@@ -374,8 +376,8 @@ struct DefGeo {
     constexpr int B = DefShape<DIM>::BUF;
     constexpr int W = PatchShape<DIM>::ELEMS;
     constexpr int B0 = W, B1 = W + B, B2 = W + 2 * B, B3 = W + 3 * B;
-    const T* Sm = coef<T>() + LAY.S[l];
-    const T* Dm = coef<T>() + LAY.Dq[l];
+    const T* Sm = ctab<T>() + LAY.S[l];
+    const T* Dm = ctab<T>() + LAY.Dq[l];
     constexpr int MZ = DIM == 3 ? mf : 1, QZ = DIM == 3 ? Q : 1;
     // expand d onto the patch grid (zero on its boundary) in B0: (mf, mf, MZ)
     pfor<ipow(mf, DIM)>(pb, [&](int g, int i) {
