@@ -86,6 +86,16 @@ enum pmg_patch_layout {
                                  SM use the patch-major layout, when the config's, every level uses it */
 };
 
+/* Arithmetic of the FP64 operator apply. */
+enum pmg_outer_apply {
+  PMG_OUTER_APPLY_FP64 = 0,         /* IEEE double (default) */
+  PMG_OUTER_APPLY_FLOAT_FLOAT = 1   /* Cartesian only: FP64 vectors in and out, every product and sum carried
+                                       as an unevaluated pair of floats (about 48 significant bits, relative
+                                       error of A x within a few 1e-14 of |A| |x|) on the FP32 pipes -- on
+                                       GB300 several times faster than the FP64 pipes; the coarse-matrix
+                                       assembly stays in FP64 */
+};
+
 typedef struct pmg_ctx pmg_ctx;
 
 typedef struct pmg_config {
@@ -119,6 +129,8 @@ typedef struct pmg_config {
                           PMG_PATCH_AUTO (default) = timed at creation among the admissible layouts and
                           block shapes; PMG_PATCH_MAJOR or PMG_PATCH_INTERLEAVED to fix the layout */
   int patch_threads;   /* PMG_PATCH_INTERLEAVED: threads per block (multiple of 32), 0 = autotuned */
+  int outer_apply;     /* arithmetic of every FP64 operator apply (pmg_apply / pmg_residual with PMG_FP64,
+                          the outer solver's A p and residuals): enum pmg_outer_apply */
 } pmg_config;
 
 typedef struct pmg_solve_info {
@@ -274,7 +286,8 @@ const char* pmg_last_error(void);
  * of pmg_num_dofs(finest) doubles each -- pinned memory for overlapping
  * copies -- tolerance, iteration cap); pmg_server_poll never blocks: it
  * admits queued requests in arrival order while fewer than max_active run
- * and the request's pmg_bytes_required fits in the budget (an idle resident
+ * and the request's pmg_bytes_required fits in the budget (in the order of
+ * pmg_server_set_policy; an idle resident
  * context is reused when the request's configuration would build the same
  * operator and preconditioner: every pmg_config field pmg_create reads -- dim,
  * n, degree, levels, precision, geometry and, for the deformed geometry, its
@@ -301,6 +314,16 @@ int pmg_server_poll(pmg_server* server, int* n_running, int* n_queued);
  * steady clock: submission, admission, completion. */
 int pmg_server_result(pmg_server* server, int64_t request_id, int* state, pmg_solve_info* info, double* t_submit,
                       double* t_start, double* t_done);
+/* Admission order of a server (default PMG_SERVE_FIFO, arrival order).
+ * PMG_SERVE_SHORTEST_FIRST admits the queued request with the least
+ * estimated work (finest-grid nodes x (degree + 2)) first, except that a
+ * request queued for max_wait_s seconds or more goes first (oldest first),
+ * and runs requests whose estimated work is below small_work on
+ * high-priority CUDA streams, so that small solves are not held behind the
+ * blocks of large ones.  Applies to requests admitted after the call. */
+enum pmg_serve_policy { PMG_SERVE_FIFO = 0, PMG_SERVE_SHORTEST_FIRST = 1 };
+int pmg_server_set_policy(pmg_server* server, int policy, double max_wait_s, double small_work);
+
 /* Forget a finished (done or failed) request: its id becomes unknown.  The
  * server keeps every request until it is released or the server destroyed,
  * so a long-running driver releases each request once it has read the

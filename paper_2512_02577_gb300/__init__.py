@@ -29,6 +29,8 @@ FP64, FP32 = 0, 1
 OUTER_CG, OUTER_GMRES = 0, 1
 ADDITIVE, MULTIPLICATIVE = 0, 1
 PATCH_AUTO, PATCH_MAJOR, PATCH_INTERLEAVED = 0, 1, 2
+SERVE_FIFO, SERVE_SHORTEST_FIRST = 0, 1
+APPLY_FP64, APPLY_FLOAT_FLOAT = 0, 1
 
 # Every entry point declared in include/pmg.h.
 EXPORTED = [
@@ -39,6 +41,7 @@ EXPORTED = [
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
     "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release", "pmg_patch_layout",
+    "pmg_server_set_policy",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -58,7 +61,7 @@ class Config(ctypes.Structure):
         ("smooth_steps", ctypes.c_int), ("patches_per_block", ctypes.c_int),
         ("local_half", ctypes.c_int), ("outer_solver", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("smoother", ctypes.c_int), ("vertex_disp", ctypes.c_void_p),
-        ("patch_layout", ctypes.c_int), ("patch_threads", ctypes.c_int),
+        ("patch_layout", ctypes.c_int), ("patch_threads", ctypes.c_int), ("outer_apply", ctypes.c_int),
     ]
 
 
@@ -114,6 +117,7 @@ def load_library(path=LIB_PATH):
         "pmg_damping": (cint, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_default_damping": (cint, [cint, cint, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_server_release": (cint, [vp, i64]),
+        "pmg_server_set_policy": (cint, [vp, cint, dbl, dbl]),
         "pmg_patch_layout": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]),
     }
     for name, (res, args) in sigs.items():
@@ -133,7 +137,7 @@ def _check(code):
 def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, deform_amp=0.05,
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
                 smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
-                smoother=ADDITIVE, vertex_disp=None, patch_layout=PATCH_AUTO, patch_threads=0):
+                smoother=ADDITIVE, vertex_disp=None, patch_layout=PATCH_AUTO, patch_threads=0, outer_apply=APPLY_FP64):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -150,6 +154,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.gmres_restart = gmres_restart
     c.smoother = smoother
     c.patch_layout, c.patch_threads = patch_layout, patch_threads
+    c.outer_apply = outer_apply
     if vertex_disp is not None:
         # ((n+1)^d, d) float64 displacements of the finest mesh's vertices;
         # the config keeps a reference so the array outlives it
@@ -333,12 +338,14 @@ class Server:
     and x; poll() never blocks; result() reports state, solve info and the
     submit/admit/done host times."""
 
-    def __init__(self, memory_budget_bytes=0, max_active=8):
+    def __init__(self, memory_budget_bytes=0, max_active=8, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0):
         lib = load_library()
         h = ctypes.c_void_p()
         _check(lib.pmg_server_create(int(memory_budget_bytes), int(max_active), ctypes.byref(h)))
         self.handle = h
         self._keep = {}
+        if policy != SERVE_FIFO:
+            _check(lib.pmg_server_set_policy(h, policy, float(max_wait_s), float(small_work)))
 
     def submit(self, cfg, b_host, x_host, rtol=1e-8, maxit=500):
         for t in (b_host, x_host):

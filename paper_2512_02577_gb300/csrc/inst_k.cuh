@@ -55,6 +55,39 @@ static cudaError_t cart_apply(int dim, int prec, const void* x, void* y, const v
                               s);
 }
 
+// y = A x or y = b - A x for FP64 vectors in float-float arithmetic
+// (cart_pass_ff); t0..t3: FP64-sized scratch, each holding a float-pair plane
+template <int DIM>
+static cudaError_t cart_apply_ff_t(const double* x, double* y, const double* b, void* t0, void* t1, void* t2,
+                                   void* t3, int n, double scale, cudaStream_t st) {
+  const int N1 = K * n + 1;
+  const int64_t work = (int64_t)(n + 1) * (DIM == 3 ? (int64_t)N1 * N1 : N1);
+  const int bs = 256;
+  const int g = grid_for(work, bs);
+  const float sh = (float)scale;
+  const ff s{sh, (float)(scale - (double)sh)};
+  float *f0 = (float*)t0, *f1 = (float*)t1, *f2 = (float*)t2, *f3 = (float*)t3;
+  if (DIM == 3) {
+    cart_pass_ff<3, 0, 0, false><<<g, bs, 0, st>>>(x, nullptr, f0, f1, nullptr, n, s);
+    cart_pass_ff<3, 1, 1, false><<<g, bs, 0, st>>>(f0, f1, f2, f3, nullptr, n, s);
+    if (b) cart_pass_ff<3, 2, 2, true><<<g, bs, 0, st>>>(f2, f3, y, nullptr, b, n, s);
+    else cart_pass_ff<3, 2, 2, false><<<g, bs, 0, st>>>(f2, f3, y, nullptr, nullptr, n, s);
+    g_launches += 3;
+  } else {
+    cart_pass_ff<2, 0, 0, false><<<g, bs, 0, st>>>(x, nullptr, f0, f1, nullptr, n, s);
+    if (b) cart_pass_ff<2, 1, 2, true><<<g, bs, 0, st>>>(f0, f1, y, nullptr, b, n, s);
+    else cart_pass_ff<2, 1, 2, false><<<g, bs, 0, st>>>(f0, f1, y, nullptr, nullptr, n, s);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t cart_apply_ff(int dim, const double* x, double* y, const double* b, void* t0, void* t1, void* t2,
+                                 void* t3, int n, double scale, cudaStream_t s) {
+  if (dim != DP) return cudaErrorInvalidValue;
+  return cart_apply_ff_t<DP>(x, y, b, t0, t1, t2, t3, n, scale, s);
+}
+
 static int patch_threads(int dim) { return dim == 3 ? PatchShape<3>::TPP : PatchShape<2>::TPP; }
 
 static int patch_smem(int dim, int prec, int n_iter) {
@@ -263,6 +296,7 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::patch_il_of,
       PMG_KNS::patch_cart_il,
       PMG_KNS::patch_il_max_threads,
+      PMG_KNS::cart_apply_ff,
   };
   return &t;
 }

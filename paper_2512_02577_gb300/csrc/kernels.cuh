@@ -168,6 +168,182 @@ __global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, cons
 }
 
 // ===========================================================================
+// The same three passes in float-float arithmetic: FP64 input x and output y,
+// every product and sum carried as an unevaluated pair of floats (hi + lo,
+// about 48 significant bits) on the FP32 pipes, which on GB300 run about 60x
+// faster than FP64.  Error-free transformations: Knuth's TwoSum (s + e = a + b
+// exactly) and the FMA TwoProduct (p + e = a b exactly); sums keep their hi
+// part by TwoSum and collect every low-order part in a float accumulator,
+// renormalised at the end (Dekker's FastTwoSum).  Coefficients are split
+// into float pairs from the FP64 tables at compile time.  Intermediates are
+// float-pair planes: a vector of N pairs stored as N his then N los.
+// ===========================================================================
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ ff ff_of(double v) {
+  const float h = (float)v;
+  return ff{h, (float)(v - (double)h)};
+}
+
+// hi/lo split of the FP64 coefficient c (constant-folded when c is)
+__device__ __forceinline__ ff ff_const(double c) { return ff_of(c); }
+
+// running sum of products c_j x_j
+struct ff_acc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void mac(ff c, ff x) {
+    const float p = c.hi * x.hi;
+    float t = __fmaf_rn(c.hi, x.hi, -p);  // exact: p + t = c.hi x.hi
+    t = __fmaf_rn(c.hi, x.lo, t);
+    t = __fmaf_rn(c.lo, x.hi, t);
+    float e;
+    two_sum(hi, p, hi, e);
+    lo += e + t;
+  }
+  __device__ __forceinline__ void add(ff_acc o) {
+    float e;
+    two_sum(hi, o.hi, hi, e);
+    lo += e + o.lo;
+  }
+  __device__ __forceinline__ ff value() const {
+    const float s = hi + lo;  // FastTwoSum (|hi| >= |lo|)
+    return ff{s, lo - (s - hi)};
+  }
+};
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float t = __fmaf_rn(a.hi, b.hi, -p);
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  const float s = p + t;
+  return ff{s, t - (s - p)};
+}
+
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// MODE as cart_pass; in0 is FP64 in MODE 0 (x), else a float-pair plane;
+// out0 / out1 are float-pair planes in MODE 0, 1; in MODE 2 out0 is FP64.
+template <int DIM, int AX, int MODE, bool RESID>
+__global__ void __launch_bounds__(256) cart_pass_ff(const void* __restrict__ in0_, const float* __restrict__ in1,
+                                                    void* __restrict__ out0_, float* __restrict__ out1,
+                                                    const double* __restrict__ bvec, int n, ff s) {
+  const int N1 = K * n + 1;
+  const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
+  const int64_t total = (int64_t)(n + 1) * lines;
+  const int64_t NN = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;  // plane length
+  const double* xin = static_cast<const double*>(in0_);
+  const float* in0 = static_cast<const float*>(in0_);
+  float* out0 = static_cast<float*>(out0_);
+  double* yout = static_cast<double*>(out0_);
+  const double* C = ctab<double>();
+  auto load0 = [&](int64_t o) -> ff {
+    if constexpr (MODE == 0) return ff_of(xin[o]);
+    else return ff{in0[o], in0[NN + o]};
+  };
+  auto load1 = [&](int64_t o) -> ff { return ff{in1[o], in1[NN + o]}; };
+  auto store = [&](float* pl, int64_t o, ff v) {
+    pl[o] = v.hi;
+    pl[NN + o] = v.lo;
+  };
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c, p, q;
+    if (AX == 0) {
+      c = (int)(t % (n + 1));
+      const int64_t r = t / (n + 1);
+      p = (int)(r % N1);
+      q = (int)(r / N1);
+    } else {
+      p = (int)(t % N1);
+      const int64_t r = t / N1;
+      c = (int)(r % (n + 1));
+      q = (int)(r / (n + 1));
+    }
+    int64_t base, stride;
+    if (DIM == 3) {
+      if (AX == 0) { base = ((int64_t)q * N1 + p) * N1; stride = 1; }
+      else if (AX == 1) { base = (int64_t)q * N1 * N1 + p; stride = N1; }
+      else { base = (int64_t)q * N1 + p; stride = (int64_t)N1 * N1; }
+    } else {
+      if (AX == 0) { base = (int64_t)p * N1; stride = 1; }
+      else { base = p; stride = N1; }
+    }
+    if (c == n) {  // the last grid node of the line is on the boundary
+      const int64_t o = base + (int64_t)K * n * stride;
+      if (MODE == 2) yout[o] = 0.0;
+      else { store(out0, o, ff{0.f, 0.f}); store(out1, o, ff{0.f, 0.f}); }
+      continue;
+    }
+    bool line_zero = false;
+    if (MODE == 0) line_zero = (p == 0 || p == N1 - 1 || (DIM == 3 && (q == 0 || q == N1 - 1)));
+    ff xr0[K + 1], xl0[K + 1], xr1[K + 1], xl1[K + 1];
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      const int g = K * c + b;
+      ff v = load0(base + (int64_t)g * stride);
+      if (MODE == 0 && (line_zero || g == 0 || g == K * n)) v = ff{0.f, 0.f};
+      xr0[b] = v;
+      xr1[b] = MODE == 0 ? ff{0.f, 0.f} : load1(base + (int64_t)g * stride);
+      if (c > 0) {
+        const int gl = K * (c - 1) + b;
+        ff w = load0(base + (int64_t)gl * stride);
+        if (MODE == 0 && (line_zero || gl == 0)) w = ff{0.f, 0.f};
+        xl0[b] = w;
+        xl1[b] = MODE == 0 ? ff{0.f, 0.f} : load1(base + (int64_t)gl * stride);
+      } else {
+        xl0[b] = ff{0.f, 0.f};
+        xl1[b] = ff{0.f, 0.f};
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const int g = K * c + a;
+      ff_acc m0, k0, m1;
+#pragma unroll
+      for (int b = 0; b <= K; ++b) {
+        const ff me = ff_const(C[LAY.Me + a * (K + 1) + b]), ke = ff_const(C[LAY.Ke + a * (K + 1) + b]);
+        m0.mac(me, xr0[b]);
+        k0.mac(ke, xr0[b]);
+        if (MODE != 0) m1.mac(me, xr1[b]);
+      }
+      if (a == 0) {  // vertex node: add the row of the left cell
+#pragma unroll
+        for (int b = 0; b <= K; ++b) {
+          const ff me = ff_const(C[LAY.Me + K * (K + 1) + b]), ke = ff_const(C[LAY.Ke + K * (K + 1) + b]);
+          m0.mac(me, xl0[b]);
+          k0.mac(ke, xl0[b]);
+          if (MODE != 0) m1.mac(me, xl1[b]);
+        }
+      }
+      const bool bnd = (g == 0) || (MODE == 2 && (p == 0 || p == N1 - 1 || (DIM == 3 && (q == 0 || q == N1 - 1))));
+      const int64_t o = base + (int64_t)g * stride;
+      if (MODE == 0) {
+        store(out0, o, bnd ? ff{0.f, 0.f} : m0.value());
+        store(out1, o, bnd ? ff{0.f, 0.f} : k0.value());
+      } else if (MODE == 1) {
+        k0.add(m1);
+        store(out0, o, bnd ? ff{0.f, 0.f} : m0.value());
+        store(out1, o, bnd ? ff{0.f, 0.f} : k0.value());
+      } else {
+        k0.add(m1);
+        double v = ff_to_double(ff_mul(s, k0.value()));
+        if (RESID) v = bvec[o] - v;
+        yout[o] = bnd ? 0.0 : v;
+      }
+    }
+  }
+}
+
+// ===========================================================================
 // Vertex-patch smoother with the local p-multigrid solver (§2.1, §2.2, §3).
 // A thread block owns `np` patches, processed in lockstep.  Every step of
 // the local V-cycle is a set of independent 1D line contractions (or

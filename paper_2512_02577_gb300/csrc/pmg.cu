@@ -151,6 +151,10 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   if (cfg->patch_layout != PMG_PATCH_AUTO && cfg->patch_layout != PMG_PATCH_MAJOR &&
       cfg->patch_layout != PMG_PATCH_INTERLEAVED)
     return fail(PMG_ERR_ARG, "unknown patch_layout");
+  if (cfg->outer_apply != PMG_OUTER_APPLY_FP64 && cfg->outer_apply != PMG_OUTER_APPLY_FLOAT_FLOAT)
+    return fail(PMG_ERR_ARG, "unknown outer_apply");
+  if (cfg->outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT && cfg->geometry != PMG_GEOM_CARTESIAN)
+    return fail(PMG_ERR_UNSUPPORTED, "the float-float operator is Cartesian only");
   if (cfg->patches_per_block < 0 || cfg->patch_threads < 0)
     return fail(PMG_ERR_ARG, "patches_per_block, patch_threads >= 0");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
@@ -342,10 +346,15 @@ QuadTab make_tab(int p, int nq) {
 }
 
 // r = b - A u (b != nullptr) or r = A u on mesh level `level`, precision prec.
-int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const void* b) {
+// FP64 on a context with outer_apply FLOAT_FLOAT runs in float-float
+// arithmetic, unless exact64 (the coarse-matrix assembly).
+int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const void* b, bool exact64 = false) {
   LevelData& L = c->lv[level];
   cudaError_t e;
-  if (c->deformed) {
+  if (prec == PMG_FP64 && !exact64 && c->cfg.outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT) {
+    e = c->kt[PMG_FP64]->cart_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b, c->t64[0], c->t64[1],
+                                       c->t64[2], c->t64[3], L.n, L.scale, c->stream);
+  } else if (c->deformed) {
     e = c->kt[prec]->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cellbuf, L.n, c->stream);
   } else {
     void** t = prec == PMG_FP64 ? (void**)c->t64 : c->t_mg;
@@ -499,7 +508,7 @@ int ensure_coarse(pmg_ctx* c) {
     PMG_CUDA(cudaMemsetAsync(bad, 0, 4, c->stream));
     for (int j = 0; j < nc; ++j) {
       PMG_CUDA(coarse_unit(xd, C.N, idx[j], c->stream));
-      int rc = level_apply(c, 0, PMG_FP64, xd, yd, nullptr);
+      int rc = level_apply(c, 0, PMG_FP64, xd, yd, nullptr, true);
       if (rc) return rc;
       PMG_CUDA(coarse_gather_row(yd, c->cidx, nc, A, j, c->stream));
     }
@@ -916,6 +925,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->vertex_disp = nullptr;
   cfg->patch_layout = PMG_PATCH_AUTO;
   cfg->patch_threads = 0;
+  cfg->outer_apply = PMG_OUTER_APPLY_FP64;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {

@@ -73,6 +73,10 @@ struct KernelTable {
   cudaError_t (*patch_cart_il)(int dim, int prec, const void* r, void* dst, int n, int threads, int n_iter,
                                const void* dinv, const PatchParamsHost& P, cudaStream_t s);
   int (*patch_il_max_threads)(int dim, int prec);
+  // y = A x (b == nullptr) or y = b - A x for FP64 x, y, b on a Cartesian
+  // level, computed in float-float arithmetic; t0..t3: scratch of N doubles
+  cudaError_t (*cart_apply_ff)(int dim, const double* x, double* y, const double* b, void* t0, void* t1, void* t2,
+                               void* t3, int n, double scale, cudaStream_t s);
 };
 
 // nullptr when k, dim or prec is out of range

@@ -47,18 +47,18 @@ int fail(int code, const std::string& msg) {
 struct Key {
   int dim = 0, n_cells = 0, degree = 0, mg_precision = 0, geometry = 0, n_levels = 0, local_cycles = 0,
       smooth_steps = 0, local_half = 0, outer_solver = 0, gmres_restart = 0, smoother = 0, patches_per_block = 0,
-      patch_layout = 0, patch_threads = 0;
+      patch_layout = 0, patch_threads = 0, outer_apply = 0;
   double deform_amp = 0, omega_patch = 0, omega_jacobi[4] = {0, 0, 0, 0};
   uint64_t disp_hash = 0;
   const std::vector<double>* disp = nullptr;  // the request's own copy (distorted only)
 
   bool operator==(const Key& o) const {
     if (std::tie(dim, n_cells, degree, mg_precision, geometry, n_levels, local_cycles, smooth_steps, local_half,
-                 outer_solver, gmres_restart, smoother, patches_per_block, patch_layout, patch_threads, deform_amp,
-                 omega_patch, disp_hash) !=
+                 outer_solver, gmres_restart, smoother, patches_per_block, patch_layout, patch_threads, outer_apply,
+                 deform_amp, omega_patch, disp_hash) !=
         std::tie(o.dim, o.n_cells, o.degree, o.mg_precision, o.geometry, o.n_levels, o.local_cycles,
                  o.smooth_steps, o.local_half, o.outer_solver, o.gmres_restart, o.smoother, o.patches_per_block,
-                 o.patch_layout, o.patch_threads, o.deform_amp, o.omega_patch, o.disp_hash))
+                 o.patch_layout, o.patch_threads, o.outer_apply, o.deform_amp, o.omega_patch, o.disp_hash))
       return false;
     for (int i = 0; i < 4; ++i)
       if (omega_jacobi[i] != o.omega_jacobi[i]) return false;
@@ -95,6 +95,7 @@ Key key_of(const pmg_config& c, const std::vector<double>* disp) {
   k.patches_per_block = c.patches_per_block;
   k.patch_layout = c.patch_layout;
   k.patch_threads = c.patch_threads;
+  k.outer_apply = c.outer_apply;
   k.deform_amp = c.geometry == PMG_GEOM_DEFORMED ? c.deform_amp : 0.0;
   k.omega_patch = c.omega_patch > 0 ? c.omega_patch : 0.0;
   for (int i = 0; i < 4; ++i) k.omega_jacobi[i] = c.omega_jacobi[i] > 0 ? c.omega_jacobi[i] : 0.0;
@@ -117,6 +118,7 @@ struct Slot {
 
 struct Request {
   int64_t id = 0;
+  double work = 0;  // estimated cost of the solve (admission order, stream priority)
   pmg_config cfg{};
   std::vector<double> disp;  // copy of cfg.vertex_disp taken at submit (distorted geometry)
   const double* b = nullptr;
@@ -142,6 +144,10 @@ double now_s() {
 struct pmg_server {
   int64_t budget = 0;
   int max_active = 8;
+  int policy = PMG_SERVE_FIFO;
+  double max_wait_s = 2.0;      // shortest-first: a request queued this long goes first
+  double small_work = 0;        // requests below this estimated work get high-priority streams
+  int prio_low = 0, prio_high = 0;
   int64_t used = 0;
   int64_t tick = 0;
   int64_t next_id = 1;
@@ -185,7 +191,10 @@ Slot* acquire_slot(pmg_server* s, Request* r, int* err) {
   }
   if ((int64_t)free_b < r->bytes + (int64_t)(256 << 20)) return nullptr;
   Slot* sl = new Slot();
-  if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // small solves on high-priority streams: their kernels are scheduled ahead
+  // of the pending blocks of large ones, so they are not stuck behind them
+  const int prio = (s->policy == PMG_SERVE_SHORTEST_FIRST && r->work < s->small_work) ? s->prio_high : s->prio_low;
+  if (cudaStreamCreateWithPriority(&sl->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
     cudaGetLastError();
     delete sl;
     *err = fail(PMG_ERR_CUDA, "cudaStreamCreate failed");
@@ -205,6 +214,21 @@ Slot* acquire_slot(pmg_server* s, Request* r, int* err) {
   s->slots.push_back(sl);
   ++s->created_contexts;
   return sl;
+}
+
+// The queued request to admit next: the oldest (FIFO), or the one with the
+// least estimated work, except that requests queued for max_wait_s or longer
+// go first, oldest first (shortest-first with aging, so large requests are
+// not starved).
+std::deque<Request*>::iterator next_request(pmg_server* s) {
+  auto it = s->queue.begin();
+  if (s->policy != PMG_SERVE_SHORTEST_FIRST || s->queue.size() < 2) return it;
+  const double now = now_s();
+  if (now - (*it)->t_submit >= s->max_wait_s) return it;  // the oldest has waited too long
+  auto best = it;
+  for (; it != s->queue.end(); ++it)
+    if ((*it)->work < (*best)->work) best = it;
+  return best;
 }
 
 }  // namespace
@@ -227,6 +251,10 @@ int pmg_server_create(int64_t memory_budget_bytes, int max_active, pmg_server** 
   }
   s->budget = memory_budget_bytes;
   s->max_active = max_active;
+  if (cudaDeviceGetStreamPriorityRange(&s->prio_low, &s->prio_high) != cudaSuccess) {
+    cudaGetLastError();
+    s->prio_low = s->prio_high = 0;
+  }
   now_s();
   *out = s;
   return PMG_OK;
@@ -266,6 +294,14 @@ int pmg_server_submit(pmg_server* s, const pmg_config* cfg, const double* b_host
   r->rtol = rtol;
   r->maxit = maxit;
   r->bytes = bytes;
+  // estimated work: nodes of the finest grid times the degree (a local
+  // p-multigrid solve costs roughly k operations per patch-interior value
+  // more than a low-degree one)
+  {
+    double n1 = (double)cfg->degree * cfg->n_cells + 1, nodes = 1;
+    for (int d = 0; d < cfg->dim; ++d) nodes *= n1;
+    r->work = nodes * (cfg->degree + 2);
+  }
   r->t_submit = now_s();
   s->requests[r->id] = r;
   s->queue.push_back(r);
@@ -275,20 +311,20 @@ int pmg_server_submit(pmg_server* s, const pmg_config* cfg, const double* b_host
 
 int pmg_server_poll(pmg_server* s, int* n_running, int* n_queued) {
   if (!s) return fail(PMG_ERR_ARG, "NULL server");
-  // admit in arrival order
   while (!s->queue.empty() && (int)s->running.size() < s->max_active) {
-    Request* r = s->queue.front();
+    auto pos = next_request(s);
+    Request* r = *pos;
     int err = PMG_OK;
     Slot* sl = acquire_slot(s, r, &err);
     if (err != PMG_OK) {
-      s->queue.pop_front();
+      s->queue.erase(pos);
       r->state = 3;
       r->status = err;
       r->t_done = now_s();
       continue;
     }
     if (!sl) break;  // wait for memory or a slot
-    s->queue.pop_front();
+    s->queue.erase(pos);
     sl->busy = true;
     r->slot = sl;
     r->t_start = now_s();
@@ -337,6 +373,16 @@ int pmg_server_result(pmg_server* s, int64_t id, int* state, pmg_solve_info* inf
   if (t_start) *t_start = r->t_start;
   if (t_done) *t_done = r->t_done;
   return r->state == 3 ? r->status : PMG_OK;
+}
+
+int pmg_server_set_policy(pmg_server* s, int policy, double max_wait_s, double small_work) {
+  if (!s) return fail(PMG_ERR_ARG, "NULL server");
+  if (policy != PMG_SERVE_FIFO && policy != PMG_SERVE_SHORTEST_FIRST) return fail(PMG_ERR_ARG, "unknown policy");
+  if (!(max_wait_s > 0) || small_work < 0) return fail(PMG_ERR_ARG, "max_wait_s > 0, small_work >= 0");
+  s->policy = policy;
+  s->max_wait_s = max_wait_s;
+  s->small_work = small_work;
+  return PMG_OK;
 }
 
 int pmg_server_release(pmg_server* s, int64_t id) {

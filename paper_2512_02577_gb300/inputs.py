@@ -29,18 +29,34 @@ def random_vector(dim, n, k, seed):
     return v
 
 
+# Mesh sizes a served request may have: n = n_0 2^L with a coarse level
+# small enough for the dense coarse solve ((k n_0 - 1)^3 <= 4096), i.e.
+# n_0 = 3 allowed up to degree 5, only n_0 = 1 (powers of two) above.
+SIZES_LOW_DEGREE = (8, 12, 16, 24, 32, 48, 64)
+SIZES_HIGH_DEGREE = (8, 16, 32, 64)
+
+
 def serving_requests(n_requests=256, rate=50.0, arrival_seed=7, size_seed=11, rhs_seed0=1000,
-                     n_lo=8, n_hi=64, k_lo=2, k_hi=7):
+                     n_lo=8, n_hi=64, k_lo=2, k_hi=7, snap="pow2"):
     """Serving workload: Poisson arrivals at ``rate`` per second; cells per
-    side log-uniform in [n_lo, n_hi] snapped in log space to a power of two
-    (so every mesh coarsens to one cell); degree uniform in k_lo..k_hi."""
+    side log-uniform in [n_lo, n_hi], snapped in log space to the nearest
+    allowed size: ``snap="pow2"`` a power of two (every mesh coarsens to one
+    cell), ``snap="coarse"`` the sizes above (with n_0 = 3 meshes for
+    k <= 5); degree uniform in k_lo..k_hi; right-hand-side seed rhs_seed0 + i.
+    The degree is drawn before the size is snapped."""
     ra = np.random.default_rng(arrival_seed)
     rs = np.random.default_rng(size_seed)
     gaps = ra.exponential(1.0 / rate, n_requests)
     t = np.cumsum(gaps) - gaps[0]
     logn = rs.uniform(np.log2(n_lo), np.log2(n_hi), n_requests)
-    ns = (2 ** np.round(logn)).astype(int)
     ks = rs.integers(k_lo, k_hi + 1, n_requests)
+    ns = []
+    for ln, k in zip(logn, ks):
+        if snap == "pow2":
+            ns.append(int(2 ** np.round(ln)))
+        else:
+            allowed = [n for n in (SIZES_LOW_DEGREE if k <= 5 else SIZES_HIGH_DEGREE) if n_lo <= n <= n_hi]
+            ns.append(min(allowed, key=lambda n: (abs(np.log2(n) - ln), n)))
     return [dict(id=i, t_arrival=float(t[i]), n=int(ns[i]), k=int(ks[i]), rhs_seed=rhs_seed0 + i)
             for i in range(n_requests)]
 

@@ -11,7 +11,7 @@ import time
 import numpy as np
 import torch
 
-from . import CARTESIAN, FP32, Server, make_config
+from . import CARTESIAN, FP32, SERVE_FIFO, Server, make_config
 from .inputs import interior_mask
 
 
@@ -25,16 +25,17 @@ def _rhs(dim, n, k, seed):
 
 
 def run(requests, dim=3, precision=FP32, geometry=CARTESIAN, max_active=8, budget=0, rtol=1e-8, maxit=300,
-        time_scale=1.0, poll_sleep=0.0):
+        time_scale=1.0, poll_sleep=0.0, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0):
     """Serve ``requests`` (dicts with t_arrival, n, k, rhs_seed) and return
-    per-request records plus summary statistics."""
+    per-request records plus summary statistics.  policy / max_wait_s /
+    small_work: the server's admission order (pmg_server_set_policy)."""
     prepared = []
     for r in requests:
         cfg = make_config(dim=dim, n_cells=r["n"], degree=r["k"], mg_precision=precision, geometry=geometry)
         b = _rhs(dim, r["n"], r["k"], r["rhs_seed"])
         x = torch.zeros_like(b).pin_memory()
         prepared.append((r, cfg, b, x))
-    server = Server(budget, max_active)
+    server = Server(budget, max_active, policy=policy, max_wait_s=max_wait_s, small_work=small_work)
     ids = {}
     pending = list(range(len(prepared)))
     t0 = time.perf_counter()
