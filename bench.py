@@ -141,18 +141,24 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_child(seconds, n_steps=0):
+def oracle_child(seconds, n_steps=0, case="sample"):
     """Runs in a fresh single-threaded process: time the oracle's step
-    (apply + sweep + PCG solve) on the bounded sample, set-up excluded;
-    exactly n_steps steps if n_steps > 0, else for about ``seconds``."""
+    (apply + sweep + PCG solve) on the bounded sample of the benchmark
+    workload (case "sample": 3D Q4 on ORACLE_N^3 cells) or on the 2D 16x16 Q2
+    three-level problem in full (case "cfg1"), set-up excluded; exactly
+    n_steps steps if n_steps > 0, else for about ``seconds``."""
     import numpy as np
     from oracle import constants, fem, solver
-    m = fem.Mesh(D, ORACLE_N, K)
-    L, nn = 1, ORACLE_N
-    while nn % 2 == 0:
-        nn //= 2
-        L += 1
-    h = solver.Hierarchy(m, L, constants.omega_jacobi(D, K), constants.omega_patch(D))
+    if case == "cfg1":
+        d, n, k, L = 2, 16, 2, 3
+    else:
+        d, n, k = D, ORACLE_N, K
+        L, nn = 1, n
+        while nn % 2 == 0:
+            nn //= 2
+            L += 1
+    m = fem.Mesh(d, n, k)
+    h = solver.Hierarchy(m, L, constants.omega_jacobi(d, k), constants.omega_patch(d))
     b = fem.rhs_manufactured(m)[m.interior_index()]
     fine = h.levels[-1]
     times = []
@@ -166,11 +172,11 @@ def oracle_child(seconds, n_steps=0):
     print(json.dumps({"dofs": m.n_dofs, "times": times, "iterations": it}))
 
 
-def run_oracle(seconds, n_steps=0):
+def run_oracle(seconds, n_steps=0, case="sample"):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(seconds),
-                        "--oracle-steps", str(n_steps)],
+                        "--oracle-steps", str(n_steps), "--oracle-case", case],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle child failed:\n" + r.stderr[-2000:])
@@ -179,7 +185,7 @@ def run_oracle(seconds, n_steps=0):
 
 def cpu_baseline_entry(res):
     t = statistics.median(res["times"])
-    return {"value": res["dofs"] / t, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
+    return {"value": res["dofs"] / t, "unit": "DoFs/s", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": "same step (apply + sweep + PCG/GMG solve to 1e-8, FP64, Q4, 3D, manufactured RHS) on "
                       "4^3 cells (%d DoFs), set-up excluded, median of %d steps, single thread"
                       % (res["dofs"], len(res["times"]))}
@@ -242,19 +248,39 @@ def extra_sections(p, torch, dev, stream, flush):
     del b, b32, y32, x
     out["outer_solvers_32_q4"] = outer_solver_section(p, torch, dev, stream, flush)
     out["distorted_64_q3_mixed"] = distorted_section(p, torch, dev, stream, flush)
+    out["serving_cfg4"] = serving_section(p, torch)
+    return out
+
+
+def serving_section(p, torch):
+    """The served configuration as stated: 256 Poisson solve requests,
+    Poisson arrivals at 50/s (seed 7), n log-uniform in [8, 64] snapped to
+    {8, 12, 16, 24, 32, 48, 64} for k <= 5 and to powers of two above (seed
+    11), k uniform in 2..7, N(0,1) right-hand sides (seeds 1000 + i), FP32
+    V-cycle, FP64 CG to 1e-8, 16 slots, a fresh server per pass.  Passes: the
+    process's first (cold: kernel modules loaded, smoother layouts tuned),
+    then warm passes with the FP64 outer operator and with the float-float
+    one, arrival-order admission."""
+    import numpy as np
     from paper_2512_02577_gb300 import serve
     from paper_2512_02577_gb300.inputs import serving_requests
-    reqs = serving_requests(n_requests=64, rate=50.0, n_hi=32)
-    workload = ("64 Poisson solves, Poisson arrivals 50/s, n in {8,16,32} (log-uniform, snapped), k uniform 2..7, "
-                "N(0,1) RHS, FP32 V-cycle, FP64 CG, rtol 1e-8, 16 slots")
-    # first pass: the process's first contexts of each degree (kernel modules
-    # loaded, smoother blocks tuned); second pass: the same stream again on a
-    # fresh server (every context created anew, per-process caches warm)
-    _, summ = serve.run(reqs, precision=p.FP32, max_active=16)
-    out["serving_sample"] = dict(summ, workload=workload, process="cold")
-    _, summ = serve.run(reqs, precision=p.FP32, max_active=16)
-    out["serving_sample_warm"] = dict(summ, workload=workload, process="warm")
-    return out
+    reqs = serving_requests(n_requests=256, rate=50.0, snap="coarse")
+    t0 = time.perf_counter()
+    bufs = serve.prepare(reqs)
+    prep_s = time.perf_counter() - t0
+    res = {"workload": "256 requests, Poisson arrivals 50/s, n log-uniform 8..64 snapped to "
+                       "{8,12,16,24,32,48,64} (k <= 5) / {8,16,32,64} (k >= 6), k uniform 2..7, N(0,1) RHS, "
+                       "FP32 V-cycle, FP64 CG to 1e-8, 16 slots, FIFO admission",
+           "total_dofs": int(sum((r["k"] * r["n"] + 1) ** 3 for r in reqs)), "prepare_s": prep_s}
+    for label, kw in (("cold_fp64_operator", {}), ("warm_fp64_operator", {}),
+                      ("warm_float_float_operator", dict(outer_apply=p.APPLY_FLOAT_FLOAT))):
+        recs, summ = serve.run(reqs, precision=p.FP32, max_active=16, buffers=bufs, **kw)
+        lat = np.array([r["latency_s"] for r in recs])
+        res[label] = {k: summ[k] for k in ("p50_ms", "p99_ms", "mean_ms", "makespan_s", "dofs_per_s", "failed",
+                                           "max_iterations", "created_contexts")}
+        res[label]["queue_p50_ms"] = float(np.median([r["queue_s"] for r in recs]) * 1e3)
+    del bufs
+    return res
 
 
 def distorted_section(p, torch, dev, stream, flush):
@@ -330,9 +356,11 @@ def outer_solver_section(p, torch, dev, stream, flush):
 
 
 def degree_sweep():
-    """k = 1..8 on the unit cube: apply and sweep at n = round(200/k) (~8M
-    DoFs), FP64 and mixed solves on the nearest power-of-two mesh whose
-    coarse level stays small; N(0,1) right-hand side (seed 20251202 + k)."""
+    """k = 1..8 on the unit cube: apply and smoother step at n = round(200/k)
+    (~8M DoFs; odd n: single-level contexts, the step on that level), FP64,
+    mixed and mixed with the float-float outer operator solves on the
+    nearest power-of-two mesh whose coarse level stays small; N(0,1)
+    right-hand side (seed 20251202 + k)."""
     import torch
     import paper_2512_02577_gb300 as p
     from paper_2512_02577_gb300.inputs import random_vector
@@ -356,27 +384,27 @@ def degree_sweep():
                 row["dofs_apply"] = N
                 row["apply_%s_ms" % tag] = ta
                 row["apply_%s_gdofs" % tag] = N / ta / 1e6
-                if n % 2 == 0:
-                    ph = ctx.smoother_phase_times(reps=2)
-                    row["sweep_%s_ms" % tag] = sum(ph)
-                    row["sweep_%s_gdofs" % tag] = N / sum(ph) / 1e6
+                ph = ctx.smoother_phase_times(reps=2)   # finest level (odd n: the single level)
+                row["sweep_%s_ms" % tag] = sum(ph)
+                row["sweep_%s_gdofs" % tag] = N / sum(ph) / 1e6
                 ctx.close()
             ns = 2 ** int(round(__import__("math").log2(200.0 / k)))
             row["n_solve"] = ns
-            for prec in (p.FP64, p.FP32):
-                ctx = p.Context(p.make_config(dim=3, n_cells=ns, degree=k, mg_precision=prec), stream=stream,
-                                device=dev)
+            for prec, apply, tag in ((p.FP64, p.APPLY_FP64, "fp64"), (p.FP32, p.APPLY_FP64, "mixed"),
+                                     (p.FP32, p.APPLY_FLOAT_FLOAT, "mixed_ff")):
+                ctx = p.Context(p.make_config(dim=3, n_cells=ns, degree=k, mg_precision=prec, outer_apply=apply),
+                                stream=stream, device=dev)
                 b = torch.tensor(random_vector(3, ns, k, seed=20251202 + k), device=dev)
                 x = torch.zeros_like(b)
                 ctx.solve(b, x)
                 infos = [ctx.solve(b, x) for _ in range(2)]
-                tag = "fp64" if prec == p.FP64 else "mixed"
                 row["dofs_solve"] = ctx.num_dofs()
                 row["solve_%s_ms" % tag] = min(i.time_ms for i in infos)
                 row["iterations_%s" % tag] = infos[-1].iterations
                 row["rel_residual_%s" % tag] = infos[-1].rel_residual
                 ctx.close()
             row["mixed_speedup"] = row["solve_fp64_ms"] / row["solve_mixed_ms"]
+            row["mixed_ff_speedup"] = row["solve_fp64_ms"] / row["solve_mixed_ff_ms"]
             print(json.dumps(row), flush=True)
             rows.append(row)
     print(json.dumps({"degree_sweep": rows}))
@@ -455,6 +483,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-child", type=float, default=None)
     ap.add_argument("--oracle-steps", type=int, default=0)
+    ap.add_argument("--oracle-case", default="sample", choices=["sample", "cfg1"])
     ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "deformed"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
     ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
@@ -462,7 +491,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="degree sweep k = 1..8 at ~8M DoFs (separate JSON)")
     args = ap.parse_args()
     if args.oracle_child is not None:
-        oracle_child(args.oracle_child, args.oracle_steps)
+        oracle_child(args.oracle_child, args.oracle_steps, args.oracle_case)
         return
     if args.profile_region:
         profile_region(args.profile_region, args.profile_n)
@@ -502,9 +531,14 @@ def main():
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     # CPU baseline before any GPU work of this process's children
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_entry(run_oracle(args.oracle_seconds))
+        r1 = run_oracle(min(args.oracle_seconds, 5.0), case="cfg1")
+        t1 = statistics.median(r1["times"])
+        cpu1 = {"workload": "2D unit square, 16x16 Q2, 3 levels (1,089 DoFs), manufactured RHS, in full",
+                "step_ms": t1 * 1e3, "dofs_per_s": r1["dofs"] / t1, "cg_iterations": r1["iterations"],
+                "cores": 1, "host_cores": os.cpu_count(), "steps": len(r1["times"])}
 
     stream = torch.cuda.Stream(device=dev)
     cfg = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP64)
@@ -590,6 +624,23 @@ def main():
         ctx.solve(b, xs)
         l2err64 = ctx.l2_error_manufactured(xs)
         solve32 = [i.time_ms for i in info32]
+        # mixed precision with the float-float outer operator
+        ctxff = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32,
+                                        outer_apply=p.APPLY_FLOAT_FLOAT), stream=stream, device=dev)
+        infoff = []
+        for _ in range(2):
+            ctxff.solve(b, xs)
+        for _ in range(max(args.steps, 5)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            infoff.append(ctxff.solve(b, xs, rtol=1e-8))
+        Axs = torch.empty_like(xs)
+        ctx.apply(xs, Axs)                        # true residual with the FP64 operator
+        true_res_ff = float(torch.linalg.norm(b - Axs) / torch.linalg.norm(b))
+        l2err_ff = ctxff.l2_error_manufactured(xs)
+        t_apply_ff = timed(lambda: ctxff.apply(xa, ya), 20)
+        solveff = [i.time_ms for i in infoff]
+        ctxff.close()
 
         # roofline of the dominant kernel: the FP64 patch launch (every local
         # solve of the finest level), timed live on the library's stream
@@ -648,6 +699,11 @@ def main():
         "solve_mixed_ms": {"p50": pct(solve32, 50), "p99": pct(solve32, 99), "iterations": info32[-1].iterations,
                            "rel_residual": info32[-1].rel_residual, "l2_error": l2err},
         "mixed_speedup_vs_fp64": pct(solve64, 50) / pct(solve32, 50),
+        "solve_mixed_float_float_operator_ms": {
+            "p50": pct(solveff, 50), "p99": pct(solveff, 99), "iterations": infoff[-1].iterations,
+            "rel_residual": infoff[-1].rel_residual, "true_rel_residual_fp64_operator": true_res_ff,
+            "l2_error": l2err_ff, "apply_ms": statistics.median(t_apply_ff),
+            "speedup_vs_fp64": pct(solve64, 50) / pct(solveff, 50)},
         "roofline": {"kernel": "patch_cart_kernel<3,double> (all 29,791 patches of the finest level)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": PATCH64_TRAFFIC_BYTES,
@@ -664,6 +720,7 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+        line["cpu_oracle_2d_16_q2"] = cpu1
     line.update(extra)
     print(json.dumps(line))
 

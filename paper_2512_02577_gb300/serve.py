@@ -24,16 +24,29 @@ def _rhs(dim, n, k, seed):
     return b
 
 
+def prepare(requests, dim=3):
+    """Pinned host right-hand sides (N(0,1), seed rhs_seed) and solution
+    buffers for ``requests``; pass the result to run() to reuse them."""
+    out = []
+    for r in requests:
+        b = _rhs(dim, r["n"], r["k"], r["rhs_seed"])
+        out.append((b, torch.zeros_like(b).pin_memory()))
+    return out
+
+
 def run(requests, dim=3, precision=FP32, geometry=CARTESIAN, max_active=8, budget=0, rtol=1e-8, maxit=300,
-        time_scale=1.0, poll_sleep=0.0, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0):
+        time_scale=1.0, poll_sleep=0.0, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0, buffers=None,
+        **config):
     """Serve ``requests`` (dicts with t_arrival, n, k, rhs_seed) and return
     per-request records plus summary statistics.  policy / max_wait_s /
-    small_work: the server's admission order (pmg_server_set_policy)."""
+    small_work: the server's admission order (pmg_server_set_policy);
+    buffers: prepare(requests) to reuse; config: further make_config
+    arguments (e.g. outer_apply) for every request."""
+    buffers = prepare(requests, dim) if buffers is None else buffers
     prepared = []
-    for r in requests:
-        cfg = make_config(dim=dim, n_cells=r["n"], degree=r["k"], mg_precision=precision, geometry=geometry)
-        b = _rhs(dim, r["n"], r["k"], r["rhs_seed"])
-        x = torch.zeros_like(b).pin_memory()
+    for r, (b, x) in zip(requests, buffers):
+        cfg = make_config(dim=dim, n_cells=r["n"], degree=r["k"], mg_precision=precision, geometry=geometry, **config)
+        x.zero_()
         prepared.append((r, cfg, b, x))
     server = Server(budget, max_active, policy=policy, max_wait_s=max_wait_s, small_work=small_work)
     ids = {}
