@@ -218,8 +218,217 @@ __global__ void __launch_bounds__(256) cell_gather_kernel(const T* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Deformed apply for degrees K <= 3 in 3D: one half-warp per cell, every 1D
+// contraction in registers.  Each of the (K+1)^2 active lanes owns one line
+// of K+1 values along x (lane (y, z)), y (lane (x, z)) or z (lane (x, y));
+// between directions the lines are transposed through a padded shared tile
+// of the cell (each value stored and loaded once, __syncwarp only).  The
+// gradient at the Gauss points is formed with the derivative folded into
+// the interpolation passes (DS = Dq S: derivative of the nodal basis at the
+// points): grad_x = S_z S_y DS_x u, grad_y = S_z DS_y S_x u, grad_z =
+// DS_z S_y S_x u; after the q-op with the stored G_q, the transposed passes
+// run in reverse.  Cells of one parity colour share no node, so launch c
+// adds the contributions of the cells of colour c straight into y: the
+// cell of lowest colour among those holding a node (even parity in every
+// direction in which the node is shared) initialises it (y = s, or b - s),
+// the others add -- deterministic, no per-cell buffer, no atomics.
+template <typename T>
+struct DefFast {
+  static constexpr int n1 = K + 1;
+  static constexpr int PY = n1;                                 // tile row pitch
+  static constexpr int PZ = n1 * n1 + (n1 == 4 ? 4 : 1);        // tile plane pitch (bank spread)
+  static constexpr int TILE = PZ * n1;
+  static constexpr int CELL = 3 * TILE;                         // three tiles per cell
+  static constexpr int CELLS = 16;                              // cells (half-warps) per 256-thread block
+};
+
+template <bool RESID, typename T>
+__global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, T* __restrict__ y,
+                                                       const T* __restrict__ b, const float* __restrict__ G, int n,
+                                                       int colour) {
+  using F = DefFast<T>;
+  constexpr int n1 = F::n1, NP = n1 * n1 * n1, L = nlev(K) - 1;
+  constexpr int PY = F::PY, PZ = F::PZ, TILE = F::TILE;
+  __shared__ T tiles[F::CELLS * F::CELL];
+  constexpr int OS = LAY.S[L], OD = LAY.Dq[L];
+  const double* C = ctab<double>();
+  auto S = [&](int q, int a) -> T { return (T)C[OS + q * n1 + a]; };
+  auto DS = [&](int q, int a) -> T {  // derivative of nodal basis a at point q
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < n1; ++j) s += C[OD + q * n1 + j] * C[OS + j * n1 + a];
+    return (T)s;
+  };
+  const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
+  const bool on = lane < n1 * n1;
+  const int la = on ? lane % n1 : 0, lb = on ? lane / n1 : 0;
+  T* tl = tiles + hw * F::CELL;
+  // this half-warp's cell among those of parity colour `colour`
+  int bit[3], cnt[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    bit[d] = (colour >> d) & 1;
+    cnt[d] = (n - bit[d] + 1) / 2;
+  }
+  const int64_t ncol = (int64_t)cnt[0] * cnt[1] * cnt[2];
+  const int64_t cid = (int64_t)blockIdx.x * F::CELLS + hw;
+  const bool live = on && cid < ncol;
+  int c[3];
+  {
+    int64_t t = live ? cid : 0;
+    c[0] = bit[0] + 2 * (int)(t % cnt[0]);
+    t /= cnt[0];
+    c[1] = bit[1] + 2 * (int)(t % cnt[1]);
+    c[2] = bit[2] + 2 * (int)(t / cnt[1]);
+  }
+  const int N1 = K * n + 1;
+  // transposes through tile k: element (ix, iy, iz) at ix + PY iy + PZ iz
+  auto put = [&](int k, int ix, int iy, int iz, T v) { if (on) tl[k * TILE + ix + PY * iy + PZ * iz] = v; };
+  auto get = [&](int k, int ix, int iy, int iz) -> T { return on ? tl[k * TILE + ix + PY * iy + PZ * iz] : T(0); };
+
+  // ---- every global load of the cell first (one memory latency per cell):
+  // the nodal x-line, the value each output node starts from (y of an
+  // earlier colour, b, or nothing), and G_q at this lane's points of the
+  // z-line ownership used by the q-op
+  T u[n1], prior[n1];
+  bool first[n1], bnd[n1];
+  const int gy = K * c[1] + la, gz = K * c[2] + lb;
+  const bool yz_bnd = gy == 0 || gy == N1 - 1 || gz == 0 || gz == N1 - 1;
+  const int64_t row = (int64_t)N1 * (gy + (int64_t)N1 * gz) + K * c[0];
+#pragma unroll
+  for (int i = 0; i < n1; ++i) {
+    const int gx = K * c[0] + i;
+    bnd[i] = yz_bnd || gx == 0 || gx == N1 - 1;
+    const int li[3] = {i, la, lb};
+    bool f = true;  // lowest colour among the cells holding this node
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const bool shared = (li[d] == 0 && c[d] > 0) || (li[d] == K && c[d] < n - 1);
+      if (shared && (c[d] & 1)) f = false;
+    }
+    first[i] = f;
+    u[i] = (live && !bnd[i]) ? x[row + i] : T(0);
+    prior[i] = (live && !bnd[i]) ? (f ? (RESID ? b[row + i] : T(0)) : y[row + i]) : T(0);
+  }
+  const int64_t cell = c[0] + (int64_t)n * (c[1] + (int64_t)n * c[2]);
+  const float* Gc = G + cell * 6 * NP + la + n1 * lb;
+  float gq[6][n1];
+#pragma unroll
+  for (int q = 0; q < n1; ++q)
+#pragma unroll
+    for (int m = 0; m < 6; ++m) gq[m][q] = live ? Gc[m * NP + n1 * n1 * q] : 0.f;
+  T P[n1], Pd[n1];
+#pragma unroll
+  for (int q = 0; q < n1; ++q) {
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int i = 0; i < n1; ++i) { s0 += S(q, i) * u[i]; s1 += DS(q, i) * u[i]; }
+    P[q] = s0;
+    Pd[q] = s1;
+  }
+  // ---- X -> Y: lane (x = la, z = lb)
+#pragma unroll
+  for (int q = 0; q < n1; ++q) { put(0, q, la, lb, P[q]); put(1, q, la, lb, Pd[q]); }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < n1; ++j) { P[j] = get(0, la, j, lb); Pd[j] = get(1, la, j, lb); }
+  __syncwarp();
+  T Q[n1], Qx[n1], Qy[n1];  // S_y P, S_y P', DS_y P
+#pragma unroll
+  for (int q = 0; q < n1; ++q) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+    for (int j = 0; j < n1; ++j) { s0 += S(q, j) * P[j]; s1 += S(q, j) * Pd[j]; s2 += DS(q, j) * P[j]; }
+    Q[q] = s0;
+    Qx[q] = s1;
+    Qy[q] = s2;
+  }
+  // ---- Y -> Z: lane (x = la, y = lb)
+#pragma unroll
+  for (int q = 0; q < n1; ++q) { put(0, la, q, lb, Q[q]); put(1, la, q, lb, Qx[q]); put(2, la, q, lb, Qy[q]); }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < n1; ++k) { Q[k] = get(0, la, lb, k); Qx[k] = get(1, la, lb, k); Qy[k] = get(2, la, lb, k); }
+  __syncwarp();
+  // gradients at the points (la, lb, q) and the q-op with G_q
+  T fx[n1], fy[n1], fz[n1];
+#pragma unroll
+  for (int q = 0; q < n1; ++q) {
+    T gx = T(0), gy2 = T(0), gz2 = T(0);
+#pragma unroll
+    for (int k = 0; k < n1; ++k) { gx += S(q, k) * Qx[k]; gy2 += S(q, k) * Qy[k]; gz2 += DS(q, k) * Q[k]; }
+    const T G00 = (T)gq[0][q], G01 = (T)gq[1][q], G02 = (T)gq[2][q];
+    const T G11 = (T)gq[3][q], G12 = (T)gq[4][q], G22 = (T)gq[5][q];
+    fx[q] = G00 * gx + G01 * gy2 + G02 * gz2;
+    fy[q] = G01 * gx + G11 * gy2 + G12 * gz2;
+    fz[q] = G02 * gx + G12 * gy2 + G22 * gz2;
+  }
+  // ---- transposed passes: Z-own A1 = S_z^T fx, A2 = S_z^T fy, A3 = DS_z^T fz
+#pragma unroll
+  for (int k = 0; k < n1; ++k) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+    for (int q = 0; q < n1; ++q) { s0 += S(q, k) * fx[q]; s1 += S(q, k) * fy[q]; s2 += DS(q, k) * fz[q]; }
+    Q[k] = s0;
+    Qx[k] = s1;
+    Qy[k] = s2;
+  }
+  // ---- Z -> Y: lane (x = la, z = lb)
+#pragma unroll
+  for (int k = 0; k < n1; ++k) { put(0, la, lb, k, Q[k]); put(1, la, lb, k, Qx[k]); put(2, la, lb, k, Qy[k]); }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < n1; ++q) { Q[q] = get(0, la, q, lb); Qx[q] = get(1, la, q, lb); Qy[q] = get(2, la, q, lb); }
+  __syncwarp();
+  // B1 = S_y^T A1, B23 = DS_y^T A2 + S_y^T A3
+#pragma unroll
+  for (int j = 0; j < n1; ++j) {
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int q = 0; q < n1; ++q) { s0 += S(q, j) * Q[q]; s1 += DS(q, j) * Qx[q] + S(q, j) * Qy[q]; }
+    P[j] = s0;
+    Pd[j] = s1;
+  }
+  // ---- Y -> X: lane (y = la, z = lb)
+#pragma unroll
+  for (int j = 0; j < n1; ++j) { put(0, la, j, lb, P[j]); put(1, la, j, lb, Pd[j]); }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < n1; ++q) { P[q] = get(0, q, la, lb); Pd[q] = get(1, q, la, lb); }
+  // out = DS_x^T B1 + S_x^T B23, added into y node by node
+#pragma unroll
+  for (int i = 0; i < n1; ++i) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < n1; ++q) s += DS(q, i) * P[q] + S(q, i) * Pd[q];
+    if (!live || (bnd[i] && !first[i])) continue;
+    y[row + i] = bnd[i] ? T(0) : (RESID ? prior[i] - s : prior[i] + s);
+  }
+}
+
+// true when the fast deformed apply covers this degree, dimension and
+// precision: FP32 only -- it spends about 28% more multiply-adds per cell than
+// the shared-memory cell operator (the derivative folded into the
+// interpolation passes), which pays where memory bounds the apply (FP32) and
+// not where GB300's FP64 rate does
+template <int DIM, typename T>
+constexpr bool def_fast_ok() { return DIM == 3 && K <= 3 && sizeof(T) == 4; }
+
 template <int DIM, typename T>
 static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, T* cellbuf, int n, cudaStream_t st) {
+  if constexpr (def_fast_ok<DIM, T>()) {
+    for (int colour = 0; colour < 8; ++colour) {
+      int64_t ncol = 1;
+      for (int d = 0; d < 3; ++d) ncol *= (n - ((colour >> d) & 1) + 1) / 2;
+      if (ncol == 0) continue;
+      const unsigned blocks = (unsigned)((ncol + DefFast<T>::CELLS - 1) / DefFast<T>::CELLS);
+      if (b) def_fast_kernel<true, T><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
+      else def_fast_kernel<false, T><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
+      g_launches += 1;
+    }
+    return cudaGetLastError();
+  }
   constexpr int n1 = K + 1;
   constexpr int NP = ipow(n1, DIM);
   constexpr int LINES = ipow(n1, DIM - 1);
