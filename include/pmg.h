@@ -131,6 +131,10 @@ typedef struct pmg_config {
   int patch_threads;   /* PMG_PATCH_INTERLEAVED: threads per block (multiple of 32), 0 = autotuned */
   int outer_apply;     /* arithmetic of every FP64 operator apply (pmg_apply / pmg_residual with PMG_FP64,
                           the outer solver's A p and residuals): enum pmg_outer_apply */
+  int geom_precision;  /* deformed and distorted geometry: storage of the quadrature-point tensors G_q
+                          (6 components per Gauss point in 3D): PMG_FP32 (default; the discrete operator
+                          of every precision is the one of the rounded G_q) or PMG_FP64 (twice the bytes;
+                          the FP64 operator then uses G_q as computed) */
 } pmg_config;
 
 typedef struct pmg_solve_info {

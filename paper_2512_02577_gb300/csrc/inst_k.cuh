@@ -248,7 +248,8 @@ static int max_threads_of(const void* k) {
 
 static int patch_max_threads(int dim, int prec, int deformed) {
   if (!mine(dim, prec)) return 0;
-  return deformed ? max_threads_of((const void*)patch_def_kernel<DP, TP>)
+  return deformed ? std::min(max_threads_of((const void*)patch_def_kernel<DP, TP, float>),
+                             max_threads_of((const void*)patch_def_kernel<DP, TP, double>))
                   : max_threads_of((const void*)patch_cart_kernel<DP, TP>);
 }
 
@@ -266,8 +267,10 @@ static cudaError_t prepare() {
   auto acc = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
   acc(allow_smem(patch_cart_kernel<DP, TP>, optin));
   if (patch_il<DP, TP>() > 0) acc(allow_smem(patch_cart_il_kernel<DP, TP>, optin));
-  acc(allow_smem(patch_def_kernel<DP, TP>, optin));
-  acc(allow_smem(def_cell_kernel<DP, TP>, optin));
+  acc(allow_smem(patch_def_kernel<DP, TP, float>, optin));
+  acc(allow_smem(patch_def_kernel<DP, TP, double>, optin));
+  acc(allow_smem(def_cell_kernel<DP, TP, float>, optin));
+  acc(allow_smem(def_cell_kernel<DP, TP, double>, optin));
   return r;
 }
 

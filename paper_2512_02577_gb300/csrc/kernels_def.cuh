@@ -3,8 +3,8 @@
 // per cell, interpolate the nodal values from the Gauss-Lobatto nodes to the
 // (p+1)^d Gauss points (d 1D contractions with S), take reference gradients
 // by collocation derivatives at the Gauss points (Dq), multiply by the stored
-// symmetric tensor G_q = w_q det J J^{-1} J^{-T} (float32, §3's
-// quadrature-point "evaluation kernel"), and apply the transposed steps.
+// symmetric tensor G_q = w_q det J J^{-1} J^{-T} (stored in FP32 or FP64,
+// §3's quadrature-point "evaluation kernel"), and apply the transposed steps.
 // Cells of one parity colour share no node, so colour-by-colour launches
 // accumulate without atomics and in a fixed order.
 #pragma once
@@ -80,7 +80,7 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
     pfor_n<NC * NP>(ng, [&](int g, int t) {
       const int c = t / NP, q = t - c * NP;
       T* A = tile(g, c);
-      const float* Gc = gptr(g, c);
+      const auto* Gc = gptr(g, c);
       const T g0 = A[B0 + q], g1 = A[B1 + q], g2 = A[B2 + q];
       const T G00 = (T)Gc[0 * NP + q], G01 = (T)Gc[1 * NP + q], G02 = (T)Gc[2 * NP + q];
       const T G11 = (T)Gc[3 * NP + q], G12 = (T)Gc[4 * NP + q], G22 = (T)Gc[5 * NP + q];
@@ -112,7 +112,7 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
     pfor_n<NC * NP>(ng, [&](int g, int t) {
       const int c = t / NP, q = t - c * NP;
       T* A = tile(g, c);
-      const float* Gc = gptr(g, c);
+      const auto* Gc = gptr(g, c);
       const T g0 = A[B0 + q], g1 = A[B1 + q];
       const T G00 = (T)Gc[0 * NP + q], G01 = (T)Gc[1 * NP + q], G11 = (T)Gc[2 * NP + q];
       A[B0 + q] = G00 * g0 + G01 * g1;
@@ -139,9 +139,9 @@ __device__ __forceinline__ void cell_op(int ng, const Tile& tile, const GPtr& gp
 // Global deformed apply, all cells in one launch: the cell results go to a
 // per-cell buffer (cell-major, (K+1)^DIM values each) and cell_gather_kernel
 // sums, per node, the contributions of the (at most 2^d) cells holding it in
-// a fixed order.  `cpb` cells per block.
-template <int DIM, typename T>
-__global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ cellout, const float* __restrict__ G, int n,
+// a fixed order.  `cpb` cells per block.  TG: storage type of G_q.
+template <int DIM, typename T, typename TG>
+__global__ void def_cell_kernel(const T* __restrict__ x, T* __restrict__ cellout, const TG* __restrict__ G, int n,
                                 int cpb) {
   constexpr int l = nlev(K) - 1;
   constexpr int n1 = K + 1;
@@ -415,9 +415,9 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
 template <int DIM, typename T>
 constexpr bool def_fast_ok() { return DIM == 3 && K <= 3 && sizeof(T) == 4; }
 
-template <int DIM, typename T>
-static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, T* cellbuf, int n, cudaStream_t st) {
-  if constexpr (def_fast_ok<DIM, T>()) {
+template <int DIM, typename T, typename TG>
+static cudaError_t def_apply_t(const T* x, T* y, const T* b, const TG* G, T* cellbuf, int n, cudaStream_t st) {
+  if constexpr (def_fast_ok<DIM, T>() && sizeof(TG) == 4) {
     for (int colour = 0; colour < 8; ++colour) {
       int64_t ncol = 1;
       for (int d = 0; d < 3; ++d) ncol *= (n - ((colour >> d) & 1) + 1) / 2;
@@ -440,18 +440,20 @@ static cudaError_t def_apply_t(const T* x, T* y, const T* b, const float* G, T* 
   const int smem = cpb * 5 * NP * (int)sizeof(T);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
   const int64_t ncell = DIM == 3 ? (int64_t)n * n * n : (int64_t)n * n;
-  def_cell_kernel<DIM, T><<<(unsigned)((ncell + cpb - 1) / cpb), threads, smem, st>>>(x, cellbuf, G, n, cpb);
+  def_cell_kernel<DIM, T, TG><<<(unsigned)((ncell + cpb - 1) / cpb), threads, smem, st>>>(x, cellbuf, G, n, cpb);
   const int64_t N = ipow(K * n + 1, DIM);
   cell_gather_kernel<DIM, T><<<grid_for(N, 256), 256, 0, st>>>(cellbuf, y, b, n);
   g_launches += 2;
   return cudaGetLastError();
 }
 
-static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const void* b, const float* G, void* cellbuf,
-                             int n, cudaStream_t s) {
+static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const void* b, const void* G, int gprec,
+                             void* cellbuf, int n, cudaStream_t s) {
   if (dim != PMG_DIM || prec != PMG_PREC) return cudaErrorInvalidValue;
   using TP = std::conditional_t<PMG_PREC == 0, double, float>;
-  return def_apply_t<PMG_DIM, TP>((const TP*)x, (TP*)y, (const TP*)b, G, (TP*)cellbuf, n, s);
+  if (gprec == 0)
+    return def_apply_t<PMG_DIM, TP, double>((const TP*)x, (TP*)y, (const TP*)b, (const double*)G, (TP*)cellbuf, n, s);
+  return def_apply_t<PMG_DIM, TP, float>((const TP*)x, (TP*)y, (const TP*)b, (const float*)G, (TP*)cellbuf, n, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -479,9 +481,9 @@ struct DefShape {
   static constexpr int elems() { return PS::ELEMS + WORK; }
 };
 
-template <typename T>
+template <typename T, typename TG>
 struct DefLevelT {
-  const float* G[4];
+  const TG* G[4];
   const T* dinv[4];
 };
 
@@ -557,9 +559,9 @@ __device__ __forceinline__ void patch_axis(const T* Sm, const T* Dm, const PBloc
 
 // Deformed patch geometry: patch vmult by patch-level sum factorisation
 // (§3.2.1); inverse diagonals from the level's global degree-p diagonals.
-template <int DIM, typename T>
+template <int DIM, typename T, typename TG>
 struct DefGeo {
-  DefLevelT<T> lev;
+  DefLevelT<T, TG> lev;
   const PatchMeta* meta;
   const T* inv_a0;  // per patch of the block (shared memory)
   int n;
@@ -623,7 +625,7 @@ struct DefGeo {
       const int* v = meta[g].v;
       const int64_t cell = (v[0] - 1 + (c & 1)) +
                            (int64_t)n * ((v[1] - 1 + ((c >> 1) & 1)) + (int64_t)n * (DIM == 3 ? v[2] - 1 + ((c >> 2) & 1) : 0));
-      const float* Gc = lev.G[l] + cell * ncomp<DIM>() * NPc + pt;
+      const TG* Gc = lev.G[l] + cell * ncomp<DIM>() * NPc + pt;
       if constexpr (DIM == 3) {
         const T g0 = sm[GX + qi], g1 = sm[GY + qi], g2 = sm[GZ + qi];
         const T G00 = (T)Gc[0], G01 = (T)Gc[NPc], G02 = (T)Gc[2 * NPc];
@@ -669,9 +671,9 @@ struct DefGeo {
   }
 };
 
-template <int DIM, typename T>
+template <int DIM, typename T, typename TG>
 __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
-                                 DefLevelT<T> lev, const T* __restrict__ dinv1, PatchParams<T> P) {
+                                 DefLevelT<T, TG> lev, const T* __restrict__ dinv1, PatchParams<T> P) {
   using S = PatchShape<DIM>;
   using DS = DefShape<DIM>;
   constexpr int SZT = S::SZT;
@@ -694,7 +696,7 @@ __global__ void patch_def_kernel(const T* __restrict__ r, T* __restrict__ dst, i
     pb.at(g)[RT + i] = m.active ? r[patch_node<DIM>(m, i, N1)] : T(0);
   });
   __syncthreads();
-  DefGeo<DIM, T> geo;
+  DefGeo<DIM, T, TG> geo;
   geo.lev = lev;
   geo.meta = meta;
   geo.inv_a0 = inv_a0;
@@ -722,7 +724,7 @@ static int patch_def_smem(int dim, int prec, int n_iter) {
   return elems * es;
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, typename TG>
 static cudaError_t patch_def_t(const T* r, T* dst, int n, int np, int n_iter, const DefLevel& L,
                                const PatchParamsHost& H, cudaStream_t st) {
   const int64_t npatch = patch_count(DIM, n, H.colour);
@@ -731,14 +733,14 @@ static cudaError_t patch_def_t(const T* r, T* dst, int n, int np, int n_iter, co
   const int smem = np * patch_def_smem(DIM, sizeof(T) == 8 ? 0 : 1, n_iter);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
   const int threads = std::min(1024, (np * DefShape<DIM>::LINES + 31) / 32 * 32);
-  DefLevelT<T> lev;
+  DefLevelT<T, TG> lev;
   for (int i = 0; i < 4; ++i) {
-    lev.G[i] = L.G[i];
+    lev.G[i] = (const TG*)L.G[i];
     lev.dinv[i] = (const T*)L.dinv[i];
   }
   const unsigned blocks = (unsigned)((npatch + np - 1) / np);
-  patch_def_kernel<DIM, T><<<blocks, threads, smem, st>>>(r, dst, n, np, n_iter, lev, (const T*)L.dinv1,
-                                                          to_params<T>(H));
+  patch_def_kernel<DIM, T, TG><<<blocks, threads, smem, st>>>(r, dst, n, np, n_iter, lev, (const T*)L.dinv1,
+                                                              to_params<T>(H));
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -747,7 +749,8 @@ static cudaError_t patch_def(int dim, int prec, const void* r, void* dst, int n,
                              const DefLevel& L, const PatchParamsHost& P, cudaStream_t s) {
   if (dim != PMG_DIM || prec != PMG_PREC) return cudaErrorInvalidValue;
   using TP = std::conditional_t<PMG_PREC == 0, double, float>;
-  return patch_def_t<PMG_DIM, TP>((const TP*)r, (TP*)dst, n, np, n_iter, L, P, s);
+  if (L.gprec == 0) return patch_def_t<PMG_DIM, TP, double>((const TP*)r, (TP*)dst, n, np, n_iter, L, P, s);
+  return patch_def_t<PMG_DIM, TP, float>((const TP*)r, (TP*)dst, n, np, n_iter, L, P, s);
 }
 
 }  // namespace PMG_KNS

@@ -95,14 +95,14 @@ struct LevelData {
   void *b = nullptr, *u = nullptr, *r = nullptr;  // MG precision
   double scale = 1.0;                             // h^{d-2}
   double inv_a0 = 0.0;                            // Cartesian 1 / A_{j,1}
-  float* G[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* G[4] = {nullptr, nullptr, nullptr, nullptr};  // G_q per p-level (FP64 or FP32: geom_precision)
   void* dinv[4] = {nullptr, nullptr, nullptr, nullptr};
   void* dinv1 = nullptr;
 };
 
 // Byte layout of every device array of a context.
 struct Plan {
-  int dim = 3, K = 2, nlev = 1, nplev = 1, n0 = 1, mg_es = 8;
+  int dim = 3, K = 2, nlev = 1, nplev = 1, n0 = 1, mg_es = 8, g_es = 4;
   bool deformed = false, mg32 = false;
   std::vector<int> ns;
   int nc = 0;  // free DoFs on the coarsest level (0 if above the dense limit)
@@ -155,6 +155,8 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_ARG, "unknown outer_apply");
   if (cfg->outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT && cfg->geometry != PMG_GEOM_CARTESIAN)
     return fail(PMG_ERR_UNSUPPORTED, "the float-float operator is Cartesian only");
+  if (cfg->geom_precision != PMG_FP64 && cfg->geom_precision != PMG_FP32)
+    return fail(PMG_ERR_ARG, "unknown geom_precision");
   if (cfg->patches_per_block < 0 || cfg->patch_threads < 0)
     return fail(PMG_ERR_ARG, "patches_per_block, patch_threads >= 0");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
@@ -164,6 +166,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   P.deformed = cfg->geometry != PMG_GEOM_CARTESIAN;  // general geometry: stored G_q
   P.mg32 = cfg->mg_precision == PMG_FP32;
   P.mg_es = P.mg32 ? 4 : 8;
+  P.g_es = cfg->geom_precision == PMG_FP64 ? 8 : 4;
   P.nplev = nlev(P.K);
   // mesh levels: n_l = n_0 2^l
   int n = cfg->n_cells, L = cfg->n_levels;
@@ -206,7 +209,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
         const int p = plev(P.K, pl);
         const bool top = pl == P.nplev - 1;
         if (!top && !smoothed) continue;  // coarsest level: only the operator itself
-        o.G[pl] = bump(cur, ipow64(nl, P.dim) * ipow64(p + 1, P.dim) * ncomp * 4);
+        o.G[pl] = bump(cur, ipow64(nl, P.dim) * ipow64(p + 1, P.dim) * ncomp * P.g_es);
         if (smoothed && pl > 0) o.dinv[pl] = bump(cur, ipow64((int64_t)p * nl + 1, P.dim) * P.mg_es);
       }
       if (smoothed) o.dinv1 = bump(cur, ipow64(nl + 1, P.dim) * P.mg_es);
@@ -355,7 +358,8 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
     e = c->kt[PMG_FP64]->cart_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b, c->t64[0], c->t64[1],
                                        c->t64[2], c->t64[3], L.n, L.scale, c->stream);
   } else if (c->deformed) {
-    e = c->kt[prec]->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cellbuf, L.n, c->stream);
+    e = c->kt[prec]->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cfg.geom_precision, c->cellbuf, L.n,
+                               c->stream);
   } else {
     void** t = prec == PMG_FP64 ? (void**)c->t64 : c->t_mg;
     e = c->kt[prec]->cart_apply(c->dim, prec, u, r, b, t[0], t[1], t[2], t[3], L.n, L.scale, c->stream);
@@ -387,6 +391,7 @@ int patch_solves(pmg_ctx* c, int level, const void* r, int colour = -1, void* u 
     DefLevel D{};
     for (int i = 0; i < 4; ++i) {
       D.G[i] = L.G[i];
+      D.gprec = c->cfg.geom_precision;
       D.dinv[i] = L.dinv[i];
     }
     D.dinv1 = L.dinv1;
@@ -771,7 +776,7 @@ int setup_context(pmg_ctx* c) {
     // Cartesian A_{j,1} = h^{d-2} d (2) (2/3)^{d-1}
     D.inv_a0 = 1.0 / (D.scale * c->dim * 2.0 * std::pow(2.0 / 3.0, c->dim - 1));
     for (int i = 0; i < 4; ++i) {
-      D.G[i] = (float*)at(c, P.lo[l].G[i]);
+      D.G[i] = at(c, P.lo[l].G[i]);
       D.dinv[i] = at(c, P.lo[l].dinv[i]);
     }
     D.dinv1 = at(c, P.lo[l].dinv1);
@@ -873,13 +878,16 @@ int setup_context(pmg_ctx* c) {
       for (int pl = 0; pl < c->nplev; ++pl) {
         if (!D.G[pl]) continue;
         const int p = plev(c->K, pl);
-        PMG_CUDA(compute_geometry(c->dim, D.n, p, geom_desc(c), make_tab(p, p + 1), D.G[pl], geobad, c->stream));
+        PMG_CUDA(compute_geometry(c->dim, D.n, p, geom_desc(c), make_tab(p, p + 1), D.G[pl], c->cfg.geom_precision,
+                                  geobad, c->stream));
         if (D.dinv[pl])
-          PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, p, make_tab(p, p + 1), D.G[pl], c->t64[0], D.dinv[pl],
+          PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, p, make_tab(p, p + 1), D.G[pl], c->cfg.geom_precision,
+                                            c->t64[0], D.dinv[pl],
                                             c->mgprec, c->stream));
       }
       if (D.dinv1)
-        PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, 1, make_tab(1, 2), D.G[0], c->t64[0], D.dinv1, c->mgprec,
+        PMG_CUDA(compute_inverse_diagonal(c->dim, D.n, 1, make_tab(1, 2), D.G[0], c->cfg.geom_precision, c->t64[0],
+                                          D.dinv1, c->mgprec,
                                           c->stream));
     }
     int bad = 0;
@@ -926,6 +934,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->patch_layout = PMG_PATCH_AUTO;
   cfg->patch_threads = 0;
   cfg->outer_apply = PMG_OUTER_APPLY_FP64;
+  cfg->geom_precision = PMG_FP32;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {

@@ -26,7 +26,8 @@ struct PatchParamsHost {
 
 // Deformed-geometry arrays of one mesh level (device pointers).
 struct DefLevel {
-  const float* G[4];      // per p-level l >= 1: per cell, (p+1)^d points x ncomp (x fastest), float32
+  const void* G[4];       // per p-level: per cell, ncomp x (p+1)^d points (x fastest), FP64 or FP32 (gprec)
+  int gprec;              // storage precision of G: 0 double, 1 float
   const void* dinv[4];    // per p-level l >= 1: inverse diagonal on the degree-p global grid (MG precision)
   const void* dinv1;      // p = 1: inverse Q1 diagonal on the vertex grid (n+1)^d (MG precision)
 };
@@ -54,10 +55,10 @@ struct KernelTable {
                                cudaStream_t s);
   cudaError_t (*h_restrict)(int dim, int prec, const void* rf, void* rc, void* t0, void* t1, int nc,
                             cudaStream_t s);
-  // deformed geometry: y = A x or y = b - A x with stored G (float32); cellbuf:
-  // n^d (K+1)^d scratch values
-  cudaError_t (*def_apply)(int dim, int prec, const void* x, void* y, const void* b, const float* G, void* cellbuf,
-                           int n, cudaStream_t s);
+  // deformed geometry: y = A x or y = b - A x with stored G (FP64 if gprec is
+  // 0, else FP32); cellbuf: n^d (K+1)^d scratch values
+  cudaError_t (*def_apply)(int dim, int prec, const void* x, void* y, const void* b, const void* G, int gprec,
+                           void* cellbuf, int n, cudaStream_t s);
   // deformed patch smoother, every patch of the level (output as patch_cart)
   cudaError_t (*patch_def)(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                            const DefLevel& lev, const PatchParamsHost& P, cudaStream_t s);

@@ -453,8 +453,10 @@ __device__ void map_geo(int dim, const GeomDesc& g, int n, const int* c, const d
   }
 }
 
-// G[cell][comp][q] = w_q det J J^{-1} J^{-T} with J = dF/dX h, rounded to float.
-__global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab, float* __restrict__ G,
+// G[cell][comp][q] = w_q det J J^{-1} J^{-T} with J = dF/dX h, stored in TG
+// (float: rounded to nearest; double: as computed).
+template <typename TG>
+__global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab, TG* __restrict__ G,
                                 int* __restrict__ bad) {
   const int nq = p + 1;
   const int NP = dim == 3 ? nq * nq * nq : nq * nq;
@@ -510,34 +512,38 @@ __global__ void geometry_kernel(int dim, int n, int p, GeomDesc geo, QuadTab tab
       for (int i = 0; i < 2; ++i)
         for (int k = 0; k < 2; ++k) Gq[i][k] = w * det * (inv[i][0] * inv[k][0] + inv[i][1] * inv[k][1]);
     }
-    float* Gc = G + cell * nc * NP;
+    TG* Gc = G + cell * nc * NP;
     if (dim == 3) {
-      Gc[0 * NP + q] = (float)Gq[0][0];
-      Gc[1 * NP + q] = (float)Gq[0][1];
-      Gc[2 * NP + q] = (float)Gq[0][2];
-      Gc[3 * NP + q] = (float)Gq[1][1];
-      Gc[4 * NP + q] = (float)Gq[1][2];
-      Gc[5 * NP + q] = (float)Gq[2][2];
+      Gc[0 * NP + q] = (TG)Gq[0][0];
+      Gc[1 * NP + q] = (TG)Gq[0][1];
+      Gc[2 * NP + q] = (TG)Gq[0][2];
+      Gc[3 * NP + q] = (TG)Gq[1][1];
+      Gc[4 * NP + q] = (TG)Gq[1][2];
+      Gc[5 * NP + q] = (TG)Gq[2][2];
     } else {
-      Gc[0 * NP + q] = (float)Gq[0][0];
-      Gc[1 * NP + q] = (float)Gq[0][1];
-      Gc[2 * NP + q] = (float)Gq[1][1];
+      Gc[0 * NP + q] = (TG)Gq[0][0];
+      Gc[1 * NP + q] = (TG)Gq[0][1];
+      Gc[2 * NP + q] = (TG)Gq[1][1];
     }
   }
 }
 
-cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G, int* bad,
-                             cudaStream_t st) {
+cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, void* G, int gprec,
+                             int* bad, cudaStream_t st) {
   const int nq = p + 1;
   const int64_t work = (dim == 3 ? (int64_t)n * n * n * nq * nq * nq : (int64_t)n * n * nq * nq);
-  geometry_kernel<<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, geo, tab, G, bad);
+  if (gprec == 0)
+    geometry_kernel<double><<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, geo, tab, (double*)G, bad);
+  else
+    geometry_kernel<float><<<grid_for(work, 256, 152 * 32), 256, 0, st>>>(dim, n, p, geo, tab, (float*)G, bad);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 // Diagonal of the degree-p operator, one parity colour of cells:
 // diag[node] += sum_q grad phi_a^T G_q grad phi_a.
-__global__ void diag_kernel(int dim, int n, int p, QuadTab tab, const float* __restrict__ G, double* __restrict__ diag,
+template <typename TG>
+__global__ void diag_kernel(int dim, int n, int p, QuadTab tab, const TG* __restrict__ G, double* __restrict__ diag,
                             int colour) {
   const int n1 = p + 1;
   const int NP = dim == 3 ? n1 * n1 * n1 : n1 * n1;
@@ -557,7 +563,7 @@ __global__ void diag_kernel(int dim, int n, int p, QuadTab tab, const float* __r
     const int c2 = dim == 3 ? 2 * (int)ci + ((colour >> 2) & 1) : 0;
     const int64_t cell = c0 + (int64_t)n * (c1 + (int64_t)n * c2);
     const int ai[3] = {a % n1, (a / n1) % n1, dim == 3 ? a / (n1 * n1) : 0};
-    const float* Gc = G + cell * nc * NP;
+    const TG* Gc = G + cell * nc * NP;
     double s = 0.0;
     for (int q = 0; q < NP; ++q) {
       const int qi[3] = {q % n1, (q / n1) % n1, dim == 3 ? q / (n1 * n1) : 0};
@@ -593,8 +599,8 @@ __global__ void invert_kernel(const double* __restrict__ diag, void* inv, int pr
   }
 }
 
-cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
-                                     void* inv, int prec, cudaStream_t st) {
+cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const void* G, int gprec,
+                                     double* diag_tmp, void* inv, int prec, cudaStream_t st) {
   const int N1 = p * n + 1;
   const int64_t N = dim == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
   cudaError_t e = cudaMemsetAsync(diag_tmp, 0, sizeof(double) * N, st);
@@ -602,7 +608,12 @@ cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, 
   const int NP = dim == 3 ? (p + 1) * (p + 1) * (p + 1) : (p + 1) * (p + 1);
   for (int colour = 0; colour < (1 << dim); ++colour) {
     const int64_t work = (dim == 3 ? (int64_t)n * n * n : (int64_t)n * n) / (1 << dim) * NP + NP * 8;
-    diag_kernel<<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, p, tab, G, diag_tmp, colour);
+    if (gprec == 0)
+      diag_kernel<double><<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, p, tab, (const double*)G, diag_tmp,
+                                                                         colour);
+    else
+      diag_kernel<float><<<grid_for(work, 128, 152 * 32), 128, 0, st>>>(dim, n, p, tab, (const float*)G, diag_tmp,
+                                                                        colour);
     g_launches += 1;
   }
   invert_kernel<<<grid_for(N, 256), 256, 0, st>>>(diag_tmp, inv, prec, dim, N1);

@@ -80,11 +80,13 @@ struct GeomDesc {
   const double* verts;
   int n_fine;
 };
-// *bad |= 1 where a cell's det J <= 0 at a quadrature point (inverted cell)
-cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, float* G, int* bad,
-                             cudaStream_t st);
-cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const float* G, double* diag_tmp,
-                                     void* inv, int prec, cudaStream_t st);
+// G_q of every cell at the (p+1)^d Gauss points, stored in FP64 (gprec 0)
+// or FP32 (gprec 1); *bad |= 1 where a cell's det J <= 0 at a quadrature
+// point (inverted cell)
+cudaError_t compute_geometry(int dim, int n, int p, const GeomDesc& geo, const QuadTab& tab, void* G, int gprec,
+                             int* bad, cudaStream_t st);
+cudaError_t compute_inverse_diagonal(int dim, int n, int p, const QuadTab& tab, const void* G, int gprec,
+                                     double* diag_tmp, void* inv, int prec, cudaStream_t st);
 cudaError_t rhs_manufactured(int dim, int n, int K, const GeomDesc& geo, const QuadTab& tab, double* b,
                              cudaStream_t st);
 cudaError_t l2_error_partials(int dim, int n, int K, const GeomDesc& geo, const QuadTab& tab, const double* x,
