@@ -245,7 +245,23 @@ def extra_sections(p, torch, dev, stream, flush):
         "smoother_phases_ms": {"residual": phases[0], "patch": phases[1], "gather": phases[2]},
     }
     ctx.close()
-    del b, b32, y32, x
+    # the same solve with the quadrature-point tensors stored in FP64: time
+    # and the difference the FP32 storage makes to the solution
+    ctx64g = p.Context(p.make_config(dim=3, n_cells=n, degree=k, geometry=p.DEFORMED, mg_precision=p.FP32,
+                                     geom_precision=p.FP64), stream=stream, device=dev)
+    x64g = torch.zeros_like(b)
+    ctx64g.solve(b, x64g)
+    solves64g = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        solves64g.append(ctx64g.solve(b, x64g))
+    out["deformed_96_q3_mixed"]["fp64_geometry"] = {
+        "solve_ms_p50": pct([s_.time_ms for s_ in solves64g], 50), "iterations": solves64g[-1].iterations,
+        "l2_error": ctx64g.l2_error_manufactured(x64g),
+        "rel_diff_x_fp32_vs_fp64_geometry": float(torch.linalg.norm(x - x64g) / torch.linalg.norm(x64g))}
+    ctx64g.close()
+    del b, b32, y32, x, x64g
     out["outer_solvers_32_q4"] = outer_solver_section(p, torch, dev, stream, flush)
     out["distorted_64_q3_mixed"] = distorted_section(p, torch, dev, stream, flush)
     out["serving_cfg4"] = serving_section(p, torch)
