@@ -429,17 +429,18 @@ def degree_sweep():
 # ----------------------------------------------------------------- profiling
 def profile_region(region, n_def):
     """One NVTX range named 'profile' after warm-up, for
-    ncu --nvtx --nvtx-include "profile/": either one mixed-precision solve of
-    the 32^3 Q4 problem, or one FP32 apply and one FP32 sweep of the deformed
-    Q3 problem on n_def^3 cells."""
+    ncu --nvtx --nvtx-include "profile/": one mixed-precision solve of the
+    32^3 Q4 problem (with the FP64 or the float-float outer operator), or one
+    FP32 apply and one FP32 sweep of the deformed Q3 problem on n_def^3 cells."""
     import torch
     import paper_2512_02577_gb300 as p
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        if region == "mixed_solve":
-            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32), stream=stream,
-                            device=dev)
+        if region in ("mixed_solve", "mixed_solve_ff"):
+            apply = p.APPLY_FLOAT_FLOAT if region == "mixed_solve_ff" else p.APPLY_FP64
+            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32, outer_apply=apply),
+                            stream=stream, device=dev)
             b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
             ctx.rhs_manufactured(b)
             x = torch.zeros_like(b)
@@ -500,7 +501,7 @@ def main():
     ap.add_argument("--oracle-child", type=float, default=None)
     ap.add_argument("--oracle-steps", type=int, default=0)
     ap.add_argument("--oracle-case", default="sample", choices=["sample", "cfg1"])
-    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "deformed"],
+    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "mixed_solve_ff", "deformed"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
     ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
     ap.add_argument("--no-extras", action="store_true", help="skip the deformed and serving sections")
