@@ -34,9 +34,9 @@ ORACLE_N = 4          # bounded CPU sample: same degree and dimension, 4^3 cells
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (measured 1.255 with a project FMA probe)
 FP32_PEAK_TFLOPS = 78.5  # measured FP32 FMA (128 lanes x 152 SMs x 2 x ~2.0 GHz)
 # DRAM bytes (read + write) of one FP64 patch launch at 32^3 Q4, from one ncu
-# capture of that launch (57.21 MB + 54.93 MB); to be re-taken whenever
+# capture of that launch (57.12 MB + 54.64 MB); to be re-taken whenever
 # patch_cart_kernel changes.
-PATCH64_TRAFFIC_BYTES = 112135168
+PATCH64_TRAFFIC_BYTES = 111762432
 
 
 # ----------------------------------------------------------------- flop model

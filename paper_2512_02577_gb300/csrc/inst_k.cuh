@@ -90,7 +90,16 @@ static cudaError_t cart_apply_ff(int dim, const double* x, double* y, const doub
 
 static int patch_threads(int dim) { return dim == 3 ? PatchShape<3>::TPP : PatchShape<2>::TPP; }
 
+// shared bytes per patch of the patch-major layout
 static int patch_smem(int dim, int prec, int n_iter) {
+  const int es = prec == 0 ? 8 : 4;
+  const int elems = dim == 3 ? (prec == 0 ? PatchShape<3>::stride<double>(n_iter) : PatchShape<3>::stride<float>(n_iter))
+                             : (prec == 0 ? PatchShape<2>::stride<double>(n_iter) : PatchShape<2>::stride<float>(n_iter));
+  return elems * es;
+}
+
+// shared bytes per patch of the interleaved layout (no padding)
+static int patch_il_smem(int dim, int prec, int n_iter) {
   const int es = prec == 0 ? 8 : 4;
   const int elems = dim == 3 ? PatchShape<3>::ELEMS + (n_iter > 1 ? 2 * PatchShape<3>::SZT : 0)
                              : PatchShape<2>::ELEMS + (n_iter > 1 ? 2 * PatchShape<2>::SZT : 0);
@@ -137,7 +146,7 @@ static int patch_il_of(int dim, int prec, int n_iter) {
   if (!mine(dim, prec)) return 0;
   constexpr int il = patch_il<DP, TP>();
   if (il == 0) return 0;
-  const int smem = il * patch_smem(dim, prec, n_iter) + patch_cart_extra_smem(dim, prec);
+  const int smem = il * patch_il_smem(dim, prec, n_iter) + patch_cart_extra_smem(dim, prec);
   return smem <= kMaxDynSmem ? il : 0;
 }
 
@@ -149,7 +158,7 @@ static cudaError_t patch_cart_il_t(const T* r, T* dst, int n, int threads, int n
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const int il = patch_il_of(DIM, prec, n_iter);
   if (il == 0 || threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
-  const int smem = il * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
+  const int smem = il * patch_il_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
   patch_cart_il_kernel<DIM, T><<<(unsigned)((np + il - 1) / il), threads, smem, st>>>(r, dst, n, n_iter, dinv,
                                                                                    dinv_len(DIM), to_params<T>(H));
   g_launches += 1;

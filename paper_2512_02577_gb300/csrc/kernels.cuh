@@ -368,6 +368,17 @@ struct PatchShape {
   }
   static constexpr int off_d(int l) { return off_r(l) + (l == 0 ? 1 : SZ(l)); }
   static constexpr int ELEMS = ((off_r(0) + 2) + 1) / 2 * 2;
+  // Elements between consecutive patches of a block in the patch-major
+  // layout (N_iter > 1 adds r_j and the running correction).  FP32: padded
+  // to 17 mod 32 so that the lines of the two patches a warp may straddle
+  // fall on different banks (a bank model of the residual passes at k = 4
+  // gives 1.76 instead of 1.94 wavefronts per warp access).  FP64 work is
+  // bound by the FP64 pipe, not by shared memory: unpadded.
+  template <typename T>
+  static constexpr int stride(int n_iter) {
+    const int e = ELEMS + (n_iter > 1 ? 2 * SZT : 0);
+    return sizeof(T) == 8 ? e : e + ((17 - e % 32) + 32) % 32;
+  }
 };
 
 constexpr int kMaxPatchesPerBlock = 64;
@@ -873,7 +884,7 @@ __device__ __forceinline__ void patch_cart_body(const T* __restrict__ r, T* __re
   constexpr int RT = S::off_r(S::L - 1), DT = S::off_d(S::L - 1);
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ PatchMeta meta[kMaxPatchesPerBlock];
-  const int stride = S::ELEMS + (n_iter > 1 ? 2 * SZT : 0);
+  const int stride = IL ? S::ELEMS + (n_iter > 1 ? 2 * SZT : 0) : S::template stride<T>(n_iter);
   const PBlock<T, IL> pb{reinterpret_cast<T*>(smraw), stride, np};
   T* sdinv = reinterpret_cast<T*>(smraw) + np * stride;  // inverse-diagonal tables of all p-levels
   for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
