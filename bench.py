@@ -261,7 +261,23 @@ def extra_sections(p, torch, dev, stream, flush):
         "l2_error": ctx64g.l2_error_manufactured(x64g),
         "rel_diff_x_fp32_vs_fp64_geometry": float(torch.linalg.norm(x - x64g) / torch.linalg.norm(x64g))}
     ctx64g.close()
-    del b, b32, y32, x, x64g
+    # the same solve with the float-float outer operator
+    ctxff = p.Context(p.make_config(dim=3, n_cells=n, degree=k, geometry=p.DEFORMED, mg_precision=p.FP32,
+                                    outer_apply=p.APPLY_FLOAT_FLOAT), stream=stream, device=dev)
+    xff = torch.zeros_like(b)
+    ctxff.solve(b, xff)
+    solvesff = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        solvesff.append(ctxff.solve(b, xff))
+    t_applyff = _timed_ms(torch, stream, flush, lambda: ctxff.apply(b, x64g, prec=p.FP64), reps=3)
+    out["deformed_96_q3_mixed"]["float_float_operator"] = {
+        "solve_ms_p50": pct([s_.time_ms for s_ in solvesff], 50), "iterations": solvesff[-1].iterations,
+        "apply_ms": t_applyff, "l2_error": ctxff.l2_error_manufactured(xff),
+        "rel_diff_x_vs_fp64_operator": float(torch.linalg.norm(x - xff) / torch.linalg.norm(x))}
+    ctxff.close()
+    del b, b32, y32, x, x64g, xff
     out["outer_solvers_32_q4"] = outer_solver_section(p, torch, dev, stream, flush)
     out["distorted_64_q3_mixed"] = distorted_section(p, torch, dev, stream, flush)
     out["serving_cfg4"] = serving_section(p, torch)

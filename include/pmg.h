@@ -89,11 +89,12 @@ enum pmg_patch_layout {
 /* Arithmetic of the FP64 operator apply. */
 enum pmg_outer_apply {
   PMG_OUTER_APPLY_FP64 = 0,         /* IEEE double (default) */
-  PMG_OUTER_APPLY_FLOAT_FLOAT = 1   /* Cartesian only: FP64 vectors in and out, every product and sum carried
-                                       as an unevaluated pair of floats (about 48 significant bits, relative
-                                       error of A x within a few 1e-14 of |A| |x|) on the FP32 pipes -- on
-                                       GB300 several times faster than the FP64 pipes; the coarse-matrix
-                                       assembly stays in FP64 */
+  PMG_OUTER_APPLY_FLOAT_FLOAT = 1   /* FP64 vectors in and out, every product and sum carried as an unevaluated
+                                       pair of floats (about 48 significant bits, relative error of A x within
+                                       a few 1e-14 of |A| |x|) on the FP32 pipes -- on GB300 several times
+                                       faster than the FP64 pipes; the coarse-matrix assembly stays in FP64.
+                                       Cartesian meshes; deformed and distorted ones in 3D with degree <= 3
+                                       and geom_precision PMG_FP32 (else PMG_ERR_UNSUPPORTED) */
 };
 
 typedef struct pmg_ctx pmg_ctx;

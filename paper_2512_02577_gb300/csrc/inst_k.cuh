@@ -309,6 +309,7 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::patch_cart_il,
       PMG_KNS::patch_il_max_threads,
       PMG_KNS::cart_apply_ff,
+      PMG_KNS::def_apply_ff,
   };
   return &t;
 }

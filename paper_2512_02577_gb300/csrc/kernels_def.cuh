@@ -233,37 +233,74 @@ __global__ void __launch_bounds__(256) cell_gather_kernel(const T* __restrict__ 
 // cell of lowest colour among those holding a node (even parity in every
 // direction in which the node is shared) initialises it (y = s, or b - s),
 // the others add -- deterministic, no per-cell buffer, no atomics.
-template <typename T>
+// Arithmetic of the half-warp kernel: AF32 (FP32 vectors, float lines) or
+// AFF (FP64 vectors, float-float lines: each value a pair of floats, every
+// product and sum by the error-free transformations of cart_pass_ff; the
+// FP32-stored G_q enters the products exactly).  W = floats per line value.
+struct AF32 {
+  using IO = float;
+  using V = float;
+  using Acc = float;
+  static constexpr int W = 1;
+  static __device__ __forceinline__ V zero() { return 0.f; }
+  static __device__ __forceinline__ void mac(Acc& a, double c, V x) { a += (float)c * x; }
+  static __device__ __forceinline__ void macg(Acc& a, float g, V x) { a += g * x; }
+  static __device__ __forceinline__ V val(const Acc& a) { return a; }
+  static __device__ __forceinline__ V in(IO v) { return v; }
+  static __device__ __forceinline__ IO out(V v) { return v; }
+  static __device__ __forceinline__ void put(float* t, int stride, V v) { t[0] = v; }
+  static __device__ __forceinline__ V get(const float* t, int stride) { return t[0]; }
+};
+struct AFF {
+  using IO = double;
+  using V = ff;
+  using Acc = ff_acc;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ V zero() { return ff{0.f, 0.f}; }
+  static __device__ __forceinline__ void mac(Acc& a, double c, V x) { a.mac(ff_const(c), x); }
+  static __device__ __forceinline__ void macg(Acc& a, float g, V x) { a.mac(ff{g, 0.f}, x); }
+  static __device__ __forceinline__ V val(const Acc& a) { return a.value(); }
+  static __device__ __forceinline__ V in(IO v) { return ff_of(v); }
+  static __device__ __forceinline__ IO out(V v) { return ff_to_double(v); }
+  static __device__ __forceinline__ void put(float* t, int stride, V v) { t[0] = v.hi; t[stride] = v.lo; }
+  static __device__ __forceinline__ V get(const float* t, int stride) { return ff{t[0], t[stride]}; }
+};
+
+template <class A>
 struct DefFast {
   static constexpr int n1 = K + 1;
   static constexpr int PY = n1;                                 // tile row pitch
   static constexpr int PZ = n1 * n1 + (n1 == 4 ? 4 : 1);        // tile plane pitch (bank spread)
   static constexpr int TILE = PZ * n1;
-  static constexpr int CELL = 3 * TILE;                         // three tiles per cell
+  static constexpr int CELL = 3 * TILE * A::W;                  // three tiles per cell (floats)
   static constexpr int CELLS = 16;                              // cells (half-warps) per 256-thread block
 };
 
-template <bool RESID, typename T>
-__global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, T* __restrict__ y,
-                                                       const T* __restrict__ b, const float* __restrict__ G, int n,
-                                                       int colour) {
-  using F = DefFast<T>;
+template <bool RESID, class A>
+__global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __restrict__ x,
+                                                       typename A::IO* __restrict__ y,
+                                                       const typename A::IO* __restrict__ b,
+                                                       const float* __restrict__ G, int n, int colour) {
+  using F = DefFast<A>;
+  using V = typename A::V;
+  using Acc = typename A::Acc;
+  using IO = typename A::IO;
   constexpr int n1 = F::n1, NP = n1 * n1 * n1, L = nlev(K) - 1;
   constexpr int PY = F::PY, PZ = F::PZ, TILE = F::TILE;
-  __shared__ T tiles[F::CELLS * F::CELL];
   constexpr int OS = LAY.S[L], OD = LAY.Dq[L];
+  __shared__ float tiles[F::CELLS * F::CELL];
   const double* C = ctab<double>();
-  auto S = [&](int q, int a) -> T { return (T)C[OS + q * n1 + a]; };
-  auto DS = [&](int q, int a) -> T {  // derivative of nodal basis a at point q
+  auto S = [&](int q, int a) -> double { return C[OS + q * n1 + a]; };
+  auto DS = [&](int q, int a) -> double {  // derivative of nodal basis a at point q
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < n1; ++j) s += C[OD + q * n1 + j] * C[OS + j * n1 + a];
-    return (T)s;
+    return s;
   };
   const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
   const bool on = lane < n1 * n1;
   const int la = on ? lane % n1 : 0, lb = on ? lane / n1 : 0;
-  T* tl = tiles + hw * F::CELL;
+  float* tl = tiles + hw * F::CELL;
   // this half-warp's cell among those of parity colour `colour`
   int bit[3], cnt[3];
 #pragma unroll
@@ -284,14 +321,20 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
   }
   const int N1 = K * n + 1;
   // transposes through tile k: element (ix, iy, iz) at ix + PY iy + PZ iz
-  auto put = [&](int k, int ix, int iy, int iz, T v) { if (on) tl[k * TILE + ix + PY * iy + PZ * iz] = v; };
-  auto get = [&](int k, int ix, int iy, int iz) -> T { return on ? tl[k * TILE + ix + PY * iy + PZ * iz] : T(0); };
+  // (a float-float value's low part one tile-set further)
+  auto put = [&](int k, int ix, int iy, int iz, V v) {
+    if (on) A::put(tl + k * TILE + ix + PY * iy + PZ * iz, 3 * TILE, v);
+  };
+  auto get = [&](int k, int ix, int iy, int iz) -> V {
+    return on ? A::get(tl + k * TILE + ix + PY * iy + PZ * iz, 3 * TILE) : A::zero();
+  };
 
   // ---- every global load of the cell first (one memory latency per cell):
   // the nodal x-line, the value each output node starts from (y of an
   // earlier colour, b, or nothing), and G_q at this lane's points of the
   // z-line ownership used by the q-op
-  T u[n1], prior[n1];
+  V u[n1];
+  IO prior[n1];
   bool first[n1], bnd[n1];
   const int gy = K * c[1] + la, gz = K * c[2] + lb;
   const bool yz_bnd = gy == 0 || gy == N1 - 1 || gz == 0 || gz == N1 - 1;
@@ -308,8 +351,8 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
       if (shared && (c[d] & 1)) f = false;
     }
     first[i] = f;
-    u[i] = (live && !bnd[i]) ? x[row + i] : T(0);
-    prior[i] = (live && !bnd[i]) ? (f ? (RESID ? b[row + i] : T(0)) : y[row + i]) : T(0);
+    u[i] = (live && !bnd[i]) ? A::in(x[row + i]) : A::zero();
+    prior[i] = (live && !bnd[i]) ? (f ? (RESID ? b[row + i] : IO(0)) : y[row + i]) : IO(0);
   }
   const int64_t cell = c[0] + (int64_t)n * (c[1] + (int64_t)n * c[2]);
   const float* Gc = G + cell * 6 * NP + la + n1 * lb;
@@ -318,14 +361,16 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
   for (int q = 0; q < n1; ++q)
 #pragma unroll
     for (int m = 0; m < 6; ++m) gq[m][q] = live ? Gc[m * NP + n1 * n1 * q] : 0.f;
-  T P[n1], Pd[n1];
+
+  // ---- X-own (lane (y = la, z = lb)): P = S_x u, Pd = DS_x u
+  V P[n1], Pd[n1];
 #pragma unroll
   for (int q = 0; q < n1; ++q) {
-    T s0 = T(0), s1 = T(0);
+    Acc s0{}, s1{};
 #pragma unroll
-    for (int i = 0; i < n1; ++i) { s0 += S(q, i) * u[i]; s1 += DS(q, i) * u[i]; }
-    P[q] = s0;
-    Pd[q] = s1;
+    for (int i = 0; i < n1; ++i) { A::mac(s0, S(q, i), u[i]); A::mac(s1, DS(q, i), u[i]); }
+    P[q] = A::val(s0);
+    Pd[q] = A::val(s1);
   }
   // ---- X -> Y: lane (x = la, z = lb)
 #pragma unroll
@@ -334,15 +379,15 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
 #pragma unroll
   for (int j = 0; j < n1; ++j) { P[j] = get(0, la, j, lb); Pd[j] = get(1, la, j, lb); }
   __syncwarp();
-  T Q[n1], Qx[n1], Qy[n1];  // S_y P, S_y P', DS_y P
+  V Q[n1], Qx[n1], Qy[n1];  // S_y P, S_y P', DS_y P
 #pragma unroll
   for (int q = 0; q < n1; ++q) {
-    T s0 = T(0), s1 = T(0), s2 = T(0);
+    Acc s0{}, s1{}, s2{};
 #pragma unroll
-    for (int j = 0; j < n1; ++j) { s0 += S(q, j) * P[j]; s1 += S(q, j) * Pd[j]; s2 += DS(q, j) * P[j]; }
-    Q[q] = s0;
-    Qx[q] = s1;
-    Qy[q] = s2;
+    for (int j = 0; j < n1; ++j) { A::mac(s0, S(q, j), P[j]); A::mac(s1, S(q, j), Pd[j]); A::mac(s2, DS(q, j), P[j]); }
+    Q[q] = A::val(s0);
+    Qx[q] = A::val(s1);
+    Qy[q] = A::val(s2);
   }
   // ---- Y -> Z: lane (x = la, y = lb)
 #pragma unroll
@@ -352,27 +397,30 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
   for (int k = 0; k < n1; ++k) { Q[k] = get(0, la, lb, k); Qx[k] = get(1, la, lb, k); Qy[k] = get(2, la, lb, k); }
   __syncwarp();
   // gradients at the points (la, lb, q) and the q-op with G_q
-  T fx[n1], fy[n1], fz[n1];
+  V fx[n1], fy[n1], fz[n1];
 #pragma unroll
   for (int q = 0; q < n1; ++q) {
-    T gx = T(0), gy2 = T(0), gz2 = T(0);
+    Acc a0{}, a1{}, a2{};
 #pragma unroll
-    for (int k = 0; k < n1; ++k) { gx += S(q, k) * Qx[k]; gy2 += S(q, k) * Qy[k]; gz2 += DS(q, k) * Q[k]; }
-    const T G00 = (T)gq[0][q], G01 = (T)gq[1][q], G02 = (T)gq[2][q];
-    const T G11 = (T)gq[3][q], G12 = (T)gq[4][q], G22 = (T)gq[5][q];
-    fx[q] = G00 * gx + G01 * gy2 + G02 * gz2;
-    fy[q] = G01 * gx + G11 * gy2 + G12 * gz2;
-    fz[q] = G02 * gx + G12 * gy2 + G22 * gz2;
+    for (int k = 0; k < n1; ++k) { A::mac(a0, S(q, k), Qx[k]); A::mac(a1, S(q, k), Qy[k]); A::mac(a2, DS(q, k), Q[k]); }
+    const V gx = A::val(a0), gy2 = A::val(a1), gz2 = A::val(a2);
+    Acc f0{}, f1{}, f2{};
+    A::macg(f0, gq[0][q], gx); A::macg(f0, gq[1][q], gy2); A::macg(f0, gq[2][q], gz2);
+    A::macg(f1, gq[1][q], gx); A::macg(f1, gq[3][q], gy2); A::macg(f1, gq[4][q], gz2);
+    A::macg(f2, gq[2][q], gx); A::macg(f2, gq[4][q], gy2); A::macg(f2, gq[5][q], gz2);
+    fx[q] = A::val(f0);
+    fy[q] = A::val(f1);
+    fz[q] = A::val(f2);
   }
   // ---- transposed passes: Z-own A1 = S_z^T fx, A2 = S_z^T fy, A3 = DS_z^T fz
 #pragma unroll
   for (int k = 0; k < n1; ++k) {
-    T s0 = T(0), s1 = T(0), s2 = T(0);
+    Acc s0{}, s1{}, s2{};
 #pragma unroll
-    for (int q = 0; q < n1; ++q) { s0 += S(q, k) * fx[q]; s1 += S(q, k) * fy[q]; s2 += DS(q, k) * fz[q]; }
-    Q[k] = s0;
-    Qx[k] = s1;
-    Qy[k] = s2;
+    for (int q = 0; q < n1; ++q) { A::mac(s0, S(q, k), fx[q]); A::mac(s1, S(q, k), fy[q]); A::mac(s2, DS(q, k), fz[q]); }
+    Q[k] = A::val(s0);
+    Qx[k] = A::val(s1);
+    Qy[k] = A::val(s2);
   }
   // ---- Z -> Y: lane (x = la, z = lb)
 #pragma unroll
@@ -384,11 +432,11 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
   // B1 = S_y^T A1, B23 = DS_y^T A2 + S_y^T A3
 #pragma unroll
   for (int j = 0; j < n1; ++j) {
-    T s0 = T(0), s1 = T(0);
+    Acc s0{}, s1{};
 #pragma unroll
-    for (int q = 0; q < n1; ++q) { s0 += S(q, j) * Q[q]; s1 += DS(q, j) * Qx[q] + S(q, j) * Qy[q]; }
-    P[j] = s0;
-    Pd[j] = s1;
+    for (int q = 0; q < n1; ++q) { A::mac(s0, S(q, j), Q[q]); A::mac(s1, DS(q, j), Qx[q]); A::mac(s1, S(q, j), Qy[q]); }
+    P[j] = A::val(s0);
+    Pd[j] = A::val(s1);
   }
   // ---- Y -> X: lane (y = la, z = lb)
 #pragma unroll
@@ -399,12 +447,41 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const T* __restrict__ x, 
   // out = DS_x^T B1 + S_x^T B23, added into y node by node
 #pragma unroll
   for (int i = 0; i < n1; ++i) {
-    T s = T(0);
+    Acc s{};
 #pragma unroll
-    for (int q = 0; q < n1; ++q) s += DS(q, i) * P[q] + S(q, i) * Pd[q];
+    for (int q = 0; q < n1; ++q) { A::mac(s, DS(q, i), P[q]); A::mac(s, S(q, i), Pd[q]); }
     if (!live || (bnd[i] && !first[i])) continue;
-    y[row + i] = bnd[i] ? T(0) : (RESID ? prior[i] - s : prior[i] + s);
+    const IO v = A::out(A::val(s));
+    y[row + i] = bnd[i] ? IO(0) : (RESID ? prior[i] - v : prior[i] + v);
   }
+}
+
+// the 2^3 colour launches of the half-warp kernel (3D, k <= 3)
+template <class A>
+static cudaError_t def_fast_apply(const typename A::IO* x, typename A::IO* y, const typename A::IO* b,
+                                  const float* G, int n, cudaStream_t st) {
+  if constexpr (K <= 3) {
+    for (int colour = 0; colour < 8; ++colour) {
+      int64_t ncol = 1;
+      for (int d = 0; d < 3; ++d) ncol *= (n - ((colour >> d) & 1) + 1) / 2;
+      if (ncol == 0) continue;
+      const unsigned blocks = (unsigned)((ncol + DefFast<A>::CELLS - 1) / DefFast<A>::CELLS);
+      if (b) def_fast_kernel<true, A><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
+      else def_fast_kernel<false, A><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
+      g_launches += 1;
+    }
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+// FP64 deformed apply in float-float arithmetic (3D, k <= 3, FP32-stored
+// G_q); cudaErrorInvalidValue for other parts
+static cudaError_t def_apply_ff(int dim, const double* x, double* y, const double* b, const float* G, int n,
+                                cudaStream_t st) {
+  if (dim != 3 || PMG_DIM != 3 || K > 3) return cudaErrorInvalidValue;
+  return def_fast_apply<AFF>(x, y, b, G, n, st);
 }
 
 // true when the fast deformed apply covers this degree, dimension and
@@ -418,16 +495,7 @@ constexpr bool def_fast_ok() { return DIM == 3 && K <= 3 && sizeof(T) == 4; }
 template <int DIM, typename T, typename TG>
 static cudaError_t def_apply_t(const T* x, T* y, const T* b, const TG* G, T* cellbuf, int n, cudaStream_t st) {
   if constexpr (def_fast_ok<DIM, T>() && sizeof(TG) == 4) {
-    for (int colour = 0; colour < 8; ++colour) {
-      int64_t ncol = 1;
-      for (int d = 0; d < 3; ++d) ncol *= (n - ((colour >> d) & 1) + 1) / 2;
-      if (ncol == 0) continue;
-      const unsigned blocks = (unsigned)((ncol + DefFast<T>::CELLS - 1) / DefFast<T>::CELLS);
-      if (b) def_fast_kernel<true, T><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
-      else def_fast_kernel<false, T><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
-      g_launches += 1;
-    }
-    return cudaGetLastError();
+    return def_fast_apply<AF32>(x, y, b, G, n, st);
   }
   constexpr int n1 = K + 1;
   constexpr int NP = ipow(n1, DIM);

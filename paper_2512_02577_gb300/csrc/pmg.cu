@@ -153,8 +153,10 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_ARG, "unknown patch_layout");
   if (cfg->outer_apply != PMG_OUTER_APPLY_FP64 && cfg->outer_apply != PMG_OUTER_APPLY_FLOAT_FLOAT)
     return fail(PMG_ERR_ARG, "unknown outer_apply");
-  if (cfg->outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT && cfg->geometry != PMG_GEOM_CARTESIAN)
-    return fail(PMG_ERR_UNSUPPORTED, "the float-float operator is Cartesian only");
+  if (cfg->outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT && cfg->geometry != PMG_GEOM_CARTESIAN &&
+      !(cfg->dim == 3 && cfg->degree <= 3 && cfg->geom_precision == PMG_FP32))
+    return fail(PMG_ERR_UNSUPPORTED,
+                "the float-float operator on deformed or distorted meshes needs 3D, degree <= 3 and FP32 geometry");
   if (cfg->geom_precision != PMG_FP64 && cfg->geom_precision != PMG_FP32)
     return fail(PMG_ERR_ARG, "unknown geom_precision");
   if (cfg->patches_per_block < 0 || cfg->patch_threads < 0)
@@ -355,8 +357,12 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   LevelData& L = c->lv[level];
   cudaError_t e;
   if (prec == PMG_FP64 && !exact64 && c->cfg.outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT) {
-    e = c->kt[PMG_FP64]->cart_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b, c->t64[0], c->t64[1],
-                                       c->t64[2], c->t64[3], L.n, L.scale, c->stream);
+    if (c->deformed)
+      e = c->kt[PMG_FP64]->def_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b,
+                                        (const float*)L.G[c->nplev - 1], L.n, c->stream);
+    else
+      e = c->kt[PMG_FP64]->cart_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b, c->t64[0],
+                                         c->t64[1], c->t64[2], c->t64[3], L.n, L.scale, c->stream);
   } else if (c->deformed) {
     e = c->kt[prec]->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cfg.geom_precision, c->cellbuf, L.n,
                                c->stream);

@@ -78,6 +78,9 @@ struct KernelTable {
   // level, computed in float-float arithmetic; t0..t3: scratch of N doubles
   cudaError_t (*cart_apply_ff)(int dim, const double* x, double* y, const double* b, void* t0, void* t1, void* t2,
                                void* t3, int n, double scale, cudaStream_t s);
+  // the same on a deformed or distorted level (3D, K <= 3, FP32-stored G)
+  cudaError_t (*def_apply_ff)(int dim, const double* x, double* y, const double* b, const float* G, int n,
+                              cudaStream_t s);
 };
 
 // nullptr when k, dim or prec is out of range

@@ -85,7 +85,45 @@ def test_mixed_solve_with_float_float_operator(d, n, k, L):
     assert abs(its[p.APPLY_FP64] - its[p.APPLY_FLOAT_FLOAT]) <= 1, its
 
 
-def test_float_float_operator_is_cartesian_only():
+@pytest.mark.parametrize("d,n,k", [(3, 4, 3), (3, 3, 2), (3, 4, 1)])
+def test_float_float_deformed_apply_and_residual(d, n, k):
+    # the half-warp cell kernel in float-float arithmetic on the FP32-stored
+    # G_q (the same discrete operator as the FP64 apply and the oracle's)
+    ctx = make_ctx(d, n, k, L=1, geom="deformed", **FF)
+    lev = oracle_operator(d, n, k, "deformed")
+    x = random_vector(d, n, k, seed=40 + n + k)
+    y = torch.empty(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    ctx.apply(to_dev(x), y)
+    y_ref = fem.apply_full(lev.mesh, lev.A, x)
+    assert rel(y, y_ref) < 1e-12
+    b = random_vector(d, n, k, seed=97)
+    r = torch.empty_like(y)
+    ctx.residual(to_dev(b), to_dev(x), r)
+    assert rel(r, b - y_ref) < 1e-12
+
+
+def test_float_float_distorted_mixed_solve():
+    from paper_2512_02577_gb300.inputs import vertex_displacements
+    d, n, k = 3, 8, 3
+    disp = vertex_displacements(d, n, 0.2, 31)
+    its = {}
+    for apply in (p.APPLY_FP64, p.APPLY_FLOAT_FLOAT):
+        ctx = p.Context(p.make_config(dim=d, n_cells=n, degree=k, geometry=p.DISTORTED, vertex_disp=disp,
+                                      mg_precision=p.FP32, outer_apply=apply), device=DEV)
+        b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+        ctx.rhs_manufactured(b)
+        x = torch.zeros_like(b)
+        info = ctx.solve(b, x, rtol=1e-8)
+        assert info.status == 0 and info.rel_residual <= 1e-8
+        its[apply] = (info.iterations, x)
+    assert abs(its[p.APPLY_FP64][0] - its[p.APPLY_FLOAT_FLOAT][0]) <= 1
+    assert rel(its[p.APPLY_FLOAT_FLOAT][1], its[p.APPLY_FP64][1]) < 1e-7
+
+
+@pytest.mark.parametrize("kw", [dict(dim=2, n_cells=4, degree=2, geometry=p.DEFORMED),
+                                dict(dim=3, n_cells=4, degree=4, geometry=p.DEFORMED),
+                                dict(dim=3, n_cells=4, degree=2, geometry=p.DEFORMED, geom_precision=p.FP64)])
+def test_float_float_operator_limits(kw):
     with pytest.raises(p.PmgError) as e:
-        make_ctx(3, 4, 2, geom="deformed", **FF)
+        p.Context(p.make_config(**kw, **FF), device=DEV)
     assert e.value.code == p.PMG_ERR_UNSUPPORTED
