@@ -136,6 +136,9 @@ typedef struct pmg_config {
                           (6 components per Gauss point in 3D): PMG_FP32 (default; the discrete operator
                           of every precision is the one of the rounded G_q) or PMG_FP64 (twice the bytes;
                           the FP64 operator then uses G_q as computed) */
+  int apply_cells_per_block; /* deformed and distorted geometry: cells per thread block of the operator
+                          apply, 0 = autotuned (admissible values: 4, 8, 16 for the 3D k <= 3 FP32
+                          kernel, else 1, 2, 4, ... while the cell tiles fit) */
 } pmg_config;
 
 typedef struct pmg_solve_info {
@@ -255,6 +258,13 @@ int64_t pmg_launch_count(void);
  * cached for the process and, if the environment variable PMG_TUNE_FILE
  * names a file, in that file). */
 int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
+
+/* Cells per thread block of a deformed or distorted context's operator
+ * apply in the multigrid precision: the autotuned value (timed at creation
+ * per dimension, degree, precision, geometry storage and finest n on the
+ * finest level's apply; meshes below 32^3 cells use the kernel's rule and
+ * report 0), 0 on Cartesian contexts. */
+int pmg_apply_cells_per_block(const pmg_ctx* ctx, int* cells_per_block);
 
 /* The patch-kernel layout of a context's finest level (enum
  * pmg_patch_layout, never AUTO), its patches per block and threads per

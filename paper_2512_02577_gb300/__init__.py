@@ -41,7 +41,7 @@ EXPORTED = [
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
     "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release", "pmg_patch_layout",
-    "pmg_server_set_policy",
+    "pmg_server_set_policy", "pmg_apply_cells_per_block",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -62,7 +62,7 @@ class Config(ctypes.Structure):
         ("local_half", ctypes.c_int), ("outer_solver", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("smoother", ctypes.c_int), ("vertex_disp", ctypes.c_void_p),
         ("patch_layout", ctypes.c_int), ("patch_threads", ctypes.c_int), ("outer_apply", ctypes.c_int),
-        ("geom_precision", ctypes.c_int),
+        ("geom_precision", ctypes.c_int), ("apply_cells_per_block", ctypes.c_int),
     ]
 
 
@@ -119,6 +119,7 @@ def load_library(path=LIB_PATH):
         "pmg_default_damping": (cint, [cint, cint, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_server_release": (cint, [vp, i64]),
         "pmg_server_set_policy": (cint, [vp, cint, dbl, dbl]),
+        "pmg_apply_cells_per_block": (cint, [vp, ctypes.POINTER(cint)]),
         "pmg_patch_layout": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]),
     }
     for name, (res, args) in sigs.items():
@@ -139,7 +140,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
                 smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
                 smoother=ADDITIVE, vertex_disp=None, patch_layout=PATCH_AUTO, patch_threads=0, outer_apply=APPLY_FP64,
-                geom_precision=FP32):
+                geom_precision=FP32, apply_cells_per_block=0):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -158,6 +159,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.patch_layout, c.patch_threads = patch_layout, patch_threads
     c.outer_apply = outer_apply
     c.geom_precision = geom_precision
+    c.apply_cells_per_block = apply_cells_per_block
     if vertex_disp is not None:
         # ((n+1)^d, d) float64 displacements of the finest mesh's vertices;
         # the config keeps a reference so the array outlives it
@@ -318,6 +320,12 @@ class Context:
         wp, wj = ctypes.c_double(), (ctypes.c_double * 4)()
         _check(_lib.pmg_damping(self.handle, ctypes.byref(wp), wj))
         return wp.value, list(wj)
+
+    def apply_cells_per_block(self):
+        """Cells per block of the deformed apply (0: the kernel's rule)."""
+        v = ctypes.c_int()
+        _check(_lib.pmg_apply_cells_per_block(self.handle, ctypes.byref(v)))
+        return v.value
 
     def patch_layout(self):
         """(layout, patches per block, threads per block) of the finest level."""

@@ -310,6 +310,7 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::patch_il_max_threads,
       PMG_KNS::cart_apply_ff,
       PMG_KNS::def_apply_ff,
+      PMG_KNS::def_apply_candidates,
   };
   return &t;
 }

@@ -273,7 +273,7 @@ struct DefFast {
   static constexpr int PZ = n1 * n1 + (n1 == 4 ? 4 : 1);        // tile plane pitch (bank spread)
   static constexpr int TILE = PZ * n1;
   static constexpr int CELL = 3 * TILE * A::W;                  // three tiles per cell (floats)
-  static constexpr int CELLS = 16;                              // cells (half-warps) per 256-thread block
+  static constexpr int CELLS = 16;                              // largest cells (half-warps) per block
 };
 
 template <bool RESID, class A>
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __r
     cnt[d] = (n - bit[d] + 1) / 2;
   }
   const int64_t ncol = (int64_t)cnt[0] * cnt[1] * cnt[2];
-  const int64_t cid = (int64_t)blockIdx.x * F::CELLS + hw;
+  const int64_t cid = (int64_t)blockIdx.x * (blockDim.x >> 4) + hw;
   const bool live = on && cid < ncol;
   int c[3];
   {
@@ -457,17 +457,20 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __r
 }
 
 // the 2^3 colour launches of the half-warp kernel (3D, k <= 3)
+// cpb: cells (half-warps) per block, 4, 8 or 16 (0: 16)
 template <class A>
 static cudaError_t def_fast_apply(const typename A::IO* x, typename A::IO* y, const typename A::IO* b,
-                                  const float* G, int n, cudaStream_t st) {
+                                  const float* G, int n, int cpb, cudaStream_t st) {
   if constexpr (K <= 3) {
+    if (cpb == 0) cpb = DefFast<A>::CELLS;
+    if (cpb != 4 && cpb != 8 && cpb != 16) return cudaErrorInvalidValue;
     for (int colour = 0; colour < 8; ++colour) {
       int64_t ncol = 1;
       for (int d = 0; d < 3; ++d) ncol *= (n - ((colour >> d) & 1) + 1) / 2;
       if (ncol == 0) continue;
-      const unsigned blocks = (unsigned)((ncol + DefFast<A>::CELLS - 1) / DefFast<A>::CELLS);
-      if (b) def_fast_kernel<true, A><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
-      else def_fast_kernel<false, A><<<blocks, 256, 0, st>>>(x, y, b, G, n, colour);
+      const unsigned blocks = (unsigned)((ncol + cpb - 1) / cpb);
+      if (b) def_fast_kernel<true, A><<<blocks, 16 * cpb, 0, st>>>(x, y, b, G, n, colour);
+      else def_fast_kernel<false, A><<<blocks, 16 * cpb, 0, st>>>(x, y, b, G, n, colour);
       g_launches += 1;
     }
     return cudaGetLastError();
@@ -478,10 +481,10 @@ static cudaError_t def_fast_apply(const typename A::IO* x, typename A::IO* y, co
 
 // FP64 deformed apply in float-float arithmetic (3D, k <= 3, FP32-stored
 // G_q); cudaErrorInvalidValue for other parts
-static cudaError_t def_apply_ff(int dim, const double* x, double* y, const double* b, const float* G, int n,
+static cudaError_t def_apply_ff(int dim, const double* x, double* y, const double* b, const float* G, int n, int cpb,
                                 cudaStream_t st) {
   if (dim != 3 || PMG_DIM != 3 || K > 3) return cudaErrorInvalidValue;
-  return def_fast_apply<AFF>(x, y, b, G, n, st);
+  return def_fast_apply<AFF>(x, y, b, G, n, cpb, st);
 }
 
 // true when the fast deformed apply covers this degree, dimension and
@@ -492,18 +495,24 @@ static cudaError_t def_apply_ff(int dim, const double* x, double* y, const doubl
 template <int DIM, typename T>
 constexpr bool def_fast_ok() { return DIM == 3 && K <= 3 && sizeof(T) == 4; }
 
+// cpb: cells per block (0: the rule below); the half-warp kernel takes 4, 8
+// or 16, the shared-memory cell kernel any count whose tiles fit
 template <int DIM, typename T, typename TG>
-static cudaError_t def_apply_t(const T* x, T* y, const T* b, const TG* G, T* cellbuf, int n, cudaStream_t st) {
+static cudaError_t def_apply_t(const T* x, T* y, const T* b, const TG* G, T* cellbuf, int n, int cpb,
+                               cudaStream_t st) {
   if constexpr (def_fast_ok<DIM, T>() && sizeof(TG) == 4) {
-    return def_fast_apply<AF32>(x, y, b, G, n, st);
+    return def_fast_apply<AF32>(x, y, b, G, n, cpb, st);
   }
   constexpr int n1 = K + 1;
   constexpr int NP = ipow(n1, DIM);
   constexpr int LINES = ipow(n1, DIM - 1);
-  int cpb = 256 / LINES;
-  while (cpb > 1 && cpb * 5 * NP * (int)sizeof(T) > 96 * 1024) --cpb;
+  if (cpb <= 0) {
+    cpb = 256 / LINES;
+    while (cpb > 1 && cpb * 5 * NP * (int)sizeof(T) > 96 * 1024) --cpb;
+  }
   if (cpb < 1) cpb = 1;
   if (cpb > kMaxPatchesPerBlock) cpb = kMaxPatchesPerBlock;
+  if (cpb * LINES > 1024) return cudaErrorInvalidValue;
   const int threads = std::min(256, (cpb * LINES + 31) / 32 * 32);
   const int smem = cpb * 5 * NP * (int)sizeof(T);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
@@ -516,12 +525,33 @@ static cudaError_t def_apply_t(const T* x, T* y, const T* b, const TG* G, T* cel
 }
 
 static cudaError_t def_apply(int dim, int prec, const void* x, void* y, const void* b, const void* G, int gprec,
-                             void* cellbuf, int n, cudaStream_t s) {
+                             void* cellbuf, int n, int cpb, cudaStream_t s) {
   if (dim != PMG_DIM || prec != PMG_PREC) return cudaErrorInvalidValue;
   using TP = std::conditional_t<PMG_PREC == 0, double, float>;
   if (gprec == 0)
-    return def_apply_t<PMG_DIM, TP, double>((const TP*)x, (TP*)y, (const TP*)b, (const double*)G, (TP*)cellbuf, n, s);
-  return def_apply_t<PMG_DIM, TP, float>((const TP*)x, (TP*)y, (const TP*)b, (const float*)G, (TP*)cellbuf, n, s);
+    return def_apply_t<PMG_DIM, TP, double>((const TP*)x, (TP*)y, (const TP*)b, (const double*)G, (TP*)cellbuf, n,
+                                            cpb, s);
+  return def_apply_t<PMG_DIM, TP, float>((const TP*)x, (TP*)y, (const TP*)b, (const float*)G, (TP*)cellbuf, n, cpb,
+                                         s);
+}
+
+// cells-per-block candidates of this part's deformed apply (3D k <= 3 FP32:
+// the half-warp kernel; else the shared-memory cell kernel)
+static int def_apply_candidates(int dim, int prec, int gprec, int* out, int max) {
+  if (dim != PMG_DIM || prec != PMG_PREC) return 0;
+  using TP = std::conditional_t<PMG_PREC == 0, double, float>;
+  int c = 0;
+  if (def_fast_ok<PMG_DIM, TP>() && gprec == 1) {
+    for (int v : {4, 8, 16})
+      if (c < max) out[c++] = v;
+    return c;
+  }
+  constexpr int n1 = K + 1;
+  constexpr int NP = ipow(n1, PMG_DIM);
+  constexpr int LINES = ipow(n1, PMG_DIM - 1);
+  for (int v : {1, 2, 4, 8, 16, 32})
+    if (v * LINES <= 1024 && v * 5 * NP * (int)sizeof(TP) <= kMaxDynSmem && c < max) out[c++] = v;
+  return c;
 }
 
 // ---------------------------------------------------------------------------

@@ -159,8 +159,8 @@ int make_plan(const pmg_config* cfg, Plan& P) {
                 "the float-float operator on deformed or distorted meshes needs 3D, degree <= 3 and FP32 geometry");
   if (cfg->geom_precision != PMG_FP64 && cfg->geom_precision != PMG_FP32)
     return fail(PMG_ERR_ARG, "unknown geom_precision");
-  if (cfg->patches_per_block < 0 || cfg->patch_threads < 0)
-    return fail(PMG_ERR_ARG, "patches_per_block, patch_threads >= 0");
+  if (cfg->patches_per_block < 0 || cfg->patch_threads < 0 || cfg->apply_cells_per_block < 0)
+    return fail(PMG_ERR_ARG, "patches_per_block, patch_threads, apply_cells_per_block >= 0");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
     return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
@@ -301,6 +301,7 @@ struct pmg_ctx {
   double* verts = nullptr;  // distorted geometry: finest-mesh vertex positions
   int ppc = 1;          // patch-major layout: patches per block
   int il_threads = 0;   // > 0: interleaved layout (Cartesian), threads per block
+  int def_cpb = 0;      // deformed apply: cells per block (0: the kernel part's rule)
   double omega_as = 0;
   double omega_j[4] = {1, 1, 1, 1};
   cudaGraphExec_t vgraph = nullptr;
@@ -359,13 +360,13 @@ int level_apply(pmg_ctx* c, int level, int prec, const void* u, void* r, const v
   if (prec == PMG_FP64 && !exact64 && c->cfg.outer_apply == PMG_OUTER_APPLY_FLOAT_FLOAT) {
     if (c->deformed)
       e = c->kt[PMG_FP64]->def_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b,
-                                        (const float*)L.G[c->nplev - 1], L.n, c->stream);
+                                        (const float*)L.G[c->nplev - 1], L.n, c->def_cpb, c->stream);
     else
       e = c->kt[PMG_FP64]->cart_apply_ff(c->dim, (const double*)u, (double*)r, (const double*)b, c->t64[0],
                                          c->t64[1], c->t64[2], c->t64[3], L.n, L.scale, c->stream);
   } else if (c->deformed) {
     e = c->kt[prec]->def_apply(c->dim, prec, u, r, b, L.G[c->nplev - 1], c->cfg.geom_precision, c->cellbuf, L.n,
-                               c->stream);
+                               prec == c->mgprec ? c->def_cpb : 0, c->stream);
   } else {
     void** t = prec == PMG_FP64 ? (void**)c->t64 : c->t_mg;
     e = c->kt[prec]->cart_apply(c->dim, prec, u, r, b, t[0], t[1], t[2], t[3], L.n, L.scale, c->stream);
@@ -760,6 +761,86 @@ int choose_patch_layout(pmg_ctx* c) {
   return PMG_OK;
 }
 
+// Cells per block of the deformed operator apply in the multigrid precision
+// (the residuals of every smoothing step), per (dim, degree, precision,
+// geometry storage, finest n): each admissible value is timed on the finest
+// level's apply, best of 3 after a warm-up, and kept for the process; meshes
+// below 32^3 cells (2D: 256^2) use the kernel part's rule.  The float-float
+// outer operator uses the same value.
+struct DefTuneKey {
+  int dim, K, prec, gprec, n;
+  bool operator<(const DefTuneKey& o) const {
+    return std::tie(dim, K, prec, gprec, n) < std::tie(o.dim, o.K, o.prec, o.gprec, o.n);
+  }
+};
+std::map<DefTuneKey, int> g_def_tune;
+
+int choose_def_cpb(pmg_ctx* c) {
+  c->def_cpb = 0;
+  if (!c->deformed) return PMG_OK;
+  if (c->cfg.apply_cells_per_block > 0) {  // the caller's value, if the part admits it
+    int cand[16];
+    const int nc = c->km()->def_apply_candidates(c->dim, c->mgprec, c->cfg.geom_precision, cand, 16);
+    for (int i = 0; i < nc; ++i)
+      if (cand[i] == c->cfg.apply_cells_per_block) {
+        c->def_cpb = cand[i];
+        return PMG_OK;
+      }
+    return fail(PMG_ERR_ARG, "apply_cells_per_block not admissible for this configuration");
+  }
+  LevelData& F = c->lv[c->L - 1];
+  const int64_t cells = ipow64(F.n, c->dim);
+  if (cells < (c->dim == 3 ? 32768 : 65536)) return PMG_OK;
+  const DefTuneKey key{c->dim, c->K, c->mgprec, c->cfg.geom_precision, F.n};
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_def_tune.find(key);
+    if (it != g_def_tune.end()) {
+      c->def_cpb = it->second;
+      return PMG_OK;
+    }
+  }
+  int cand[16];
+  const int nc = c->km()->def_apply_candidates(c->dim, c->mgprec, c->cfg.geom_precision, cand, 16);
+  cudaEvent_t e0, e1;
+  PMG_CUDA(cudaEventCreate(&e0));
+  PMG_CUDA(cudaEventCreate(&e1));
+  const size_t es = c->mg32 ? 4 : 8;
+  PMG_CUDA(cudaMemsetAsync(F.u, 0, es * F.N, c->stream));
+  const int64_t before = g_launches.load();
+  float best = 1e30f;
+  int best_cpb = 0;
+  for (int i = 0; i < nc; ++i) {
+    c->def_cpb = cand[i];
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      const int rc = level_apply(c, c->L - 1, c->mgprec, F.u, F.r, nullptr);
+      cudaEventRecord(e1, c->stream);
+      if (rc) {
+        cudaGetLastError();
+        tmin = 1e30f;
+        break;
+      }
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    if (tmin < best * 0.995f) {
+      best = tmin;
+      best_cpb = cand[i];
+    }
+  }
+  g_launches -= g_launches.load() - before;  // tuning launches are not the caller's work
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->def_cpb = best_cpb;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_def_tune[key] = best_cpb;
+  return PMG_OK;
+}
+
 int check_ctx(const pmg_ctx* c) { return c ? PMG_OK : fail(PMG_ERR_ARG, "context is NULL"); }
 
 // omega_AS reading: theta / 2^d with theta = 1.5 (every free DoF lies in at
@@ -904,6 +985,7 @@ int setup_context(pmg_ctx* c) {
 
   // patch-kernel layout and block shape: the autotuned choice (or the caller's)
   if (int rc = choose_patch_layout(c)) return rc;
+  if (int rc = choose_def_cpb(c)) return rc;
 
   PMG_CUDA(cudaMallocHost((void**)&c->host_scal, 8 * S_COUNT));
   PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
@@ -941,6 +1023,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->patch_threads = 0;
   cfg->outer_apply = PMG_OUTER_APPLY_FP64;
   cfg->geom_precision = PMG_FP32;
+  cfg->apply_cells_per_block = 0;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {
@@ -1404,6 +1487,12 @@ int pmg_damping(const pmg_ctx* c, double* omega_patch, double* omega_jacobi) {
 int pmg_patches_per_block(const pmg_ctx* c, int* ppc) {
   if (check_ctx(c) || !ppc) return fail(PMG_ERR_ARG, "NULL argument");
   *ppc = c->il_threads > 0 ? c->km()->patch_il(c->dim, c->mgprec, c->cfg.local_cycles) : c->ppc;
+  return PMG_OK;
+}
+
+int pmg_apply_cells_per_block(const pmg_ctx* c, int* cpb) {
+  if (check_ctx(c) || !cpb) return fail(PMG_ERR_ARG, "NULL argument");
+  *cpb = c->def_cpb;
   return PMG_OK;
 }
 

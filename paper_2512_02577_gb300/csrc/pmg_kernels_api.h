@@ -57,8 +57,10 @@ struct KernelTable {
                             cudaStream_t s);
   // deformed geometry: y = A x or y = b - A x with stored G (FP64 if gprec is
   // 0, else FP32); cellbuf: n^d (K+1)^d scratch values
+  // cpb: cells per block, 0 = the part's rule (def_apply_candidates lists the
+  // admissible values)
   cudaError_t (*def_apply)(int dim, int prec, const void* x, void* y, const void* b, const void* G, int gprec,
-                           void* cellbuf, int n, cudaStream_t s);
+                           void* cellbuf, int n, int cpb, cudaStream_t s);
   // deformed patch smoother, every patch of the level (output as patch_cart)
   cudaError_t (*patch_def)(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
                            const DefLevel& lev, const PatchParamsHost& P, cudaStream_t s);
@@ -79,8 +81,9 @@ struct KernelTable {
   cudaError_t (*cart_apply_ff)(int dim, const double* x, double* y, const double* b, void* t0, void* t1, void* t2,
                                void* t3, int n, double scale, cudaStream_t s);
   // the same on a deformed or distorted level (3D, K <= 3, FP32-stored G)
-  cudaError_t (*def_apply_ff)(int dim, const double* x, double* y, const double* b, const float* G, int n,
+  cudaError_t (*def_apply_ff)(int dim, const double* x, double* y, const double* b, const float* G, int n, int cpb,
                               cudaStream_t s);
+  int (*def_apply_candidates)(int dim, int prec, int gprec, int* out, int max);
 };
 
 // nullptr when k, dim or prec is out of range

@@ -243,3 +243,33 @@ def test_autotuner_considers_the_interleaved_layout():
     assert lay in (p.PATCH_MAJOR, p.PATCH_INTERLEAVED) and ppc >= 1 and thr % 32 == 0
     with pytest.raises(p.PmgError):                 # no interleaved layout for deformed meshes
         ctx_default(3, 4, 2, geometry=p.DEFORMED, patch_layout=p.PATCH_INTERLEAVED)
+
+
+# ------------------------------------------------------------ deformed apply block shape
+@pytest.mark.parametrize("k,prec,cands", [(3, p.FP32, (4, 8, 16)), (2, p.FP32, (4, 16)), (3, p.FP64, (1, 4, 16)),
+                                          (4, p.FP32, (1, 2, 8))])
+def test_deformed_apply_block_shapes_are_bitwise_equal(k, prec, cands):
+    # cells per block change the packing of cells into blocks, not the
+    # arithmetic of a cell: every admissible value gives the same bits
+    d, n = 3, 6
+    dt = torch.float64 if prec == p.FP64 else torch.float32
+    x = to_dev(random_vector(d, n, k, seed=391), dt)
+    outs = []
+    for cpb in cands:
+        ctx = p.Context(p.make_config(dim=d, n_cells=n, degree=k, n_levels=1, geometry=p.DEFORMED, mg_precision=prec,
+                                      apply_cells_per_block=cpb), device=DEV)
+        assert ctx.apply_cells_per_block() == cpb
+        y = torch.empty_like(x)
+        ctx.apply(x, y, prec=prec)
+        outs.append(y)
+        ctx.close()
+    assert all(torch.equal(o, outs[0]) for o in outs[1:])
+
+
+def test_deformed_apply_block_shape_is_tuned():
+    ctx = p.Context(p.make_config(dim=3, n_cells=32, degree=3, geometry=p.DEFORMED, mg_precision=p.FP32),
+                    device=DEV)
+    assert ctx.apply_cells_per_block() in (4, 8, 16)
+    with pytest.raises(p.PmgError):
+        p.Context(p.make_config(dim=3, n_cells=4, degree=3, geometry=p.DEFORMED, mg_precision=p.FP32,
+                                apply_cells_per_block=5), device=DEV)
