@@ -494,10 +494,27 @@ int vcycle_level(pmg_ctx* c, int level) {
   return smooth_level(c, level, L.b, L.u, nu, false);
 }
 
+// Inverses of Cartesian coarse matrices, shared by the contexts of a process:
+// on the unit square/cube A_0 depends only on (dimension, degree, coarse
+// cells n_0) -- not on the finest mesh -- so the set-up below runs once per
+// (device, dim, degree, n_0, precision) and later contexts copy the inverse
+// (the first solve of a served n_0 = 3, degree 5 request otherwise spends
+// ~0.27 s assembling and inverting its 2,744 x 2,744 coarse matrix).  The
+// cached buffers are device memory held until the process exits.
+struct CoarseKey {
+  int dev, dim, K, n0, prec;
+  bool operator<(const CoarseKey& o) const {
+    return std::tie(dev, dim, K, n0, prec) < std::tie(o.dev, o.dim, o.K, o.n0, o.prec);
+  }
+};
+std::mutex g_coarse_mu;
+std::map<CoarseKey, void*> g_coarse_cache;
+
 // Coarsest level, set up before the first V-cycle: assemble A_0 on the free
 // DoFs by applying the FP64 operator to unit vectors (one row per free DoF,
 // A_0 being symmetric), invert it on the device (Gauss-Jordan, SPD so no
-// pivoting), store the inverse in the MG precision.
+// pivoting), store the inverse in the MG precision; Cartesian inverses come
+// from the process cache when an earlier context computed them.
 int ensure_coarse(pmg_ctx* c) {
   if (c->coarse_ready) return PMG_OK;
   if (!c->plan.coarse_ok)
@@ -511,6 +528,21 @@ int ensure_coarse(pmg_ctx* c) {
   }
   const int nc = (int)idx.size();
   if (nc != c->plan.nc) return fail(PMG_ERR_STATE, "coarse size mismatch");
+  const size_t inv_bytes = (size_t)nc * nc * (c->mg32 ? 4 : 8);
+  int dev = 0;
+  PMG_CUDA(cudaGetDevice(&dev));
+  const CoarseKey ckey{dev, c->dim, c->K, c->plan.n0, c->mgprec};
+  if (!c->deformed && nc > 0) {
+    std::lock_guard<std::mutex> g(g_coarse_mu);
+    auto it = g_coarse_cache.find(ckey);
+    if (it != g_coarse_cache.end()) {
+      PMG_CUDA(cudaMemcpyAsync(c->cidx, idx.data(), 4 * nc, cudaMemcpyHostToDevice, c->stream));
+      PMG_CUDA(cudaMemcpyAsync(c->ainv, it->second, inv_bytes, cudaMemcpyDeviceToDevice, c->stream));
+      PMG_CUDA(cudaStreamSynchronize(c->stream));  // idx is a host temporary
+      c->coarse_ready = true;
+      return PMG_OK;
+    }
+  }
   if (nc > 0) {
     double* A = (double*)at(c, c->plan.a64);
     double* xd = (double*)at(c, c->plan.cx0);  // dedicated: the CG vectors may be live here
@@ -530,6 +562,19 @@ int ensure_coarse(pmg_ctx* c) {
     PMG_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, c->stream));
     PMG_CUDA(cudaStreamSynchronize(c->stream));
     if (hbad) return fail(PMG_ERR_STATE, "coarse matrix is not positive definite");
+    if (!c->deformed) {
+      std::lock_guard<std::mutex> g(g_coarse_mu);
+      if (!g_coarse_cache.count(ckey)) {
+        void* buf = nullptr;
+        if (cudaMalloc(&buf, inv_bytes) == cudaSuccess) {
+          cudaError_t e = cudaMemcpyAsync(buf, c->ainv, inv_bytes, cudaMemcpyDeviceToDevice, c->stream);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+          if (e == cudaSuccess) g_coarse_cache[ckey] = buf;
+          else cudaFree(buf);
+        }
+        cudaGetLastError();  // a failed cache insertion leaves this context correct
+      }
+    }
   }
   c->coarse_ready = true;
   return PMG_OK;

@@ -273,3 +273,19 @@ def test_deformed_apply_block_shape_is_tuned():
     with pytest.raises(p.PmgError):
         p.Context(p.make_config(dim=3, n_cells=4, degree=3, geometry=p.DEFORMED, mg_precision=p.FP32,
                                 apply_cells_per_block=5), device=DEV)
+
+
+def test_cached_coarse_inverse_serves_a_second_hierarchy():
+    # n = 6 and n = 12 at k = 2 share the coarse mesh n_0 = 3: the second
+    # context takes the first one's coarse inverse from the process cache;
+    # both V-cycles match the oracle
+    d, k = 3, 2
+    for n in (6, 12):
+        ctx = ctx_default(d, n, k)
+        h = hier(d, n, k)
+        fine = h.levels[-1]
+        r = random_vector(d, n, k, seed=400 + n)
+        z = torch.empty(fine.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        ctx.vcycle(to_dev(r), z)
+        assert rel(z, full(fine, h.vcycle(r[fine.I]))) < 1e-11
+        ctx.close()
