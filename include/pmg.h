@@ -139,6 +139,9 @@ typedef struct pmg_config {
   int apply_cells_per_block; /* deformed and distorted geometry: cells per thread block of the operator
                           apply, 0 = autotuned (admissible values: 4, 8, 16 for the 3D k <= 3 FP32
                           kernel, else 1, 2, 4, ... while the cell tiles fit) */
+  int patch_persistent; /* Cartesian patch launches: 0 = autotuned, 1 = persistent grids (the blocks the GPU
+                          holds at once take batches of patches from a counter; used on levels with more
+                          than one wave of batches), -1 = one block per batch */
 } pmg_config;
 
 typedef struct pmg_solve_info {
@@ -258,6 +261,9 @@ int64_t pmg_launch_count(void);
  * cached for the process and, if the environment variable PMG_TUNE_FILE
  * names a file, in that file). */
 int pmg_patches_per_block(const pmg_ctx* ctx, int* ppc);
+
+/* 1 if the context's Cartesian patch launches run as persistent grids, else 0. */
+int pmg_patch_persistent(const pmg_ctx* ctx, int* persistent);
 
 /* Cells per thread block of a deformed or distorted context's operator
  * apply in the multigrid precision: the autotuned value (timed at creation

@@ -41,7 +41,7 @@ EXPORTED = [
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
     "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release", "pmg_patch_layout",
-    "pmg_server_set_policy", "pmg_apply_cells_per_block",
+    "pmg_server_set_policy", "pmg_apply_cells_per_block", "pmg_patch_persistent",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -63,6 +63,7 @@ class Config(ctypes.Structure):
         ("smoother", ctypes.c_int), ("vertex_disp", ctypes.c_void_p),
         ("patch_layout", ctypes.c_int), ("patch_threads", ctypes.c_int), ("outer_apply", ctypes.c_int),
         ("geom_precision", ctypes.c_int), ("apply_cells_per_block", ctypes.c_int),
+        ("patch_persistent", ctypes.c_int),
     ]
 
 
@@ -120,6 +121,7 @@ def load_library(path=LIB_PATH):
         "pmg_server_release": (cint, [vp, i64]),
         "pmg_server_set_policy": (cint, [vp, cint, dbl, dbl]),
         "pmg_apply_cells_per_block": (cint, [vp, ctypes.POINTER(cint)]),
+        "pmg_patch_persistent": (cint, [vp, ctypes.POINTER(cint)]),
         "pmg_patch_layout": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]),
     }
     for name, (res, args) in sigs.items():
@@ -140,7 +142,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
                 smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
                 smoother=ADDITIVE, vertex_disp=None, patch_layout=PATCH_AUTO, patch_threads=0, outer_apply=APPLY_FP64,
-                geom_precision=FP32, apply_cells_per_block=0):
+                geom_precision=FP32, apply_cells_per_block=0, patch_persistent=0):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -160,6 +162,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.outer_apply = outer_apply
     c.geom_precision = geom_precision
     c.apply_cells_per_block = apply_cells_per_block
+    c.patch_persistent = patch_persistent
     if vertex_disp is not None:
         # ((n+1)^d, d) float64 displacements of the finest mesh's vertices;
         # the config keeps a reference so the array outlives it
@@ -320,6 +323,12 @@ class Context:
         wp, wj = ctypes.c_double(), (ctypes.c_double * 4)()
         _check(_lib.pmg_damping(self.handle, ctypes.byref(wp), wj))
         return wp.value, list(wj)
+
+    def patch_persistent(self):
+        """True if the Cartesian patch launches run as persistent grids."""
+        v = ctypes.c_int()
+        _check(_lib.pmg_patch_persistent(self.handle, ctypes.byref(v)))
+        return bool(v.value)
 
     def apply_cells_per_block(self):
         """Cells per block of the deformed apply (0: the kernel's rule)."""

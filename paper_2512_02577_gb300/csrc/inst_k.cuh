@@ -115,29 +115,53 @@ static int dinv_len(int dim) {
 // shared memory of the block besides its patches: the inverse-diagonal tables
 static int patch_cart_extra_smem(int dim, int prec) { return dinv_len(dim) * (prec == 0 ? 8 : 4); }
 
+// Grid of a persistent patch launch: every block the GPU can hold at once
+// (occupancy x SMs), at most one per batch.
+static unsigned persistent_grid(const void* kern, int threads, int smem, int64_t nbatch) {
+  int dev = 0, sms = 152, per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int64_t g = std::min<int64_t>(nbatch, (int64_t)sms * per_sm);
+  return (unsigned)std::max<int64_t>(g, 1);
+}
+
 template <int DIM, typename T>
 static cudaError_t patch_cart_t(const T* r, T* dst, int n, int ppc, int n_iter, const T* dinv,
-                                const PatchParamsHost& H, cudaStream_t st) {
+                                const PatchParamsHost& H, int* counter, cudaStream_t st) {
   using S = PatchShape<DIM>;
   const int64_t np = patch_count(DIM, n, H.colour);
   if (np == 0) return cudaSuccess;  // no interior vertex (of this colour), no patch
   if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
-  const int64_t blocks = (np + ppc - 1) / ppc;
+  const int64_t nbatch = (np + ppc - 1) / ppc;
   // more patch lines than threads is fine: every step loops over its lines
   const int threads = std::min(kPatchMaxThreads, (ppc * S::TPP + 31) / 32 * 32);
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const int smem = ppc * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
   if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
-  patch_cart_kernel<DIM, T><<<(unsigned)blocks, threads, smem, st>>>(r, dst, n, ppc, n_iter, dinv, dinv_len(DIM),
-                                                                    to_params<T>(H));
+  unsigned grid = (unsigned)nbatch;
+  if (counter) {
+    grid = persistent_grid((const void*)patch_cart_kernel<DIM, T>, threads, smem, nbatch);
+    if (grid < nbatch) {  // more than one wave: persistent blocks
+      cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+      if (e != cudaSuccess) return e;
+    } else {
+      grid = (unsigned)nbatch;
+      counter = nullptr;
+    }
+  }
+  patch_cart_kernel<DIM, T><<<grid, threads, smem, st>>>(r, dst, n, ppc, n_iter, dinv, dinv_len(DIM), to_params<T>(H),
+                                                         counter, nbatch);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 static cudaError_t patch_cart(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
-                              const void* dinv, const PatchParamsHost& P, cudaStream_t s) {
+                              const void* dinv, const PatchParamsHost& P, int* counter, cudaStream_t s) {
   if (!mine(dim, prec)) return cudaErrorInvalidValue;
-  return patch_cart_t<DP, TP>((const TP*)r, (TP*)dst, n, ppc, n_iter, (const TP*)dinv, P, s);
+  return patch_cart_t<DP, TP>((const TP*)r, (TP*)dst, n, ppc, n_iter, (const TP*)dinv, P, counter, s);
 }
 
 // Interleaved layout: patches per block of this part's interleaved kernel
@@ -152,23 +176,35 @@ static int patch_il_of(int dim, int prec, int n_iter) {
 
 template <int DIM, typename T>
 static cudaError_t patch_cart_il_t(const T* r, T* dst, int n, int threads, int n_iter, const T* dinv,
-                                   const PatchParamsHost& H, cudaStream_t st) {
+                                   const PatchParamsHost& H, int* counter, cudaStream_t st) {
   const int64_t np = patch_count(DIM, n, H.colour);
   if (np == 0) return cudaSuccess;
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const int il = patch_il_of(DIM, prec, n_iter);
   if (il == 0 || threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
   const int smem = il * patch_il_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
-  patch_cart_il_kernel<DIM, T><<<(unsigned)((np + il - 1) / il), threads, smem, st>>>(r, dst, n, n_iter, dinv,
-                                                                                   dinv_len(DIM), to_params<T>(H));
+  const int64_t nbatch = (np + il - 1) / il;
+  unsigned grid = (unsigned)nbatch;
+  if (counter) {
+    grid = persistent_grid((const void*)patch_cart_il_kernel<DIM, T>, threads, smem, nbatch);
+    if (grid < nbatch) {
+      cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+      if (e != cudaSuccess) return e;
+    } else {
+      grid = (unsigned)nbatch;
+      counter = nullptr;
+    }
+  }
+  patch_cart_il_kernel<DIM, T><<<grid, threads, smem, st>>>(r, dst, n, n_iter, dinv, dinv_len(DIM), to_params<T>(H),
+                                                            counter, nbatch);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 static cudaError_t patch_cart_il(int dim, int prec, const void* r, void* dst, int n, int threads, int n_iter,
-                                 const void* dinv, const PatchParamsHost& P, cudaStream_t s) {
+                                 const void* dinv, const PatchParamsHost& P, int* counter, cudaStream_t s) {
   if (!mine(dim, prec)) return cudaErrorInvalidValue;
-  return patch_cart_il_t<DP, TP>((const TP*)r, (TP*)dst, n, threads, n_iter, (const TP*)dinv, P, s);
+  return patch_cart_il_t<DP, TP>((const TP*)r, (TP*)dst, n, threads, n_iter, (const TP*)dinv, P, counter, s);
 }
 
 // u (+)= the summed patch corrections held in dst (add = 0: u = sum)

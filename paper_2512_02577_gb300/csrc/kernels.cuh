@@ -809,14 +809,16 @@ struct PatchMeta {
 // vertices (colour < 0) or over those of parity colour `colour` (vertex
 // index 2 i + 1 for an odd parity bit, 2 i + 2 for an even one).
 template <int DIM>
-__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n, int colour) {
+__device__ __forceinline__ void patch_meta_init(PatchMeta* meta, int np, int n, int colour,
+                                                int64_t batch = -1) {
+  if (batch < 0) batch = blockIdx.x;
   const int c0 = patch_count_1d(n, colour, 0), c1 = patch_count_1d(n, colour, 1);
   const int64_t npatch = patch_count(DIM, n, colour);
   const int step = colour < 0 ? 1 : 2;
   const int b0 = colour < 0 || (colour & 1) ? 1 : 2, b1 = colour < 0 || ((colour >> 1) & 1) ? 1 : 2;
   const int b2 = colour < 0 || ((colour >> 2) & 1) ? 1 : 2;
   for (int g = threadIdx.x; g < np; g += blockDim.x) {
-    const int64_t pid = (int64_t)blockIdx.x * np + g;
+    const int64_t pid = batch * np + g;
     PatchMeta m;
     m.active = pid < npatch;
     int64_t t = m.active ? pid : 0;
@@ -875,20 +877,21 @@ constexpr int patch_il() {
 // Body of the Cartesian patch kernels: gather r_j, Algorithm 2/3, write
 // omega_AS d_j (additive), or add d_j to u for the patches of one colour
 // (multiplicative).  IL: layout of the block's patches (PBlock).
+// Body of the Cartesian patch kernels for the patches of batch `batch` (np
+// patches, lexicographic): gather r_j, Algorithm 2/3, write omega_AS d_j
+// (additive), or add d_j to u for the patches of one colour
+// (multiplicative).  IL: layout of the block's patches (PBlock); sdinv: the
+// inverse-diagonal tables, already staged in shared memory.
 template <int DIM, typename T, int IL>
 __device__ __forceinline__ void patch_cart_body(const T* __restrict__ r, T* __restrict__ dst, int n, int np,
-                                                int n_iter, const T* __restrict__ dinv, int dinv_len,
-                                                const PatchParams<T>& P) {
+                                                int n_iter, const T* sdinv, const PatchParams<T>& P,
+                                                int64_t batch, PatchMeta* meta, T* smem) {
   using S = PatchShape<DIM>;
   constexpr int SZT = S::SZT;
   constexpr int RT = S::off_r(S::L - 1), DT = S::off_d(S::L - 1);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ PatchMeta meta[kMaxPatchesPerBlock];
   const int stride = IL ? S::ELEMS + (n_iter > 1 ? 2 * SZT : 0) : S::template stride<T>(n_iter);
-  const PBlock<T, IL> pb{reinterpret_cast<T*>(smraw), stride, np};
-  T* sdinv = reinterpret_cast<T*>(smraw) + np * stride;  // inverse-diagonal tables of all p-levels
-  for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
-  patch_meta_init<DIM>(meta, np, n, P.colour);
+  const PBlock<T, IL> pb{smem, stride, np};
+  patch_meta_init<DIM>(meta, np, n, P.colour, batch);
   __syncthreads();
   const int N1 = K * n + 1;
   pfor<SZT>(pb, [&](int g, int i) {  // gather r_j = Pi_j r
@@ -907,6 +910,39 @@ __device__ __forceinline__ void patch_cart_body(const T* __restrict__ r, T* __re
   });
 }
 
+// Driver of the body.  counter == nullptr: one batch per block (batch =
+// blockIdx.x).  Otherwise persistent: the block stages the inverse-diagonal
+// tables once, then takes batches of patches from the launch's work counter
+// (reset to 0 before every launch) until none is left, so the grid is sized
+// to the resident blocks of the GPU and the last batches go to whichever
+// blocks finish first.  Each patch's output goes to fixed locations, so the
+// result does not depend on which block computed it.
+template <int DIM, typename T, int IL>
+__device__ __forceinline__ void patch_cart_persistent(const T* __restrict__ r, T* __restrict__ dst, int n, int np,
+                                                      int n_iter, const T* __restrict__ dinv, int dinv_len,
+                                                      const PatchParams<T>& P, int* counter, int64_t nbatch) {
+  using S = PatchShape<DIM>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ PatchMeta meta[kMaxPatchesPerBlock];
+  __shared__ int64_t s_batch;
+  const int stride = IL ? S::ELEMS + (n_iter > 1 ? 2 * S::SZT : 0) : S::template stride<T>(n_iter);
+  T* smem = reinterpret_cast<T*>(smraw);
+  T* sdinv = smem + np * stride;  // inverse-diagonal tables of all p-levels
+  for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
+  if (!counter) {
+    patch_cart_body<DIM, T, IL>(r, dst, n, np, n_iter, sdinv, P, blockIdx.x, meta, smem);
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_batch = atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t batch = s_batch;
+    if (batch >= nbatch) break;  // uniform over the block
+    patch_cart_body<DIM, T, IL>(r, dst, n, np, n_iter, sdinv, P, batch, meta, smem);
+    __syncthreads();  // the batch's shared memory and s_batch are free again
+  }
+}
+
 // Patch-major layout, np patches per block.  FP64, degrees up to 4: at most
 // 256 threads per block and three blocks per SM (registers <= 85), so that
 // 24 warps keep the FP64 pipe fed.  Higher degrees need more registers per
@@ -917,8 +953,8 @@ __device__ __forceinline__ void patch_cart_body(const T* __restrict__ r, T* __re
 template <int DIM, typename T>
 __global__ void PMG_PATCH_BOUNDS
     patch_cart_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int np, int n_iter,
-                      const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
-  patch_cart_body<DIM, T, 0>(r, dst, n, np, n_iter, dinv, dinv_len, P);
+                      const T* __restrict__ dinv, int dinv_len, PatchParams<T> P, int* counter, int64_t nbatch) {
+  patch_cart_persistent<DIM, T, 0>(r, dst, n, np, n_iter, dinv, dinv_len, P, counter, nbatch);
 }
 
 // Interleaved layout, patch_il() patches per block (np = IL): conflict-free
@@ -931,9 +967,9 @@ __global__ void PMG_PATCH_BOUNDS
 template <int DIM, typename T>
 __global__ void PMG_PATCH_IL_BOUNDS
     patch_cart_il_kernel(const T* __restrict__ r, T* __restrict__ dst, int n, int n_iter,
-                         const T* __restrict__ dinv, int dinv_len, PatchParams<T> P) {
+                         const T* __restrict__ dinv, int dinv_len, PatchParams<T> P, int* counter, int64_t nbatch) {
   constexpr int IL = patch_il<DIM, T>() > 0 ? patch_il<DIM, T>() : 1;
-  patch_cart_body<DIM, T, IL>(r, dst, n, IL, n_iter, dinv, dinv_len, P);
+  patch_cart_persistent<DIM, T, IL>(r, dst, n, IL, n_iter, dinv, dinv_len, P, counter, nbatch);
 }
 
 // u (+)= sum over the patches whose interior holds the node of their

@@ -114,7 +114,7 @@ struct Plan {
   };
   std::vector<LOff> lo;
   int64_t t_mg[4], t64[4], cg[6], scal, partial, dtab64, dtab32, cidx, ainv, a64, gjrow, gjcol, gjbad, cx0, cy0;
-  int64_t pbuf = -1, cellbuf = -1;
+  int64_t pbuf = -1, cellbuf = -1, counter = -1;
   int64_t verts = -1;  // distorted: positions of the finest mesh's vertices
   int64_t dtab_len = 0;
   // flexible GMRES (outer_solver GMRES): basis v_0..v_m, z_0..z_{m-1},
@@ -161,6 +161,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     return fail(PMG_ERR_ARG, "unknown geom_precision");
   if (cfg->patches_per_block < 0 || cfg->patch_threads < 0 || cfg->apply_cells_per_block < 0)
     return fail(PMG_ERR_ARG, "patches_per_block, patch_threads, apply_cells_per_block >= 0");
+  if (cfg->patch_persistent < -1 || cfg->patch_persistent > 1) return fail(PMG_ERR_ARG, "patch_persistent in {-1, 0, 1}");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
     return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
@@ -230,6 +231,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
     P.gpart = bump(cur, (int64_t)(P.m + 1) * kDotBlocks * 8);
   }
   P.scal = bump(cur, S_COUNT * 8);
+  P.counter = bump(cur, 16);  // work counter of the persistent patch launches
   P.partial = bump(cur, kDotBlocks * 8 * 2);
   P.dtab_len = 0;
   for (int pl = 1; pl < P.nplev; ++pl) P.dtab_len += ipow64(mp(plev(P.K, pl)), P.dim);
@@ -298,6 +300,8 @@ struct pmg_ctx {
   bool coarse_ready = false;
   void* pbuf = nullptr;
   void* cellbuf = nullptr;
+  int* work_counter = nullptr;
+  bool persistent = false;  // Cartesian patch launches as persistent grids (autotuned)
   double* verts = nullptr;  // distorted geometry: finest-mesh vertex positions
   int ppc = 1;          // patch-major layout: patches per block
   int il_threads = 0;   // > 0: interleaved layout (Cartesian), threads per block
@@ -405,9 +409,10 @@ int patch_solves(pmg_ctx* c, int level, const void* r, int colour = -1, void* u 
     e = c->km()->patch_def(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, D, P, c->stream);
   } else if (use_interleaved(c, level, colour)) {
     e = c->km()->patch_cart_il(c->dim, c->mgprec, r, dst, L.n, c->il_threads, c->cfg.local_cycles, c->dtab_mg, P,
-                               c->stream);
+                               c->persistent ? c->work_counter : nullptr, c->stream);
   } else {
-    e = c->km()->patch_cart(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P, c->stream);
+    e = c->km()->patch_cart(c->dim, c->mgprec, r, dst, L.n, c->ppc, c->cfg.local_cycles, c->dtab_mg, P,
+                            c->persistent ? c->work_counter : nullptr, c->stream);
   }
   if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("patch smoother: ") + cudaGetErrorString(e));
   return PMG_OK;
@@ -634,7 +639,8 @@ int precondition(pmg_ctx* c, const double* r, double* z) {
 // wave matters) -- with CUDA events, best of 3 after a warm-up, and the
 // fastest is kept for the process; with PMG_TUNE_FILE set, results are also
 // read from and appended to that file ("dim k prec geom cycles smoother n
-// layout ppc threads" per line).  Small meshes, whose launches are too short
+// layout ppc threads persistent" per line).  The fastest candidate is then
+// timed once more as a persistent grid (Cartesian), kept if faster.  Small meshes, whose launches are too short
 // to time, use a rule (interleaved with 256 threads where available, else
 // about 256 threads of patch-major patches) without caching it.
 struct TuneKey {
@@ -645,7 +651,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int layout, ppc, threads;
+  int layout, ppc, threads, persistent;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
@@ -662,8 +668,8 @@ void tune_file_read_locked() {
   while (std::fgets(line, sizeof(line), f)) {
     TuneKey k{};
     TuneVal v{};
-    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &k.dim, &k.K, &k.prec, &k.geom, &k.cycles, &k.smoother,
-                    &k.n, &v.layout, &v.ppc, &v.threads) == 10)
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d", &k.dim, &k.K, &k.prec, &k.geom, &k.cycles,
+                    &k.smoother, &k.n, &v.layout, &v.ppc, &v.threads, &v.persistent) == 11)
       g_tune[k] = v;
   }
   std::fclose(f);
@@ -674,8 +680,8 @@ void tune_file_append_locked(const TuneKey& k, const TuneVal& v) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", k.dim, k.K, k.prec, k.geom, k.cycles, k.smoother, k.n, v.layout,
-               v.ppc, v.threads);
+  std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", k.dim, k.K, k.prec, k.geom, k.cycles, k.smoother, k.n,
+               v.layout, v.ppc, v.threads, v.persistent);
   std::fclose(f);
 }
 
@@ -705,6 +711,7 @@ int rule_ppc(const pmg_ctx* c) {
 void set_layout(pmg_ctx* c, const TuneVal& v) {
   c->ppc = v.ppc;
   c->il_threads = v.layout == PMG_PATCH_INTERLEAVED ? v.threads : 0;
+  c->persistent = v.persistent != 0;
 }
 
 int choose_patch_layout(pmg_ctx* c) {
@@ -717,6 +724,7 @@ int choose_patch_layout(pmg_ctx* c) {
                                      "the interleaved patches do not fit in shared memory)");
   c->ppc = rule_ppc(c);
   c->il_threads = 0;
+  c->persistent = cf.patch_persistent > 0 && !c->deformed;
   if (layout == PMG_PATCH_MAJOR && cf.patches_per_block > 0) {
     if (!admissible_ppc(c, cf.patches_per_block)) return fail(PMG_ERR_ARG, "patches_per_block not admissible");
     c->ppc = cf.patches_per_block;
@@ -744,7 +752,9 @@ int choose_patch_layout(pmg_ctx* c) {
     tune_file_read_locked();
     auto it = g_tune.find(key);
     if (it != g_tune.end() && valid(it->second)) {
-      set_layout(c, it->second);
+      TuneVal v = it->second;
+      if (cf.patch_persistent != 0) v.persistent = cf.patch_persistent > 0 && !c->deformed;
+      set_layout(c, v);
       return PMG_OK;
     }
   }
@@ -755,11 +765,11 @@ int choose_patch_layout(pmg_ctx* c) {
       if (!admissible_ppc(c, ppc)) continue;
       const int thr = ppc * tpp, padded = (thr + 31) / 32 * 32;
       if (ppc > 2 && thr < 0.85 * padded) continue;  // warps with many idle lanes: not worth timing
-      cand.push_back({PMG_PATCH_MAJOR, ppc, 0});
+      cand.push_back({PMG_PATCH_MAJOR, ppc, 0, 0});
     }
   if (try_il)
     for (int t : {128, 192, 256, 320, 384, 448, 512, 640, 768, 896, 1024})
-      if (admissible_il(c, t)) cand.push_back({PMG_PATCH_INTERLEAVED, c->ppc, t});
+      if (admissible_il(c, t)) cand.push_back({PMG_PATCH_INTERLEAVED, c->ppc, t, 0});
   const size_t es = c->mg32 ? 4 : 8;
   PMG_CUDA(cudaMemsetAsync(F.r, 0, es * F.N, c->stream));
   PMG_CUDA(cudaMemsetAsync(F.u, 0, es * F.N, c->stream));
@@ -767,12 +777,14 @@ int choose_patch_layout(pmg_ctx* c) {
   PMG_CUDA(cudaEventCreate(&e0));
   PMG_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  TuneVal best_v{c->il_threads > 0 ? PMG_PATCH_INTERLEAVED : PMG_PATCH_MAJOR, c->ppc, c->il_threads};
+  TuneVal best_v{c->il_threads > 0 ? PMG_PATCH_INTERLEAVED : PMG_PATCH_MAJOR, c->ppc, c->il_threads, 0};
   const int64_t before = g_launches.load();
-  for (const TuneVal& v : cand) {
+  // best of 3 timed repetitions after a warm-up; 1e30 if the device rejects
+  // a launch (resources): not a candidate
+  auto time_of = [&](const TuneVal& v) -> float {
     set_layout(c, v);
     float tmin = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+    for (int rep = 0; rep < 4; ++rep) {
       cudaEventRecord(e0, c->stream);
       int rc = PMG_OK;
       if (mult) {
@@ -781,24 +793,33 @@ int choose_patch_layout(pmg_ctx* c) {
         rc = patch_solves(c, c->L - 1, F.r);
       }
       cudaEventRecord(e1, c->stream);
-      if (rc) {  // a launch the device rejects (resources): not a candidate
+      if (rc) {
         cudaGetLastError();
-        tmin = 1e30f;
-        break;
+        return 1e30f;
       }
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) tmin = std::min(tmin, ms);
     }
-    if (tmin < best * 0.995f) {
-      best = tmin;
+    return tmin;
+  };
+  for (const TuneVal& v : cand) {
+    const float t = time_of(v);
+    if (t < best * 0.995f) {
+      best = t;
       best_v = v;
     }
+  }
+  if (!c->deformed && cf.patch_persistent == 0) {  // the winner as a persistent grid, kept if faster
+    TuneVal pv = best_v;
+    pv.persistent = 1;
+    if (time_of(pv) < best * 0.995f) best_v = pv;
   }
   g_launches -= g_launches.load() - before;  // tuning launches are not the caller's work
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (cf.patch_persistent != 0) best_v.persistent = cf.patch_persistent > 0 && !c->deformed;
   set_layout(c, best_v);
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tune[key] = best_v;
@@ -937,6 +958,7 @@ int setup_context(pmg_ctx* c) {
   c->cidx = (int*)at(c, P.cidx);
   c->ainv = at(c, P.ainv);
   c->pbuf = at(c, P.pbuf);
+  c->work_counter = (int*)at(c, P.counter);
   c->cellbuf = at(c, P.cellbuf);
   c->verts = (double*)at(c, P.verts);
 
@@ -1069,6 +1091,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->outer_apply = PMG_OUTER_APPLY_FP64;
   cfg->geom_precision = PMG_FP32;
   cfg->apply_cells_per_block = 0;
+  cfg->patch_persistent = 0;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {
@@ -1532,6 +1555,12 @@ int pmg_damping(const pmg_ctx* c, double* omega_patch, double* omega_jacobi) {
 int pmg_patches_per_block(const pmg_ctx* c, int* ppc) {
   if (check_ctx(c) || !ppc) return fail(PMG_ERR_ARG, "NULL argument");
   *ppc = c->il_threads > 0 ? c->km()->patch_il(c->dim, c->mgprec, c->cfg.local_cycles) : c->ppc;
+  return PMG_OK;
+}
+
+int pmg_patch_persistent(const pmg_ctx* c, int* persistent) {
+  if (check_ctx(c) || !persistent) return fail(PMG_ERR_ARG, "NULL argument");
+  *persistent = c->persistent ? 1 : 0;
   return PMG_OK;
 }
 

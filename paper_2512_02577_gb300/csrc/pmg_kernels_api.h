@@ -42,9 +42,12 @@ struct KernelTable {
   cudaError_t (*cart_apply)(int dim, int prec, const void* x, void* y, const void* b, void* t0, void* t1,
                             void* t2, void* t3, int n, double scale, cudaStream_t s);
   // Cartesian patch smoother, every patch of the level: omega_AS d_j written at
-  // dst[c N + node] for a patch of parity colour c (N nodes of the level)
+  // dst[c N + node] for a patch of parity colour c (N nodes of the level).
+  // counter: nullptr for one block per batch of patches, else one device int
+  // of scratch for a persistent launch (reset on the stream before it; used
+  // only when the batches exceed one wave of resident blocks).
   cudaError_t (*patch_cart)(int dim, int prec, const void* r, void* dst, int n, int ppc, int n_iter,
-                            const void* dinv, const PatchParamsHost& P, cudaStream_t s);
+                            const void* dinv, const PatchParamsHost& P, int* counter, cudaStream_t s);
   // u (+)= sum over the patches holding each node of dst (add = 0: u = sum)
   cudaError_t (*patch_gather)(int dim, int prec, const void* dst, void* u, int n, int add, cudaStream_t s);
   int (*patch_cart_extra_smem)(int dim, int prec);  // block shared bytes besides its patches
@@ -74,7 +77,7 @@ struct KernelTable {
   // multiple of 32); same output as patch_cart; largest admissible threads
   int (*patch_il)(int dim, int prec, int n_iter);
   cudaError_t (*patch_cart_il)(int dim, int prec, const void* r, void* dst, int n, int threads, int n_iter,
-                               const void* dinv, const PatchParamsHost& P, cudaStream_t s);
+                               const void* dinv, const PatchParamsHost& P, int* counter, cudaStream_t s);
   int (*patch_il_max_threads)(int dim, int prec);
   // y = A x (b == nullptr) or y = b - A x for FP64 x, y, b on a Cartesian
   // level, computed in float-float arithmetic; t0..t3: scratch of N doubles

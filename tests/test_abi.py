@@ -45,6 +45,8 @@ def test_status_strings():
     (dict(outer_solver=7), p.PMG_ERR_ARG),
     (dict(smoother=2), p.PMG_ERR_ARG),
     (dict(geometry=p.DISTORTED), p.PMG_ERR_ARG),            # no vertex displacements
+    (dict(patch_persistent=2), p.PMG_ERR_ARG),
+    (dict(patch_persistent=-2), p.PMG_ERR_ARG),
 ])
 def test_bytes_required_rejects(kw, code):
     with pytest.raises(p.PmgError) as e:

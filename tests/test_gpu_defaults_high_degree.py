@@ -289,3 +289,26 @@ def test_cached_coarse_inverse_serves_a_second_hierarchy():
         ctx.vcycle(to_dev(r), z)
         assert rel(z, full(fine, h.vcycle(r[fine.I]))) < 1e-11
         ctx.close()
+
+
+@pytest.mark.parametrize("k,prec,lay", [(4, p.FP32, p.PATCH_MAJOR), (4, p.FP64, p.PATCH_MAJOR),
+                                        (7, p.FP32, p.PATCH_MAJOR), (3, p.FP32, p.PATCH_INTERLEAVED)])
+def test_persistent_patch_launches_are_bitwise_equal(k, prec, lay):
+    # persistent grids take batches of patches from a counter; every patch is
+    # computed by the same code and written to the same place
+    d, n = 3, 32 if k <= 4 else 16
+    dt = torch.float64 if prec == p.FP64 else torch.float32
+    b = to_dev(random_vector(d, n, k, seed=395), dt)
+    outs = []
+    for pers in (-1, 1):
+        for sm in (p.ADDITIVE, p.MULTIPLICATIVE):
+            kw = dict(patches_per_block=2) if lay == p.PATCH_MAJOR else dict(patch_threads=256)
+            ctx = ctx_default(d, n, k, prec=prec, patch_layout=lay, patch_persistent=pers, smoother=sm, **kw)
+            assert ctx.patch_persistent() == (pers > 0)
+            u = torch.zeros_like(b)
+            ctx.smooth(b, u, sweeps=2)
+            outs.append((sm, u))
+            ctx.close()
+    for sm in (p.ADDITIVE, p.MULTIPLICATIVE):
+        got = [u for s_, u in outs if s_ == sm]
+        assert torch.equal(got[0], got[1])
