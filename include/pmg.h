@@ -237,6 +237,25 @@ int pmg_solve_host(pmg_ctx* ctx, const double* b_host, double* x_host, double rt
 int pmg_solve_start(pmg_ctx* ctx, const double* b, int b_on_host, double* x, int x_on_host, double rtol, int maxit);
 int pmg_solve_progress(pmg_ctx* ctx, int* done, pmg_solve_info* info);
 
+/* Solve count (1..32) systems at once, each on its own context, with every
+ * kernel launch covering all of them (not in the paper: batching of
+ * concurrent solves).  The contexts must share the dimension, degree, MG
+ * precision, smoother, local cycles, half cycle, smoothing steps and outer
+ * operator, and be Cartesian, PCG, with a coarse level of <= 4096 free DoFs;
+ * their mesh sizes (and numbers of levels) and damping may differ.  b[i],
+ * x[i]: device double vectors of context i's finest level.  The systems
+ * iterate in lockstep (one CG iteration of every unconverged system per
+ * round); each stops at its own tolerance or maxit, and its iterations and
+ * x are bitwise those of pmg_solve on its context.  Runs on ctxs[0]'s
+ * stream, after the work already enqueued on every context's stream;
+ * blocks until all are done.  info: count entries (or NULL).  Returns
+ * PMG_OK, PMG_NOT_CONVERGED if any system stopped at maxit, or the first
+ * error (PMG_ERR_ARG for a mismatched or repeated context, PMG_ERR_UNSUPPORTED
+ * for a context that cannot be grouped).  Allocates a few bytes of device
+ * memory for its duration. */
+int pmg_solve_group(pmg_ctx* const* ctxs, int count, const double* const* b, double* const* x, double rtol,
+                    int maxit, pmg_solve_info* info);
+
 /* b_i = int f phi_i with f = d pi^2 prod_i sin(pi x_i), the load for the
  * manufactured solution u = prod_i sin(pi x_i), (k+1)-point Gauss rule, on
  * the finest level (device, double). */
@@ -344,6 +363,17 @@ int pmg_server_result(pmg_server* server, int64_t request_id, int* state, pmg_so
  * blocks of large ones.  Applies to requests admitted after the call. */
 enum pmg_serve_policy { PMG_SERVE_FIFO = 0, PMG_SERVE_SHORTEST_FIRST = 1 };
 int pmg_server_set_policy(pmg_server* server, int policy, double max_wait_s, double small_work);
+
+/* Grouped launches across concurrent requests (continuous batching; off by
+ * default): a running request whose estimated work is at most max_work and
+ * whose method allows it (as pmg_solve_group) joins the group of running
+ * requests with the same method -- any mesh size -- and is solved with them
+ * in lockstep, each launch of an iteration covering every member, members
+ * joining at the next round and leaving when converged, up to max_group
+ * (1..32) members per group, each group on its own high-priority stream.
+ * Results are bitwise those of the request solved alone.  enable = 0 turns
+ * grouping off for requests admitted after the call. */
+int pmg_server_set_grouping(pmg_server* server, int enable, double max_work, int max_group);
 
 /* Forget a finished (done or failed) request: its id becomes unknown.  The
  * server keeps every request until it is released or the server destroyed,

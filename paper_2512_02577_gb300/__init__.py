@@ -41,7 +41,8 @@ EXPORTED = [
     "pmg_patches_per_block", "pmg_solve_start", "pmg_solve_progress", "pmg_server_create",
     "pmg_server_destroy", "pmg_server_submit", "pmg_server_poll", "pmg_server_result", "pmg_server_stats",
     "pmg_smoother_phase_times", "pmg_damping", "pmg_default_damping", "pmg_server_release", "pmg_patch_layout",
-    "pmg_server_set_policy", "pmg_apply_cells_per_block", "pmg_patch_persistent",
+    "pmg_server_set_policy", "pmg_apply_cells_per_block", "pmg_patch_persistent", "pmg_solve_group",
+    "pmg_server_set_grouping",
 ]
 NOALLOC_MAX_DOFS = 2097152
 
@@ -120,6 +121,8 @@ def load_library(path=LIB_PATH):
         "pmg_default_damping": (cint, [cint, cint, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pmg_server_release": (cint, [vp, i64]),
         "pmg_server_set_policy": (cint, [vp, cint, dbl, dbl]),
+        "pmg_server_set_grouping": (cint, [vp, cint, dbl, cint]),
+        "pmg_solve_group": (cint, [vp, cint, vp, vp, dbl, cint, vp]),
         "pmg_apply_cells_per_block": (cint, [vp, ctypes.POINTER(cint)]),
         "pmg_patch_persistent": (cint, [vp, ctypes.POINTER(cint)]),
         "pmg_patch_layout": (cint, [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)]),
@@ -351,6 +354,25 @@ class Context:
         _check(_lib.pmg_synchronize(self.handle))
 
 
+def solve_group(ctxs, bs, xs, rtol=1e-8, maxit=500):
+    """Solve several systems at once, every launch covering all of them
+    (pmg_solve_group): contexts of one method, any mesh sizes; bs, xs: CUDA
+    float64 vectors of each context's finest level.  Returns a SolveInfo per
+    system; raises on an error (PMG_NOT_CONVERGED is reported in the infos)."""
+    m = len(ctxs)
+    if not (len(bs) == len(xs) == m) or m < 1:
+        raise ValueError("one b and one x per context")
+    H = (ctypes.c_void_p * m)(*[c.handle.value for c in ctxs])
+    B = (ctypes.c_void_p * m)(*[_ptr(b, torch.float64, c.num_dofs()).value for c, b in zip(ctxs, bs)])
+    X = (ctypes.c_void_p * m)(*[_ptr(x, torch.float64, c.num_dofs()).value for c, x in zip(ctxs, xs)])
+    infos = (SolveInfo * m)()
+    with torch.cuda.device(ctxs[0].device):
+        rc = _lib.pmg_solve_group(H, m, B, X, rtol, maxit, infos)
+    if rc < 0:
+        _check(rc)
+    return list(infos)
+
+
 class Server:
     """Serving loop over resident contexts (native, see include/pmg.h).
 
@@ -358,7 +380,11 @@ class Server:
     and x; poll() never blocks; result() reports state, solve info and the
     submit/admit/done host times."""
 
-    def __init__(self, memory_budget_bytes=0, max_active=8, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0):
+    def __init__(self, memory_budget_bytes=0, max_active=8, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0,
+                 group_work=0.0, max_group=8):
+        """group_work > 0: requests of estimated work (finest-grid nodes x
+        (degree + 2)) up to group_work run in groups of up to max_group
+        (pmg_server_set_grouping)."""
         lib = load_library()
         h = ctypes.c_void_p()
         _check(lib.pmg_server_create(int(memory_budget_bytes), int(max_active), ctypes.byref(h)))
@@ -366,6 +392,8 @@ class Server:
         self._keep = {}
         if policy != SERVE_FIFO:
             _check(lib.pmg_server_set_policy(h, policy, float(max_wait_s), float(small_work)))
+        if group_work > 0:
+            _check(lib.pmg_server_set_grouping(h, 1, float(group_work), int(max_group)))
 
     def submit(self, cfg, b_host, x_host, rtol=1e-8, maxit=500):
         for t in (b_host, x_host):

@@ -268,6 +268,258 @@ static cudaError_t h_restrict(int dim, int prec, const void* rf, void* rc, void*
   return h_restrict_t<DP, TP>((const TP*)rf, (TP*)rc, (TP*)t0, (TP*)t1, nc, s);
 }
 
+// ---------------------------------------------------------------- grouped launches
+// One launch per pass for all jobs; every job's results are those of its own
+// launch (each thread takes the same grid-stride slice of every job; the
+// patch launch gives each batch of each job to one block).
+static int64_t apply_work(int dim, int n) {
+  const int64_t N1 = (int64_t)K * n + 1;
+  return (int64_t)(n + 1) * (dim == 3 ? N1 * N1 : N1);
+}
+
+static bool group_ok(int count) { return count >= 1 && count <= kMaxGroup; }
+
+template <int DIM, typename T>
+static cudaError_t cart_apply_group_t(int count, const ApplyJob* jobs, cudaStream_t st) {
+  GroupOf<CartPassJob<T>> g0, g1, g2;
+  g0.count = g1.count = g2.count = count;
+  int64_t work = 0;
+  bool resid = jobs[0].b != nullptr;
+  for (int j = 0; j < count; ++j) {
+    const ApplyJob& a = jobs[j];
+    if ((a.b != nullptr) != resid) return cudaErrorInvalidValue;  // one pass kind per launch
+    const T* x = (const T*)a.x;
+    T* t0 = (T*)a.t[0];
+    T* t1 = (T*)a.t[1];
+    T* t2 = (T*)a.t[2];
+    T* t3 = (T*)a.t[3];
+    const T s = (T)a.scale;
+    g0.job[j] = CartPassJob<T>{x, nullptr, t0, t1, nullptr, a.n, s};
+    if (DIM == 3) {
+      g1.job[j] = CartPassJob<T>{t0, t1, t2, t3, nullptr, a.n, s};
+      g2.job[j] = CartPassJob<T>{t2, t3, (T*)a.y, nullptr, (const T*)a.b, a.n, s};
+    } else {
+      g1.job[j] = CartPassJob<T>{t0, t1, (T*)a.y, nullptr, (const T*)a.b, a.n, s};
+    }
+    work += apply_work(DIM, a.n);
+  }
+  const int bs = 256, g = grid_for(work, bs);
+  if (DIM == 3) {
+    cart_pass_group<3, 0, 0, false, T><<<g, bs, 0, st>>>(g0);
+    cart_pass_group<3, 1, 1, false, T><<<g, bs, 0, st>>>(g1);
+    if (resid) cart_pass_group<3, 2, 2, true, T><<<g, bs, 0, st>>>(g2);
+    else cart_pass_group<3, 2, 2, false, T><<<g, bs, 0, st>>>(g2);
+    g_launches += 3;
+  } else {
+    cart_pass_group<2, 0, 0, false, T><<<g, bs, 0, st>>>(g0);
+    if (resid) cart_pass_group<2, 1, 2, true, T><<<g, bs, 0, st>>>(g1);
+    else cart_pass_group<2, 1, 2, false, T><<<g, bs, 0, st>>>(g1);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t cart_apply_group(int dim, int prec, int count, const ApplyJob* jobs, cudaStream_t s) {
+  if (!mine(dim, prec) || !group_ok(count)) return cudaErrorInvalidValue;
+  return cart_apply_group_t<DP, TP>(count, jobs, s);
+}
+
+template <int DIM>
+static cudaError_t cart_apply_ff_group_t(int count, const ApplyJob* jobs, cudaStream_t st) {
+  GroupOf<CartPassFFJob> g0, g1, g2;
+  g0.count = g1.count = g2.count = count;
+  int64_t work = 0;
+  const bool resid = jobs[0].b != nullptr;
+  for (int j = 0; j < count; ++j) {
+    const ApplyJob& a = jobs[j];
+    if ((a.b != nullptr) != resid) return cudaErrorInvalidValue;
+    const float sh = (float)a.scale;
+    const ff s{sh, (float)(a.scale - (double)sh)};
+    float *f0 = (float*)a.t[0], *f1 = (float*)a.t[1], *f2 = (float*)a.t[2], *f3 = (float*)a.t[3];
+    g0.job[j] = CartPassFFJob{a.x, nullptr, f0, f1, nullptr, a.n, s};
+    if (DIM == 3) {
+      g1.job[j] = CartPassFFJob{f0, f1, f2, f3, nullptr, a.n, s};
+      g2.job[j] = CartPassFFJob{f2, f3, a.y, nullptr, (const double*)a.b, a.n, s};
+    } else {
+      g1.job[j] = CartPassFFJob{f0, f1, a.y, nullptr, (const double*)a.b, a.n, s};
+    }
+    work += apply_work(DIM, a.n);
+  }
+  const int bs = 256, g = grid_for(work, bs);
+  if (DIM == 3) {
+    cart_pass_ff_group<3, 0, 0, false><<<g, bs, 0, st>>>(g0);
+    cart_pass_ff_group<3, 1, 1, false><<<g, bs, 0, st>>>(g1);
+    if (resid) cart_pass_ff_group<3, 2, 2, true><<<g, bs, 0, st>>>(g2);
+    else cart_pass_ff_group<3, 2, 2, false><<<g, bs, 0, st>>>(g2);
+    g_launches += 3;
+  } else {
+    cart_pass_ff_group<2, 0, 0, false><<<g, bs, 0, st>>>(g0);
+    if (resid) cart_pass_ff_group<2, 1, 2, true><<<g, bs, 0, st>>>(g1);
+    else cart_pass_ff_group<2, 1, 2, false><<<g, bs, 0, st>>>(g1);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t cart_apply_ff_group(int dim, int count, const ApplyJob* jobs, cudaStream_t s) {
+  if (dim != DP || !group_ok(count)) return cudaErrorInvalidValue;
+  return cart_apply_ff_group_t<DP>(count, jobs, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t patch_cart_group_t(int count, const PatchSolveJob* jobs, int ppc, int n_iter, const T* dinv,
+                                      int* counter, cudaStream_t st) {
+  using S = PatchShape<DIM>;
+  if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
+  GroupOf<PatchJob<T>> G;
+  G.count = 0;
+  int64_t nbatch = 0;
+  for (int j = 0; j < count; ++j) {
+    const int64_t np = patch_count(DIM, jobs[j].n, jobs[j].P.colour);
+    if (np == 0) continue;  // no patch (of this colour) on this job's level
+    PatchJob<T>& J = G.job[G.count++];
+    J.r = (const T*)jobs[j].r;
+    J.dst = (T*)jobs[j].dst;
+    J.n = jobs[j].n;
+    J.first = nbatch;
+    J.P = to_params<T>(jobs[j].P);
+    nbatch += (np + ppc - 1) / ppc;
+  }
+  if (G.count == 0) return cudaSuccess;
+  const int threads = std::min(kPatchMaxThreads, (ppc * S::TPP + 31) / 32 * 32);
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int smem = ppc * patch_smem(DIM, prec, n_iter) + patch_cart_extra_smem(DIM, prec);
+  if (smem > kMaxDynSmem) return cudaErrorInvalidConfiguration;
+  unsigned grid = (unsigned)nbatch;
+  if (counter) {
+    grid = persistent_grid((const void*)patch_cart_group_kernel<DIM, T>, threads, smem, nbatch);
+    if (grid < nbatch) {
+      cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+      if (e != cudaSuccess) return e;
+    } else {
+      grid = (unsigned)nbatch;
+      counter = nullptr;
+    }
+  }
+  patch_cart_group_kernel<DIM, T><<<grid, threads, smem, st>>>(ppc, n_iter, dinv, dinv_len(DIM), counter, nbatch, G);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+static cudaError_t patch_cart_group(int dim, int prec, int count, const PatchSolveJob* jobs, int ppc, int n_iter,
+                                    const void* dinv, int* counter, cudaStream_t s) {
+  if (!mine(dim, prec) || !group_ok(count)) return cudaErrorInvalidValue;
+  return patch_cart_group_t<DP, TP>(count, jobs, ppc, n_iter, (const TP*)dinv, counter, s);
+}
+
+template <int DIM, typename T>
+static cudaError_t patch_gather_group_t(int count, const GatherSolveJob* jobs, int add, cudaStream_t st) {
+  GroupOf<GatherJob<T>> G;
+  G.count = count;
+  int64_t work = 0;
+  for (int j = 0; j < count; ++j) {
+    G.job[j] = GatherJob<T>{(const T*)jobs[j].dst, (T*)jobs[j].u, jobs[j].n};
+    work += ipow(K * jobs[j].n + 1, DIM);
+  }
+  if (add) patch_gather_group<DIM, true, T><<<grid_for(work, 256), 256, 0, st>>>(G);
+  else patch_gather_group<DIM, false, T><<<grid_for(work, 256), 256, 0, st>>>(G);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+static cudaError_t patch_gather_group(int dim, int prec, int count, const GatherSolveJob* jobs, int add,
+                                     cudaStream_t s) {
+  if (!mine(dim, prec) || !group_ok(count)) return cudaErrorInvalidValue;
+  return patch_gather_group_t<DP, TP>(count, jobs, add, s);
+}
+
+// The passes of h_prolong_t / h_restrict_t with each job's extents.
+template <int DIM, typename T>
+static cudaError_t h_prolong_group_t(int count, const TransferSolveJob* jobs, cudaStream_t st) {
+  GroupOf<TransferJob<T>> g[3];
+  int64_t work[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i) g[i].count = count;
+  for (int j = 0; j < count; ++j) {
+    const TransferSolveJob& a = jobs[j];
+    const int nc = a.nc, c1 = K * nc + 1, f1 = 2 * K * nc + 1;
+    const T* uc = (const T*)a.in;
+    T *uf = (T*)a.out, *t0 = (T*)a.t0, *t1 = (T*)a.t1;
+    if (DIM == 3) {
+      g[0].job[j] = TransferJob<T>{uc, t0, nc, f1, c1, c1};
+      g[1].job[j] = TransferJob<T>{t0, t1, nc, f1, f1, c1};
+      g[2].job[j] = TransferJob<T>{t1, uf, nc, f1, f1, f1};
+      work[0] += (int64_t)f1 * c1 * c1;
+      work[1] += (int64_t)f1 * f1 * c1;
+      work[2] += (int64_t)f1 * f1 * f1;
+    } else {
+      g[0].job[j] = TransferJob<T>{uc, t0, nc, f1, c1, 1};
+      g[1].job[j] = TransferJob<T>{t0, uf, nc, f1, f1, 1};
+      work[0] += (int64_t)f1 * c1;
+      work[1] += (int64_t)f1 * f1;
+    }
+  }
+  const int bs = 256;
+  if (DIM == 3) {
+    hprolong_group<0, false, T><<<grid_for(work[0], bs), bs, 0, st>>>(g[0]);
+    hprolong_group<1, false, T><<<grid_for(work[1], bs), bs, 0, st>>>(g[1]);
+    hprolong_group<2, true, T><<<grid_for(work[2], bs), bs, 0, st>>>(g[2]);
+    g_launches += 3;
+  } else {
+    hprolong_group<0, false, T><<<grid_for(work[0], bs), bs, 0, st>>>(g[0]);
+    hprolong_group<1, true, T><<<grid_for(work[1], bs), bs, 0, st>>>(g[1]);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+template <int DIM, typename T>
+static cudaError_t h_restrict_group_t(int count, const TransferSolveJob* jobs, cudaStream_t st) {
+  GroupOf<TransferJob<T>> g[3];
+  int64_t work[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i) g[i].count = count;
+  for (int j = 0; j < count; ++j) {
+    const TransferSolveJob& a = jobs[j];
+    const int nc = a.nc, c1 = K * nc + 1, f1 = 2 * K * nc + 1;
+    const T* rf = (const T*)a.in;
+    T *rc = (T*)a.out, *t0 = (T*)a.t0, *t1 = (T*)a.t1;
+    if (DIM == 3) {
+      g[0].job[j] = TransferJob<T>{rf, t0, nc, f1, f1, c1};
+      g[1].job[j] = TransferJob<T>{t0, t1, nc, f1, c1, c1};
+      g[2].job[j] = TransferJob<T>{t1, rc, nc, c1, c1, c1};
+      work[0] += (int64_t)f1 * f1 * c1;
+      work[1] += (int64_t)f1 * c1 * c1;
+      work[2] += (int64_t)c1 * c1 * c1;
+    } else {
+      g[0].job[j] = TransferJob<T>{rf, t0, nc, f1, c1, 1};
+      g[1].job[j] = TransferJob<T>{t0, rc, nc, c1, c1, 1};
+      work[0] += (int64_t)f1 * c1;
+      work[1] += (int64_t)c1 * c1;
+    }
+  }
+  const int bs = 256;
+  if (DIM == 3) {
+    hrestrict_group<2, T><<<grid_for(work[0], bs), bs, 0, st>>>(g[0]);
+    hrestrict_group<1, T><<<grid_for(work[1], bs), bs, 0, st>>>(g[1]);
+    hrestrict_group<0, T><<<grid_for(work[2], bs), bs, 0, st>>>(g[2]);
+    g_launches += 3;
+  } else {
+    hrestrict_group<1, T><<<grid_for(work[0], bs), bs, 0, st>>>(g[0]);
+    hrestrict_group<0, T><<<grid_for(work[1], bs), bs, 0, st>>>(g[1]);
+    g_launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t h_prolong_add_group(int dim, int prec, int count, const TransferSolveJob* jobs, cudaStream_t s) {
+  if (!mine(dim, prec) || !group_ok(count)) return cudaErrorInvalidValue;
+  return h_prolong_group_t<DP, TP>(count, jobs, s);
+}
+
+static cudaError_t h_restrict_group(int dim, int prec, int count, const TransferSolveJob* jobs, cudaStream_t s) {
+  if (!mine(dim, prec) || !group_ok(count)) return cudaErrorInvalidValue;
+  return h_restrict_group_t<DP, TP>(count, jobs, s);
+}
+
 // Opt every kernel of this degree into the largest dynamic shared memory the
 // device allows next to the kernel's static shared memory (called once per
 // device at context creation, outside any stream capture).
@@ -311,6 +563,7 @@ static cudaError_t prepare() {
   cudaError_t r = cudaSuccess;
   auto acc = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
   acc(allow_smem(patch_cart_kernel<DP, TP>, optin));
+  acc(allow_smem(patch_cart_group_kernel<DP, TP>, optin));
   if (patch_il<DP, TP>() > 0) acc(allow_smem(patch_cart_il_kernel<DP, TP>, optin));
   acc(allow_smem(patch_def_kernel<DP, TP, float>, optin));
   acc(allow_smem(patch_def_kernel<DP, TP, double>, optin));
@@ -347,6 +600,12 @@ const KernelTable* PMG_TABLE_FN() {
       PMG_KNS::cart_apply_ff,
       PMG_KNS::def_apply_ff,
       PMG_KNS::def_apply_candidates,
+      PMG_KNS::cart_apply_group,
+      PMG_KNS::cart_apply_ff_group,
+      PMG_KNS::patch_cart_group,
+      PMG_KNS::patch_gather_group,
+      PMG_KNS::h_prolong_add_group,
+      PMG_KNS::h_restrict_group,
   };
   return &t;
 }

@@ -71,15 +71,14 @@ __device__ __forceinline__ const float* ctab<float>() { return c_tab32; }
 // One thread owns the K outputs of one cell segment of one grid line.
 // ===========================================================================
 template <int DIM, int AX, int MODE, bool RESID, typename T>
-__global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, const T* __restrict__ in1,
-                                                 T* __restrict__ out0, T* __restrict__ out1,
-                                                 const T* __restrict__ bvec, int n, T s) {
+__device__ __forceinline__ void cart_pass_body(const T* __restrict__ in0, const T* __restrict__ in1,
+                                               T* __restrict__ out0, T* __restrict__ out1,
+                                               const T* __restrict__ bvec, int n, T s, int64_t t0, int64_t tstep) {
   const int N1 = K * n + 1;
   const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
   const int64_t total = (int64_t)(n + 1) * lines;
   const T* C = ctab<T>();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < total; t += tstep) {
     int c, p, q;
     if (AX == 0) {
       c = (int)(t % (n + 1));
@@ -167,6 +166,38 @@ __global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, cons
   }
 }
 
+template <int DIM, int AX, int MODE, bool RESID, typename T>
+__global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, const T* __restrict__ in1,
+                                                 T* __restrict__ out0, T* __restrict__ out1,
+                                                 const T* __restrict__ bvec, int n, T s) {
+  cart_pass_body<DIM, AX, MODE, RESID, T>(in0, in1, out0, out1, bvec, n, s,
+                                          (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                          (int64_t)gridDim.x * blockDim.x);
+}
+
+// Grouped launch: the same pass over every job's level (jobs of one launch
+// may have different n); each thread takes the same grid-stride slice of
+// every job in turn, so a job's outputs are those of its own launch.
+template <typename T>
+struct CartPassJob {
+  const T* in0;
+  const T* in1;
+  T* out0;
+  T* out1;
+  const T* bvec;
+  int n;
+  T s;
+};
+
+template <int DIM, int AX, int MODE, bool RESID, typename T>
+__global__ void __launch_bounds__(256) cart_pass_group(const __grid_constant__ GroupOf<CartPassJob<T>> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    const CartPassJob<T>& a = G.job[j];
+    cart_pass_body<DIM, AX, MODE, RESID, T>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t0, ts);
+  }
+}
+
 // ===========================================================================
 // The same three passes in float-float arithmetic: FP64 input x and output y,
 // every product and sum carried as an unevaluated pair of floats (hi + lo,
@@ -233,9 +264,10 @@ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (do
 // MODE as cart_pass; in0 is FP64 in MODE 0 (x), else a float-pair plane;
 // out0 / out1 are float-pair planes in MODE 0, 1; in MODE 2 out0 is FP64.
 template <int DIM, int AX, int MODE, bool RESID>
-__global__ void __launch_bounds__(256) cart_pass_ff(const void* __restrict__ in0_, const float* __restrict__ in1,
-                                                    void* __restrict__ out0_, float* __restrict__ out1,
-                                                    const double* __restrict__ bvec, int n, ff s) {
+__device__ __forceinline__ void cart_pass_ff_body(const void* __restrict__ in0_, const float* __restrict__ in1,
+                                                  void* __restrict__ out0_, float* __restrict__ out1,
+                                                  const double* __restrict__ bvec, int n, ff s, int64_t t0,
+                                                  int64_t tstep) {
   const int N1 = K * n + 1;
   const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
   const int64_t total = (int64_t)(n + 1) * lines;
@@ -254,8 +286,7 @@ __global__ void __launch_bounds__(256) cart_pass_ff(const void* __restrict__ in0
     pl[o] = v.hi;
     pl[NN + o] = v.lo;
   };
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < total; t += tstep) {
     int c, p, q;
     if (AX == 0) {
       c = (int)(t % (n + 1));
@@ -340,6 +371,34 @@ __global__ void __launch_bounds__(256) cart_pass_ff(const void* __restrict__ in0
         yout[o] = bnd ? 0.0 : v;
       }
     }
+  }
+}
+
+template <int DIM, int AX, int MODE, bool RESID>
+__global__ void __launch_bounds__(256) cart_pass_ff(const void* __restrict__ in0, const float* __restrict__ in1,
+                                                    void* __restrict__ out0, float* __restrict__ out1,
+                                                    const double* __restrict__ bvec, int n, ff s) {
+  cart_pass_ff_body<DIM, AX, MODE, RESID>(in0, in1, out0, out1, bvec, n, s,
+                                          (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                          (int64_t)gridDim.x * blockDim.x);
+}
+
+struct CartPassFFJob {
+  const void* in0;
+  const float* in1;
+  void* out0;
+  float* out1;
+  const double* bvec;
+  int n;
+  ff s;
+};
+
+template <int DIM, int AX, int MODE, bool RESID>
+__global__ void __launch_bounds__(256) cart_pass_ff_group(const __grid_constant__ GroupOf<CartPassFFJob> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    const CartPassFFJob& a = G.job[j];
+    cart_pass_ff_body<DIM, AX, MODE, RESID>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t0, ts);
   }
 }
 
@@ -972,6 +1031,52 @@ __global__ void PMG_PATCH_IL_BOUNDS
   patch_cart_persistent<DIM, T, IL>(r, dst, n, IL, n_iter, dinv, dinv_len, P, counter, nbatch);
 }
 
+// Grouped patch launch: the batches of every job (one level of one system;
+// the jobs of a launch may differ in n, damping and scale) are numbered job
+// after job, and a block finds the job of its batch from the jobs' first
+// batch indices.  Patch-major layout; counter as patch_cart_persistent (the
+// batches of all jobs are one work list, so blocks that finish a small
+// system's patches go on to the next system's).  The inverse-diagonal
+// tables depend only on the dimension, degree and precision, which every
+// job of a launch shares.
+template <typename T>
+struct PatchJob {
+  const T* r;
+  T* dst;
+  int n;
+  int64_t first;  // global index of the job's first batch
+  PatchParams<T> P;
+};
+
+template <int DIM, typename T>
+__global__ void PMG_PATCH_BOUNDS patch_cart_group_kernel(int np, int n_iter, const T* __restrict__ dinv, int dinv_len,
+                                                         int* counter, int64_t nbatch,
+                                                         const __grid_constant__ GroupOf<PatchJob<T>> G) {
+  using S = PatchShape<DIM>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ PatchMeta meta[kMaxPatchesPerBlock];
+  __shared__ int64_t s_batch;
+  const int stride = S::template stride<T>(n_iter);
+  T* smem = reinterpret_cast<T*>(smraw);
+  T* sdinv = smem + np * stride;
+  for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
+  int64_t b = blockIdx.x;
+  for (;;) {
+    if (counter) {
+      if (threadIdx.x == 0) s_batch = atomicAdd(counter, 1);
+      __syncthreads();
+      b = s_batch;
+    }
+    if (b >= nbatch) break;  // uniform over the block
+    int j = 0;
+    while (j + 1 < G.count && G.job[j + 1].first <= b) ++j;
+    const PatchJob<T>& J = G.job[j];
+    patch_cart_body<DIM, T, 0>(J.r, J.dst, J.n, np, n_iter, sdinv, J.P, b - J.first, meta, smem);
+    if (!counter) break;
+    __syncthreads();  // the batch's shared memory and s_batch are free again
+  }
+}
+
 // u (+)= sum over the patches whose interior holds the node of their
 // correction.  The patch kernels write the correction of a patch of colour c
 // at dst[c N + node] (N = nodes of the level); a node is covered by colour c
@@ -979,10 +1084,11 @@ __global__ void PMG_PATCH_IL_BOUNDS
 // two vertices whose patch holds the node lies in 1..n-1.  Fixed order:
 // colours 0..2^d-1.  Boundary nodes get no contribution.
 template <int DIM, bool ADD, typename T>
-__global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ dst, T* __restrict__ u, int n) {
+__device__ __forceinline__ void patch_gather_body(const T* __restrict__ dst, T* __restrict__ u, int n, int64_t t0,
+                                                  int64_t tstep) {
   const int N1 = K * n + 1, nv = n - 1;
   const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < N; t += tstep) {
     const int gd[3] = {(int)(t % N1), (int)((t / N1) % N1), DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0};
     // per direction and parity: is there a vertex of that parity holding the node?
     unsigned has[3] = {0u, 0u, 0u};
@@ -1004,6 +1110,25 @@ __global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__
   }
 }
 
+template <int DIM, bool ADD, typename T>
+__global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ dst, T* __restrict__ u, int n) {
+  patch_gather_body<DIM, ADD, T>(dst, u, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                 (int64_t)gridDim.x * blockDim.x);
+}
+
+template <typename T>
+struct GatherJob {
+  const T* dst;
+  T* u;
+  int n;
+};
+
+template <int DIM, bool ADD, typename T>
+__global__ void __launch_bounds__(256) patch_gather_group(const __grid_constant__ GroupOf<GatherJob<T>> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) patch_gather_body<DIM, ADD, T>(G.job[j].dst, G.job[j].u, G.job[j].n, t0, ts);
+}
+
 // ===========================================================================
 // h-transfers (Eq. (2)): prolongation = embedding, one pass per axis,
 // restriction = its transpose, one pass per axis in reverse order.
@@ -1012,13 +1137,14 @@ __global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__
 // K (2 nc) + 1; e0, e1 are the extents of the two other axes (x-fastest order
 // of the remaining axes).  ADD: out += result.
 template <int AX, bool ADD, typename T>
-__global__ void hprolong_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
+__device__ __forceinline__ void hprolong_body(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey,
+                                              int ez, int64_t t0, int64_t tstep) {
   // ex, ey, ez: extents of the OUTPUT array
   const int nf = 2 * nc;
   const int nc1 = K * nc + 1;
   const int64_t total = (int64_t)ex * ey * ez;
   const T* Pt = coef<T>() + LAY.Pt;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < total; t += tstep) {
     const int x = (int)(t % ex);
     const int64_t rr = t / ex;
     const int y = (int)(rr % ey);
@@ -1045,12 +1171,13 @@ __global__ void hprolong_pass(const T* __restrict__ in, T* __restrict__ out, int
 // Restriction along AX: in has extent nf1 along AX, out nc1; outputs on the
 // boundary nodes of AX are zero (restriction acts on free DoFs).
 template <int AX, typename T>
-__global__ void hrestrict_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
+__device__ __forceinline__ void hrestrict_body(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey,
+                                               int ez, int64_t t0, int64_t tstep) {
   const int nc1 = K * nc + 1;
   const int nf1 = 2 * K * nc + 1;
   const int64_t total = (int64_t)ex * ey * ez;
   const T* Pt = coef<T>() + LAY.Pt;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < total; t += tstep) {
     const int x = (int)(t % ex);
     const int64_t rr = t / ex;
     const int y = (int)(rr % ey);
@@ -1087,6 +1214,44 @@ __global__ void hrestrict_pass(const T* __restrict__ in, T* __restrict__ out, in
       }
     }
     out[t] = acc;
+  }
+}
+
+template <int AX, bool ADD, typename T>
+__global__ void hprolong_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
+  hprolong_body<AX, ADD, T>(in, out, nc, ex, ey, ez, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x);
+}
+
+template <int AX, typename T>
+__global__ void hrestrict_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
+  hrestrict_body<AX, T>(in, out, nc, ex, ey, ez, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x);
+}
+
+// one pass of a transfer over every job (extents of the job's output array)
+template <typename T>
+struct TransferJob {
+  const T* in;
+  T* out;
+  int nc, ex, ey, ez;
+};
+
+template <int AX, bool ADD, typename T>
+__global__ void hprolong_group(const __grid_constant__ GroupOf<TransferJob<T>> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    const TransferJob<T>& a = G.job[j];
+    hprolong_body<AX, ADD, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t0, ts);
+  }
+}
+
+template <int AX, typename T>
+__global__ void hrestrict_group(const __grid_constant__ GroupOf<TransferJob<T>> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    const TransferJob<T>& a = G.job[j];
+    hrestrict_body<AX, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t0, ts);
   }
 }
 

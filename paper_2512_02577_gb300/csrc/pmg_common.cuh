@@ -91,6 +91,18 @@ constexpr int kMaxCoef = 2048;   // >= coef_layout(8).total
 // per-block opt-in of sm_103a minus room for the kernels' static arrays.
 constexpr int kMaxDynSmem = 220 * 1024;
 
+// Argument table of a grouped launch: one kernel launch does the work of up
+// to kMaxGroup jobs (the same operation on the vectors of different systems,
+// possibly of different sizes), passed by value as a __grid_constant__
+// kernel parameter (no device copy of the table, so graph capture needs no
+// allocation either).
+constexpr int kMaxGroup = 32;
+template <class J>
+struct GroupOf {
+  int count;
+  J job[kMaxGroup];
+};
+
 // Per-call scalars of the patch smoother (host fills, passed by value).
 template <typename T>
 struct PatchParams {

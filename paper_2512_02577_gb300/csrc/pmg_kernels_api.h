@@ -11,6 +11,8 @@
 
 #include <cstdint>
 
+#include "pmg_common.cuh"
+
 namespace pmg {
 
 struct PatchParamsHost {
@@ -30,6 +32,36 @@ struct DefLevel {
   int gprec;              // storage precision of G: 0 double, 1 float
   const void* dinv[4];    // per p-level l >= 1: inverse diagonal on the degree-p global grid (MG precision)
   const void* dinv1;      // p = 1: inverse Q1 diagonal on the vertex grid (n+1)^d (MG precision)
+};
+
+// Jobs of grouped launches: one launch does the operation for every job (one
+// level of one system each; sizes may differ between jobs, at most kMaxGroup
+// jobs), with each job's results those of its own ungrouped launch.
+struct ApplyJob {       // y = A x or y = b - A x (b != nullptr); t: scratch of the level's N
+  const void* x;
+  void* y;
+  const void* b;
+  void* t[4];
+  int n;
+  double scale;
+};
+struct PatchSolveJob {  // patch smoother of one level (output as patch_cart)
+  const void* r;
+  void* dst;
+  int n;
+  PatchParamsHost P;
+};
+struct GatherSolveJob {  // u (+)= the patch corrections in dst
+  const void* dst;
+  void* u;
+  int n;
+};
+struct TransferSolveJob {  // prolongation (uf += P uc) or restriction (rc = P^T rf); t: scratch of N_f
+  const void* in;
+  void* out;
+  void* t0;
+  void* t1;
+  int nc;
 };
 
 struct KernelTable {
@@ -87,6 +119,16 @@ struct KernelTable {
   cudaError_t (*def_apply_ff)(int dim, const double* x, double* y, const double* b, const float* G, int n, int cpb,
                               cudaStream_t s);
   int (*def_apply_candidates)(int dim, int prec, int gprec, int* out, int max);
+  // grouped launches (Cartesian); the patch launch uses the patch-major layout
+  // with ppc patches per block; dinv: the part's inverse-diagonal tables
+  cudaError_t (*cart_apply_group)(int dim, int prec, int count, const ApplyJob* jobs, cudaStream_t s);
+  cudaError_t (*cart_apply_ff_group)(int dim, int count, const ApplyJob* jobs, cudaStream_t s);
+  cudaError_t (*patch_cart_group)(int dim, int prec, int count, const PatchSolveJob* jobs, int ppc, int n_iter,
+                                  const void* dinv, int* counter, cudaStream_t s);
+  cudaError_t (*patch_gather_group)(int dim, int prec, int count, const GatherSolveJob* jobs, int add,
+                                    cudaStream_t s);
+  cudaError_t (*h_prolong_add_group)(int dim, int prec, int count, const TransferSolveJob* jobs, cudaStream_t s);
+  cudaError_t (*h_restrict_group)(int dim, int prec, int count, const TransferSolveJob* jobs, cudaStream_t s);
 };
 
 // nullptr when k, dim or prec is out of range

@@ -13,6 +13,11 @@
 // whose solution has reached the host.  Each slot has its own CUDA stream,
 // so kernels of different requests overlap on the device, and a request that
 // arrives while others run starts as soon as a slot and memory free up.
+// With grouping on (pmg_server_set_grouping), small requests of one method
+// instead join a group (group.h): their solves advance in lockstep with
+// every launch of a round covering all members, members joining and leaving
+// between rounds, so many small solves share each launch instead of each
+// filling a fraction of the GPU with launches of its own.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +31,7 @@
 #include <vector>
 
 #include "../../include/pmg.h"
+#include "group.h"
 
 namespace pmg {
 void set_last_error(const std::string& msg);
@@ -160,6 +166,12 @@ struct pmg_server {
   std::map<int64_t, Request*> requests;
   std::vector<Slot*> slots;
   int64_t created_contexts = 0;
+  // grouped launches across requests (pmg_server_set_grouping)
+  bool grouping = false;
+  double group_max_work = 0;
+  int max_group = 8;
+  std::vector<pmg::SolveGroup*> groups;  // kept for reuse while the server lives
+  std::vector<cudaStream_t> group_streams;
 };
 
 namespace {
@@ -235,6 +247,41 @@ std::deque<Request*>::iterator next_request(pmg_server* s) {
   return best;
 }
 
+// Start r on its slot's context: in the group of running requests with the
+// same method when grouping applies (a new group if none has room), else on
+// its own.
+int start_request(pmg_server* s, Request* r, Slot* sl) {
+  if (s->grouping && r->work <= s->group_max_work) {
+    pmg::SolveGroup* g = nullptr;
+    for (pmg::SolveGroup* cand : s->groups)
+      if (pmg::group_size(cand) < s->max_group && pmg::group_accepts(cand, sl->ctx)) {
+        // a group that already holds requests of this method comes first
+        if (!g || (pmg::group_size(g) == 0 && pmg::group_size(cand) > 0)) g = cand;
+      }
+    if (!g) {
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, s->prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        st = nullptr;
+      }
+      if (st) {
+        if (pmg::group_create(st, &g) == PMG_OK) {
+          s->groups.push_back(g);
+          s->group_streams.push_back(st);
+        } else {
+          cudaStreamDestroy(st);
+          g = nullptr;
+        }
+      }
+    }
+    if (g && pmg::group_accepts(g, sl->ctx) &&
+        pmg::group_join(g, sl->ctx, r->b, true, r->x, true, r->rtol, r->maxit) == PMG_OK)
+      return PMG_OK;
+    // not groupable (or no group could be made): on its own
+  }
+  return pmg_solve_start(sl->ctx, r->b, 1, r->x, 1, r->rtol, r->maxit);
+}
+
 }  // namespace
 
 extern "C" {
@@ -266,6 +313,12 @@ int pmg_server_create(int64_t memory_budget_bytes, int max_active, pmg_server** 
 
 int pmg_server_destroy(pmg_server* s) {
   if (!s) return PMG_OK;
+  for (size_t i = 0; i < s->groups.size(); ++i) {
+    if (pmg::group_size(s->groups[i]) > 0) pmg::group_cancel(s->groups[i]);
+    pmg::group_destroy(s->groups[i]);
+    cudaStreamDestroy(s->group_streams[i]);
+  }
+  s->groups.clear();
   for (Slot* sl : s->slots) {
     if (sl->stream) cudaStreamSynchronize(sl->stream);
   }
@@ -332,7 +385,7 @@ int pmg_server_poll(pmg_server* s, int* n_running, int* n_queued) {
     sl->busy = true;
     r->slot = sl;
     r->t_start = now_s();
-    const int rc = pmg_solve_start(sl->ctx, r->b, 1, r->x, 1, r->rtol, r->maxit);
+    const int rc = start_request(s, r, sl);
     if (rc != PMG_OK) {
       sl->busy = false;
       r->state = 3;
@@ -343,7 +396,10 @@ int pmg_server_poll(pmg_server* s, int* n_running, int* n_queued) {
     r->state = 1;
     s->running.push_back(r);
   }
-  // advance every running solve; retire finished ones
+  // advance the groups (a failed round ends its members with the error,
+  // which pmg_solve_progress reports below), then every running solve
+  for (pmg::SolveGroup* g : s->groups)
+    if (pmg::group_size(g) > 0) pmg::group_progress(g, false);
   for (size_t i = 0; i < s->running.size();) {
     Request* r = s->running[i];
     int done = 0;
@@ -386,6 +442,15 @@ int pmg_server_set_policy(pmg_server* s, int policy, double max_wait_s, double s
   s->policy = policy;
   s->max_wait_s = max_wait_s;
   s->small_work = small_work;
+  return PMG_OK;
+}
+
+int pmg_server_set_grouping(pmg_server* s, int enable, double max_work, int max_group) {
+  if (!s) return fail(PMG_ERR_ARG, "NULL server");
+  if (max_group < 1 || max_group > 32 || max_work < 0) return fail(PMG_ERR_ARG, "max_group in 1..32, max_work >= 0");
+  s->grouping = enable != 0;
+  s->group_max_work = max_work;
+  s->max_group = max_group;
   return PMG_OK;
 }
 

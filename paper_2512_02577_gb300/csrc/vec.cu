@@ -5,6 +5,7 @@
 // diagonals), the manufactured right-hand side and the L2 error.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "vec.h"
@@ -298,6 +299,203 @@ cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, con
   const int blocks = (nc * 32 + 255) / 256;
   if (prec == 0) coarse_kernel<double><<<blocks, 256, 0, st>>>((const double*)Ainv, idx, nc, (const double*)b, (double*)u);
   else coarse_kernel<float><<<blocks, 256, 0, st>>>((const float*)Ainv, idx, nc, (const float*)b, (float*)u);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ grouped forms
+// Each reduction keeps its per-job grid (kDotBlocks blocks along x, the job
+// along y) and its per-job partial sums, so a job's result is bitwise that of
+// its own launch; element-wise kernels take the same grid-stride slice of
+// every job in turn.
+static bool group_ok(int count) { return count >= 1 && count <= kMaxGroup; }
+
+__global__ void __launch_bounds__(256) dot_partial_group(const __grid_constant__ GroupOf<DotJob> G) {
+  const DotJob& a = G.job[blockIdx.y];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+    s += a.x[i] * a.y[i];
+  block_store_sum(s, a.partial + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) sum_partials_group(const __grid_constant__ GroupOf<DotJob> G) {
+  const DotJob& a = G.job[blockIdx.x];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) s += a.partial[i];
+  block_store_sum(s, a.out);
+}
+
+cudaError_t dot_group(int count, const DotJob* jobs, cudaStream_t st) {
+  if (!group_ok(count)) return cudaErrorInvalidValue;
+  GroupOf<DotJob> G;
+  G.count = count;
+  for (int j = 0; j < count; ++j) G.job[j] = jobs[j];
+  dot_partial_group<<<dim3(kDotBlocks, count), 256, 0, st>>>(G);
+  sum_partials_group<<<count, 256, 0, st>>>(G);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) cg_xr_group(const __grid_constant__ GroupOf<CgXrJob> G) {
+  const CgXrJob& a = G.job[blockIdx.y];
+  const double alpha = a.s[a.num] / a.s[a.den];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    a.x[i] += alpha * a.p[i];
+    const double ri = a.r[i] - alpha * a.Ap[i];
+    a.r[i] = ri;
+    acc += ri * ri;
+  }
+  block_store_sum(acc, a.partial + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) cg_xr_sum_group(const __grid_constant__ GroupOf<CgXrJob> G) {
+  const CgXrJob& a = G.job[blockIdx.x];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) s += a.partial[i];
+  block_store_sum(s, a.rr_out);
+}
+
+cudaError_t cg_update_xr_group(int count, const CgXrJob* jobs, cudaStream_t st) {
+  if (!group_ok(count)) return cudaErrorInvalidValue;
+  GroupOf<CgXrJob> G;
+  G.count = count;
+  for (int j = 0; j < count; ++j) G.job[j] = jobs[j];
+  cg_xr_group<<<dim3(kDotBlocks, count), 256, 0, st>>>(G);
+  cg_xr_sum_group<<<count, 256, 0, st>>>(G);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) cg_p_group(const __grid_constant__ GroupOf<CgPJob> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    const CgPJob& a = G.job[j];
+    const double beta = a.first ? 0.0 : a.s[a.num] / a.s[a.den];
+    for (int64_t i = t0; i < a.n; i += ts) a.p[i] = a.z[i] + beta * a.p[i];
+  }
+}
+
+__global__ void copy_scalar_group(const __grid_constant__ GroupOf<CgPJob> G) {
+  const int j = threadIdx.x;
+  if (j < G.count) G.job[j].s[G.job[j].den] = G.job[j].s[G.job[j].num];
+}
+
+cudaError_t cg_update_p_group(int count, const CgPJob* jobs, cudaStream_t st) {
+  if (!group_ok(count)) return cudaErrorInvalidValue;
+  GroupOf<CgPJob> G;
+  G.count = count;
+  int64_t work = 0;
+  for (int j = 0; j < count; ++j) {
+    G.job[j] = jobs[j];
+    work += jobs[j].n;
+  }
+  cg_p_group<<<grid_for(work, 256), 256, 0, st>>>(G);
+  copy_scalar_group<<<1, 32, 0, st>>>(G);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename A, typename B>
+__global__ void __launch_bounds__(256) convert_group(const __grid_constant__ GroupOf<CopyJob> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    const A* a = static_cast<const A*>(G.job[j].a);
+    B* b = static_cast<B*>(G.job[j].b);
+    for (int64_t i = t0; i < G.job[j].n; i += ts) b[i] = (B)a[i];
+  }
+}
+
+template <typename A, typename B>
+static cudaError_t convert_group_launch(int count, const CopyJob* jobs, cudaStream_t st) {
+  if (!group_ok(count)) return cudaErrorInvalidValue;
+  GroupOf<CopyJob> G;
+  G.count = count;
+  int64_t work = 0;
+  for (int j = 0; j < count; ++j) {
+    G.job[j] = jobs[j];
+    work += jobs[j].n;
+  }
+  convert_group<A, B><<<grid_for(work, 256), 256, 0, st>>>(G);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t cast_d2f_group(int count, const CopyJob* jobs, cudaStream_t st) {
+  return convert_group_launch<double, float>(count, jobs, st);
+}
+cudaError_t cast_f2d_group(int count, const CopyJob* jobs, cudaStream_t st) {
+  return convert_group_launch<float, double>(count, jobs, st);
+}
+cudaError_t copy_group(int count, const CopyJob* jobs, int elem_bytes, cudaStream_t st) {
+  if (elem_bytes == 8) return convert_group_launch<double, double>(count, jobs, st);
+  if (elem_bytes == 4) return convert_group_launch<float, float>(count, jobs, st);
+  return cudaErrorInvalidValue;
+}
+
+__global__ void __launch_bounds__(256) zero_group_kernel(const __grid_constant__ GroupOf<ZeroJob> G) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < G.count; ++j) {
+    unsigned* p = static_cast<unsigned*>(G.job[j].p);
+    const int64_t w = G.job[j].bytes / 4;
+    for (int64_t i = t0; i < w; i += ts) p[i] = 0u;
+  }
+}
+
+cudaError_t zero_group(int count, const ZeroJob* jobs, cudaStream_t st) {
+  if (!group_ok(count)) return cudaErrorInvalidValue;
+  GroupOf<ZeroJob> G;
+  G.count = count;
+  int64_t work = 0;
+  for (int j = 0; j < count; ++j) {
+    if (jobs[j].bytes % 4) return cudaErrorInvalidValue;
+    G.job[j] = jobs[j];
+    work += jobs[j].bytes / 4;
+  }
+  zero_group_kernel<<<grid_for(work, 256), 256, 0, st>>>(G);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// rows of every job's coarse solve, one warp per row as coarse_kernel
+template <typename T>
+__global__ void coarse_group_kernel(const __grid_constant__ GroupOf<CoarseJob> G) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = 0; j < G.count; ++j) {
+    const CoarseJob& a = G.job[j];
+    const T* Ainv = static_cast<const T*>(a.Ainv);
+    const T* b = static_cast<const T*>(a.b);
+    T* u = static_cast<T*>(a.u);
+    for (int w = w0; w < a.nc; w += nw) {  // uniform per warp
+      T s = T(0);
+      for (int jj = lane; jj < a.nc; jj += 32) s += Ainv[(int64_t)w * a.nc + jj] * b[a.idx[jj]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) u[a.idx[w]] = s;
+    }
+  }
+}
+
+cudaError_t coarse_solve_group(int prec, int count, const CoarseJob* jobs, cudaStream_t st) {
+  if (!group_ok(count)) return cudaErrorInvalidValue;
+  const int es = prec == 0 ? 8 : 4;
+  ZeroJob Z[kMaxGroup];
+  GroupOf<CoarseJob> G;
+  G.count = 0;
+  int64_t rows = 0;
+  for (int j = 0; j < count; ++j) {
+    Z[j] = ZeroJob{jobs[j].u, (int64_t)es * jobs[j].N};
+    if (jobs[j].nc > 0) {
+      G.job[G.count++] = jobs[j];
+      rows += jobs[j].nc;
+    }
+  }
+  cudaError_t e = zero_group(count, Z, st);
+  if (e != cudaSuccess || G.count == 0) return e;
+  const int blocks = (int)std::min<int64_t>((rows * 32 + 255) / 256, 152 * 16);
+  if (prec == 0) coarse_group_kernel<double><<<blocks, 256, 0, st>>>(G);
+  else coarse_group_kernel<float><<<blocks, 256, 0, st>>>(G);
   g_launches += 1;
   return cudaGetLastError();
 }

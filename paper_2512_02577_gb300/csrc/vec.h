@@ -5,6 +5,8 @@
 #include <atomic>
 #include <cstdint>
 
+#include "pmg_common.cuh"
+
 namespace pmg {
 
 // Process-wide count of kernel launches enqueued by the library.
@@ -23,6 +25,60 @@ struct QuadTab {
 };
 
 cudaError_t dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st);
+
+// ---- grouped forms: one launch (or one per phase) for up to kMaxGroup jobs,
+// each job's result bitwise that of its own call above (the reductions keep
+// their fixed grid and summation order per job)
+struct DotJob {
+  const double* x;
+  const double* y;
+  int64_t n;
+  double* partial;  // kDotBlocks doubles of the job's own scratch
+  double* out;
+};
+struct CgXrJob {
+  double* x;
+  double* r;
+  const double* p;
+  const double* Ap;
+  int64_t n;
+  const double* s;
+  int num, den;
+  double* partial;
+  double* rr_out;
+};
+struct CgPJob {
+  double* p;
+  const double* z;
+  int64_t n;
+  double* s;
+  int num, den, first;
+};
+struct CopyJob {  // n elements from a to b
+  const void* a;
+  void* b;
+  int64_t n;
+};
+struct ZeroJob {  // bytes: a multiple of 4
+  void* p;
+  int64_t bytes;
+};
+struct CoarseJob {  // as coarse_solve
+  const void* Ainv;
+  const int* idx;
+  int nc;
+  const void* b;
+  void* u;
+  int64_t N;
+};
+cudaError_t dot_group(int count, const DotJob* jobs, cudaStream_t st);
+cudaError_t cg_update_xr_group(int count, const CgXrJob* jobs, cudaStream_t st);
+cudaError_t cg_update_p_group(int count, const CgPJob* jobs, cudaStream_t st);
+cudaError_t cast_d2f_group(int count, const CopyJob* jobs, cudaStream_t st);
+cudaError_t cast_f2d_group(int count, const CopyJob* jobs, cudaStream_t st);
+cudaError_t copy_group(int count, const CopyJob* jobs, int elem_bytes, cudaStream_t st);  // 4 or 8
+cudaError_t zero_group(int count, const ZeroJob* jobs, cudaStream_t st);
+cudaError_t coarse_solve_group(int prec, int count, const CoarseJob* jobs, cudaStream_t st);
 cudaError_t cg_update_xr(double* x, double* r, const double* p, const double* Ap, int64_t n, const double* s,
                          int num, int den, double* partial, double* rr_out, cudaStream_t st);
 cudaError_t cg_update_p(double* p, const double* z, int64_t n, double* s, int num, int den, int first,

@@ -36,10 +36,12 @@ def prepare(requests, dim=3):
 
 def run(requests, dim=3, precision=FP32, geometry=CARTESIAN, max_active=8, budget=0, rtol=1e-8, maxit=300,
         time_scale=1.0, poll_sleep=0.0, policy=SERVE_FIFO, max_wait_s=2.0, small_work=0.0, buffers=None,
-        **config):
+        group_work=0.0, max_group=8, **config):
     """Serve ``requests`` (dicts with t_arrival, n, k, rhs_seed) and return
     per-request records plus summary statistics.  policy / max_wait_s /
     small_work: the server's admission order (pmg_server_set_policy);
+    group_work / max_group: grouped launches for requests up to that
+    estimated work (pmg_server_set_grouping; 0 = off);
     buffers: prepare(requests) to reuse; config: further make_config
     arguments (e.g. outer_apply) for every request."""
     buffers = prepare(requests, dim) if buffers is None else buffers
@@ -48,7 +50,8 @@ def run(requests, dim=3, precision=FP32, geometry=CARTESIAN, max_active=8, budge
         cfg = make_config(dim=dim, n_cells=r["n"], degree=r["k"], mg_precision=precision, geometry=geometry, **config)
         x.zero_()
         prepared.append((r, cfg, b, x))
-    server = Server(budget, max_active, policy=policy, max_wait_s=max_wait_s, small_work=small_work)
+    server = Server(budget, max_active, policy=policy, max_wait_s=max_wait_s, small_work=small_work,
+                    group_work=group_work, max_group=max_group)
     ids = {}
     pending = list(range(len(prepared)))
     t0 = time.perf_counter()
