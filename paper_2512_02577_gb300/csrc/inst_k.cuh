@@ -283,6 +283,7 @@ template <int DIM, typename T>
 static cudaError_t cart_apply_group_t(int count, const ApplyJob* jobs, cudaStream_t st) {
   GroupOf<CartPassJob<T>> g0, g1, g2;
   g0.count = g1.count = g2.count = count;
+  g0.start[0] = 0;
   int64_t work = 0;
   bool resid = jobs[0].b != nullptr;
   for (int j = 0; j < count; ++j) {
@@ -302,7 +303,9 @@ static cudaError_t cart_apply_group_t(int count, const ApplyJob* jobs, cudaStrea
       g1.job[j] = CartPassJob<T>{t0, t1, (T*)a.y, nullptr, (const T*)a.b, a.n, s};
     }
     work += apply_work(DIM, a.n);
+    g0.start[j + 1] = work;
   }
+  for (int j = 0; j <= count; ++j) g1.start[j] = g2.start[j] = g0.start[j];
   const int bs = 256, g = grid_for(work, bs);
   if (DIM == 3) {
     cart_pass_group<3, 0, 0, false, T><<<g, bs, 0, st>>>(g0);
@@ -328,6 +331,7 @@ template <int DIM>
 static cudaError_t cart_apply_ff_group_t(int count, const ApplyJob* jobs, cudaStream_t st) {
   GroupOf<CartPassFFJob> g0, g1, g2;
   g0.count = g1.count = g2.count = count;
+  g0.start[0] = 0;
   int64_t work = 0;
   const bool resid = jobs[0].b != nullptr;
   for (int j = 0; j < count; ++j) {
@@ -344,7 +348,9 @@ static cudaError_t cart_apply_ff_group_t(int count, const ApplyJob* jobs, cudaSt
       g1.job[j] = CartPassFFJob{f0, f1, a.y, nullptr, (const double*)a.b, a.n, s};
     }
     work += apply_work(DIM, a.n);
+    g0.start[j + 1] = work;
   }
+  for (int j = 0; j <= count; ++j) g1.start[j] = g2.start[j] = g0.start[j];
   const int bs = 256, g = grid_for(work, bs);
   if (DIM == 3) {
     cart_pass_ff_group<3, 0, 0, false><<<g, bs, 0, st>>>(g0);
@@ -373,6 +379,7 @@ static cudaError_t patch_cart_group_t(int count, const PatchSolveJob* jobs, int 
   if (ppc < 1 || ppc > kMaxPatchesPerBlock) return cudaErrorInvalidValue;
   GroupOf<PatchJob<T>> G;
   G.count = 0;
+  G.start[0] = 0;
   int64_t nbatch = 0;
   for (int j = 0; j < count; ++j) {
     const int64_t np = patch_count(DIM, jobs[j].n, jobs[j].P.colour);
@@ -381,9 +388,9 @@ static cudaError_t patch_cart_group_t(int count, const PatchSolveJob* jobs, int 
     J.r = (const T*)jobs[j].r;
     J.dst = (T*)jobs[j].dst;
     J.n = jobs[j].n;
-    J.first = nbatch;
     J.P = to_params<T>(jobs[j].P);
     nbatch += (np + ppc - 1) / ppc;
+    G.start[G.count] = nbatch;
   }
   if (G.count == 0) return cudaSuccess;
   const int threads = std::min(kPatchMaxThreads, (ppc * S::TPP + 31) / 32 * 32);
@@ -416,10 +423,12 @@ template <int DIM, typename T>
 static cudaError_t patch_gather_group_t(int count, const GatherSolveJob* jobs, int add, cudaStream_t st) {
   GroupOf<GatherJob<T>> G;
   G.count = count;
+  G.start[0] = 0;
   int64_t work = 0;
   for (int j = 0; j < count; ++j) {
     G.job[j] = GatherJob<T>{(const T*)jobs[j].dst, (T*)jobs[j].u, jobs[j].n};
     work += ipow(K * jobs[j].n + 1, DIM);
+    G.start[j + 1] = work;
   }
   if (add) patch_gather_group<DIM, true, T><<<grid_for(work, 256), 256, 0, st>>>(G);
   else patch_gather_group<DIM, false, T><<<grid_for(work, 256), 256, 0, st>>>(G);
@@ -438,7 +447,10 @@ template <int DIM, typename T>
 static cudaError_t h_prolong_group_t(int count, const TransferSolveJob* jobs, cudaStream_t st) {
   GroupOf<TransferJob<T>> g[3];
   int64_t work[3] = {0, 0, 0};
-  for (int i = 0; i < 3; ++i) g[i].count = count;
+  for (int i = 0; i < 3; ++i) {
+    g[i].count = count;
+    g[i].start[0] = 0;
+  }
   for (int j = 0; j < count; ++j) {
     const TransferSolveJob& a = jobs[j];
     const int nc = a.nc, c1 = K * nc + 1, f1 = 2 * K * nc + 1;
@@ -457,6 +469,7 @@ static cudaError_t h_prolong_group_t(int count, const TransferSolveJob* jobs, cu
       work[0] += (int64_t)f1 * c1;
       work[1] += (int64_t)f1 * f1;
     }
+    for (int i = 0; i < 3; ++i) g[i].start[j + 1] = work[i];
   }
   const int bs = 256;
   if (DIM == 3) {
@@ -476,7 +489,10 @@ template <int DIM, typename T>
 static cudaError_t h_restrict_group_t(int count, const TransferSolveJob* jobs, cudaStream_t st) {
   GroupOf<TransferJob<T>> g[3];
   int64_t work[3] = {0, 0, 0};
-  for (int i = 0; i < 3; ++i) g[i].count = count;
+  for (int i = 0; i < 3; ++i) {
+    g[i].count = count;
+    g[i].start[0] = 0;
+  }
   for (int j = 0; j < count; ++j) {
     const TransferSolveJob& a = jobs[j];
     const int nc = a.nc, c1 = K * nc + 1, f1 = 2 * K * nc + 1;
@@ -495,6 +511,7 @@ static cudaError_t h_restrict_group_t(int count, const TransferSolveJob* jobs, c
       work[0] += (int64_t)f1 * c1;
       work[1] += (int64_t)c1 * c1;
     }
+    for (int i = 0; i < 3; ++i) g[i].start[j + 1] = work[i];
   }
   const int bs = 256;
   if (DIM == 3) {

@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, cons
 }
 
 // Grouped launch: the same pass over every job's level (jobs of one launch
-// may have different n); each thread takes the same grid-stride slice of
-// every job in turn, so a job's outputs are those of its own launch.
+// may have different n); the grid covers the concatenated work items of the
+// jobs (G.start), each computed by the ungrouped body, so a job's outputs
+// are those of its own launch.
 template <typename T>
 struct CartPassJob {
   const T* in0;
@@ -191,10 +192,12 @@ struct CartPassJob {
 
 template <int DIM, int AX, int MODE, bool RESID, typename T>
 __global__ void __launch_bounds__(256) cart_pass_group(const __grid_constant__ GroupOf<CartPassJob<T>> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
     const CartPassJob<T>& a = G.job[j];
-    cart_pass_body<DIM, AX, MODE, RESID, T>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t0, ts);
+    cart_pass_body<DIM, AX, MODE, RESID, T>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t - G.start[j],
+                                            kOneItem);
   }
 }
 
@@ -395,10 +398,12 @@ struct CartPassFFJob {
 
 template <int DIM, int AX, int MODE, bool RESID>
 __global__ void __launch_bounds__(256) cart_pass_ff_group(const __grid_constant__ GroupOf<CartPassFFJob> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
     const CartPassFFJob& a = G.job[j];
-    cart_pass_ff_body<DIM, AX, MODE, RESID>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t0, ts);
+    cart_pass_ff_body<DIM, AX, MODE, RESID>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t - G.start[j],
+                                            kOneItem);
   }
 }
 
@@ -1033,8 +1038,8 @@ __global__ void PMG_PATCH_IL_BOUNDS
 
 // Grouped patch launch: the batches of every job (one level of one system;
 // the jobs of a launch may differ in n, damping and scale) are numbered job
-// after job, and a block finds the job of its batch from the jobs' first
-// batch indices.  Patch-major layout; counter as patch_cart_persistent (the
+// after job (G.start: prefix sums of the jobs' batches), and a block finds
+// the job of its batch by group_find.  Patch-major layout; counter as patch_cart_persistent (the
 // batches of all jobs are one work list, so blocks that finish a small
 // system's patches go on to the next system's).  The inverse-diagonal
 // tables depend only on the dimension, degree and precision, which every
@@ -1044,7 +1049,6 @@ struct PatchJob {
   const T* r;
   T* dst;
   int n;
-  int64_t first;  // global index of the job's first batch
   PatchParams<T> P;
 };
 
@@ -1068,10 +1072,9 @@ __global__ void PMG_PATCH_BOUNDS patch_cart_group_kernel(int np, int n_iter, con
       b = s_batch;
     }
     if (b >= nbatch) break;  // uniform over the block
-    int j = 0;
-    while (j + 1 < G.count && G.job[j + 1].first <= b) ++j;
+    const int j = group_find(G, b);
     const PatchJob<T>& J = G.job[j];
-    patch_cart_body<DIM, T, 0>(J.r, J.dst, J.n, np, n_iter, sdinv, J.P, b - J.first, meta, smem);
+    patch_cart_body<DIM, T, 0>(J.r, J.dst, J.n, np, n_iter, sdinv, J.P, b - G.start[j], meta, smem);
     if (!counter) break;
     __syncthreads();  // the batch's shared memory and s_batch are free again
   }
@@ -1125,8 +1128,11 @@ struct GatherJob {
 
 template <int DIM, bool ADD, typename T>
 __global__ void __launch_bounds__(256) patch_gather_group(const __grid_constant__ GroupOf<GatherJob<T>> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) patch_gather_body<DIM, ADD, T>(G.job[j].dst, G.job[j].u, G.job[j].n, t0, ts);
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
+    patch_gather_body<DIM, ADD, T>(G.job[j].dst, G.job[j].u, G.job[j].n, t - G.start[j], kOneItem);
+  }
 }
 
 // ===========================================================================
@@ -1239,19 +1245,21 @@ struct TransferJob {
 
 template <int AX, bool ADD, typename T>
 __global__ void hprolong_group(const __grid_constant__ GroupOf<TransferJob<T>> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
     const TransferJob<T>& a = G.job[j];
-    hprolong_body<AX, ADD, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t0, ts);
+    hprolong_body<AX, ADD, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t - G.start[j], kOneItem);
   }
 }
 
 template <int AX, typename T>
 __global__ void hrestrict_group(const __grid_constant__ GroupOf<TransferJob<T>> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
     const TransferJob<T>& a = G.job[j];
-    hrestrict_body<AX, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t0, ts);
+    hrestrict_body<AX, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t - G.start[j], kOneItem);
   }
 }
 

@@ -96,12 +96,32 @@ constexpr int kMaxDynSmem = 220 * 1024;
 // possibly of different sizes), passed by value as a __grid_constant__
 // kernel parameter (no device copy of the table, so graph capture needs no
 // allocation either).
+// Element-wise and line kernels spread the concatenation of the jobs' work
+// items over the grid (start: prefix sums of the items per job), so that a
+// thread handles about one item, as in an ungrouped launch.
 constexpr int kMaxGroup = 32;
 template <class J>
 struct GroupOf {
   int count;
+  int64_t start[kMaxGroup + 1];
   J job[kMaxGroup];
 };
+
+// the job that global work item t belongs to (binary search in start)
+template <class J>
+__device__ __forceinline__ int group_find(const GroupOf<J>& G, int64_t t) {
+  int lo = 0, hi = G.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (G.start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// A grid-stride step that ends a body's loop after its first item: the
+// grouped kernels call the ungrouped bodies one item at a time.
+constexpr int64_t kOneItem = int64_t(1) << 62;
 
 // Per-call scalars of the patch smoother (host fills, passed by value).
 template <typename T>

@@ -306,8 +306,8 @@ cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, con
 // ------------------------------------------------------------ grouped forms
 // Each reduction keeps its per-job grid (kDotBlocks blocks along x, the job
 // along y) and its per-job partial sums, so a job's result is bitwise that of
-// its own launch; element-wise kernels take the same grid-stride slice of
-// every job in turn.
+// its own launch; element-wise kernels spread the concatenated elements of
+// the jobs over the grid (GroupOf::start).
 static bool group_ok(int count) { return count >= 1 && count <= kMaxGroup; }
 
 __global__ void __launch_bounds__(256) dot_partial_group(const __grid_constant__ GroupOf<DotJob> G) {
@@ -368,11 +368,13 @@ cudaError_t cg_update_xr_group(int count, const CgXrJob* jobs, cudaStream_t st) 
 }
 
 __global__ void __launch_bounds__(256) cg_p_group(const __grid_constant__ GroupOf<CgPJob> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
     const CgPJob& a = G.job[j];
+    const int64_t i = t - G.start[j];
     const double beta = a.first ? 0.0 : a.s[a.num] / a.s[a.den];
-    for (int64_t i = t0; i < a.n; i += ts) a.p[i] = a.z[i] + beta * a.p[i];
+    a.p[i] = a.z[i] + beta * a.p[i];
   }
 }
 
@@ -385,10 +387,12 @@ cudaError_t cg_update_p_group(int count, const CgPJob* jobs, cudaStream_t st) {
   if (!group_ok(count)) return cudaErrorInvalidValue;
   GroupOf<CgPJob> G;
   G.count = count;
+  G.start[0] = 0;
   int64_t work = 0;
   for (int j = 0; j < count; ++j) {
     G.job[j] = jobs[j];
     work += jobs[j].n;
+    G.start[j + 1] = work;
   }
   cg_p_group<<<grid_for(work, 256), 256, 0, st>>>(G);
   copy_scalar_group<<<1, 32, 0, st>>>(G);
@@ -398,11 +402,11 @@ cudaError_t cg_update_p_group(int count, const CgPJob* jobs, cudaStream_t st) {
 
 template <typename A, typename B>
 __global__ void __launch_bounds__(256) convert_group(const __grid_constant__ GroupOf<CopyJob> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
-    const A* a = static_cast<const A*>(G.job[j].a);
-    B* b = static_cast<B*>(G.job[j].b);
-    for (int64_t i = t0; i < G.job[j].n; i += ts) b[i] = (B)a[i];
+  const int64_t total = G.start[G.count];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
+    const int64_t i = t - G.start[j];
+    static_cast<B*>(G.job[j].b)[i] = (B) static_cast<const A*>(G.job[j].a)[i];
   }
 }
 
@@ -411,10 +415,12 @@ static cudaError_t convert_group_launch(int count, const CopyJob* jobs, cudaStre
   if (!group_ok(count)) return cudaErrorInvalidValue;
   GroupOf<CopyJob> G;
   G.count = count;
+  G.start[0] = 0;
   int64_t work = 0;
   for (int j = 0; j < count; ++j) {
     G.job[j] = jobs[j];
     work += jobs[j].n;
+    G.start[j + 1] = work;
   }
   convert_group<A, B><<<grid_for(work, 256), 256, 0, st>>>(G);
   g_launches += 1;
@@ -434,11 +440,10 @@ cudaError_t copy_group(int count, const CopyJob* jobs, int elem_bytes, cudaStrea
 }
 
 __global__ void __launch_bounds__(256) zero_group_kernel(const __grid_constant__ GroupOf<ZeroJob> G) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < G.count; ++j) {
-    unsigned* p = static_cast<unsigned*>(G.job[j].p);
-    const int64_t w = G.job[j].bytes / 4;
-    for (int64_t i = t0; i < w; i += ts) p[i] = 0u;
+  const int64_t total = G.start[G.count];  // 4-byte words
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = group_find(G, t);
+    static_cast<unsigned*>(G.job[j].p)[t - G.start[j]] = 0u;
   }
 }
 
@@ -446,34 +451,37 @@ cudaError_t zero_group(int count, const ZeroJob* jobs, cudaStream_t st) {
   if (!group_ok(count)) return cudaErrorInvalidValue;
   GroupOf<ZeroJob> G;
   G.count = count;
+  G.start[0] = 0;
   int64_t work = 0;
   for (int j = 0; j < count; ++j) {
     if (jobs[j].bytes % 4) return cudaErrorInvalidValue;
     G.job[j] = jobs[j];
     work += jobs[j].bytes / 4;
+    G.start[j + 1] = work;
   }
   zero_group_kernel<<<grid_for(work, 256), 256, 0, st>>>(G);
   g_launches += 1;
   return cudaGetLastError();
 }
 
-// rows of every job's coarse solve, one warp per row as coarse_kernel
+// rows of every job's coarse solve (concatenated, G.start), one warp per
+// row as coarse_kernel
 template <typename T>
 __global__ void coarse_group_kernel(const __grid_constant__ GroupOf<CoarseJob> G) {
   const int lane = threadIdx.x & 31;
-  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int j = 0; j < G.count; ++j) {
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t rows = G.start[G.count];
+  for (int64_t wg = w0; wg < rows; wg += nw) {  // uniform per warp
+    const int j = group_find(G, wg);
     const CoarseJob& a = G.job[j];
+    const int w = (int)(wg - G.start[j]);
     const T* Ainv = static_cast<const T*>(a.Ainv);
     const T* b = static_cast<const T*>(a.b);
-    T* u = static_cast<T*>(a.u);
-    for (int w = w0; w < a.nc; w += nw) {  // uniform per warp
-      T s = T(0);
-      for (int jj = lane; jj < a.nc; jj += 32) s += Ainv[(int64_t)w * a.nc + jj] * b[a.idx[jj]];
+    T s = T(0);
+    for (int jj = lane; jj < a.nc; jj += 32) s += Ainv[(int64_t)w * a.nc + jj] * b[a.idx[jj]];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) u[a.idx[w]] = s;
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) static_cast<T*>(a.u)[a.idx[w]] = s;
   }
 }
 
@@ -483,12 +491,14 @@ cudaError_t coarse_solve_group(int prec, int count, const CoarseJob* jobs, cudaS
   ZeroJob Z[kMaxGroup];
   GroupOf<CoarseJob> G;
   G.count = 0;
+  G.start[0] = 0;
   int64_t rows = 0;
   for (int j = 0; j < count; ++j) {
     Z[j] = ZeroJob{jobs[j].u, (int64_t)es * jobs[j].N};
     if (jobs[j].nc > 0) {
       G.job[G.count++] = jobs[j];
       rows += jobs[j].nc;
+      G.start[G.count] = rows;
     }
   }
   cudaError_t e = zero_group(count, Z, st);
