@@ -311,7 +311,10 @@ def serving_section(p, torch):
            "served_as": "shortest-first admission with 2 s aging, high-priority streams below the median work, "
                         "float-float outer operator",
            "total_dofs": int(sum((r["k"] * r["n"] + 1) ** 3 for r in reqs)), "prepare_s": prep_s}
-    for label, kw in (("cold", best), ("warm", best),
+    # grouped launches for the requests below the median work (they share
+    # each launch with the other running requests of their degree)
+    grouped = dict(best, group_work=small, max_group=16)
+    for label, kw in (("cold", best), ("warm", best), ("warm_grouped", grouped),
                       ("warm_fifo_fp64_operator", {})):
         recs, summ = serve.run(reqs, precision=p.FP32, max_active=16, buffers=bufs, **kw)
         lat = np.array([r["latency_s"] for r in recs])
@@ -321,6 +324,22 @@ def serving_section(p, torch):
         small_lat = [r["latency_s"] for r in recs if (r["k"] * r["n"] + 1) ** 3 * (r["k"] + 2) < small]
         res[label]["p50_below_median_work_ms"] = float(np.median(small_lat) * 1e3)
     del bufs
+    # a stream of small requests, where grouping matters most: 256 requests
+    # arriving at 2,000/s, n log-uniform 4..16 (powers of two), k uniform 2..5,
+    # FP32 V-cycle, 32 slots; one stream per request vs groups of up to 16
+    reqs = serving_requests(n_requests=256, rate=2000.0, arrival_seed=17, size_seed=19, n_lo=4, n_hi=16, k_lo=2,
+                            k_hi=5)
+    bufs = serve.prepare(reqs)
+    small_res = {"workload": "256 requests, Poisson arrivals 2000/s, n log-uniform 4..16 (powers of two), "
+                             "k uniform 2..5, N(0,1) RHS, FP32 V-cycle, FP64 CG to 1e-8, 32 slots",
+                 "total_dofs": int(sum((r["k"] * r["n"] + 1) ** 3 for r in reqs))}
+    for label, kw in (("warmup", {}), ("streams", {}), ("grouped", dict(group_work=1e18, max_group=16))):
+        recs, summ = serve.run(reqs, precision=p.FP32, max_active=32, buffers=bufs, **kw)
+        if label != "warmup":
+            small_res[label] = {k: summ[k] for k in ("p50_ms", "p99_ms", "mean_ms", "makespan_s", "dofs_per_s",
+                                                     "failed", "created_contexts")}
+    del bufs
+    res["small_requests"] = small_res
     return res
 
 

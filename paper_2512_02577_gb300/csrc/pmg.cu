@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <string>
 #include <vector>
@@ -924,6 +925,34 @@ int check_ctx(const pmg_ctx* c) { return c ? PMG_OK : fail(PMG_ERR_ARG, "context
 // most 2^d patch interiors)
 double default_omega_patch(int dim) { return 1.5 / (1 << dim); }
 
+// Pinned host copies of the solver scalars (S_COUNT doubles per context),
+// carved from page-locked slabs that live for the process: cudaMallocHost
+// and cudaFreeHost per context would cost more than the rest of a small
+// context's set-up.
+std::mutex g_pin_mu;
+std::vector<double*> g_pin_free;
+
+double* pinned_scalars_get() {
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  if (g_pin_free.empty()) {
+    constexpr int kPerSlab = 256;
+    double* slab = nullptr;
+    if (cudaMallocHost((void**)&slab, sizeof(double) * S_COUNT * kPerSlab) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = kPerSlab - 1; i >= 0; --i) g_pin_free.push_back(slab + (size_t)i * S_COUNT);
+  }
+  double* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_scalars_put(double* p) {
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
 int setup_context(pmg_ctx* c) {
   const Plan& P = c->plan;
   c->lv.resize(c->L);
@@ -973,12 +1002,22 @@ int setup_context(pmg_ctx* c) {
   c->cellbuf = at(c, P.cellbuf);
   c->verts = (double*)at(c, P.verts);
 
-  // coefficients and kernel attributes
+  // coefficients and kernel attributes: once per device and kernel part
+  // (module state that every context of the part shares)
   std::vector<double> coef(kMaxCoef, 0.0);
   host::fill_coefficients(c->K, coef.data());
-  for (const KernelTable* t : c->kt) {
-    PMG_CUDA(t->prepare());
-    PMG_CUDA(t->upload(coef.data()));
+  {
+    static std::mutex mu;
+    static std::set<std::pair<int, const KernelTable*>> ready;
+    int dev = 0;
+    PMG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    for (const KernelTable* t : c->kt) {
+      if (ready.count({dev, t})) continue;
+      PMG_CUDA(t->prepare());
+      PMG_CUDA(t->upload(coef.data()));
+      ready.insert({dev, t});
+    }
   }
 
   // damping
@@ -1065,7 +1104,8 @@ int setup_context(pmg_ctx* c) {
   if (int rc = choose_patch_layout(c)) return rc;
   if (int rc = choose_def_cpb(c)) return rc;
 
-  PMG_CUDA(cudaMallocHost((void**)&c->host_scal, 8 * S_COUNT));
+  c->host_scal = pinned_scalars_get();
+  if (!c->host_scal) return fail(PMG_ERR_OOM, "cudaMallocHost failed");
   PMG_CUDA(cudaEventCreateWithFlags(&c->ev_rr, cudaEventDisableTiming));
   PMG_CUDA(cudaEventCreate(&c->ev0));
   PMG_CUDA(cudaEventCreate(&c->ev1));
@@ -1182,7 +1222,7 @@ int pmg_destroy(pmg_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev_done) cudaEventDestroy(c->ev_done);
-  if (c->host_scal) cudaFreeHost(c->host_scal);
+  if (c->host_scal) pinned_scalars_put(c->host_scal);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->own_stream && c->stream) {
     cudaStreamSynchronize(c->stream);

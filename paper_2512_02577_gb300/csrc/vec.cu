@@ -310,12 +310,21 @@ cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, con
 // the jobs over the grid (GroupOf::start).
 static bool group_ok(int count) { return count >= 1 && count <= kMaxGroup; }
 
+// Blocks along x take the job's kDotBlocks reduction blocks in turn (vb):
+// the partial of vb is formed exactly as by block vb of dot_partial_kernel
+// (same elements per thread, same order, same block tree), so a grouped
+// launch needs fewer than kDotBlocks blocks per job for small vectors.
+static int group_dot_blocks(int count) { return std::max(1, std::min(kDotBlocks, 4 * 152 / count)); }
+
 __global__ void __launch_bounds__(256) dot_partial_group(const __grid_constant__ GroupOf<DotJob> G) {
   const DotJob& a = G.job[blockIdx.y];
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-    s += a.x[i] * a.y[i];
-  block_store_sum(s, a.partial + blockIdx.x);
+  for (int vb = blockIdx.x; vb < kDotBlocks; vb += gridDim.x) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)kDotBlocks * blockDim.x)
+      s += a.x[i] * a.y[i];
+    block_store_sum(s, a.partial + vb);
+    __syncthreads();  // the block's reduction scratch is reused by the next vb
+  }
 }
 
 __global__ void __launch_bounds__(256) sum_partials_group(const __grid_constant__ GroupOf<DotJob> G) {
@@ -330,7 +339,7 @@ cudaError_t dot_group(int count, const DotJob* jobs, cudaStream_t st) {
   GroupOf<DotJob> G;
   G.count = count;
   for (int j = 0; j < count; ++j) G.job[j] = jobs[j];
-  dot_partial_group<<<dim3(kDotBlocks, count), 256, 0, st>>>(G);
+  dot_partial_group<<<dim3(group_dot_blocks(count), count), 256, 0, st>>>(G);
   sum_partials_group<<<count, 256, 0, st>>>(G);
   g_launches += 2;
   return cudaGetLastError();
@@ -339,14 +348,17 @@ cudaError_t dot_group(int count, const DotJob* jobs, cudaStream_t st) {
 __global__ void __launch_bounds__(256) cg_xr_group(const __grid_constant__ GroupOf<CgXrJob> G) {
   const CgXrJob& a = G.job[blockIdx.y];
   const double alpha = a.s[a.num] / a.s[a.den];
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    a.x[i] += alpha * a.p[i];
-    const double ri = a.r[i] - alpha * a.Ap[i];
-    a.r[i] = ri;
-    acc += ri * ri;
+  for (int vb = blockIdx.x; vb < kDotBlocks; vb += gridDim.x) {  // as dot_partial_group
+    double acc = 0.0;
+    for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)kDotBlocks * blockDim.x) {
+      a.x[i] += alpha * a.p[i];
+      const double ri = a.r[i] - alpha * a.Ap[i];
+      a.r[i] = ri;
+      acc += ri * ri;
+    }
+    block_store_sum(acc, a.partial + vb);
+    __syncthreads();
   }
-  block_store_sum(acc, a.partial + blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) cg_xr_sum_group(const __grid_constant__ GroupOf<CgXrJob> G) {
@@ -361,7 +373,7 @@ cudaError_t cg_update_xr_group(int count, const CgXrJob* jobs, cudaStream_t st) 
   GroupOf<CgXrJob> G;
   G.count = count;
   for (int j = 0; j < count; ++j) G.job[j] = jobs[j];
-  cg_xr_group<<<dim3(kDotBlocks, count), 256, 0, st>>>(G);
+  cg_xr_group<<<dim3(group_dot_blocks(count), count), 256, 0, st>>>(G);
   cg_xr_sum_group<<<count, 256, 0, st>>>(G);
   g_launches += 2;
   return cudaGetLastError();
