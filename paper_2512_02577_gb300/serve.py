@@ -62,8 +62,8 @@ def run(requests, dim=3, precision=FP32, geometry=CARTESIAN, max_active=8, budge
             i = pending.pop(0)
             r, cfg, b, x = prepared[i]
             ids[i] = server.submit(cfg, b, x, rtol=rtol, maxit=maxit)
-        server.poll()
-        done = sum(1 for i in ids if server.result(ids[i])["state"] >= 2)
+        running, queued = server.poll()
+        done = len(ids) - running - queued  # finished (done or failed): neither queued nor running
         if poll_sleep:
             time.sleep(poll_sleep)
     wall = time.perf_counter() - t0
