@@ -474,8 +474,10 @@ def degree_sweep():
 def profile_region(region, n_def):
     """One NVTX range named 'profile' after warm-up, for
     ncu --nvtx --nvtx-include "profile/": one mixed-precision solve of the
-    32^3 Q4 problem (with the FP64 or the float-float outer operator), or one
-    FP32 apply and one FP32 sweep of the deformed Q3 problem on n_def^3 cells."""
+    32^3 Q4 problem (with the FP64 or the float-float outer operator), one
+    FP32 apply and one FP32 sweep of the deformed Q3 problem on n_def^3 cells,
+    or one grouped solve of 16 Q3 systems on 4^3, 8^3, 16^3 and 8^3 cells
+    (four of each, FP32 V-cycle)."""
     import torch
     import paper_2512_02577_gb300 as p
     dev = torch.device("cuda", 0)
@@ -493,6 +495,20 @@ def profile_region(region, n_def):
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_push("profile")
             ctx.solve(b, x)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        elif region == "grouped":
+            from paper_2512_02577_gb300.inputs import random_vector
+            ns = [4, 8, 16, 8] * 4
+            ctxs = [p.Context(p.make_config(dim=3, n_cells=n, degree=3, mg_precision=p.FP32), stream=stream,
+                              device=dev) for n in ns]
+            bs = [torch.from_numpy(random_vector(3, n, 3, seed=i)).to(dev) for i, n in enumerate(ns)]
+            xs = [torch.zeros_like(b) for b in bs]
+            for _ in range(3):
+                p.solve_group(ctxs, bs, xs)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("profile")
+            p.solve_group(ctxs, bs, xs)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
         else:
@@ -545,7 +561,7 @@ def main():
     ap.add_argument("--oracle-child", type=float, default=None)
     ap.add_argument("--oracle-steps", type=int, default=0)
     ap.add_argument("--oracle-case", default="sample", choices=["sample", "cfg1"])
-    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "mixed_solve_ff", "deformed"],
+    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "mixed_solve_ff", "deformed", "grouped"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
     ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
     ap.add_argument("--no-extras", action="store_true", help="skip the deformed and serving sections")
