@@ -476,7 +476,8 @@ def profile_region(region, n_def):
     ncu --nvtx --nvtx-include "profile/": one mixed-precision solve of the
     32^3 Q4 problem (with the FP64 or the float-float outer operator), one
     FP32 apply and one FP32 sweep of the deformed Q3 problem on n_def^3 cells,
-    or one grouped solve of 16 Q3 systems on 4^3, 8^3, 16^3 and 8^3 cells
+    one FP32 apply of the Cartesian Q3 problem on n_def^3 cells, or one
+    grouped solve of 16 Q3 systems on 4^3, 8^3, 16^3 and 8^3 cells
     (four of each, FP32 V-cycle)."""
     import torch
     import paper_2512_02577_gb300 as p
@@ -495,6 +496,18 @@ def profile_region(region, n_def):
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_push("profile")
             ctx.solve(b, x)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        elif region == "cart_apply32":
+            ctx = p.Context(p.make_config(dim=3, n_cells=n_def, degree=3, mg_precision=p.FP32), stream=stream,
+                            device=dev)
+            x = torch.randn(ctx.num_dofs(), dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                ctx.apply(x, y, prec=p.FP32)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("profile")
+            ctx.apply(x, y, prec=p.FP32)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
         elif region == "grouped":
@@ -561,9 +574,9 @@ def main():
     ap.add_argument("--oracle-child", type=float, default=None)
     ap.add_argument("--oracle-steps", type=int, default=0)
     ap.add_argument("--oracle-case", default="sample", choices=["sample", "cfg1"])
-    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "mixed_solve_ff", "deformed", "grouped"],
+    ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "mixed_solve_ff", "deformed", "grouped", "cart_apply32"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
-    ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed profile case")
+    ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed and Cartesian-apply profile cases")
     ap.add_argument("--no-extras", action="store_true", help="skip the deformed and serving sections")
     ap.add_argument("--sweep", action="store_true", help="degree sweep k = 1..8 at ~8M DoFs (separate JSON)")
     args = ap.parse_args()

@@ -33,16 +33,25 @@ static cudaError_t cart_apply_t(const T* x, T* y, const T* b, T* t0, T* t1, T* t
   const int64_t work = (int64_t)(n + 1) * (DIM == 3 ? (int64_t)N1 * N1 : N1);
   const int bs = 256;
   const int g = grid_for(work, bs);
-  if (DIM == 3) {
-    cart_pass<3, 0, 0, false, T><<<g, bs, 0, st>>>(x, nullptr, t0, t1, nullptr, n, s);
-    cart_pass<3, 1, 1, false, T><<<g, bs, 0, st>>>(t0, t1, t2, t3, nullptr, n, s);
-    if (b) cart_pass<3, 2, 2, true, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, b, n, s);
-    else cart_pass<3, 2, 2, false, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, nullptr, n, s);
+  const FastDiv dnp1(n + 1), dN1(N1);
+  if constexpr (DIM == 3 && sizeof(T) == 4) {  // FP32: x and y passes fused per z plane (cart_xy_kernel)
+    const int tiles = (n + CartXY<T>::CX - 1) / CartXY<T>::CX;
+    cart_xy_kernel<T><<<dim3(tiles * tiles, N1), 256, 0, st>>>(x, t2, t3, n);
+    if (b) cart_pass<3, 2, 2, true, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, b, n, s, dnp1, dN1);
+    else cart_pass<3, 2, 2, false, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, nullptr, n, s, dnp1, dN1);
+    g_launches += 2;
+    (void)t0;
+    (void)t1;
+  } else if (DIM == 3) {
+    cart_pass<3, 0, 0, false, T><<<g, bs, 0, st>>>(x, nullptr, t0, t1, nullptr, n, s, dnp1, dN1);
+    cart_pass<3, 1, 1, false, T><<<g, bs, 0, st>>>(t0, t1, t2, t3, nullptr, n, s, dnp1, dN1);
+    if (b) cart_pass<3, 2, 2, true, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, b, n, s, dnp1, dN1);
+    else cart_pass<3, 2, 2, false, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, nullptr, n, s, dnp1, dN1);
     g_launches += 3;
   } else {
-    cart_pass<2, 0, 0, false, T><<<g, bs, 0, st>>>(x, nullptr, t0, t1, nullptr, n, s);
-    if (b) cart_pass<2, 1, 2, true, T><<<g, bs, 0, st>>>(t0, t1, y, nullptr, b, n, s);
-    else cart_pass<2, 1, 2, false, T><<<g, bs, 0, st>>>(t0, t1, y, nullptr, nullptr, n, s);
+    cart_pass<2, 0, 0, false, T><<<g, bs, 0, st>>>(x, nullptr, t0, t1, nullptr, n, s, dnp1, dN1);
+    if (b) cart_pass<2, 1, 2, true, T><<<g, bs, 0, st>>>(t0, t1, y, nullptr, b, n, s, dnp1, dN1);
+    else cart_pass<2, 1, 2, false, T><<<g, bs, 0, st>>>(t0, t1, y, nullptr, nullptr, n, s, dnp1, dN1);
     g_launches += 2;
   }
   return cudaGetLastError();
@@ -64,19 +73,20 @@ static cudaError_t cart_apply_ff_t(const double* x, double* y, const double* b, 
   const int64_t work = (int64_t)(n + 1) * (DIM == 3 ? (int64_t)N1 * N1 : N1);
   const int bs = 256;
   const int g = grid_for(work, bs);
+  const FastDiv dnp1(n + 1), dN1(N1);
   const float sh = (float)scale;
   const ff s{sh, (float)(scale - (double)sh)};
   float *f0 = (float*)t0, *f1 = (float*)t1, *f2 = (float*)t2, *f3 = (float*)t3;
   if (DIM == 3) {
-    cart_pass_ff<3, 0, 0, false><<<g, bs, 0, st>>>(x, nullptr, f0, f1, nullptr, n, s);
-    cart_pass_ff<3, 1, 1, false><<<g, bs, 0, st>>>(f0, f1, f2, f3, nullptr, n, s);
-    if (b) cart_pass_ff<3, 2, 2, true><<<g, bs, 0, st>>>(f2, f3, y, nullptr, b, n, s);
-    else cart_pass_ff<3, 2, 2, false><<<g, bs, 0, st>>>(f2, f3, y, nullptr, nullptr, n, s);
+    cart_pass_ff<3, 0, 0, false><<<g, bs, 0, st>>>(x, nullptr, f0, f1, nullptr, n, s, dnp1, dN1);
+    cart_pass_ff<3, 1, 1, false><<<g, bs, 0, st>>>(f0, f1, f2, f3, nullptr, n, s, dnp1, dN1);
+    if (b) cart_pass_ff<3, 2, 2, true><<<g, bs, 0, st>>>(f2, f3, y, nullptr, b, n, s, dnp1, dN1);
+    else cart_pass_ff<3, 2, 2, false><<<g, bs, 0, st>>>(f2, f3, y, nullptr, nullptr, n, s, dnp1, dN1);
     g_launches += 3;
   } else {
-    cart_pass_ff<2, 0, 0, false><<<g, bs, 0, st>>>(x, nullptr, f0, f1, nullptr, n, s);
-    if (b) cart_pass_ff<2, 1, 2, true><<<g, bs, 0, st>>>(f0, f1, y, nullptr, b, n, s);
-    else cart_pass_ff<2, 1, 2, false><<<g, bs, 0, st>>>(f0, f1, y, nullptr, nullptr, n, s);
+    cart_pass_ff<2, 0, 0, false><<<g, bs, 0, st>>>(x, nullptr, f0, f1, nullptr, n, s, dnp1, dN1);
+    if (b) cart_pass_ff<2, 1, 2, true><<<g, bs, 0, st>>>(f0, f1, y, nullptr, b, n, s, dnp1, dN1);
+    else cart_pass_ff<2, 1, 2, false><<<g, bs, 0, st>>>(f0, f1, y, nullptr, nullptr, n, s, dnp1, dN1);
     g_launches += 2;
   }
   return cudaGetLastError();
@@ -211,8 +221,8 @@ static cudaError_t patch_cart_il(int dim, int prec, const void* r, void* dst, in
 template <int DIM, typename T>
 static cudaError_t patch_gather_t(const T* dst, T* u, int n, int add, cudaStream_t st) {
   const int64_t N = ipow(K * n + 1, DIM);
-  if (add) patch_gather_kernel<DIM, true, T><<<grid_for(N, 256), 256, 0, st>>>(dst, u, n);
-  else patch_gather_kernel<DIM, false, T><<<grid_for(N, 256), 256, 0, st>>>(dst, u, n);
+  if (add) patch_gather_kernel<DIM, true, T><<<grid_for(N, 256), 256, 0, st>>>(dst, u, n, FastDiv(K * n + 1));
+  else patch_gather_kernel<DIM, false, T><<<grid_for(N, 256), 256, 0, st>>>(dst, u, n, FastDiv(K * n + 1));
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -227,13 +237,13 @@ static cudaError_t h_prolong_t(const T* uc, T* uf, T* t0, T* t1, int nc, cudaStr
   const int c1 = K * nc + 1, f1 = 2 * K * nc + 1;
   const int bs = 256;
   if (DIM == 3) {
-    hprolong_pass<0, false, T><<<grid_for((int64_t)f1 * c1 * c1, bs), bs, 0, st>>>(uc, t0, nc, f1, c1, c1);
-    hprolong_pass<1, false, T><<<grid_for((int64_t)f1 * f1 * c1, bs), bs, 0, st>>>(t0, t1, nc, f1, f1, c1);
-    hprolong_pass<2, true, T><<<grid_for((int64_t)f1 * f1 * f1, bs), bs, 0, st>>>(t1, uf, nc, f1, f1, f1);
+    hprolong_pass<0, false, T><<<grid_for((int64_t)f1 * c1 * c1, bs), bs, 0, st>>>(uc, t0, nc, f1, c1, c1, FastDiv(f1), FastDiv(c1));
+    hprolong_pass<1, false, T><<<grid_for((int64_t)f1 * f1 * c1, bs), bs, 0, st>>>(t0, t1, nc, f1, f1, c1, FastDiv(f1), FastDiv(f1));
+    hprolong_pass<2, true, T><<<grid_for((int64_t)f1 * f1 * f1, bs), bs, 0, st>>>(t1, uf, nc, f1, f1, f1, FastDiv(f1), FastDiv(f1));
     g_launches += 3;
   } else {
-    hprolong_pass<0, false, T><<<grid_for((int64_t)f1 * c1, bs), bs, 0, st>>>(uc, t0, nc, f1, c1, 1);
-    hprolong_pass<1, true, T><<<grid_for((int64_t)f1 * f1, bs), bs, 0, st>>>(t0, uf, nc, f1, f1, 1);
+    hprolong_pass<0, false, T><<<grid_for((int64_t)f1 * c1, bs), bs, 0, st>>>(uc, t0, nc, f1, c1, 1, FastDiv(f1), FastDiv(c1));
+    hprolong_pass<1, true, T><<<grid_for((int64_t)f1 * f1, bs), bs, 0, st>>>(t0, uf, nc, f1, f1, 1, FastDiv(f1), FastDiv(f1));
     g_launches += 2;
   }
   return cudaGetLastError();
@@ -244,13 +254,13 @@ static cudaError_t h_restrict_t(const T* rf, T* rc, T* t0, T* t1, int nc, cudaSt
   const int c1 = K * nc + 1, f1 = 2 * K * nc + 1;
   const int bs = 256;
   if (DIM == 3) {
-    hrestrict_pass<2, T><<<grid_for((int64_t)f1 * f1 * c1, bs), bs, 0, st>>>(rf, t0, nc, f1, f1, c1);
-    hrestrict_pass<1, T><<<grid_for((int64_t)f1 * c1 * c1, bs), bs, 0, st>>>(t0, t1, nc, f1, c1, c1);
-    hrestrict_pass<0, T><<<grid_for((int64_t)c1 * c1 * c1, bs), bs, 0, st>>>(t1, rc, nc, c1, c1, c1);
+    hrestrict_pass<2, T><<<grid_for((int64_t)f1 * f1 * c1, bs), bs, 0, st>>>(rf, t0, nc, f1, f1, c1, FastDiv(f1), FastDiv(f1));
+    hrestrict_pass<1, T><<<grid_for((int64_t)f1 * c1 * c1, bs), bs, 0, st>>>(t0, t1, nc, f1, c1, c1, FastDiv(f1), FastDiv(c1));
+    hrestrict_pass<0, T><<<grid_for((int64_t)c1 * c1 * c1, bs), bs, 0, st>>>(t1, rc, nc, c1, c1, c1, FastDiv(c1), FastDiv(c1));
     g_launches += 3;
   } else {
-    hrestrict_pass<1, T><<<grid_for((int64_t)f1 * c1, bs), bs, 0, st>>>(rf, t0, nc, f1, c1, 1);
-    hrestrict_pass<0, T><<<grid_for((int64_t)c1 * c1, bs), bs, 0, st>>>(t0, rc, nc, c1, c1, 1);
+    hrestrict_pass<1, T><<<grid_for((int64_t)f1 * c1, bs), bs, 0, st>>>(rf, t0, nc, f1, c1, 1, FastDiv(f1), FastDiv(c1));
+    hrestrict_pass<0, T><<<grid_for((int64_t)c1 * c1, bs), bs, 0, st>>>(t0, rc, nc, c1, c1, 1, FastDiv(c1), FastDiv(c1));
     g_launches += 2;
   }
   return cudaGetLastError();
@@ -295,12 +305,12 @@ static cudaError_t cart_apply_group_t(int count, const ApplyJob* jobs, cudaStrea
     T* t2 = (T*)a.t[2];
     T* t3 = (T*)a.t[3];
     const T s = (T)a.scale;
-    g0.job[j] = CartPassJob<T>{x, nullptr, t0, t1, nullptr, a.n, s};
+    g0.job[j] = CartPassJob<T>{x, nullptr, t0, t1, nullptr, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
     if (DIM == 3) {
-      g1.job[j] = CartPassJob<T>{t0, t1, t2, t3, nullptr, a.n, s};
-      g2.job[j] = CartPassJob<T>{t2, t3, (T*)a.y, nullptr, (const T*)a.b, a.n, s};
+      g1.job[j] = CartPassJob<T>{t0, t1, t2, t3, nullptr, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
+      g2.job[j] = CartPassJob<T>{t2, t3, (T*)a.y, nullptr, (const T*)a.b, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
     } else {
-      g1.job[j] = CartPassJob<T>{t0, t1, (T*)a.y, nullptr, (const T*)a.b, a.n, s};
+      g1.job[j] = CartPassJob<T>{t0, t1, (T*)a.y, nullptr, (const T*)a.b, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
     }
     work += apply_work(DIM, a.n);
     g0.start[j + 1] = work;
@@ -340,12 +350,12 @@ static cudaError_t cart_apply_ff_group_t(int count, const ApplyJob* jobs, cudaSt
     const float sh = (float)a.scale;
     const ff s{sh, (float)(a.scale - (double)sh)};
     float *f0 = (float*)a.t[0], *f1 = (float*)a.t[1], *f2 = (float*)a.t[2], *f3 = (float*)a.t[3];
-    g0.job[j] = CartPassFFJob{a.x, nullptr, f0, f1, nullptr, a.n, s};
+    g0.job[j] = CartPassFFJob{a.x, nullptr, f0, f1, nullptr, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
     if (DIM == 3) {
-      g1.job[j] = CartPassFFJob{f0, f1, f2, f3, nullptr, a.n, s};
-      g2.job[j] = CartPassFFJob{f2, f3, a.y, nullptr, (const double*)a.b, a.n, s};
+      g1.job[j] = CartPassFFJob{f0, f1, f2, f3, nullptr, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
+      g2.job[j] = CartPassFFJob{f2, f3, a.y, nullptr, (const double*)a.b, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
     } else {
-      g1.job[j] = CartPassFFJob{f0, f1, a.y, nullptr, (const double*)a.b, a.n, s};
+      g1.job[j] = CartPassFFJob{f0, f1, a.y, nullptr, (const double*)a.b, a.n, s, FastDiv(a.n + 1), FastDiv(K * a.n + 1)};
     }
     work += apply_work(DIM, a.n);
     g0.start[j + 1] = work;
@@ -426,7 +436,7 @@ static cudaError_t patch_gather_group_t(int count, const GatherSolveJob* jobs, i
   G.start[0] = 0;
   int64_t work = 0;
   for (int j = 0; j < count; ++j) {
-    G.job[j] = GatherJob<T>{(const T*)jobs[j].dst, (T*)jobs[j].u, jobs[j].n};
+    G.job[j] = GatherJob<T>{(const T*)jobs[j].dst, (T*)jobs[j].u, jobs[j].n, FastDiv(K * jobs[j].n + 1)};
     work += ipow(K * jobs[j].n + 1, DIM);
     G.start[j + 1] = work;
   }
@@ -457,15 +467,15 @@ static cudaError_t h_prolong_group_t(int count, const TransferSolveJob* jobs, cu
     const T* uc = (const T*)a.in;
     T *uf = (T*)a.out, *t0 = (T*)a.t0, *t1 = (T*)a.t1;
     if (DIM == 3) {
-      g[0].job[j] = TransferJob<T>{uc, t0, nc, f1, c1, c1};
-      g[1].job[j] = TransferJob<T>{t0, t1, nc, f1, f1, c1};
-      g[2].job[j] = TransferJob<T>{t1, uf, nc, f1, f1, f1};
+      g[0].job[j] = TransferJob<T>{uc, t0, nc, f1, c1, c1, FastDiv(f1), FastDiv(c1)};
+      g[1].job[j] = TransferJob<T>{t0, t1, nc, f1, f1, c1, FastDiv(f1), FastDiv(f1)};
+      g[2].job[j] = TransferJob<T>{t1, uf, nc, f1, f1, f1, FastDiv(f1), FastDiv(f1)};
       work[0] += (int64_t)f1 * c1 * c1;
       work[1] += (int64_t)f1 * f1 * c1;
       work[2] += (int64_t)f1 * f1 * f1;
     } else {
-      g[0].job[j] = TransferJob<T>{uc, t0, nc, f1, c1, 1};
-      g[1].job[j] = TransferJob<T>{t0, uf, nc, f1, f1, 1};
+      g[0].job[j] = TransferJob<T>{uc, t0, nc, f1, c1, 1, FastDiv(f1), FastDiv(c1)};
+      g[1].job[j] = TransferJob<T>{t0, uf, nc, f1, f1, 1, FastDiv(f1), FastDiv(f1)};
       work[0] += (int64_t)f1 * c1;
       work[1] += (int64_t)f1 * f1;
     }
@@ -499,15 +509,15 @@ static cudaError_t h_restrict_group_t(int count, const TransferSolveJob* jobs, c
     const T* rf = (const T*)a.in;
     T *rc = (T*)a.out, *t0 = (T*)a.t0, *t1 = (T*)a.t1;
     if (DIM == 3) {
-      g[0].job[j] = TransferJob<T>{rf, t0, nc, f1, f1, c1};
-      g[1].job[j] = TransferJob<T>{t0, t1, nc, f1, c1, c1};
-      g[2].job[j] = TransferJob<T>{t1, rc, nc, c1, c1, c1};
+      g[0].job[j] = TransferJob<T>{rf, t0, nc, f1, f1, c1, FastDiv(f1), FastDiv(f1)};
+      g[1].job[j] = TransferJob<T>{t0, t1, nc, f1, c1, c1, FastDiv(f1), FastDiv(c1)};
+      g[2].job[j] = TransferJob<T>{t1, rc, nc, c1, c1, c1, FastDiv(c1), FastDiv(c1)};
       work[0] += (int64_t)f1 * f1 * c1;
       work[1] += (int64_t)f1 * c1 * c1;
       work[2] += (int64_t)c1 * c1 * c1;
     } else {
-      g[0].job[j] = TransferJob<T>{rf, t0, nc, f1, c1, 1};
-      g[1].job[j] = TransferJob<T>{t0, rc, nc, c1, c1, 1};
+      g[0].job[j] = TransferJob<T>{rf, t0, nc, f1, c1, 1, FastDiv(f1), FastDiv(c1)};
+      g[1].job[j] = TransferJob<T>{t0, rc, nc, c1, c1, 1, FastDiv(c1), FastDiv(c1)};
       work[0] += (int64_t)f1 * c1;
       work[1] += (int64_t)c1 * c1;
     }

@@ -73,14 +73,29 @@ __device__ __forceinline__ const float* ctab<float>() { return c_tab32; }
 template <int DIM, int AX, int MODE, bool RESID, typename T>
 __device__ __forceinline__ void cart_pass_body(const T* __restrict__ in0, const T* __restrict__ in1,
                                                T* __restrict__ out0, T* __restrict__ out1,
-                                               const T* __restrict__ bvec, int n, T s, int64_t t0, int64_t tstep) {
+                                               const T* __restrict__ bvec, int n, T s, FastDiv dnp1, FastDiv dN1,
+                                               int64_t t0, int64_t tstep) {
   const int N1 = K * n + 1;
   const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
   const int64_t total = (int64_t)(n + 1) * lines;
   const T* C = ctab<T>();
+  const bool fast = total < kFastDivItems;
   for (int64_t t = t0; t < total; t += tstep) {
     int c, p, q;
-    if (AX == 0) {
+    if (fast) {  // 32-bit decoding by the launch's reciprocals
+      const uint32_t u = (uint32_t)t;
+      if (AX == 0) {
+        const uint32_t r = dnp1.div(u);
+        c = (int)(u - r * dnp1.d);
+        q = (int)dN1.div(r);
+        p = (int)(r - (uint32_t)q * dN1.d);
+      } else {
+        const uint32_t r = dN1.div(u);
+        p = (int)(u - r * dN1.d);
+        q = (int)dnp1.div(r);
+        c = (int)(r - (uint32_t)q * dnp1.d);
+      }
+    } else if (AX == 0) {
       c = (int)(t % (n + 1));
       const int64_t r = t / (n + 1);
       p = (int)(r % N1);
@@ -169,10 +184,156 @@ __device__ __forceinline__ void cart_pass_body(const T* __restrict__ in0, const 
 template <int DIM, int AX, int MODE, bool RESID, typename T>
 __global__ void __launch_bounds__(256) cart_pass(const T* __restrict__ in0, const T* __restrict__ in1,
                                                  T* __restrict__ out0, T* __restrict__ out1,
-                                                 const T* __restrict__ bvec, int n, T s) {
-  cart_pass_body<DIM, AX, MODE, RESID, T>(in0, in1, out0, out1, bvec, n, s,
+                                                 const T* __restrict__ bvec, int n, T s, FastDiv dnp1,
+                                                 FastDiv dN1) {
+  cart_pass_body<DIM, AX, MODE, RESID, T>(in0, in1, out0, out1, bvec, n, s, dnp1, dN1,
                                           (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                           (int64_t)gridDim.x * blockDim.x);
+}
+
+// ===========================================================================
+// First two passes of the 3D apply in one launch (x and y directions of one
+// z plane; FP32, where the three passes are bound by memory traffic): a
+// block loads a tile of x on plane z -- TO x TO owned nodes plus the rows and
+// columns of the neighbouring cells that the 1D matrices reach (K before,
+// one after) -- into shared memory, applies M and K along x to every loaded
+// row, then M and K along y to the owned nodes, and writes the two results
+// of cart_pass MODE 1 (t2 = M_y M_x x, t3 = K_y M_x x + M_y K_x x) for the
+// last pass (MODE 2).  x is read about 1.3 times (tile halos, mostly from
+// L2) instead of the x pass writing and the y pass re-reading two
+// intermediates: 6 words of traffic per node instead of 10.  Every output is
+// formed with cart_pass's arithmetic in cart_pass's order, so the results
+// are bitwise those of the first two passes.
+// ===========================================================================
+template <typename T>
+struct CartXY {
+  static constexpr int CX = K >= 32 ? 1 : 32 / K;  // cells per tile side
+  static constexpr int TO = K * CX;                // owned nodes per side
+  static constexpr int TH = TO + K + 1;            // loaded nodes per side
+  static constexpr int PT = TO | 1;                // row pitch of the x-pass results (odd: no bank conflicts)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) cart_xy_kernel(const T* __restrict__ x, T* __restrict__ t2,
+                                                      T* __restrict__ t3, int n) {
+  using X = CartXY<T>;
+  constexpr int TH = X::TH, PT = X::PT, CX = X::CX;
+  __shared__ T xs[TH * TH];
+  __shared__ T s0[TH * PT];
+  __shared__ T s1[TH * PT];
+  const int N1 = K * n + 1;
+  const int tiles = (n + CX - 1) / CX;
+  const int cx0 = (blockIdx.x % tiles) * CX, cy0 = (blockIdx.x / tiles) * CX;
+  const int ncx = min(CX, n - cx0), ncy = min(CX, n - cy0);
+  const int gz = blockIdx.y;
+  const int64_t plane = (int64_t)gz * N1 * N1;
+  const bool last_x = cx0 + ncx == n, last_y = cy0 + ncy == n;
+  const int OX = K * ncx + (last_x ? 1 : 0), OY = K * ncy + (last_y ? 1 : 0);  // owned nodes
+  if (gz == 0 || gz == N1 - 1) {  // x is zero on the boundary planes: so are both results
+    for (int i = threadIdx.x; i < OX * OY; i += blockDim.x) {
+      const int64_t o = plane + (int64_t)(K * cy0 + i / OX) * N1 + K * cx0 + i % OX;
+      t2[o] = T(0);
+      t3[o] = T(0);
+    }
+    return;
+  }
+  const T* C = ctab<T>();
+  const T* Me = C + LAY.Me;
+  const T* Ke = C + LAY.Ke;
+  // x restricted to the free nodes: rows K (cy0 - 1) .. K (cy0 + ncy), columns likewise
+  const int RY = K * (ncy + 1) + 1, RX = K * (ncx + 1) + 1;
+  // loops decode their items with the compile-time tile sizes (cheap
+  // divisions) and skip the items of a partial tile
+  for (int i = threadIdx.x; i < TH * TH; i += blockDim.x) {
+    const int r = i / TH, c = i - r * TH;
+    if (r >= RY || c >= RX) continue;
+    const int gy = K * (cy0 - 1) + r, gx = K * (cx0 - 1) + c;
+    xs[r * TH + c] = (gy >= 1 && gy <= N1 - 2 && gx >= 1 && gx <= N1 - 2) ? x[plane + (int64_t)gy * N1 + gx] : T(0);
+  }
+  __syncthreads();
+  // x pass (cart_pass MODE 0) on every loaded row, owned cells; rows fastest
+  for (int i = threadIdx.x; i < TH * CX; i += blockDim.x) {
+    const int cc = i / TH, r = i - cc * TH, c = cx0 + cc;
+    if (r >= RY || cc >= ncx) continue;
+    T xr0[K + 1], xl0[K + 1];
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      xr0[b] = xs[r * TH + K * (cc + 1) + b];
+      xl0[b] = c > 0 ? xs[r * TH + K * cc + b] : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      T m0 = 0, k0 = 0;
+#pragma unroll
+      for (int b = 0; b <= K; ++b) {
+        m0 += Me[a * (K + 1) + b] * xr0[b];
+        k0 += Ke[a * (K + 1) + b] * xr0[b];
+      }
+      if (a == 0) {
+#pragma unroll
+        for (int b = 0; b <= K; ++b) {
+          m0 += Me[K * (K + 1) + b] * xl0[b];
+          k0 += Ke[K * (K + 1) + b] * xl0[b];
+        }
+      }
+      const bool bnd = K * c + a == 0;
+      s0[r * PT + K * cc + a] = bnd ? T(0) : m0;
+      s1[r * PT + K * cc + a] = bnd ? T(0) : k0;
+    }
+  }
+  __syncthreads();
+  // y pass (cart_pass MODE 1) on the owned nodes; columns fastest (coalesced stores)
+  const int CW = K * ncx;
+  constexpr int TO = X::TO;
+  for (int i = threadIdx.x; i < TO * CX; i += blockDim.x) {
+    const int cc = i / TO, j = i - cc * TO, cy = cy0 + cc;
+    if (j >= CW || cc >= ncy) continue;
+    T xr0[K + 1], xl0[K + 1], xr1[K + 1], xl1[K + 1];
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      xr0[b] = s0[(K * (cc + 1) + b) * PT + j];
+      xr1[b] = s1[(K * (cc + 1) + b) * PT + j];
+      xl0[b] = cy > 0 ? s0[(K * cc + b) * PT + j] : T(0);
+      xl1[b] = cy > 0 ? s1[(K * cc + b) * PT + j] : T(0);
+    }
+    const int64_t col = plane + K * cx0 + j;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      T m0 = 0, k0 = 0, m1 = 0;
+#pragma unroll
+      for (int b = 0; b <= K; ++b) {
+        m0 += Me[a * (K + 1) + b] * xr0[b];
+        k0 += Ke[a * (K + 1) + b] * xr0[b];
+        m1 += Me[a * (K + 1) + b] * xr1[b];
+      }
+      if (a == 0) {
+#pragma unroll
+        for (int b = 0; b <= K; ++b) {
+          m0 += Me[K * (K + 1) + b] * xl0[b];
+          k0 += Ke[K * (K + 1) + b] * xl0[b];
+          m1 += Me[K * (K + 1) + b] * xl1[b];
+        }
+      }
+      const int g = K * cy + a;
+      const bool bnd = g == 0;
+      const int64_t o = col + (int64_t)g * N1;
+      t2[o] = bnd ? T(0) : m0;
+      t3[o] = bnd ? T(0) : k0 + m1;
+    }
+  }
+  // the last node of a line is on the boundary: zero (as the passes write it)
+  if (last_y)
+    for (int j = threadIdx.x; j < OX; j += blockDim.x) {
+      const int64_t o = plane + (int64_t)(N1 - 1) * N1 + K * cx0 + j;
+      t2[o] = T(0);
+      t3[o] = T(0);
+    }
+  if (last_x)
+    for (int r = threadIdx.x; r < K * ncy; r += blockDim.x) {
+      const int64_t o = plane + (int64_t)(K * cy0 + r) * N1 + N1 - 1;
+      t2[o] = T(0);
+      t3[o] = T(0);
+    }
 }
 
 // Grouped launch: the same pass over every job's level (jobs of one launch
@@ -188,6 +349,7 @@ struct CartPassJob {
   const T* bvec;
   int n;
   T s;
+  FastDiv dnp1, dN1;  // n + 1, K n + 1
 };
 
 template <int DIM, int AX, int MODE, bool RESID, typename T>
@@ -196,8 +358,8 @@ __global__ void __launch_bounds__(256) cart_pass_group(const __grid_constant__ G
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = group_find(G, t);
     const CartPassJob<T>& a = G.job[j];
-    cart_pass_body<DIM, AX, MODE, RESID, T>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t - G.start[j],
-                                            kOneItem);
+    cart_pass_body<DIM, AX, MODE, RESID, T>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, a.dnp1, a.dN1,
+                                            t - G.start[j], kOneItem);
   }
 }
 
@@ -269,8 +431,8 @@ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (do
 template <int DIM, int AX, int MODE, bool RESID>
 __device__ __forceinline__ void cart_pass_ff_body(const void* __restrict__ in0_, const float* __restrict__ in1,
                                                   void* __restrict__ out0_, float* __restrict__ out1,
-                                                  const double* __restrict__ bvec, int n, ff s, int64_t t0,
-                                                  int64_t tstep) {
+                                                  const double* __restrict__ bvec, int n, ff s, FastDiv dnp1,
+                                                  FastDiv dN1, int64_t t0, int64_t tstep) {
   const int N1 = K * n + 1;
   const int64_t lines = DIM == 3 ? (int64_t)N1 * N1 : (int64_t)N1;
   const int64_t total = (int64_t)(n + 1) * lines;
@@ -289,9 +451,23 @@ __device__ __forceinline__ void cart_pass_ff_body(const void* __restrict__ in0_,
     pl[o] = v.hi;
     pl[NN + o] = v.lo;
   };
+  const bool fast = total < kFastDivItems;
   for (int64_t t = t0; t < total; t += tstep) {
     int c, p, q;
-    if (AX == 0) {
+    if (fast) {  // 32-bit decoding by the launch's reciprocals
+      const uint32_t u = (uint32_t)t;
+      if (AX == 0) {
+        const uint32_t r = dnp1.div(u);
+        c = (int)(u - r * dnp1.d);
+        q = (int)dN1.div(r);
+        p = (int)(r - (uint32_t)q * dN1.d);
+      } else {
+        const uint32_t r = dN1.div(u);
+        p = (int)(u - r * dN1.d);
+        q = (int)dnp1.div(r);
+        c = (int)(r - (uint32_t)q * dnp1.d);
+      }
+    } else if (AX == 0) {
       c = (int)(t % (n + 1));
       const int64_t r = t / (n + 1);
       p = (int)(r % N1);
@@ -380,8 +556,9 @@ __device__ __forceinline__ void cart_pass_ff_body(const void* __restrict__ in0_,
 template <int DIM, int AX, int MODE, bool RESID>
 __global__ void __launch_bounds__(256) cart_pass_ff(const void* __restrict__ in0, const float* __restrict__ in1,
                                                     void* __restrict__ out0, float* __restrict__ out1,
-                                                    const double* __restrict__ bvec, int n, ff s) {
-  cart_pass_ff_body<DIM, AX, MODE, RESID>(in0, in1, out0, out1, bvec, n, s,
+                                                    const double* __restrict__ bvec, int n, ff s, FastDiv dnp1,
+                                                    FastDiv dN1) {
+  cart_pass_ff_body<DIM, AX, MODE, RESID>(in0, in1, out0, out1, bvec, n, s, dnp1, dN1,
                                           (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                           (int64_t)gridDim.x * blockDim.x);
 }
@@ -394,6 +571,7 @@ struct CartPassFFJob {
   const double* bvec;
   int n;
   ff s;
+  FastDiv dnp1, dN1;
 };
 
 template <int DIM, int AX, int MODE, bool RESID>
@@ -402,8 +580,8 @@ __global__ void __launch_bounds__(256) cart_pass_ff_group(const __grid_constant_
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = group_find(G, t);
     const CartPassFFJob& a = G.job[j];
-    cart_pass_ff_body<DIM, AX, MODE, RESID>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, t - G.start[j],
-                                            kOneItem);
+    cart_pass_ff_body<DIM, AX, MODE, RESID>(a.in0, a.in1, a.out0, a.out1, a.bvec, a.n, a.s, a.dnp1, a.dN1,
+                                            t - G.start[j], kOneItem);
   }
 }
 
@@ -1087,12 +1265,29 @@ __global__ void PMG_PATCH_BOUNDS patch_cart_group_kernel(int np, int n_iter, con
 // two vertices whose patch holds the node lies in 1..n-1.  Fixed order:
 // colours 0..2^d-1.  Boundary nodes get no contribution.
 template <int DIM, bool ADD, typename T>
-__device__ __forceinline__ void patch_gather_body(const T* __restrict__ dst, T* __restrict__ u, int n, int64_t t0,
-                                                  int64_t tstep) {
+__device__ __forceinline__ void patch_gather_body(const T* __restrict__ dst, T* __restrict__ u, int n, FastDiv dN1,
+                                                  int64_t t0, int64_t tstep) {
   const int N1 = K * n + 1, nv = n - 1;
   const int64_t N = DIM == 3 ? (int64_t)N1 * N1 * N1 : (int64_t)N1 * N1;
+  const bool fast = N < kFastDivItems;
   for (int64_t t = t0; t < N; t += tstep) {
-    const int gd[3] = {(int)(t % N1), (int)((t / N1) % N1), DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0};
+    int gd[3];
+    if (fast) {
+      const uint32_t v = (uint32_t)t, r = dN1.div(v);
+      gd[0] = (int)(v - r * dN1.d);
+      if (DIM == 3) {
+        const uint32_t z = dN1.div(r);
+        gd[1] = (int)(r - z * dN1.d);
+        gd[2] = (int)z;
+      } else {
+        gd[1] = (int)r;
+        gd[2] = 0;
+      }
+    } else {
+      gd[0] = (int)(t % N1);
+      gd[1] = (int)((t / N1) % N1);
+      gd[2] = DIM == 3 ? (int)(t / ((int64_t)N1 * N1)) : 0;
+    }
     // per direction and parity: is there a vertex of that parity holding the node?
     unsigned has[3] = {0u, 0u, 0u};
 #pragma unroll
@@ -1114,8 +1309,9 @@ __device__ __forceinline__ void patch_gather_body(const T* __restrict__ dst, T* 
 }
 
 template <int DIM, bool ADD, typename T>
-__global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ dst, T* __restrict__ u, int n) {
-  patch_gather_body<DIM, ADD, T>(dst, u, n, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+__global__ void __launch_bounds__(256) patch_gather_kernel(const T* __restrict__ dst, T* __restrict__ u, int n,
+                                                           FastDiv dN1) {
+  patch_gather_body<DIM, ADD, T>(dst, u, n, dN1, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                  (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -1124,6 +1320,7 @@ struct GatherJob {
   const T* dst;
   T* u;
   int n;
+  FastDiv dN1;
 };
 
 template <int DIM, bool ADD, typename T>
@@ -1131,7 +1328,7 @@ __global__ void __launch_bounds__(256) patch_gather_group(const __grid_constant_
   const int64_t total = G.start[G.count];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = group_find(G, t);
-    patch_gather_body<DIM, ADD, T>(G.job[j].dst, G.job[j].u, G.job[j].n, t - G.start[j], kOneItem);
+    patch_gather_body<DIM, ADD, T>(G.job[j].dst, G.job[j].u, G.job[j].n, G.job[j].dN1, t - G.start[j], kOneItem);
   }
 }
 
@@ -1144,17 +1341,26 @@ __global__ void __launch_bounds__(256) patch_gather_group(const __grid_constant_
 // of the remaining axes).  ADD: out += result.
 template <int AX, bool ADD, typename T>
 __device__ __forceinline__ void hprolong_body(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey,
-                                              int ez, int64_t t0, int64_t tstep) {
+                                              int ez, FastDiv dex, FastDiv dey, int64_t t0, int64_t tstep) {
   // ex, ey, ez: extents of the OUTPUT array
   const int nf = 2 * nc;
   const int nc1 = K * nc + 1;
   const int64_t total = (int64_t)ex * ey * ez;
   const T* Pt = coef<T>() + LAY.Pt;
+  const bool fast = total < kFastDivItems;
   for (int64_t t = t0; t < total; t += tstep) {
-    const int x = (int)(t % ex);
-    const int64_t rr = t / ex;
-    const int y = (int)(rr % ey);
-    const int z = (int)(rr / ey);
+    int x, y, z;
+    if (fast) {
+      const uint32_t u = (uint32_t)t, rr = dex.div(u), zz = dey.div(rr);
+      x = (int)(u - rr * dex.d);
+      y = (int)(rr - zz * dey.d);
+      z = (int)zz;
+    } else {
+      x = (int)(t % ex);
+      const int64_t rr = t / ex;
+      y = (int)(rr % ey);
+      z = (int)(rr / ey);
+    }
     const int gf = AX == 0 ? x : (AX == 1 ? y : z);
     const int cf = min(gf / K, nf - 1);
     const int a = gf - K * cf;
@@ -1178,16 +1384,25 @@ __device__ __forceinline__ void hprolong_body(const T* __restrict__ in, T* __res
 // boundary nodes of AX are zero (restriction acts on free DoFs).
 template <int AX, typename T>
 __device__ __forceinline__ void hrestrict_body(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey,
-                                               int ez, int64_t t0, int64_t tstep) {
+                                               int ez, FastDiv dex, FastDiv dey, int64_t t0, int64_t tstep) {
   const int nc1 = K * nc + 1;
   const int nf1 = 2 * K * nc + 1;
   const int64_t total = (int64_t)ex * ey * ez;
   const T* Pt = coef<T>() + LAY.Pt;
+  const bool fast = total < kFastDivItems;
   for (int64_t t = t0; t < total; t += tstep) {
-    const int x = (int)(t % ex);
-    const int64_t rr = t / ex;
-    const int y = (int)(rr % ey);
-    const int z = (int)(rr / ey);
+    int x, y, z;
+    if (fast) {
+      const uint32_t u = (uint32_t)t, rr = dex.div(u), zz = dey.div(rr);
+      x = (int)(u - rr * dex.d);
+      y = (int)(rr - zz * dey.d);
+      z = (int)zz;
+    } else {
+      x = (int)(t % ex);
+      const int64_t rr = t / ex;
+      y = (int)(rr % ey);
+      z = (int)(rr / ey);
+    }
     const int gc = AX == 0 ? x : (AX == 1 ? y : z);
     if (gc == 0 || gc == nc1 - 1) { out[t] = T(0); continue; }
     const int ix = AX == 0 ? nf1 : ex, iy = AX == 1 ? nf1 : ey;
@@ -1224,14 +1439,18 @@ __device__ __forceinline__ void hrestrict_body(const T* __restrict__ in, T* __re
 }
 
 template <int AX, bool ADD, typename T>
-__global__ void hprolong_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
-  hprolong_body<AX, ADD, T>(in, out, nc, ex, ey, ez, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+__global__ void hprolong_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez,
+                              FastDiv dex, FastDiv dey) {
+  hprolong_body<AX, ADD, T>(in, out, nc, ex, ey, ez, dex, dey,
+                            (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                             (int64_t)gridDim.x * blockDim.x);
 }
 
 template <int AX, typename T>
-__global__ void hrestrict_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez) {
-  hrestrict_body<AX, T>(in, out, nc, ex, ey, ez, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+__global__ void hrestrict_pass(const T* __restrict__ in, T* __restrict__ out, int nc, int ex, int ey, int ez,
+                               FastDiv dex, FastDiv dey) {
+  hrestrict_body<AX, T>(in, out, nc, ex, ey, ez, dex, dey,
+                        (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                         (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -1241,6 +1460,7 @@ struct TransferJob {
   const T* in;
   T* out;
   int nc, ex, ey, ez;
+  FastDiv dex, dey;
 };
 
 template <int AX, bool ADD, typename T>
@@ -1249,7 +1469,7 @@ __global__ void hprolong_group(const __grid_constant__ GroupOf<TransferJob<T>> G
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = group_find(G, t);
     const TransferJob<T>& a = G.job[j];
-    hprolong_body<AX, ADD, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t - G.start[j], kOneItem);
+    hprolong_body<AX, ADD, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, a.dex, a.dey, t - G.start[j], kOneItem);
   }
 }
 
@@ -1259,7 +1479,7 @@ __global__ void hrestrict_group(const __grid_constant__ GroupOf<TransferJob<T>> 
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = group_find(G, t);
     const TransferJob<T>& a = G.job[j];
-    hrestrict_body<AX, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, t - G.start[j], kOneItem);
+    hrestrict_body<AX, T>(a.in, a.out, a.nc, a.ex, a.ey, a.ez, a.dex, a.dey, t - G.start[j], kOneItem);
   }
 }
 

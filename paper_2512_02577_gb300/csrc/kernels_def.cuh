@@ -332,7 +332,9 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __r
   // ---- every global load of the cell first (one memory latency per cell):
   // the nodal x-line, the value each output node starts from (y of an
   // earlier colour, b, or nothing), and G_q at this lane's points of the
-  // z-line ownership used by the q-op
+  // z-line ownership used by the q-op.  G_q is read once per apply and is
+  // most of its bytes: streaming loads (evict first) keep it from pushing x
+  // and y, which the colour launches revisit, out of L2.
   V u[n1];
   IO prior[n1];
   bool first[n1], bnd[n1];
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __r
 #pragma unroll
   for (int q = 0; q < n1; ++q)
 #pragma unroll
-    for (int m = 0; m < 6; ++m) gq[m][q] = live ? Gc[m * NP + n1 * n1 * q] : 0.f;
+    for (int m = 0; m < 6; ++m) gq[m][q] = live ? __ldcs(Gc + m * NP + n1 * n1 * q) : 0.f;
 
   // ---- X-own (lane (y = la, z = lb)): P = S_x u, Pd = DS_x u
   V P[n1], Pd[n1];

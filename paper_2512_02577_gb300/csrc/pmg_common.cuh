@@ -91,6 +91,33 @@ constexpr int kMaxCoef = 2048;   // >= coef_layout(8).total
 // per-block opt-in of sm_103a minus room for the kernels' static arrays.
 constexpr int kMaxDynSmem = 220 * 1024;
 
+// Unsigned 32-bit division by a divisor fixed for a launch, by multiplying
+// with a precomputed reciprocal (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, unsigned case):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, then for any 32-bit n
+// t = mulhi(m, n) and n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+// The grid-stride line kernels decode their item index with it instead of
+// 64-bit division (tens of instructions per divide).  1 <= d < 2^31.
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+  __host__ __device__ FastDiv() : d(1), m(1), s1(0), s2(0) {}
+  __host__ explicit FastDiv(uint32_t d_) : d(d_) {
+    uint32_t l = 0;
+    while (l < 31 && (uint64_t(1) << l) < d) ++l;
+    m = (uint32_t)((((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d) + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+#ifdef __CUDACC__
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+#endif
+};
+// work items of a grid-stride loop that the 32-bit decoding covers
+constexpr int64_t kFastDivItems = int64_t(1) << 32;
+
 // Argument table of a grouped launch: one kernel launch does the work of up
 // to kMaxGroup jobs (the same operation on the vectors of different systems,
 // possibly of different sizes), passed by value as a __grid_constant__
