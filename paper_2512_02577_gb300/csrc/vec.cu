@@ -310,21 +310,39 @@ cudaError_t coarse_solve(int prec, const void* Ainv, const int* idx, int nc, con
 // the jobs over the grid (GroupOf::start).
 static bool group_ok(int count) { return count >= 1 && count <= kMaxGroup; }
 
-// Blocks along x take the job's kDotBlocks reduction blocks in turn (vb):
-// the partial of vb is formed exactly as by block vb of dot_partial_kernel
-// (same elements per thread, same order, same block tree), so a grouped
-// launch needs fewer than kDotBlocks blocks per job for small vectors.
-static int group_dot_blocks(int count) { return std::max(1, std::min(kDotBlocks, 4 * 152 / count)); }
+// A warp forms the partial of one of the job's kDotBlocks reduction blocks
+// (vb): lane l sums the elements of each of the block's 256 threads wl * 32 +
+// l (wl = 0..7) exactly as that thread of dot_partial_kernel does, each of
+// the eight warp sums is formed by the same shuffle tree, and the eight are
+// combined as block_store_sum combines its warps -- the same partial, bitwise,
+// without shared memory or block barriers (kDotBlocks / 8 blocks per job).
+constexpr int kGroupDotBlocks = kDotBlocks / 8;
+static_assert(kDotBlocks % 8 == 0, "a block of the grouped reductions covers 8 reduction blocks");
+
+__device__ __forceinline__ double combine_warp_sums(const double (&s)[8]) {
+  // s[wl]: this lane's share of warp wl's sum; lane 0 of warp_sum holds each total
+  double t = 0.0;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int wl = 0; wl < 8; ++wl) {
+    const double v = __shfl_sync(0xffffffffu, warp_sum(s[wl]), 0);
+    if (lane == wl) t = v;
+  }
+  return warp_sum(t);  // lanes >= 8 hold 0, as in block_store_sum
+}
 
 __global__ void __launch_bounds__(256) dot_partial_group(const __grid_constant__ GroupOf<DotJob> G) {
   const DotJob& a = G.job[blockIdx.y];
-  for (int vb = blockIdx.x; vb < kDotBlocks; vb += gridDim.x) {
-    double s = 0.0;
-    for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)kDotBlocks * blockDim.x)
-      s += a.x[i] * a.y[i];
-    block_store_sum(s, a.partial + vb);
-    __syncthreads();  // the block's reduction scratch is reused by the next vb
+  const int vb = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  double s[8];
+#pragma unroll
+  for (int wl = 0; wl < 8; ++wl) {
+    s[wl] = 0.0;
+    for (int64_t i = (int64_t)vb * 256 + wl * 32 + lane; i < a.n; i += (int64_t)kDotBlocks * 256)
+      s[wl] += a.x[i] * a.y[i];
   }
+  const double t = combine_warp_sums(s);
+  if (lane == 0) a.partial[vb] = t;
 }
 
 __global__ void __launch_bounds__(256) sum_partials_group(const __grid_constant__ GroupOf<DotJob> G) {
@@ -339,7 +357,7 @@ cudaError_t dot_group(int count, const DotJob* jobs, cudaStream_t st) {
   GroupOf<DotJob> G;
   G.count = count;
   for (int j = 0; j < count; ++j) G.job[j] = jobs[j];
-  dot_partial_group<<<dim3(group_dot_blocks(count), count), 256, 0, st>>>(G);
+  dot_partial_group<<<dim3(kGroupDotBlocks, count), 256, 0, st>>>(G);
   sum_partials_group<<<count, 256, 0, st>>>(G);
   g_launches += 2;
   return cudaGetLastError();
@@ -348,17 +366,20 @@ cudaError_t dot_group(int count, const DotJob* jobs, cudaStream_t st) {
 __global__ void __launch_bounds__(256) cg_xr_group(const __grid_constant__ GroupOf<CgXrJob> G) {
   const CgXrJob& a = G.job[blockIdx.y];
   const double alpha = a.s[a.num] / a.s[a.den];
-  for (int vb = blockIdx.x; vb < kDotBlocks; vb += gridDim.x) {  // as dot_partial_group
-    double acc = 0.0;
-    for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)kDotBlocks * blockDim.x) {
+  const int vb = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  double s[8];  // as dot_partial_group, for cg_xr_kernel's updates and sums
+#pragma unroll
+  for (int wl = 0; wl < 8; ++wl) {
+    s[wl] = 0.0;
+    for (int64_t i = (int64_t)vb * 256 + wl * 32 + lane; i < a.n; i += (int64_t)kDotBlocks * 256) {
       a.x[i] += alpha * a.p[i];
       const double ri = a.r[i] - alpha * a.Ap[i];
       a.r[i] = ri;
-      acc += ri * ri;
+      s[wl] += ri * ri;
     }
-    block_store_sum(acc, a.partial + vb);
-    __syncthreads();
   }
+  const double t = combine_warp_sums(s);
+  if (lane == 0) a.partial[vb] = t;
 }
 
 __global__ void __launch_bounds__(256) cg_xr_sum_group(const __grid_constant__ GroupOf<CgXrJob> G) {
@@ -373,7 +394,7 @@ cudaError_t cg_update_xr_group(int count, const CgXrJob* jobs, cudaStream_t st) 
   GroupOf<CgXrJob> G;
   G.count = count;
   for (int j = 0; j < count; ++j) G.job[j] = jobs[j];
-  cg_xr_group<<<dim3(group_dot_blocks(count), count), 256, 0, st>>>(G);
+  cg_xr_group<<<dim3(kGroupDotBlocks, count), 256, 0, st>>>(G);
   cg_xr_sum_group<<<count, 256, 0, st>>>(G);
   g_launches += 2;
   return cudaGetLastError();
