@@ -177,3 +177,32 @@ def test_server_grouping_same_alone_and_in_the_mix():
         assert a["iterations"] == b["iterations"]
         assert torch.equal(a["x"], b["x"])
     assert grouped_launches < plain_launches
+
+
+def test_solve_group_limits():
+    ctxs = [_ctx(3, 1, 2) for _ in range(33)]
+    bs = [_rhs(3, 1, 2, i) for i in range(33)]
+    with pytest.raises(p.PmgError) as e:
+        p.solve_group(ctxs, bs, [b.clone() for b in bs])
+    assert e.value.code == p.PMG_ERR_ARG
+    infos = p.solve_group(ctxs[:32], bs[:32], [torch.zeros_like(b) for b in bs[:32]])
+    assert all(i.status == 0 for i in infos)
+
+
+def test_server_closed_while_groups_run():
+    # closing the server cancels the rounds in flight; the device stays usable
+    from paper_2512_02577_gb300.inputs import serving_requests
+    srv = p.Server(0, 8, group_work=1e18, max_group=8)
+    keep = []
+    for r in serving_requests(n_requests=8, rate=1e6, arrival_seed=1, size_seed=2, n_lo=8, n_hi=16, k_lo=3, k_hi=3):
+        cfg = p.make_config(dim=3, n_cells=r["n"], degree=r["k"], mg_precision=p.FP32)
+        b = serve._rhs(3, r["n"], r["k"], r["rhs_seed"])
+        x = torch.zeros_like(b).pin_memory()
+        keep.append((cfg, b, x, srv.submit(cfg, b, x)))
+    for _ in range(3):
+        srv.poll()
+    srv.close()
+    ctx = _ctx(3, 8, 3, mg_precision=p.FP32)
+    b = _rhs(3, 8, 3, 9)
+    x = torch.zeros_like(b)
+    assert ctx.solve(b, x).status == 0
