@@ -487,3 +487,27 @@ def test_full_size_k8_apply_samples():
     y32 = torch.empty(m.n_dofs, dtype=torch.float32, device=DEV)
     ctx.apply(to_dev(x, torch.float32), y32, prec=p.FP32)
     assert np.abs(y32.cpu().double().numpy()[rows] - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,k", [(23, 3), (13, 5), (9, 8)])
+def test_fp32_apply_across_tiles_and_ragged_tail(n, k):
+    # The FP32 3D apply forms its x and y passes on tiles of 32 / k cells per
+    # side of one z plane: these meshes span several tiles with a partial last
+    # one.  Rows on the tile seams (every 32 / k cells), on the last partial
+    # tile and random rows, against the oracle's element matrices.
+    d = 3
+    ctx = make_ctx(d, n, k, prec=p.FP32)
+    m = fem.Mesh(d, n, k)
+    N = m.n_dofs
+    x = random_vector(d, n, k, seed=91)
+    y = torch.empty(N, dtype=torch.float32, device=DEV)
+    ctx.apply(to_dev(x, torch.float32), y, prec=p.FP32)
+    n1, cx = m.n1, max(1, 32 // k)
+    seams = sorted({min(n1 - 1, max(0, k * c + a)) for c in range(0, n + 1, cx) for a in (-1, 0, 1)} | {n1 - 2, n1 - 1})
+    rng = np.random.default_rng(92)
+    rows = [int(xx + n1 * (yy + n1 * zz)) for xx in seams for yy in seams for zz in rng.choice(n1, 2)]
+    rows += list(rng.integers(0, N, 200))
+    ref = _sampled_apply_rows(m, x.astype(np.float32).astype(np.float64), rows)
+    got = y.cpu().numpy().astype(np.float64)[rows]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 2e-5 * scale
