@@ -192,7 +192,17 @@ def cpu_baseline_entry(res):
 
 
 # ----------------------------------------------------------------- extra sections
-HBM_GBS = 6794.8  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+def _measured_hbm_gbs():
+    """The machine's measured copy bandwidth (generated MEASURED_PEAKS.json
+    beside this file), else the profiling recipe's fallback of 6.8 TB/s."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+HBM_GBS, HBM_PEAK_KIND = _measured_hbm_gbs()
 
 
 def _timed_ms(torch, stream, flush, fn, reps=5):
@@ -240,6 +250,7 @@ def extra_sections(p, torch, dev, stream, flush):
         "rel_residual": solves[-1].rel_residual, "l2_error": err,
         "apply_fp32_ms": t_apply32, "apply_fp64_ms": t_apply64,
         "apply_fp32_roofline": {"bound": "hbm", "achieved": alg_bytes / (t_apply32 * 1e-3) / 1e9, "peak": HBM_GBS,
+                                "peak_kind": HBM_PEAK_KIND,
                                 "unit": "GB/s", "frac": alg_bytes / (t_apply32 * 1e-3) / 1e9 / HBM_GBS,
                                 "algorithmic_bytes": alg_bytes},
         "smoother_phases_ms": {"residual": phases[0], "patch": phases[1], "gather": phases[2]},
