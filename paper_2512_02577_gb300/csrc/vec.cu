@@ -336,10 +336,15 @@ __global__ void __launch_bounds__(256) dot_partial_group(const __grid_constant__
   const int vb = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   double s[8];
 #pragma unroll
-  for (int wl = 0; wl < 8; ++wl) {
-    s[wl] = 0.0;
-    for (int64_t i = (int64_t)vb * 256 + wl * 32 + lane; i < a.n; i += (int64_t)kDotBlocks * 256)
-      s[wl] += a.x[i] * a.y[i];
+  for (int wl = 0; wl < 8; ++wl) s[wl] = 0.0;
+  // the eight threads' k-th elements together (independent loads), each
+  // thread's elements in its own order
+  for (int64_t base = (int64_t)vb * 256 + lane; base < a.n; base += (int64_t)kDotBlocks * 256) {
+#pragma unroll
+    for (int wl = 0; wl < 8; ++wl) {
+      const int64_t i = base + wl * 32;
+      if (i < a.n) s[wl] += a.x[i] * a.y[i];
+    }
   }
   const double t = combine_warp_sums(s);
   if (lane == 0) a.partial[vb] = t;
@@ -369,13 +374,17 @@ __global__ void __launch_bounds__(256) cg_xr_group(const __grid_constant__ Group
   const int vb = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   double s[8];  // as dot_partial_group, for cg_xr_kernel's updates and sums
 #pragma unroll
-  for (int wl = 0; wl < 8; ++wl) {
-    s[wl] = 0.0;
-    for (int64_t i = (int64_t)vb * 256 + wl * 32 + lane; i < a.n; i += (int64_t)kDotBlocks * 256) {
-      a.x[i] += alpha * a.p[i];
-      const double ri = a.r[i] - alpha * a.Ap[i];
-      a.r[i] = ri;
-      s[wl] += ri * ri;
+  for (int wl = 0; wl < 8; ++wl) s[wl] = 0.0;
+  for (int64_t base = (int64_t)vb * 256 + lane; base < a.n; base += (int64_t)kDotBlocks * 256) {
+#pragma unroll
+    for (int wl = 0; wl < 8; ++wl) {
+      const int64_t i = base + wl * 32;
+      if (i < a.n) {
+        a.x[i] += alpha * a.p[i];
+        const double ri = a.r[i] - alpha * a.Ap[i];
+        a.r[i] = ri;
+        s[wl] += ri * ri;
+      }
     }
   }
   const double t = combine_warp_sums(s);
