@@ -276,19 +276,20 @@ struct DefFast {
   static constexpr int CELLS = 16;                              // largest cells (half-warps) per block
 };
 
-template <bool RESID, class A>
-__global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __restrict__ x,
-                                                       typename A::IO* __restrict__ y,
-                                                       const typename A::IO* __restrict__ b,
-                                                       const float* __restrict__ G, int n, int colour) {
+// The cell operator of the half-warp kernel for one cell: lane (la, lb) holds
+// the nodal x-line u (y = la, z = lb) and G_q at its z-line points (x = la,
+// y = lb, z = q); res receives A_cell u on the lane's x-line.  tl: the
+// half-warp's three transposition tiles (F::CELL floats); every lane of the
+// warp calls it (lanes with on = false hold zeros and store nothing).
+template <class A>
+__device__ __forceinline__ void def_fast_core(const typename A::V (&u)[K + 1], const float (&gq)[6][K + 1], float* tl,
+                                              bool on, int la, int lb, typename A::V (&res)[K + 1]) {
   using F = DefFast<A>;
   using V = typename A::V;
   using Acc = typename A::Acc;
-  using IO = typename A::IO;
-  constexpr int n1 = F::n1, NP = n1 * n1 * n1, L = nlev(K) - 1;
+  constexpr int n1 = F::n1, L = nlev(K) - 1;
   constexpr int PY = F::PY, PZ = F::PZ, TILE = F::TILE;
   constexpr int OS = LAY.S[L], OD = LAY.Dq[L];
-  __shared__ float tiles[F::CELLS * F::CELL];
   const double* C = ctab<double>();
   auto S = [&](int q, int a) -> double { return C[OS + q * n1 + a]; };
   auto DS = [&](int q, int a) -> double {  // derivative of nodal basis a at point q
@@ -297,73 +298,12 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __r
     for (int j = 0; j < n1; ++j) s += C[OD + q * n1 + j] * C[OS + j * n1 + a];
     return s;
   };
-  const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
-  const bool on = lane < n1 * n1;
-  const int la = on ? lane % n1 : 0, lb = on ? lane / n1 : 0;
-  float* tl = tiles + hw * F::CELL;
-  // this half-warp's cell among those of parity colour `colour`
-  int bit[3], cnt[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    bit[d] = (colour >> d) & 1;
-    cnt[d] = (n - bit[d] + 1) / 2;
-  }
-  const int64_t ncol = (int64_t)cnt[0] * cnt[1] * cnt[2];
-  const int64_t cid = (int64_t)blockIdx.x * (blockDim.x >> 4) + hw;
-  const bool live = on && cid < ncol;
-  int c[3];
-  {
-    int64_t t = live ? cid : 0;
-    c[0] = bit[0] + 2 * (int)(t % cnt[0]);
-    t /= cnt[0];
-    c[1] = bit[1] + 2 * (int)(t % cnt[1]);
-    c[2] = bit[2] + 2 * (int)(t / cnt[1]);
-  }
-  const int N1 = K * n + 1;
-  // transposes through tile k: element (ix, iy, iz) at ix + PY iy + PZ iz
-  // (a float-float value's low part one tile-set further)
   auto put = [&](int k, int ix, int iy, int iz, V v) {
     if (on) A::put(tl + k * TILE + ix + PY * iy + PZ * iz, 3 * TILE, v);
   };
   auto get = [&](int k, int ix, int iy, int iz) -> V {
     return on ? A::get(tl + k * TILE + ix + PY * iy + PZ * iz, 3 * TILE) : A::zero();
   };
-
-  // ---- every global load of the cell first (one memory latency per cell):
-  // the nodal x-line, the value each output node starts from (y of an
-  // earlier colour, b, or nothing), and G_q at this lane's points of the
-  // z-line ownership used by the q-op.  G_q is read once per apply and is
-  // most of its bytes: streaming loads (evict first) keep it from pushing x
-  // and y, which the colour launches revisit, out of L2.
-  V u[n1];
-  IO prior[n1];
-  bool first[n1], bnd[n1];
-  const int gy = K * c[1] + la, gz = K * c[2] + lb;
-  const bool yz_bnd = gy == 0 || gy == N1 - 1 || gz == 0 || gz == N1 - 1;
-  const int64_t row = (int64_t)N1 * (gy + (int64_t)N1 * gz) + K * c[0];
-#pragma unroll
-  for (int i = 0; i < n1; ++i) {
-    const int gx = K * c[0] + i;
-    bnd[i] = yz_bnd || gx == 0 || gx == N1 - 1;
-    const int li[3] = {i, la, lb};
-    bool f = true;  // lowest colour among the cells holding this node
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const bool shared = (li[d] == 0 && c[d] > 0) || (li[d] == K && c[d] < n - 1);
-      if (shared && (c[d] & 1)) f = false;
-    }
-    first[i] = f;
-    u[i] = (live && !bnd[i]) ? A::in(x[row + i]) : A::zero();
-    prior[i] = (live && !bnd[i]) ? (f ? (RESID ? b[row + i] : IO(0)) : y[row + i]) : IO(0);
-  }
-  const int64_t cell = c[0] + (int64_t)n * (c[1] + (int64_t)n * c[2]);
-  const float* Gc = G + cell * 6 * NP + la + n1 * lb;
-  float gq[6][n1];
-#pragma unroll
-  for (int q = 0; q < n1; ++q)
-#pragma unroll
-    for (int m = 0; m < 6; ++m) gq[m][q] = live ? __ldcs(Gc + m * NP + n1 * n1 * q) : 0.f;
-
   // ---- X-own (lane (y = la, z = lb)): P = S_x u, Pd = DS_x u
   V P[n1], Pd[n1];
 #pragma unroll
@@ -446,14 +386,91 @@ __global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __r
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < n1; ++q) { P[q] = get(0, q, la, lb); Pd[q] = get(1, q, la, lb); }
-  // out = DS_x^T B1 + S_x^T B23, added into y node by node
+  // out = DS_x^T B1 + S_x^T B23
 #pragma unroll
   for (int i = 0; i < n1; ++i) {
     Acc s{};
 #pragma unroll
     for (int q = 0; q < n1; ++q) { A::mac(s, DS(q, i), P[q]); A::mac(s, S(q, i), Pd[q]); }
+    res[i] = A::val(s);
+  }
+}
+
+template <bool RESID, class A>
+__global__ void __launch_bounds__(256) def_fast_kernel(const typename A::IO* __restrict__ x,
+                                                       typename A::IO* __restrict__ y,
+                                                       const typename A::IO* __restrict__ b,
+                                                       const float* __restrict__ G, int n, int colour) {
+  using F = DefFast<A>;
+  using V = typename A::V;
+  using IO = typename A::IO;
+  constexpr int n1 = F::n1, NP = n1 * n1 * n1;
+  __shared__ float tiles[F::CELLS * F::CELL];
+  const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
+  const bool on = lane < n1 * n1;
+  const int la = on ? lane % n1 : 0, lb = on ? lane / n1 : 0;
+  float* tl = tiles + hw * F::CELL;
+  // this half-warp's cell among those of parity colour `colour`
+  int bit[3], cnt[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    bit[d] = (colour >> d) & 1;
+    cnt[d] = (n - bit[d] + 1) / 2;
+  }
+  const int64_t ncol = (int64_t)cnt[0] * cnt[1] * cnt[2];
+  const int64_t cid = (int64_t)blockIdx.x * (blockDim.x >> 4) + hw;
+  const bool live = on && cid < ncol;
+  int c[3];
+  {
+    int64_t t = live ? cid : 0;
+    c[0] = bit[0] + 2 * (int)(t % cnt[0]);
+    t /= cnt[0];
+    c[1] = bit[1] + 2 * (int)(t % cnt[1]);
+    c[2] = bit[2] + 2 * (int)(t / cnt[1]);
+  }
+  const int N1 = K * n + 1;
+  // ---- every global load of the cell first (one memory latency per cell):
+  // the nodal x-line, the value each output node starts from (y of an
+  // earlier colour, b, or nothing), and G_q at this lane's points of the
+  // z-line ownership used by the q-op.  G_q is read once per apply and is
+  // most of its bytes: streaming loads (evict first) keep it from pushing x
+  // and y, which the colour launches revisit, out of L2.
+  V u[n1];
+  IO prior[n1];
+  bool first[n1], bnd[n1];
+  const int gy = K * c[1] + la, gz = K * c[2] + lb;
+  const bool yz_bnd = gy == 0 || gy == N1 - 1 || gz == 0 || gz == N1 - 1;
+  const int64_t row = (int64_t)N1 * (gy + (int64_t)N1 * gz) + K * c[0];
+#pragma unroll
+  for (int i = 0; i < n1; ++i) {
+    const int gx = K * c[0] + i;
+    bnd[i] = yz_bnd || gx == 0 || gx == N1 - 1;
+    const int li[3] = {i, la, lb};
+    bool f = true;  // lowest colour among the cells holding this node
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const bool shared = (li[d] == 0 && c[d] > 0) || (li[d] == K && c[d] < n - 1);
+      if (shared && (c[d] & 1)) f = false;
+    }
+    first[i] = f;
+    u[i] = (live && !bnd[i]) ? A::in(x[row + i]) : A::zero();
+    prior[i] = (live && !bnd[i]) ? (f ? (RESID ? b[row + i] : IO(0)) : y[row + i]) : IO(0);
+  }
+  const int64_t cell = c[0] + (int64_t)n * (c[1] + (int64_t)n * c[2]);
+  const float* Gc = G + cell * 6 * NP + la + n1 * lb;
+  float gq[6][n1];
+#pragma unroll
+  for (int q = 0; q < n1; ++q)
+#pragma unroll
+    for (int m = 0; m < 6; ++m) gq[m][q] = live ? __ldcs(Gc + m * NP + n1 * n1 * q) : 0.f;
+
+  V res[n1];
+  def_fast_core<A>(u, gq, tl, on, la, lb, res);
+  // added into y node by node
+#pragma unroll
+  for (int i = 0; i < n1; ++i) {
     if (!live || (bnd[i] && !first[i])) continue;
-    const IO v = A::out(A::val(s));
+    const IO v = A::out(res[i]);
     y[row + i] = bnd[i] ? IO(0) : (RESID ? prior[i] - v : prior[i] + v);
   }
 }
@@ -679,8 +696,88 @@ struct DefGeo {
 
   static constexpr bool kFusedSmoothing = false;  // Jacobi steps as separate pointwise passes
 
+  // The top level of an FP32 patch (FP32 G_q, 3D, K = 2, 3) applies its
+  // operator cell by cell with the half-warp cell operator of the deformed
+  // apply (def_fast_core: line contractions in registers, shared memory only
+  // for the transpositions) instead of sum factorisation on the whole patch
+  // grid: the patch residual is r - sum over the patch's 8 cells of A_cell d
+  // (d extended by zero to the patch boundary), each cell's results summed
+  // into a node in a fixed cell order.
+  template <int l>
+  static constexpr bool cellwise() {
+    return DIM == 3 && K >= 2 && K <= 3 && l == nlev(K) - 1 && std::is_same<T, float>::value &&
+           std::is_same<TG, float>::value;
+  }
+
+  template <int l, class PB>
+  __device__ __forceinline__ void resid_cells(const PB& pb, int od, int orr, int oo) const {
+    using F = DefFast<AF32>;
+    constexpr int n1 = K + 1, NP = n1 * n1 * n1, m = mp(K), mf = 2 * K + 1;
+    constexpr int W = PatchShape<3>::ELEMS, CT = F::CELL;  // cell c's tiles at W + c CT
+    static_assert(8 * CT <= DefShape<3>::WORK, "the cells' tiles fit the work area of a patch");
+    // (patch, cell, lane) items: a half-warp per cell, the two half-warps of
+    // a warp on two cells of one patch
+    pfor<8 * 16>(pb, [&](int g, int it) {
+      float* sm = &pb.at(g)[0];
+      const int c = it >> 4, lane = it & 15;
+      const bool on = lane < n1 * n1;
+      const int la = on ? lane % n1 : 0, lb = on ? lane / n1 : 0;
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+      const bool live = on && meta[g].active;
+      float* tl = sm + W + c * CT;
+      // the cell's nodal x-line (y = la, z = lb): d on the patch interior, 0 on its boundary
+      float u[n1];
+      const int fy = K * cy + la, fz = K * cz + lb;
+      const bool yz_in = fy >= 1 && fy <= mf - 2 && fz >= 1 && fz <= mf - 2;
+#pragma unroll
+      for (int i = 0; i < n1; ++i) {
+        const int fx = K * cx + i;
+        u[i] = (live && yz_in && fx >= 1 && fx <= mf - 2) ? sm[od + (fx - 1) + m * ((fy - 1) + m * (fz - 1))] : 0.f;
+      }
+      const int* v = meta[g].v;
+      const int64_t cell =
+          live ? (v[0] - 1 + cx) + (int64_t)n * ((v[1] - 1 + cy) + (int64_t)n * (v[2] - 1 + cz)) : 0;
+      const float* Gc = reinterpret_cast<const float*>(lev.G[l]) + cell * 6 * NP + la + n1 * lb;
+      float gq[6][n1];
+#pragma unroll
+      for (int q = 0; q < n1; ++q)
+#pragma unroll
+        for (int mm = 0; mm < 6; ++mm) gq[mm][q] = live ? Gc[mm * NP + n1 * n1 * q] : 0.f;
+      float res[n1];
+      def_fast_core<AF32>(u, gq, tl, on, la, lb, res);
+      __syncwarp();  // the half-warp's last reads of its tiles are done
+      if (on) {
+#pragma unroll
+        for (int i = 0; i < n1; ++i) tl[i + n1 * (la + n1 * lb)] = res[i];
+      }
+    });
+    __syncthreads();
+    pfor<m * m * m>(pb, [&](int g, int i) {
+      auto sm = pb.at(g);
+      const int f[3] = {i % m + 1, (i / m) % m + 1, i / (m * m) + 1};
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        int ix[3];
+        bool in = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          ix[d] = f[d] - K * ((c >> d) & 1);
+          in = in && ix[d] >= 0 && ix[d] <= K;
+        }
+        if (in) acc += sm[W + c * CT + ix[0] + n1 * (ix[1] + n1 * ix[2])];
+      }
+      sm[oo + i] = sm[orr + i] - acc;
+    });
+    __syncthreads();
+  }
+
   template <int l, class PB>
   __device__ __forceinline__ void resid(const PB& pb, int od, int orr, int oo) const {
+    if constexpr (cellwise<l>()) {
+      resid_cells<l>(pb, od, orr, oo);
+      return;
+    }
     constexpr int p = plev(K, l);
     constexpr int m = mp(p), mf = 2 * p + 1, nq = p + 1, Q = 2 * nq;
     constexpr int NPc = ipow(nq, DIM);  // points per cell
