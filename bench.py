@@ -484,10 +484,11 @@ def degree_sweep():
 
 
 # ----------------------------------------------------------------- profiling
-def profile_region(region, n_def):
+def profile_region(region, n_def, k_prof=0):
     """One NVTX range named 'profile' after warm-up, for
     ncu --nvtx --nvtx-include "profile/": one mixed-precision solve of the
-    32^3 Q4 problem (with the FP64 or the float-float outer operator), one
+    32^3 Q4 problem (degree k_prof instead of 4 if given; with the FP64 or
+    the float-float outer operator), one
     FP32 apply and one FP32 sweep of the deformed Q3 problem on n_def^3 cells,
     one FP32 apply of the Cartesian Q3 problem on n_def^3 cells, or one
     grouped solve of 16 Q3 systems on 4^3, 8^3, 16^3 and 8^3 cells
@@ -499,7 +500,8 @@ def profile_region(region, n_def):
     with torch.cuda.stream(stream):
         if region in ("mixed_solve", "mixed_solve_ff"):
             apply = p.APPLY_FLOAT_FLOAT if region == "mixed_solve_ff" else p.APPLY_FP64
-            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32, outer_apply=apply),
+            k = k_prof or K
+            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=k, mg_precision=p.FP32, outer_apply=apply),
                             stream=stream, device=dev)
             b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
             ctx.rhs_manufactured(b)
@@ -589,6 +591,7 @@ def main():
     ap.add_argument("--oracle-case", default="sample", choices=["sample", "cfg1"])
     ap.add_argument("--profile-region", default=None, choices=["mixed_solve", "mixed_solve_ff", "deformed", "grouped", "cart_apply32"],
                     help="warm up, then run one NVTX-marked region 'profile' for ncu and exit")
+    ap.add_argument("--profile-k", type=int, default=0, help="degree of the mixed-solve profile case (0: 4)")
     ap.add_argument("--profile-n", type=int, default=48, help="cells per side of the deformed and Cartesian-apply profile cases")
     ap.add_argument("--no-extras", action="store_true", help="skip the deformed and serving sections")
     ap.add_argument("--sweep", action="store_true", help="degree sweep k = 1..8 at ~8M DoFs (separate JSON)")
@@ -597,7 +600,7 @@ def main():
         oracle_child(args.oracle_child, args.oracle_steps, args.oracle_case)
         return
     if args.profile_region:
-        profile_region(args.profile_region, args.profile_n)
+        profile_region(args.profile_region, args.profile_n, args.profile_k)
         return
     if args.sweep:
         degree_sweep()
