@@ -123,7 +123,12 @@ static int dinv_len(int dim) {
 }
 
 // shared memory of the block besides its patches: the inverse-diagonal tables
-static int patch_cart_extra_smem(int dim, int prec) { return dinv_len(dim) * (prec == 0 ? 8 : 4); }
+// when the block stages them (stage_dinv)
+static int patch_cart_extra_smem(int dim, int prec) {
+  const bool staged = dim == 3 ? (prec == 0 ? stage_dinv<3, double>() : stage_dinv<3, float>())
+                               : (prec == 0 ? stage_dinv<2, double>() : stage_dinv<2, float>());
+  return staged ? dinv_len(dim) * (prec == 0 ? 8 : 4) : 0;
+}
 
 // Grid of a persistent patch launch: every block the GPU can hold at once
 // (occupancy x SMs), at most one per batch.

@@ -625,6 +625,20 @@ struct PatchShape {
 
 constexpr int kMaxPatchesPerBlock = 64;
 
+// Inverse-diagonal tables of the Cartesian patch levels p > 1 (scale-free,
+// one table per level): a block stages them in shared memory when they are
+// small; the larger tables of k >= 6 (6-23 KB per block) are read through
+// L1 instead, which leaves that shared memory to further blocks on the SM
+// (at k = 7 a block of 5 patches otherwise takes 190 KB, one block per SM).
+template <int DIM>
+constexpr int patch_dinv_len() {
+  int len = 0;
+  for (int l = 1; l < nlev(K); ++l) len += ipow(mp(plev(K, l)), DIM);
+  return len;
+}
+template <int DIM, typename T>
+constexpr bool stage_dinv() { return patch_dinv_len<DIM>() * (int)sizeof(T) <= 4096; }
+
 template <int AX, int EX, int EY, int EZ>
 __device__ __forceinline__ int line_base(int L) {
   if constexpr (AX == 0) return L * EX;
@@ -1169,8 +1183,12 @@ __device__ __forceinline__ void patch_cart_persistent(const T* __restrict__ r, T
   __shared__ int64_t s_batch;
   const int stride = IL ? S::ELEMS + (n_iter > 1 ? 2 * S::SZT : 0) : S::template stride<T>(n_iter);
   T* smem = reinterpret_cast<T*>(smraw);
-  T* sdinv = smem + np * stride;  // inverse-diagonal tables of all p-levels
-  for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
+  const T* sdinv = dinv;  // inverse-diagonal tables of all p-levels
+  if constexpr (stage_dinv<DIM, T>()) {
+    T* st = smem + np * stride;
+    for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) st[i] = dinv[i];
+    sdinv = st;  // visible after the body's first barrier
+  }
   if (!counter) {
     patch_cart_body<DIM, T, IL>(r, dst, n, np, n_iter, sdinv, P, blockIdx.x, meta, smem);
     return;
@@ -1240,8 +1258,12 @@ __global__ void PMG_PATCH_BOUNDS patch_cart_group_kernel(int np, int n_iter, con
   __shared__ int64_t s_batch;
   const int stride = S::template stride<T>(n_iter);
   T* smem = reinterpret_cast<T*>(smraw);
-  T* sdinv = smem + np * stride;
-  for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) sdinv[i] = dinv[i];
+  const T* sdinv = dinv;
+  if constexpr (stage_dinv<DIM, T>()) {
+    T* st = smem + np * stride;
+    for (int i = threadIdx.x; i < dinv_len; i += blockDim.x) st[i] = dinv[i];
+    sdinv = st;
+  }
   int64_t b = blockIdx.x;
   for (;;) {
     if (counter) {
