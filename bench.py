@@ -30,6 +30,12 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "3D unit cube, 32^3 hexes, Q4 (2,146,689 DoFs), FP64: apply + patch sweep + PCG/GMG solve to 1e-8"
 METRIC = "DoFs/s of operator apply + patch smoother; solve time to 1e-8 residual, FP32-MG vs FP64; p50/p99"
 D, NCELL, K = 3, 32, 4
+# Coarsest level of the 32^3 hierarchies: the first mesh of the halving
+# sequence with at most 4,096 free DoFs (4^3 cells at k = 4: 3,375), solved
+# by the dense coarse inverse.  Coarsening further (to 2^3 and 1 cell) adds
+# two levels whose patch launches hold one or a few blocks -- a block's
+# latency each, about 0.2 ms in FP64 -- and no work worth the launch.
+COARSE_DOFS = 4096
 ORACLE_N = 4          # bounded CPU sample: same degree and dimension, 4^3 cells (4,913 DoFs)
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (measured 1.255 with a project FMA probe)
 FP32_PEAK_TFLOPS = 78.5  # measured FP32 FMA (128 lanes x 152 SMs x 2 x ~2.0 GHz)
@@ -410,7 +416,8 @@ def outer_solver_section(p, torch, dev, stream, flush):
                                       (p.MULTIPLICATIVE, 0, p.OUTER_CG, "mult_full_cg"),
                                       (p.MULTIPLICATIVE, 1, p.OUTER_GMRES, "mult_half_gmres")):
             ctx = p.Context(p.make_config(dim=3, n_cells=32, degree=4, mg_precision=prec, local_half=half,
-                                          outer_solver=outer, smoother=sm), stream=stream, device=dev)
+                                          outer_solver=outer, smoother=sm, coarse_dofs=COARSE_DOFS),
+                            stream=stream, device=dev)
             b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
             ctx.rhs_manufactured(b)
             x = torch.zeros_like(b)
@@ -501,7 +508,8 @@ def profile_region(region, n_def, k_prof=0):
         if region in ("mixed_solve", "mixed_solve_ff"):
             apply = p.APPLY_FLOAT_FLOAT if region == "mixed_solve_ff" else p.APPLY_FP64
             k = k_prof or K
-            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=k, mg_precision=p.FP32, outer_apply=apply),
+            ctx = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=k, mg_precision=p.FP32, outer_apply=apply,
+                                          coarse_dofs=COARSE_DOFS),
                             stream=stream, device=dev)
             b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=dev)
             ctx.rhs_manufactured(b)
@@ -647,8 +655,8 @@ def main():
                 "cores": 1, "host_cores": os.cpu_count(), "steps": len(r1["times"])}
 
     stream = torch.cuda.Stream(device=dev)
-    cfg = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP64)
-    cfg32 = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32)
+    cfg = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP64, coarse_dofs=COARSE_DOFS)
+    cfg32 = p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32, coarse_dofs=COARSE_DOFS)
     with torch.cuda.stream(stream):
         ctx = p.Context(cfg, stream=stream, device=dev)
         ctx32 = p.Context(cfg32, stream=stream, device=dev)
@@ -732,7 +740,8 @@ def main():
         solve32 = [i.time_ms for i in info32]
         # mixed precision with the float-float outer operator
         ctxff = p.Context(p.make_config(dim=D, n_cells=NCELL, degree=K, mg_precision=p.FP32,
-                                        outer_apply=p.APPLY_FLOAT_FLOAT), stream=stream, device=dev)
+                                        outer_apply=p.APPLY_FLOAT_FLOAT, coarse_dofs=COARSE_DOFS),
+                          stream=stream, device=dev)
         infoff = []
         for _ in range(2):
             ctxff.solve(b, xs)
@@ -796,7 +805,8 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "dofs": N, "l2_flush": "512 MB write between timed steps",
                    "parallelism": "replicas" if world > 1 else "single GPU", "smoother": "additive vertex patch",
-                   "local_solver": "full p-multigrid V-cycle", "levels": ctx.n_levels},
+                   "local_solver": "full p-multigrid V-cycle", "levels": ctx.n_levels,
+                   "coarsest": "%d^3 cells, dense inverse (coarse_dofs %d)" % (NCELL >> (ctx.n_levels - 1), COARSE_DOFS)},
         "gpu_launches": launches,
         "apply_dofs_per_s": N / (statistics.median(t_apply) * 1e-3),
         "sweep_dofs_per_s": N / (sweep_ms * 1e-3),

@@ -142,6 +142,10 @@ typedef struct pmg_config {
   int patch_persistent; /* Cartesian patch launches: 0 = autotuned, 1 = persistent grids (the blocks the GPU
                           holds at once take batches of patches from a counter; used on levels with more
                           than one wave of batches), -1 = one block per batch */
+  int coarse_dofs;      /* with n_levels = 0: 0 = coarsen while n is even; c > 0 (<= 4096) = stop at the
+                          first mesh whose free DoFs are <= c, which is then solved by the dense coarse
+                          solve (fewer, larger coarse levels: the smoother launches on meshes of a few
+                          patches are latency, not work) */
 } pmg_config;
 
 typedef struct pmg_solve_info {

@@ -64,7 +64,7 @@ class Config(ctypes.Structure):
         ("smoother", ctypes.c_int), ("vertex_disp", ctypes.c_void_p),
         ("patch_layout", ctypes.c_int), ("patch_threads", ctypes.c_int), ("outer_apply", ctypes.c_int),
         ("geom_precision", ctypes.c_int), ("apply_cells_per_block", ctypes.c_int),
-        ("patch_persistent", ctypes.c_int),
+        ("patch_persistent", ctypes.c_int), ("coarse_dofs", ctypes.c_int),
     ]
 
 
@@ -145,7 +145,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
                 mg_precision=FP64, omega_patch=0.0, omega_jacobi=None, local_cycles=1,
                 smooth_steps=1, patches_per_block=0, local_half=0, outer_solver=None, gmres_restart=30,
                 smoother=ADDITIVE, vertex_disp=None, patch_layout=PATCH_AUTO, patch_threads=0, outer_apply=APPLY_FP64,
-                geom_precision=FP32, apply_cells_per_block=0, patch_persistent=0):
+                geom_precision=FP32, apply_cells_per_block=0, patch_persistent=0, coarse_dofs=0):
     """A pmg_config; outer_solver defaults to GMRES for the half local
     V-cycle (local_half=1) and to CG otherwise."""
     lib = load_library()
@@ -166,6 +166,7 @@ def make_config(dim=3, n_cells=8, degree=2, n_levels=0, geometry=CARTESIAN, defo
     c.geom_precision = geom_precision
     c.apply_cells_per_block = apply_cells_per_block
     c.patch_persistent = patch_persistent
+    c.coarse_dofs = coarse_dofs
     if vertex_disp is not None:
         # ((n+1)^d, d) float64 displacements of the finest mesh's vertices;
         # the config keeps a reference so the array outlives it

@@ -165,6 +165,7 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   if (cfg->patches_per_block < 0 || cfg->patch_threads < 0 || cfg->apply_cells_per_block < 0)
     return fail(PMG_ERR_ARG, "patches_per_block, patch_threads, apply_cells_per_block >= 0");
   if (cfg->patch_persistent < -1 || cfg->patch_persistent > 1) return fail(PMG_ERR_ARG, "patch_persistent in {-1, 0, 1}");
+  if (cfg->coarse_dofs < 0 || cfg->coarse_dofs > kMaxCoarse) return fail(PMG_ERR_ARG, "coarse_dofs in 0..4096");
   if (cfg->local_half && cfg->outer_solver == PMG_OUTER_CG)
     return fail(PMG_ERR_UNSUPPORTED, "the half local V-cycle makes the preconditioner nonsymmetric: use GMRES");
   P.dim = cfg->dim;
@@ -176,9 +177,15 @@ int make_plan(const pmg_config* cfg, Plan& P) {
   P.nplev = nlev(P.K);
   // mesh levels: n_l = n_0 2^l
   int n = cfg->n_cells, L = cfg->n_levels;
+  auto free_dofs = [&](int m) { return ipow64(std::max<int64_t>((int64_t)P.K * m - 1, 0), P.dim); };
   if (L <= 0) {
+    // halve while n is even; with coarse_dofs > 0, stop at the first mesh
+    // whose free DoFs fit that dense coarse solve
     L = 1;
-    while (n % 2 == 0 && n / 2 >= 1) { n /= 2; ++L; }
+    while (n % 2 == 0 && n / 2 >= 1 && !(cfg->coarse_dofs > 0 && free_dofs(n) <= cfg->coarse_dofs)) {
+      n /= 2;
+      ++L;
+    }
   } else {
     for (int i = 1; i < L; ++i) {
       if (n % 2) return fail(PMG_ERR_UNSUPPORTED, "n_cells must be divisible by 2^(n_levels-1)");
@@ -1143,6 +1150,7 @@ void pmg_config_default(pmg_config* cfg) {
   cfg->geom_precision = PMG_FP32;
   cfg->apply_cells_per_block = 0;
   cfg->patch_persistent = 0;
+  cfg->coarse_dofs = 0;
 }
 
 int pmg_bytes_required(const pmg_config* cfg, int64_t* bytes) {

@@ -53,7 +53,8 @@ int fail(int code, const std::string& msg) {
 struct Key {
   int dim = 0, n_cells = 0, degree = 0, mg_precision = 0, geometry = 0, n_levels = 0, local_cycles = 0,
       smooth_steps = 0, local_half = 0, outer_solver = 0, gmres_restart = 0, smoother = 0, patches_per_block = 0,
-      patch_layout = 0, patch_threads = 0, outer_apply = 0, geom_precision = 0, apply_cpb = 0, persistent = 0;
+      patch_layout = 0, patch_threads = 0, outer_apply = 0, geom_precision = 0, apply_cpb = 0, persistent = 0,
+      coarse_dofs = 0;
   double deform_amp = 0, omega_patch = 0, omega_jacobi[4] = {0, 0, 0, 0};
   uint64_t disp_hash = 0;
   const std::vector<double>* disp = nullptr;  // the request's own copy (distorted only)
@@ -61,11 +62,11 @@ struct Key {
   bool operator==(const Key& o) const {
     if (std::tie(dim, n_cells, degree, mg_precision, geometry, n_levels, local_cycles, smooth_steps, local_half,
                  outer_solver, gmres_restart, smoother, patches_per_block, patch_layout, patch_threads, outer_apply,
-                 geom_precision, apply_cpb, persistent, deform_amp, omega_patch, disp_hash) !=
+                 geom_precision, apply_cpb, persistent, coarse_dofs, deform_amp, omega_patch, disp_hash) !=
         std::tie(o.dim, o.n_cells, o.degree, o.mg_precision, o.geometry, o.n_levels, o.local_cycles,
                  o.smooth_steps, o.local_half, o.outer_solver, o.gmres_restart, o.smoother, o.patches_per_block,
                  o.patch_layout, o.patch_threads, o.outer_apply, o.geom_precision, o.apply_cpb, o.persistent,
-                 o.deform_amp, o.omega_patch, o.disp_hash))
+                 o.coarse_dofs, o.deform_amp, o.omega_patch, o.disp_hash))
       return false;
     for (int i = 0; i < 4; ++i)
       if (omega_jacobi[i] != o.omega_jacobi[i]) return false;
@@ -106,6 +107,7 @@ Key key_of(const pmg_config& c, const std::vector<double>* disp) {
   k.geom_precision = c.geometry == PMG_GEOM_CARTESIAN ? 0 : c.geom_precision;
   k.apply_cpb = c.geometry == PMG_GEOM_CARTESIAN ? 0 : c.apply_cells_per_block;
   k.persistent = c.patch_persistent;
+  k.coarse_dofs = c.n_levels > 0 ? 0 : c.coarse_dofs;
   k.deform_amp = c.geometry == PMG_GEOM_DEFORMED ? c.deform_amp : 0.0;
   k.omega_patch = c.omega_patch > 0 ? c.omega_patch : 0.0;
   for (int i = 0; i < 4; ++i) k.omega_jacobi[i] = c.omega_jacobi[i] > 0 ? c.omega_jacobi[i] : 0.0;

@@ -96,3 +96,14 @@ def test_distorted_config_keeps_its_displacements():
     assert p.bytes_required(cfg) > p.bytes_required(p.make_config(dim=3, n_cells=4, degree=2, geometry=p.DEFORMED))
     with pytest.raises(ValueError):
         p.make_config(dim=3, n_cells=4, degree=2, geometry=p.DISTORTED, vertex_disp=np.zeros((10, 3)))
+
+
+def test_coarse_dofs_stops_automatic_coarsening():
+    # 32^3 Q4: free DoFs per level 127^3, 63^3, 31^3, 15^3 = 3375, 7^3, 3^3;
+    # coarse_dofs = 4096 stops at 4^3 cells, whose dense inverse the plan holds
+    small = p.bytes_required(p.make_config(dim=3, n_cells=32, degree=4))
+    big = p.bytes_required(p.make_config(dim=3, n_cells=32, degree=4, coarse_dofs=4096))
+    assert big > small + 3375 * 3375 * 8      # the dense FP64 coarse inverse of 3375 free DoFs
+    with pytest.raises(p.PmgError) as e:
+        p.bytes_required(p.make_config(dim=3, n_cells=32, degree=4, coarse_dofs=5000))
+    assert e.value.code == p.PMG_ERR_ARG

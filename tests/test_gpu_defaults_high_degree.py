@@ -312,3 +312,33 @@ def test_persistent_patch_launches_are_bitwise_equal(k, prec, lay):
     for sm in (p.ADDITIVE, p.MULTIPLICATIVE):
         got = [u for s_, u in outs if s_ == sm]
         assert torch.equal(got[0], got[1])
+
+
+@pytest.mark.parametrize("cd,levels", [(0, 6), (4096, 4), (3375, 4), (3374, 5), (343, 5), (27, 6)])
+def test_coarse_dofs_levels(cd, levels):
+    ctx = ctx_default(3, 32, 4, prec=p.FP32, coarse_dofs=cd)
+    assert ctx.n_levels == levels
+    ctx.close()
+
+
+def test_coarse_dofs_solve_matches_the_oracle_hierarchy():
+    # 2D 32^2 Q3 stopped at 4^2 cells (11^2 = 121 free DoFs <= 128): the same
+    # solve as the oracle's 4-level hierarchy with the same damping
+    d, n, k = 2, 32, 3
+    wj, wp = constants.omega_jacobi(d, k), constants.omega_patch(d)
+    ctx = p.Context(p.make_config(dim=d, n_cells=n, degree=k, coarse_dofs=128, omega_jacobi=wj, omega_patch=wp),
+                    device=DEV)
+    assert ctx.n_levels == 4
+    m = fem.Mesh(d, n, k)
+    h = solver.Hierarchy(m, 4, wj, wp)
+    fine = h.levels[-1]
+    b_ref = fem.rhs_manufactured(m)
+    b = torch.empty(m.n_dofs, dtype=torch.float64, device=DEV)
+    ctx.rhs_manufactured(b)
+    x = torch.zeros_like(b)
+    info = ctx.solve(b, x, rtol=1e-8)
+    x_ref, it_ref, _ = solver.solve(h, b_ref[fine.I], rtol=1e-8)
+    assert abs(info.iterations - it_ref) <= 1
+    xf = np.zeros(m.n_dofs)
+    xf[fine.I] = x_ref
+    assert np.abs(x.cpu().numpy() - xf).max() <= 1e-6 * np.abs(xf).max()
