@@ -309,9 +309,10 @@ def serving_section(p, torch):
     V-cycle, FP64 CG to 1e-8, 16 slots, a fresh server per pass.  Passes: the
     process's first (cold: kernel modules loaded, smoother layouts tuned,
     coarse inverses computed) and a warm one, both served shortest-first
-    with grouped launches below the median work and the float-float outer
-    operator, then warm passes without grouping, and in arrival order with
-    the FP64 outer operator, for comparison."""
+    with the float-float outer operator, then warm passes with grouped
+    launches below the median work, and in arrival order with the FP64
+    outer operator, for comparison; and a stream of small requests served
+    with and without grouping."""
     import numpy as np
     from paper_2512_02577_gb300 import serve
     from paper_2512_02577_gb300.inputs import serving_requests
@@ -322,18 +323,18 @@ def serving_section(p, torch):
     # shortest-first: requests below the median estimated work (nodes x
     # (k + 2)) also get high-priority streams
     small = float(np.median([(r["k"] * r["n"] + 1) ** 3 * (r["k"] + 2) for r in reqs]))
-    # requests below the median work also run in groups: their iterations
-    # share each launch with the other running requests of their degree
-    ungrouped = dict(policy=p.SERVE_SHORTEST_FIRST, max_wait_s=2.0, small_work=small,
-                     outer_apply=p.APPLY_FLOAT_FLOAT)
-    best = dict(ungrouped, group_work=small, max_group=16)
+    best = dict(policy=p.SERVE_SHORTEST_FIRST, max_wait_s=2.0, small_work=small, outer_apply=p.APPLY_FLOAT_FLOAT)
+    # for comparison: requests below the median work in groups (their
+    # iterations share each launch with the other running requests of their
+    # degree and depth)
+    grouped = dict(best, group_work=small, max_group=16)
     res = {"workload": "256 requests, Poisson arrivals 50/s, n log-uniform 8..64 snapped to "
                        "{8,12,16,24,32,48,64} (k <= 5) / {8,16,32,64} (k >= 6), k uniform 2..7, N(0,1) RHS, "
                        "FP32 V-cycle, FP64 CG to 1e-8, 16 slots",
-           "served_as": "shortest-first admission with 2 s aging, high-priority streams and grouped launches "
-                        "(up to 16 per group) below the median work, float-float outer operator",
+           "served_as": "shortest-first admission with 2 s aging, high-priority streams below the median work, "
+                        "float-float outer operator",
            "total_dofs": int(sum((r["k"] * r["n"] + 1) ** 3 for r in reqs)), "prepare_s": prep_s}
-    for label, kw in (("cold", best), ("warm", best), ("warm_ungrouped", ungrouped),
+    for label, kw in (("cold", best), ("warm", best), ("warm_grouped", grouped),
                       ("warm_fifo_fp64_operator", {})):
         recs, summ = serve.run(reqs, precision=p.FP32, max_active=16, buffers=bufs, **kw)
         lat = np.array([r["latency_s"] for r in recs])
