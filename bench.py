@@ -326,7 +326,7 @@ def serving_section(p, torch):
     best = dict(policy=p.SERVE_SHORTEST_FIRST, max_wait_s=2.0, small_work=small, outer_apply=p.APPLY_FLOAT_FLOAT)
     # for comparison: requests below the median work in groups (their
     # iterations share each launch with the other running requests of their
-    # degree and depth)
+    # degree)
     grouped = dict(best, group_work=small, max_group=16)
     res = {"workload": "256 requests, Poisson arrivals 50/s, n log-uniform 8..64 snapped to "
                        "{8,12,16,24,32,48,64} (k <= 5) / {8,16,32,64} (k >= 6), k uniform 2..7, N(0,1) RHS, "

@@ -371,8 +371,7 @@ int pmg_server_set_policy(pmg_server* server, int policy, double max_wait_s, dou
 /* Grouped launches across concurrent requests (continuous batching; off by
  * default): a running request whose estimated work is at most max_work and
  * whose method allows it (as pmg_solve_group) joins the group of running
- * requests with the same method and number of mesh levels -- a round lasts
- * as long as its deepest member's V-cycle -- and is solved with them
+ * requests with the same method -- any mesh size -- and is solved with them
  * in lockstep, each launch of an iteration covering every member, members
  * joining at the next round and leaving when converged, up to max_group
  * (1..32) members per group, each group on its own high-priority stream.

@@ -12,10 +12,7 @@ namespace pmg {
 struct SolveGroup;
 
 // A group whose launches go on `stream` (nullptr: a stream of its own).
-// same_depth: admit only systems with as many mesh levels as the group's
-// first (a round lasts as long as its deepest member's V-cycle, so a
-// shallow system grouped with a deep one waits through the extra levels).
-int group_create(cudaStream_t stream, bool same_depth, SolveGroup** out);
+int group_create(cudaStream_t stream, SolveGroup** out);
 // PMG_ERR_STATE while systems are running or joining.
 int group_destroy(SolveGroup* g);
 // running plus joining systems

@@ -1696,7 +1696,6 @@ struct SolveGroup {
   cudaEvent_t ev = nullptr;   // after the residual norms of the last round reached the host
   bool pending = false;       // a round is enqueued and ev not yet seen
   int* counter = nullptr;     // work counter of the persistent patch launches
-  bool same_depth = false;    // admit only systems with as many levels as the group's
   std::vector<pmg_ctx*> members;  // running
   std::vector<pmg_ctx*> joining;  // start at the next round
   // The preconditioner step of a round as a CUDA graph, for the member list
@@ -2109,10 +2108,9 @@ void g_abort(SolveGroup* G, int error) {
 
 }  // namespace
 
-int group_create(cudaStream_t stream, bool same_depth, SolveGroup** out) {
+int group_create(cudaStream_t stream, SolveGroup** out) {
   *out = nullptr;
   SolveGroup* G = new SolveGroup();
-  G->same_depth = same_depth;
   cudaError_t e = cudaSuccess;
   if (stream) {
     G->stream = stream;
@@ -2155,7 +2153,7 @@ int group_cancel(SolveGroup* G) {
 bool group_accepts(const SolveGroup* G, const pmg_ctx* c) {
   if (!groupable(c) || c->group || group_size(G) >= kMaxGroup) return false;
   const pmg_ctx* ref = !G->members.empty() ? G->members[0] : (!G->joining.empty() ? G->joining[0] : nullptr);
-  return !ref || (group_key_equal(ref, c) && (!G->same_depth || ref->L == c->L));
+  return !ref || group_key_equal(ref, c);
 }
 
 int group_join(SolveGroup* G, pmg_ctx* c, const double* b, bool b_host, double* x, bool x_host, double rtol,
@@ -2225,7 +2223,7 @@ int pmg_solve_group(pmg_ctx* const* ctxs, int count, const double* const* b, dou
       if (ctxs[j] == ctxs[i]) return fail(PMG_ERR_ARG, "a context appears twice");
   }
   SolveGroup* G = nullptr;
-  if (int rc = group_create(ctxs[0]->stream, false, &G)) return rc;
+  if (int rc = group_create(ctxs[0]->stream, &G)) return rc;
   int first_err = PMG_OK;
   int joined = 0;
   for (; joined < count; ++joined) {

@@ -267,7 +267,7 @@ int start_request(pmg_server* s, Request* r, Slot* sl) {
         st = nullptr;
       }
       if (st) {
-        if (pmg::group_create(st, true, &g) == PMG_OK) {
+        if (pmg::group_create(st, &g) == PMG_OK) {
           s->groups.push_back(g);
           s->group_streams.push_back(st);
         } else {
