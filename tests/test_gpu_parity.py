@@ -511,3 +511,31 @@ def test_fp32_apply_across_tiles_and_ragged_tail(n, k):
     got = y.cpu().numpy().astype(np.float64)[rows]
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 2e-5 * scale
+
+
+@pytest.mark.parametrize("n", [49, 52])
+def test_deformed_fast_apply_whole_lines(n):
+    # The FP32 and the float-float deformed apply (half-warp per cell, eight
+    # parity launches adding into y) on odd and even n: whole x-lines of a
+    # few (y, z) -- every node of a line, shared or not -- and random rows,
+    # against the oracle's element matrices on the same FP32-stored geometry.
+    d, k = 3, 3
+    m = fem.Mesh(d, n, k, "deformed", 0.05, geom_fp32=True)
+    N, n1 = m.n_dofs, m.n1
+    x = random_vector(d, n, k, seed=93)
+    rng = np.random.default_rng(94)
+    rows = [int(xx + n1 * (yy + n1 * zz)) for yy, zz in ((1, 1), (3, 4), (n1 // 2, n1 - 2), (6, 3 * (n // 2)))
+            for xx in range(n1)]
+    rows += list(rng.integers(0, N, 100))
+    ref = _sampled_apply_rows(m, x, rows)
+    scale = np.abs(ref).max()
+    ctx = make_ctx(d, n, k, geom="deformed", prec=p.FP32)
+    y32 = torch.empty(N, dtype=torch.float32, device=DEV)
+    ctx.apply(to_dev(x, torch.float32), y32, prec=p.FP32)
+    ref32 = _sampled_apply_rows(m, x.astype(np.float32).astype(np.float64), rows)
+    assert np.abs(y32.cpu().numpy().astype(np.float64)[rows] - ref32).max() <= 2e-5 * scale
+    ctx.close()
+    ctx = make_ctx(d, n, k, geom="deformed", prec=p.FP32, outer_apply=p.APPLY_FLOAT_FLOAT)
+    y = torch.empty(N, dtype=torch.float64, device=DEV)
+    ctx.apply(to_dev(x), y)
+    assert np.abs(y.cpu().numpy()[rows] - ref).max() <= 1e-11 * scale
