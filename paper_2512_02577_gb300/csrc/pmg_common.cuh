@@ -108,12 +108,14 @@ struct FastDiv {
     s1 = l < 1 ? l : 1;
     s2 = l > 1 ? l - 1 : 0;
   }
-#ifdef __CUDACC__
-  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+  __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
     const uint32_t t = __umulhi(m, n);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)m * n) >> 32);
+#endif
     return (t + ((n - t) >> s1)) >> s2;
   }
-#endif
 };
 // work items of a grid-stride loop that the 32-bit decoding covers
 constexpr int64_t kFastDivItems = int64_t(1) << 32;
