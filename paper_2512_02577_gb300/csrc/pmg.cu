@@ -798,12 +798,16 @@ int choose_patch_layout(pmg_ctx* c) {
   float best = 1e30f;
   TuneVal best_v{c->il_threads > 0 ? PMG_PATCH_INTERLEAVED : PMG_PATCH_MAJOR, c->ppc, c->il_threads, 0};
   const int64_t before = g_launches.load();
-  // best of 3 timed repetitions after a warm-up; 1e30 if the device rejects
-  // a launch (resources): not a candidate
+  // best of 3 timed repetitions after a warm-up (one when the warm-up took
+  // over 2 ms: launches that long time reproducibly, and the set-up of a
+  // large context is on its first request's critical path; none when the
+  // warm-up took 1.5x the best time so far); 1e30 if the device rejects a
+  // launch (resources): not a candidate
   auto time_of = [&](const TuneVal& v) -> float {
     set_layout(c, v);
     float tmin = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
+    int reps = 4;
+    for (int rep = 0; rep < reps; ++rep) {
       cudaEventRecord(e0, c->stream);
       int rc = PMG_OK;
       if (mult) {
@@ -820,6 +824,8 @@ int choose_patch_layout(pmg_ctx* c) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) tmin = std::min(tmin, ms);
+      else if (ms > 1.5f * best) return ms;  // far behind the best so far: not timed further
+      else if (ms > 2.f) reps = 2;
     }
     return tmin;
   };
