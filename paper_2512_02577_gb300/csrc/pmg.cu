@@ -655,8 +655,9 @@ int precondition(pmg_ctx* c, const double* r, double* z) {
 // candidate is timed on the patch launches of one finest-level sweep -- the
 // one launch over all patches (additive) or the 2^d colour launches
 // (multiplicative, each over an eighth of the patches in 3D, where the last
-// wave matters) -- with CUDA events, best of 3 after a warm-up, and the
-// fastest is kept for the process; with PMG_TUNE_FILE set, results are also
+// wave matters) -- with CUDA events, best of 3 after a warm-up (fewer for
+// long or clearly slower launches, see time_of), and the fastest is kept
+// for the process; with PMG_TUNE_FILE set, results are also
 // read from and appended to that file ("dim k prec geom cycles smoother n
 // layout ppc threads persistent" per line).  The fastest candidate is then
 // timed once more as a persistent grid (Cartesian), kept if faster.  Small meshes, whose launches are too short
