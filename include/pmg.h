@@ -44,7 +44,9 @@ enum pmg_status {
                                 local_cycles >= 2, Cartesian k = 8 with local_cycles >= 2) */
   PMG_ERR_OOM = -3,          /* device workspace could not be allocated / too small */
   PMG_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed */
-  PMG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired */
+  PMG_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired (reserved: no kernel of the library waits
+                                  on another block or device -- the persistent patch launches take work from
+                                  an atomic counter and never spin -- so nothing returns it today) */
   PMG_ERR_STATE = -6         /* call not valid in the context's current state */
 };
 
