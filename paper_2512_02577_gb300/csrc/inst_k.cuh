@@ -36,7 +36,7 @@ static cudaError_t cart_apply_t(const T* x, T* y, const T* b, T* t0, T* t1, T* t
   const FastDiv dnp1(n + 1), dN1(N1);
   if constexpr (DIM == 3 && sizeof(T) == 4) {  // FP32: x and y passes fused per z plane (cart_xy_kernel)
     const int tiles = (n + CartXY<T>::CX - 1) / CartXY<T>::CX;
-    cart_xy_kernel<T><<<dim3(tiles * tiles, N1), 256, 0, st>>>(x, t2, t3, n);
+    cart_xy_kernel<T><<<dim3(tiles, tiles, N1), 256, 0, st>>>(x, t2, t3, n);
     if (b) cart_pass<3, 2, 2, true, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, b, n, s, dnp1, dN1);
     else cart_pass<3, 2, 2, false, T><<<g, bs, 0, st>>>(t2, t3, y, nullptr, nullptr, n, s, dnp1, dN1);
     g_launches += 2;

@@ -217,20 +217,22 @@ template <typename T>
 __global__ void __launch_bounds__(256) cart_xy_kernel(const T* __restrict__ x, T* __restrict__ t2,
                                                       T* __restrict__ t3, int n) {
   using X = CartXY<T>;
-  constexpr int TH = X::TH, PT = X::PT, CX = X::CX;
+  constexpr int TH = X::TH, PT = X::PT, CX = X::CX, TO = X::TO;
+  constexpr int NT = 256;       // threads per block (the launch bound)
+  constexpr int RS = NT / TH;   // rows loaded per step of the load loop
   __shared__ T xs[TH * TH];
   __shared__ T s0[TH * PT];
   __shared__ T s1[TH * PT];
   const int N1 = K * n + 1;
-  const int tiles = (n + CX - 1) / CX;
-  const int cx0 = (blockIdx.x % tiles) * CX, cy0 = (blockIdx.x / tiles) * CX;
+  // grid: (tile x, tile y, z plane)
+  const int cx0 = blockIdx.x * CX, cy0 = blockIdx.y * CX;
   const int ncx = min(CX, n - cx0), ncy = min(CX, n - cy0);
-  const int gz = blockIdx.y;
+  const int gz = blockIdx.z;
   const int64_t plane = (int64_t)gz * N1 * N1;
   const bool last_x = cx0 + ncx == n, last_y = cy0 + ncy == n;
   const int OX = K * ncx + (last_x ? 1 : 0), OY = K * ncy + (last_y ? 1 : 0);  // owned nodes
   if (gz == 0 || gz == N1 - 1) {  // x is zero on the boundary planes: so are both results
-    for (int i = threadIdx.x; i < OX * OY; i += blockDim.x) {
+    for (int i = threadIdx.x; i < OX * OY; i += NT) {
       const int64_t o = plane + (int64_t)(K * cy0 + i / OX) * N1 + K * cx0 + i % OX;
       t2[o] = T(0);
       t3[o] = T(0);
@@ -240,21 +242,25 @@ __global__ void __launch_bounds__(256) cart_xy_kernel(const T* __restrict__ x, T
   const T* C = ctab<T>();
   const T* Me = C + LAY.Me;
   const T* Ke = C + LAY.Ke;
-  // x restricted to the free nodes: rows K (cy0 - 1) .. K (cy0 + ncy), columns likewise
+  // x restricted to the free nodes: rows K (cy0 - 1) .. K (cy0 + ncy), columns
+  // likewise.  A thread loads one column, every RS-th row.
   const int RY = K * (ncy + 1) + 1, RX = K * (ncx + 1) + 1;
-  // loops decode their items with the compile-time tile sizes (cheap
-  // divisions) and skip the items of a partial tile
-  for (int i = threadIdx.x; i < TH * TH; i += blockDim.x) {
-    const int r = i / TH, c = i - r * TH;
-    if (r >= RY || c >= RX) continue;
-    const int gy = K * (cy0 - 1) + r, gx = K * (cx0 - 1) + c;
-    xs[r * TH + c] = (gy >= 1 && gy <= N1 - 2 && gx >= 1 && gx <= N1 - 2) ? x[plane + (int64_t)gy * N1 + gx] : T(0);
+  {
+    const int c = threadIdx.x % TH, r0 = threadIdx.x / TH;
+    if (r0 < RS && c < RX) {
+      const int gx = K * (cx0 - 1) + c;
+      const bool col_free = gx >= 1 && gx <= N1 - 2;
+      int gy = K * (cy0 - 1) + r0;
+      int64_t off = plane + (int64_t)gy * N1 + gx;  // read only where the node is free
+      for (int r = r0; r < RY; r += RS, gy += RS, off += (int64_t)RS * N1)
+        xs[r * TH + c] = (col_free && gy >= 1 && gy <= N1 - 2) ? x[off] : T(0);
+    }
   }
   __syncthreads();
   // x pass (cart_pass MODE 0) on every loaded row, owned cells; rows fastest
-  for (int i = threadIdx.x; i < TH * CX; i += blockDim.x) {
+  for (int i = threadIdx.x; i < TH * CX; i += NT) {
     const int cc = i / TH, r = i - cc * TH, c = cx0 + cc;
-    if (r >= RY || cc >= ncx) continue;
+    if (r >= RY || cc >= ncx) continue;  // outside a partial tile
     T xr0[K + 1], xl0[K + 1];
 #pragma unroll
     for (int b = 0; b <= K; ++b) {
@@ -284,8 +290,7 @@ __global__ void __launch_bounds__(256) cart_xy_kernel(const T* __restrict__ x, T
   __syncthreads();
   // y pass (cart_pass MODE 1) on the owned nodes; columns fastest (coalesced stores)
   const int CW = K * ncx;
-  constexpr int TO = X::TO;
-  for (int i = threadIdx.x; i < TO * CX; i += blockDim.x) {
+  for (int i = threadIdx.x; i < TO * CX; i += NT) {
     const int cc = i / TO, j = i - cc * TO, cy = cy0 + cc;
     if (j >= CW || cc >= ncy) continue;
     T xr0[K + 1], xl0[K + 1], xr1[K + 1], xl1[K + 1];
@@ -323,13 +328,13 @@ __global__ void __launch_bounds__(256) cart_xy_kernel(const T* __restrict__ x, T
   }
   // the last node of a line is on the boundary: zero (as the passes write it)
   if (last_y)
-    for (int j = threadIdx.x; j < OX; j += blockDim.x) {
+    for (int j = threadIdx.x; j < OX; j += NT) {
       const int64_t o = plane + (int64_t)(N1 - 1) * N1 + K * cx0 + j;
       t2[o] = T(0);
       t3[o] = T(0);
     }
   if (last_x)
-    for (int r = threadIdx.x; r < K * ncy; r += blockDim.x) {
+    for (int r = threadIdx.x; r < K * ncy; r += NT) {
       const int64_t o = plane + (int64_t)(K * cy0 + r) * N1 + N1 - 1;
       t2[o] = T(0);
       t3[o] = T(0);
